@@ -1,0 +1,331 @@
+"""Pins of the CPU oracle against facts fixed by theory (no GPU).
+
+Each test checks the oracle against something other than itself: the
+brute-force Fock-space module (exact e^{-T} H e^{T}, FCI, Rayleigh-
+Schroedinger MP2), closed forms (Koopmans' theorem at zero coupling),
+invariances (spinor phases, virtual rotations), symmetries (Kramers pairs,
+real inputs) and scaling limits. A dropped term, wrong sign, wrong index or
+transposed operand in the working equations fails at least one of them.
+"""
+import numpy as np
+import pytest
+
+from paper_2506_06805_gb300 import synth
+from oracle import ccsd, davidson, fci, fns, integrals, ipeom, mp2
+
+
+def _system(o, v, X, seed=1, scale=1.0, kramers=False):
+    rng = np.random.default_rng(seed)
+    eps = synth.make_eps(rng, o, v, kramers)
+    L = synth.make_cholesky(rng, o + v, X, kramers) * scale
+    return eps, L
+
+
+def _random_amplitudes(rng, o, v, s=0.05):
+    t1 = s * (rng.standard_normal((o, v)) + 1j * rng.standard_normal((o, v)))
+    t2 = s * (rng.standard_normal((o, o, v, v))
+              + 1j * rng.standard_normal((o, o, v, v)))
+    t2 = t2 - t2.transpose(1, 0, 2, 3)
+    t2 = 0.5 * (t2 - t2.transpose(0, 1, 3, 2))
+    return t1, t2
+
+
+def _offdiag_mask(o, v):
+    m = np.ones((o, o, v, v), bool)
+    for i in range(o):
+        m[i, i] = False
+    for a in range(v):
+        m[:, :, a, a] = False
+    return m
+
+
+# --- integrals (Eq. 23) ------------------------------------------------------
+
+def test_integral_symmetries():
+    eps, L = _system(3, 6, 15, scale=5.0)
+    g = integrals.antisym_full(L)
+    scale = np.abs(g).max()
+    assert np.abs(g + g.transpose(1, 0, 2, 3)).max() <= 1e-15 * scale
+    assert np.abs(g + g.transpose(0, 1, 3, 2)).max() <= 1e-15 * scale
+    # Hermitian L^P  =>  <pq||rs> = <rs||pq>*
+    assert np.abs(g - g.transpose(2, 3, 0, 1).conj()).max() <= 1e-15 * scale
+
+
+def test_integrals_against_scalar_loop():
+    """Eq. 23 evaluated element by element in plain Python."""
+    eps, L = _system(2, 3, 4, scale=3.0)
+    g = integrals.antisym_full(L)
+    n = L.shape[1]
+    rng = np.random.default_rng(0)
+    for _ in range(40):
+        p, q, r, s = rng.integers(0, n, size=4)
+        ref = 0j
+        for P in range(L.shape[0]):
+            ref += L[P, p, r] * L[P, q, s] - L[P, p, s] * L[P, q, r]
+        assert abs(g[p, q, r, s] - ref) <= 1e-15
+
+
+# --- MP2 ---------------------------------------------------------------------
+
+def test_mp2_equals_rayleigh_schroedinger_second_order():
+    eps, L = _system(3, 5, 12, scale=8.0)
+    G = integrals.antisym_full(L)
+    g = integrals.Blocks(G, 3)
+    bf = fci.BruteForce(eps, G, 3)
+    e_bf = bf.mp2_energy()
+    e_or = mp2.energy(g, mp2.amplitudes(g, eps))
+    assert abs(e_or - e_bf) <= 1e-13 * abs(e_bf)
+    assert abs(e_or.imag) <= 1e-15
+
+
+def test_ccsd_energy_at_mp2_amplitudes_is_mp2():
+    eps, L = _system(3, 5, 12, scale=8.0)
+    g = integrals.blocks_from_cholesky(L, 3)
+    t2 = mp2.amplitudes(g, eps)
+    t1 = np.zeros((3, 5), complex)
+    assert ccsd.energy(g, t1, t2) == mp2.energy(g, t2)
+
+
+# --- CCSD working equations vs exact similarity transform --------------------
+
+@pytest.mark.parametrize("o,v,X,seed", [(3, 5, 12, 1), (2, 6, 10, 2),
+                                        (4, 4, 9, 3)])
+def test_ccsd_residual_equals_bruteforce_projection(o, v, X, seed):
+    """<mu| e^{-T} H e^{T} |0> = R - D t for ANY amplitudes (Eqs. 13-15)."""
+    eps, L = _system(o, v, X, seed=seed, scale=10.0)
+    G = integrals.antisym_full(L)
+    g = integrals.Blocks(G, o)
+    bf = fci.BruteForce(eps, G, o)
+    rng = np.random.default_rng(seed)
+    t1, t2 = _random_amplitudes(rng, o, v)
+    e_tot, P1, P2 = bf.projections(t1, t2)
+    R1, R2 = ccsd.residuals(g, eps, t1, t2)
+    D1 = mp2.denom1(eps, o)
+    D2 = mp2.denom2(eps, o)
+    assert abs((e_tot - bf.e_ref) - ccsd.energy(g, t1, t2)) <= 1e-13
+    assert np.abs(P1 - (R1 - D1 * t1)).max() <= 1e-13
+    m = _offdiag_mask(o, v)
+    assert np.abs((P2 - (R2 - D2 * t2))[m]).max() <= 1e-13
+
+
+def test_ladder_term_alone_equals_bruteforce():
+    """With only virtual-virtual Cholesky blocks and eps = 0, every integral
+    but <ab||cd> vanishes and the doubles projection at t1 = 0 is the ladder
+    1/2 sum_cd <ab||cd> t_ij^cd alone."""
+    o, v, X = 2, 5, 8
+    eps, L = _system(o, v, X, scale=10.0)
+    L[:, :o, :] = 0.0
+    L[:, :, :o] = 0.0
+    eps = np.zeros_like(eps)
+    G = integrals.antisym_full(L)
+    bf = fci.BruteForce(eps, G, o)
+    rng = np.random.default_rng(5)
+    _, t2 = _random_amplitudes(rng, o, v)
+    t1 = np.zeros((o, v), complex)
+    _, _, P2 = bf.projections(t1, t2)
+    lad = ccsd.ladder_term(G[o:, o:, o:, o:], t2)
+    m = _offdiag_mask(o, v)
+    assert np.abs((P2 - lad)[m]).max() <= 1e-14
+    assert np.abs(lad).max() > 1e-3
+
+
+def test_ccsd_two_electrons_is_fci():
+    """n_occ = 2: CCSD is exact; 1h + 2h1p spans the whole one-electron
+    sector, so the IP-EOM roots are FCI(N-1) - FCI(N)."""
+    o, v, X = 2, 6, 14
+    eps, L = _system(o, v, X, seed=4, scale=8.0)
+    G = integrals.antisym_full(L)
+    g = integrals.Blocks(G, o)
+    res = ccsd.solve(g, eps, tol=1e-12, max_iter=300)
+    assert res["converged"]
+    bf = fci.BruteForce(eps, G, o)
+    e_fci = np.linalg.eigvals(bf.H_N)
+    # the CC root is the FCI root closest to the CC energy (the ground state)
+    e_cc = bf.e_ref + res["e_corr"]
+    e0 = e_fci[np.argmin(np.abs(e_fci - e_cc))]
+    assert e0.real == pytest.approx(np.min(e_fci.real), abs=1e-12)
+    assert abs(e_cc - e0) <= 1e-10
+    H = ipeom.hbar(g, eps, res["t1"], res["t2"])
+    w = np.sort_complex(np.linalg.eigvals(ipeom.dense_matrix(H, o, v)))
+    w_fci = np.sort_complex(np.linalg.eigvals(bf.H_Nm1) - e0)
+    assert np.abs(w - w_fci).max() <= 1e-9
+
+
+@pytest.mark.parametrize("o,v,X,seed", [(3, 5, 12, 1), (4, 3, 10, 6)])
+def test_ip_matrix_equals_bruteforce(o, v, X, seed):
+    """H-bar_IP from the sigma equations equals <mu|Hbar - E|nu> exactly
+    (n_occ >= 3 is where the truncation matters)."""
+    eps, L = _system(o, v, X, seed=seed, scale=10.0)
+    G = integrals.antisym_full(L)
+    g = integrals.Blocks(G, o)
+    res = ccsd.solve(g, eps, tol=1e-13, max_iter=400)
+    assert res["converged"]
+    bf = fci.BruteForce(eps, G, o)
+    e_tot, P1, P2 = bf.projections(res["t1"], res["t2"])
+    assert np.abs(P1).max() < 1e-11 and np.abs(P2).max() < 1e-11
+    M_bf = bf.ip_matrix(res["t1"], res["t2"])
+    H = ipeom.hbar(g, eps, res["t1"], res["t2"])
+    M = ipeom.dense_matrix(H, o, v)
+    assert np.abs(M - M_bf).max() <= 1e-10 * max(1.0, np.abs(M_bf).max())
+
+
+# --- closed forms and invariances ---------------------------------------------
+
+def test_koopmans_at_zero_coupling():
+    o, v = 4, 6
+    eps, L = _system(o, v, 5)
+    L[:] = 0.0
+    g = integrals.blocks_from_cholesky(L, o)
+    res = ccsd.solve(g, eps, tol=1e-12)
+    assert res["e_corr"] == 0.0
+    assert np.all(res["t1"] == 0) and np.all(res["t2"] == 0)
+    H = ipeom.hbar(g, eps, res["t1"], res["t2"])
+    w = np.sort(np.linalg.eigvals(ipeom.dense_matrix(H, o, v)).real)
+    eo, ev = eps[:o], eps[o:]
+    exact = [-e for e in eo]
+    for i in range(o):
+        for j in range(i + 1, o):
+            exact += [b - eo[i] - eo[j] for b in ev]
+    assert np.array_equal(w, np.sort(exact)) or np.abs(
+        w - np.sort(exact)).max() <= 1e-15
+
+
+def test_weak_coupling_limits():
+    """L -> lam L: E_CCSD / E_MP2 -> 1 and IP - Koopmans = O(lam^4)."""
+    o, v, X = 4, 8, 16
+    eps, L0 = _system(o, v, X, seed=3, scale=6.0)
+    ratios, shifts = [], []
+    for lam in (1.0, 0.5, 0.25):
+        g = integrals.blocks_from_cholesky(L0 * lam, o)
+        res = ccsd.solve(g, eps, tol=1e-13, max_iter=200)
+        ratios.append((res["e_corr"] / mp2.energy(
+            g, mp2.amplitudes(g, eps))).real)
+        H = ipeom.hbar(g, eps, res["t1"], res["t2"])
+        w, _ = ipeom.dense_roots(H, o, v, 1)
+        shifts.append(abs(w[0] - (-eps[o - 1])))
+    assert abs(ratios[2] - 1) < abs(ratios[1] - 1) < abs(ratios[0] - 1)
+    assert abs(ratios[2] - 1) < 1e-2
+    # halving lam divides the shift by ~16
+    assert 12.0 < shifts[1] / shifts[2] < 20.0
+
+
+def test_gauge_invariance():
+    """Spinor phases change amplitudes but not E or the IPs. Catches
+    conjugation mistakes that real tests cannot see."""
+    o, v, X = 4, 8, 16
+    eps, L = _system(o, v, X, seed=7, scale=6.0)
+    theta = np.random.default_rng(9).uniform(0, 2 * np.pi, o + v)
+    out = []
+    for LL in (L, synth.gauge_transform(L, theta)):
+        g = integrals.blocks_from_cholesky(LL, o)
+        res = ccsd.solve(g, eps, tol=1e-13, max_iter=200)
+        H = ipeom.hbar(g, eps, res["t1"], res["t2"])
+        w, _ = ipeom.dense_roots(H, o, v, 5)
+        out.append((res["e_corr"], w))
+    assert abs(out[0][0] - out[1][0]) <= 1e-13
+    assert np.abs(out[0][1] - out[1][1]).max() <= 1e-11
+
+
+def test_real_inputs_give_real_results():
+    o, v, X = 4, 6, 12
+    eps, L = _system(o, v, X, seed=8, scale=6.0)
+    L = L.real.astype(complex)
+    g = integrals.blocks_from_cholesky(L, o)
+    res = ccsd.solve(g, eps, tol=1e-13, max_iter=200)
+    assert np.abs(res["t2"].imag).max() == 0.0
+    assert res["e_corr"].imag == 0.0
+
+
+def test_kramers_pairs_are_degenerate():
+    o, v, X = 4, 8, 16
+    eps, L = _system(o, v, X, seed=2, scale=6.0, kramers=True)
+    g = integrals.blocks_from_cholesky(L, o)
+    res = ccsd.solve(g, eps, tol=1e-13, max_iter=200)
+    assert abs(res["e_corr"].imag) <= 1e-14
+    H = ipeom.hbar(g, eps, res["t1"], res["t2"])
+    w, _ = ipeom.dense_roots(H, o, v, 8)
+    w = np.sort(w.real)
+    assert np.abs(w[0::2] - w[1::2]).max() <= 1e-10
+    assert np.min(np.diff(w[0::2])) > 1e-4
+
+
+# --- frozen natural spinors (Eqs. 24-28) ---------------------------------------
+
+def test_fns_density_properties():
+    o, v, X = 4, 10, 20
+    eps, L = _system(o, v, X, seed=5, scale=6.0)
+    D = fns.vv_density(L, eps, o)
+    assert np.abs(D - D.conj().T).max() <= 1e-15 * np.abs(D).max()
+    n = np.linalg.eigvalsh(D)
+    assert n.min() >= -1e-15
+    g = integrals.blocks_from_cholesky(L, o)
+    t2 = mp2.amplitudes(g, eps)
+    assert abs(np.trace(D) - 0.5 * np.sum(np.abs(t2) ** 2)) <= 1e-14
+    # Eq. 24 element against a plain loop
+    G = integrals.antisym_full(L)
+    ev, eo = eps[o:], eps[:o]
+    a, b = 2, 7
+    ref = 0j
+    for c in range(v):
+        for i in range(o):
+            for j in range(o):
+                ref += (G[o + a, o + c, i, j] * G[i, j, o + b, o + c]
+                        / ((eo[i] + eo[j] - ev[a] - ev[c])
+                           * (eo[i] + eo[j] - ev[b] - ev[c])))
+    assert abs(D[a, b] - 0.5 * ref) <= 1e-15
+
+
+def test_fns_keep_all_is_invariant():
+    """Threshold 0 keeps every virtual: CCSD and IP-EOM are invariant under
+    the unitary virtual rotation U (Eq. 28)."""
+    o, v, X = 4, 8, 16
+    eps, L = _system(o, v, X, seed=6, scale=6.0)
+    out = fns.frozen_natural_spinors(L, eps, o, n_keep=v)
+    U = out["U"]
+    assert np.abs(U.conj().T @ U - np.eye(v)).max() <= 1e-13
+    assert np.abs(np.linalg.eigvalsh(out["F_ns"]) - out["eps_virt"]).max() \
+        <= 1e-13
+    res = []
+    for ee, LL in ((eps, L), (out["eps"], out["L"])):
+        # the Fock matrix in the rotated basis is diag(eps~): semicanonical
+        g = integrals.blocks_from_cholesky(LL, o)
+        r = ccsd.solve(g, ee, tol=1e-13, max_iter=200)
+        H = ipeom.hbar(g, ee, r["t1"], r["t2"])
+        w, _ = ipeom.dense_roots(H, o, v, 4)
+        res.append((r["e_corr"], w))
+    assert abs(res[0][0] - res[1][0]) <= 1e-10
+    assert np.abs(res[0][1] - res[1][1]).max() <= 1e-10
+
+
+def test_fns_truncation_keeps_largest_occupations():
+    o, v, X = 4, 12, 24
+    eps, L = _system(o, v, X, seed=6, scale=6.0)
+    occ = fns.natural_spinors(fns.vv_density(L, eps, o))[0]
+    thr = 0.5 * (occ[5] + occ[6])
+    out = fns.frozen_natural_spinors(L, eps, o, threshold=thr)
+    assert out["n_keep"] == 6
+    assert out["L"].shape == (X, o + 6, o + 6)
+    Lr = out["L"]
+    assert np.abs(Lr - Lr.conj().transpose(0, 2, 1)).max() <= 1e-15
+    # truncated CCSD recovers most of the correlation energy
+    e_full = ccsd.solve(integrals.blocks_from_cholesky(L, o), eps,
+                        tol=1e-10)["e_corr"].real
+    e_fns = ccsd.solve(integrals.blocks_from_cholesky(Lr, o), out["eps"],
+                       tol=1e-10)["e_corr"].real
+    assert 0.5 * e_full > e_fns > 1.05 * e_full or e_full < e_fns < 0
+
+
+# --- Davidson -------------------------------------------------------------------
+
+def test_davidson_matches_dense():
+    o, v, X = 5, 8, 16
+    eps, L = _system(o, v, X, seed=11, scale=6.0)
+    g = integrals.blocks_from_cholesky(L, o)
+    res = ccsd.solve(g, eps, tol=1e-12, max_iter=200)
+    H = ipeom.hbar(g, eps, res["t1"], res["t2"])
+    w_dense, _ = ipeom.dense_roots(H, o, v, 6)
+    w, X_, it, conv = davidson.davidson(
+        lambda x: ipeom.sigma(H, x, o, v), ipeom.diagonal(H, o, v), 6,
+        tol=1e-9)
+    assert conv
+    assert np.abs(w - w_dense).max() <= 1e-9
