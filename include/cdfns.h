@@ -1,0 +1,212 @@
+/*
+ * cdfns.h -- C ABI of the GB300 CD/FNS IP-EOM-CCSD library (libcdfns.so).
+ *
+ * The library computes ionisation potentials with the equation-of-motion
+ * coupled-cluster method at the singles-and-doubles level (IP-EOM-CCSD,
+ * Eqs. 16-18) on top of CCSD (Eqs. 12-15), with two-electron integrals
+ * assembled from complex Cholesky vectors (Eqs. 21-23) and an optional
+ * frozen-natural-spinor truncation of the virtual space (Eqs. 24-28).
+ * Every contraction runs in CUDA kernels of this library on one GPU.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Return value: CC_OK (0) or a negative CC_ERR_* code. After an error,
+ *   cc_last_error() returns a one-line message. A call that fails with
+ *   CC_ERR_ARG, CC_ERR_INPUT or CC_ERR_STATE leaves the context unchanged.
+ * - Complex numbers are interleaved (re, im) doubles ("complex128").
+ * - Spinor index p in [0, n), n = n_occ + n_virt, occupied spinors first.
+ *   All arrays are row-major (C order).
+ * - Units: Hartree. IPs are positive: omega = E(N-1) - E(N) (Eq. 18).
+ * - Ownership: inputs are copied; the library keeps no caller pointer and
+ *   writes only to the output arguments of the call. Host pointers are
+ *   named *_host or documented as host; *_dev pointers are device memory
+ *   on the context's device.
+ * - Call order: cc_init -> [fns_truncate] -> ccsd_solve -> ipeom_solve.
+ * - Streams: work is issued on the context's stream (cc_set_stream); calls
+ *   that return host results synchronise that stream before returning.
+ */
+#ifndef CDFNS_H
+#define CDFNS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CC_OK 0
+#define CC_ERR_ARG (-1)           /* bad argument (size, pointer, range) */
+#define CC_ERR_INPUT (-2)         /* input data invalid: NaN/Inf, non-Hermitian L */
+#define CC_ERR_OOM (-3)           /* device allocation failed */
+#define CC_ERR_CUDA (-4)          /* CUDA runtime/driver error */
+#define CC_ERR_NOT_CONVERGED (-5) /* iteration limit reached; results written */
+#define CC_ERR_NUMERIC (-6)       /* NaN/Inf appeared during the iterations */
+#define CC_ERR_TIMEOUT (-7)       /* a bounded device wait gave up */
+#define CC_ERR_STATE (-8)         /* call made out of order */
+#define CC_ERR_UNSUPPORTED (-9)   /* feature not available on this device */
+
+/* Precision tiers of the contractions (cc_set_precision). Control steps
+ * (denominators, DIIS, energies, norms, Davidson subspace) are FP64 in
+ * every tier. */
+#define CC_TIER_FP64 0   /* complex FP64 on the FP64 pipe (plain path) */
+#define CC_TIER_TF32 1   /* tcgen05 kind::tf32, one pass, FP32 accumulate */
+#define CC_TIER_TF32X3 2 /* tcgen05 tf32, hi/lo split, 3 products */
+#define CC_TIER_BF16X3 3 /* tcgen05 kind::f16 bf16, hi/lo split, 3 products */
+
+typedef struct cc_ctx cc_ctx; /* one molecular (synthetic) system */
+
+/* Process-wide defaults picked up by contexts created afterwards.
+ * alloc(bytes, user) must return device memory aligned to 256 bytes or NULL;
+ * free(ptr, user) releases it. Pass NULLs to restore cudaMalloc/cudaFree.
+ * stream is a cudaStream_t (NULL = legacy default stream). */
+int cc_set_default_allocator(void *(*alloc)(size_t, void *),
+                             void (*free_fn)(void *, void *), void *user);
+int cc_set_default_stream(void *stream);
+
+/*
+ * cc_init: create a context from orbital energies and Cholesky vectors.
+ *   n_occ, n_virt >= 1; n_aux >= 1.
+ *   eps  host double[n]: orbital energies, occupied first. The Fock operator
+ *        is taken diagonal, f = diag(eps) (semicanonical spinors, Eqs. 26-27).
+ *   L    host complex128 [n_aux][n][n]: Cholesky vectors in the spinor basis
+ *        (Eq. 22), each L^P Hermitian in (p, q). The integrals are
+ *        <pq||rs> = sum_P (L^P_pr L^P_qs - L^P_ps L^P_qr) (Eq. 23).
+ *   out  receives the new context.
+ * Errors: CC_ERR_ARG (sizes, NULL pointers), CC_ERR_INPUT (NaN/Inf in eps or
+ * L, or L^P not Hermitian to 1e-12 relative), CC_ERR_OOM, CC_ERR_CUDA.
+ * The stored integrals with at most two virtual indices (the implementation
+ * section's storage policy) are built at the first solver call, in the
+ * precision tier current at that point.
+ */
+int cc_init(int n_occ, int n_virt, int n_aux, const double *eps,
+            const double *L, cc_ctx **out);
+
+/* Chunked variant for inputs too large for one host array: create the
+ * context with eps, then pass L^P for P in [p0, p1) in any order with
+ * cc_add_cholesky (host complex128 [p1-p0][n][n]); the integrals are built at
+ * the first solver call once every P has been given (else CC_ERR_STATE). */
+int cc_init_chunked(int n_occ, int n_virt, int n_aux, const double *eps,
+                    cc_ctx **out);
+int cc_add_cholesky(cc_ctx *ctx, int p0, int p1, const double *L_chunk);
+
+int cc_set_precision(cc_ctx *ctx, int tier); /* CC_TIER_*; default FP64 */
+/* Tier of the IP-EOM sigma contractions (-1: same as cc_set_precision).
+ * The one-body parts of sigma always run in FP64. */
+int cc_set_precision_eom(cc_ctx *ctx, int tier);
+int cc_set_stream(cc_ctx *ctx, void *stream); /* cudaStream_t */
+/* Upper bound (bytes) of the ladder's staging slab of (ac|bd) values formed
+ * from L for a block of a (default 4 GiB); the full v^4 tensor is never
+ * stored. Smaller budgets mean more, smaller blocks. */
+int cc_set_slab_budget(cc_ctx *ctx, size_t bytes);
+
+/* Sizes of the current (possibly truncated) spaces. */
+int cc_get_sizes(const cc_ctx *ctx, int *n_occ, int *n_virt, int *n_aux);
+
+/*
+ * fns_truncate: frozen natural spinors (Eqs. 24-28).
+ * Builds the MP2 virtual-virtual density D_ab (Eq. 24), diagonalises it
+ * (Eq. 25), keeps natural spinors with occupation >= threshold, builds and
+ * diagonalises F^NS (Eqs. 26-27), forms U = V~ Z~ (Eq. 28, read as
+ * V~ times Z~) and rotates the virtual indices of L; eps_virt becomes eps~.
+ * threshold >= 0. n_virt_kept (host, may be NULL) receives the new n_virt.
+ * Must precede ccsd_solve. Errors: CC_ERR_ARG, CC_ERR_STATE (after CCSD or
+ * if nothing would be kept).
+ */
+int fns_truncate(cc_ctx *ctx, double threshold, int *n_virt_kept);
+/* Same, keeping the n_keep natural spinors of largest occupation. */
+int fns_truncate_count(cc_ctx *ctx, int n_keep);
+/* Host double[n_virt_before]: occupations of the last FNS step, descending. */
+int fns_get_occupations(const cc_ctx *ctx, double *occ_host, int n);
+
+/*
+ * ccsd_solve: CCSD amplitudes (Eqs. 13-14) and energy (Eq. 15).
+ * Start t1 = 0, t2 = MP2 (or amplitudes given by cc_set_amplitudes).
+ * Jacobi updates with FP64 denominators and Pulay DIIS (8 vectors, from
+ * iteration 3). Converged when ||dt||_2 over unique amplitudes < tol and
+ * |dE| < tol.
+ * e_corr  host double[2]: complex correlation energy (re, im).
+ * n_iter  host int (may be NULL): iterations taken.
+ * Errors: CC_ERR_NOT_CONVERGED (results still written), CC_ERR_NUMERIC.
+ */
+int ccsd_solve(cc_ctx *ctx, double tol, int max_iter, double *e_corr,
+               int *n_iter);
+
+/*
+ * ipeom_solve: the n_roots IP-EOM-CCSD roots of smallest real part
+ * (Eqs. 17-18) by block Davidson with all roots' sigma vectors built in
+ * one batch. H-bar elements with at most two virtual indices are built
+ * once from the converged amplitudes.
+ * omega      host double[n_roots][2]: complex IPs, sorted by real part.
+ * r1_weight  host double[n_roots] (may be NULL): ||r1||^2 / ||r||^2.
+ * n_iter     host int (may be NULL): Davidson iterations.
+ * Converged when every residual ||sigma - omega r||_2 (||r|| = 1) < tol.
+ * Errors: CC_ERR_STATE (no converged CCSD), CC_ERR_NOT_CONVERGED.
+ */
+int ipeom_solve(cc_ctx *ctx, int n_roots, double tol, int max_iter,
+                double *omega, double *r1_weight, int *n_iter);
+
+/* Amplitudes as unique elements, host complex128: t1 [o][v] then t2 for
+ * i<j, a<b in row-major pair order ([o(o-1)/2][v(v-1)/2]). */
+int cc_get_amplitudes(const cc_ctx *ctx, double *t1_host, double *t2_host);
+/* Forget amplitudes and H-bar: the next ccsd_solve starts from t1 = 0,
+ * t2 = MP2 again (integrals and any FNS truncation are kept). */
+int cc_reset_amplitudes(cc_ctx *ctx);
+int cc_set_amplitudes(cc_ctx *ctx, const double *t1_host,
+                      const double *t2_host);
+
+/*
+ * Component entry points (device pointers, context stream, current tier).
+ * cc_ladder_dev: out[i][j][a][b] = 1/2 sum_cd <ab||cd> tau[i][j][c][d],
+ *   the particle-particle ladder of the doubles equation with <ab||cd> from
+ *   the context's virtual Cholesky block (Eq. 23), never stored whole.
+ *   tau and out: complex128 [o][o][v][v], tau antisymmetric in (i,j), (c,d).
+ *   out is overwritten.
+ * cc_residual_dev: one evaluation of the CCSD equations at (t1, t2):
+ *   r1 [o][v], r2 [o][o][v][v] (complex128) receive the right-hand sides R
+ *   with the Jacobi form t = R / D (D = eps_occ sums minus eps_virt sums).
+ * ipeom_sigma_dev: sigma vectors for n_vec packed IP vectors
+ *   r[n_vec][dim] -> s[n_vec][dim], dim = o + o(o-1)/2 v, layout r_i then
+ *   r_ij^b for i<j (row-major pairs), b fastest. Needs H-bar (ccsd_solve).
+ */
+int cc_ladder_dev(cc_ctx *ctx, const double *tau_dev, double *out_dev);
+int cc_residual_dev(cc_ctx *ctx, const double *t1_dev, const double *t2_dev,
+                    double *r1_dev, double *r2_dev);
+int ipeom_sigma_dev(cc_ctx *ctx, int n_vec, const double *r_dev,
+                    double *s_dev);
+
+/*
+ * cc_zgemm_dev: the library's complex GEMM on device buffers,
+ *   C[m][n] = sum_k A[m][k] * B[n][k]   (complex128, row-major, C overwritten)
+ * in the given tier (CC_TIER_*), on the default stream. The dense
+ * contraction core of every step above; exposed for tests and profiling.
+ * Allocates its operand planes with cudaMalloc. Errors: CC_ERR_ARG.
+ */
+int cc_zgemm_dev(int tier, long M, long N, long K, const double *A_dev,
+                 const double *B_dev, double *C_dev);
+
+/*
+ * cc_dump_integrals: bit-reproducible FP64 evaluation of Eq. 23 for one
+ * block (0: <ij||kl>, 1: <ij||ka>, 2: <ij||ab>, 3: <ia||bj>), host
+ * complex128 output in row-major block order. The sum over P runs in
+ * ascending order with each complex product formed as
+ * (ar*br - ai*bi, ar*bi + ai*br), round-to-nearest, no fused multiply-add,
+ * and each term added as (direct - exchange): the result is identical bit
+ * for bit to any other evaluation in that order.
+ */
+int cc_dump_integrals(cc_ctx *ctx, int block, double *out_host);
+
+/* Timing and counters of the last solver calls (host double[n], n <= 16):
+ * [0] ladder ms (sum over calls), [1] ladder calls, [2] ladder algorithmic
+ * flops per call, [3] fns ms, [4] ccsd ms, [5] ipeom ms, [6] kernel launches
+ * since the context was created, [7] ccsd iterations, [8] Davidson
+ * iterations, [9] tensor-core GEMM ms inside the ladder, [10] tc GEMM
+ * launches inside the ladder. */
+int cc_get_stats(const cc_ctx *ctx, double *out_host, int n);
+
+const char *cc_last_error(const cc_ctx *ctx); /* NULL ctx: last global */
+void cc_free(cc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CDFNS_H */

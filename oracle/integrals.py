@@ -54,3 +54,34 @@ class Blocks:
 
 def blocks_from_cholesky(L, n_occ):
     return Blocks(antisym_full(L), n_occ)
+
+
+def antisym_fixed_order(L, p, q, r, s):
+    """Eq. 23 for index ranges p, q, r, s (slices), in one fixed order.
+
+    The sum over P runs in ascending order; each complex product is formed
+    as (ar*br - ai*bi, ar*bi + ai*br) with every multiply and add rounded
+    separately (no fused multiply-add), the term is direct - exchange, and
+    it is added to the running sum. Any evaluation that follows the same
+    order gives the same bits.
+    """
+    L = np.asarray(L, dtype=np.complex128)
+    Lpr = L[:, p, r]
+    Lqs = L[:, q, s]
+    Lps = L[:, p, s]
+    Lqr = L[:, q, r]
+    shape = (Lpr.shape[1], Lqs.shape[1], Lpr.shape[2], Lqs.shape[2])
+    acc_r = np.zeros(shape)
+    acc_i = np.zeros(shape)
+    for P in range(L.shape[0]):
+        a = Lpr[P][:, None, :, None]
+        b = Lqs[P][None, :, None, :]
+        c = Lps[P][:, None, None, :]
+        d = Lqr[P][None, :, :, None]
+        d1r = a.real * b.real - a.imag * b.imag
+        d1i = a.real * b.imag + a.imag * b.real
+        d2r = c.real * d.real - c.imag * d.imag
+        d2i = c.real * d.imag + c.imag * d.real
+        acc_r = acc_r + (d1r - d2r)
+        acc_i = acc_i + (d1i - d2i)
+    return acc_r + 1j * acc_i

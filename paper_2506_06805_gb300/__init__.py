@@ -1,0 +1,311 @@
+"""GB300 CD/FNS IP-EOM-CCSD: Python binding of libcdfns.so.
+
+Argument marshalling only: every step of the method runs in the CUDA
+kernels of ``libcdfns.so`` (declared in ``include/cdfns.h``). PyTorch
+supplies device memory (its caching allocator serves the library's
+workspace) and the CUDA stream. There is no CPU fallback: importing
+:func:`lib` without the built library, or calling it without a GPU, raises.
+
+Typical use::
+
+    from paper_2506_06805_gb300 import System, synth
+    eps, L = synth.make_system(40, 300, 1200, kramers=True)
+    with System(eps, L, n_occ=40, tier="tf32") as s:
+        e = s.ccsd(tol=1e-8)
+        w, r1w = s.ipeom(8, tol=1e-7)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = ["lib", "System", "CCError", "TIERS", "LIB_PATH"]
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcdfns.so")
+
+TIERS = {"fp64": 0, "tf32": 1, "tf32x3": 2, "bf16x3": 3}
+_ERRORS = {
+    -1: "CC_ERR_ARG", -2: "CC_ERR_INPUT", -3: "CC_ERR_OOM", -4: "CC_ERR_CUDA",
+    -5: "CC_ERR_NOT_CONVERGED", -6: "CC_ERR_NUMERIC", -7: "CC_ERR_TIMEOUT",
+    -8: "CC_ERR_STATE", -9: "CC_ERR_UNSUPPORTED",
+}
+
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+_ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+_SIGS = {
+    "cc_set_default_allocator": (ctypes.c_int, [_ALLOC, _FREE, _P]),
+    "cc_set_default_stream": (ctypes.c_int, [_P]),
+    "cc_init": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D,
+                               ctypes.POINTER(_P)]),
+    "cc_init_chunked": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       _D, ctypes.POINTER(_P)]),
+    "cc_add_cholesky": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _D]),
+    "cc_set_precision": (ctypes.c_int, [_P, ctypes.c_int]),
+    "cc_set_precision_eom": (ctypes.c_int, [_P, ctypes.c_int]),
+    "cc_set_stream": (ctypes.c_int, [_P, _P]),
+    "cc_set_slab_budget": (ctypes.c_int, [_P, ctypes.c_size_t]),
+    "cc_get_sizes": (ctypes.c_int, [_P, _I, _I, _I]),
+    "fns_truncate": (ctypes.c_int, [_P, ctypes.c_double, _I]),
+    "fns_truncate_count": (ctypes.c_int, [_P, ctypes.c_int]),
+    "fns_get_occupations": (ctypes.c_int, [_P, _D, ctypes.c_int]),
+    "ccsd_solve": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, _D, _I]),
+    "ipeom_solve": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                   _D, _D, _I]),
+    "cc_get_amplitudes": (ctypes.c_int, [_P, _D, _D]),
+    "cc_set_amplitudes": (ctypes.c_int, [_P, _D, _D]),
+    "cc_reset_amplitudes": (ctypes.c_int, [_P]),
+    "cc_ladder_dev": (ctypes.c_int, [_P, _P, _P]),
+    "cc_residual_dev": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "ipeom_sigma_dev": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "cc_dump_integrals": (ctypes.c_int, [_P, ctypes.c_int, _D]),
+    "cc_zgemm_dev": (ctypes.c_int, [ctypes.c_int, ctypes.c_long, ctypes.c_long,
+                                    ctypes.c_long, _P, _P, _P]),
+    "cc_get_stats": (ctypes.c_int, [_P, _D, ctypes.c_int]),
+    "cc_last_error": (ctypes.c_char_p, [_P]),
+    "cc_free": (None, [_P]),
+}
+
+_lib = None
+
+
+class CCError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def header_symbols():
+    """Function names declared in include/cdfns.h."""
+    import re
+    hdr = os.path.join(os.path.dirname(os.path.dirname(LIB_PATH)), "include",
+                       "cdfns.h")
+    text = open(hdr).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(c[c]?_\w+|fns_\w+|ccsd_\w+|ipeom_\w+)\s*\(",
+                                 text, re.M)))
+
+
+def lib():
+    """Load libcdfns.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"{LIB_PATH} is missing: build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_D)
+
+
+def _check(rc, ctx=None, ok=(0,)):
+    if rc not in ok:
+        msg = lib().cc_last_error(ctx)
+        raise CCError(rc, msg.decode() if msg else "")
+    return rc
+
+
+_TORCH_HOOKS = None
+
+
+def use_torch_memory():
+    """Route the library's device allocations through PyTorch's caching
+    allocator and issue its work on torch's current stream."""
+    global _TORCH_HOOKS
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("a CUDA device is required")
+    dev = torch.cuda.current_device()
+
+    def _alloc(n, _user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(n), dev)
+        except RuntimeError:
+            return None
+
+    def _free(p, _user):
+        torch.cuda.caching_allocator_delete(p)
+
+    hooks = (_ALLOC(_alloc), _FREE(_free))
+    _check(lib().cc_set_default_allocator(hooks[0], hooks[1], None))
+    _check(lib().cc_set_default_stream(torch.cuda.current_stream().cuda_stream))
+    _TORCH_HOOKS = hooks
+
+
+def zgemm_dev(A, B, C, tier="fp64"):
+    """C[m][n] = sum_k A[m][k] B[n][k] on device tensors (complex128)."""
+    t = TIERS[tier] if isinstance(tier, str) else int(tier)
+    M, K = A.shape
+    N = B.shape[0]
+    _check(lib().cc_zgemm_dev(t, M, N, K, _P(A.data_ptr()), _P(B.data_ptr()),
+                              _P(C.data_ptr())))
+
+
+class System:
+    """One system: orbital energies eps[n] and Cholesky vectors L[X][n][n]."""
+
+    def __init__(self, eps, L=None, n_occ=None, n_aux=None, tier="fp64",
+                 eom_tier=None, torch_memory=True, chunks=None):
+        if torch_memory and _TORCH_HOOKS is None:
+            use_torch_memory()
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        n = eps.shape[0]
+        if n_occ is None:
+            n_occ = int(np.count_nonzero(eps < 0))
+        self.n_occ = n_occ
+        self._ctx = _P()
+        if L is not None:
+            L = np.ascontiguousarray(L, dtype=np.complex128)
+            X = L.shape[0]
+            if L.shape != (X, n, n):
+                raise ValueError("L must be [n_aux][n][n]")
+            rc = lib().cc_init(n_occ, n - n_occ, X, _dptr(eps),
+                               L.view(np.float64).ctypes.data_as(_D),
+                               ctypes.byref(self._ctx))
+        else:
+            X = n_aux
+            rc = lib().cc_init_chunked(n_occ, n - n_occ, X, _dptr(eps),
+                                       ctypes.byref(self._ctx))
+            if rc == 0 and chunks is not None:
+                for p0, p1, Lc in chunks:
+                    Lc = np.ascontiguousarray(Lc, dtype=np.complex128)
+                    _check(lib().cc_add_cholesky(self._ctx, p0, p1,
+                                                 Lc.view(np.float64).ctypes.data_as(_D)),
+                           self._ctx)
+        _check(rc, None)
+        self.set_precision(tier, eom_tier)
+
+    # ---- lifecycle ----
+    def close(self):
+        if self._ctx:
+            lib().cc_free(self._ctx)
+            self._ctx = _P()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- configuration ----
+    def set_precision(self, tier, eom_tier=None):
+        t = TIERS[tier] if isinstance(tier, str) else int(tier)
+        _check(lib().cc_set_precision(self._ctx, t), self._ctx)
+        if eom_tier is not None:
+            e = TIERS[eom_tier] if isinstance(eom_tier, str) else int(eom_tier)
+            _check(lib().cc_set_precision_eom(self._ctx, e), self._ctx)
+
+    def set_stream(self, stream_handle):
+        _check(lib().cc_set_stream(self._ctx, _P(stream_handle)), self._ctx)
+
+    def set_slab_budget(self, nbytes):
+        _check(lib().cc_set_slab_budget(self._ctx, int(nbytes)), self._ctx)
+
+    def sizes(self):
+        o, v, x = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().cc_get_sizes(self._ctx, ctypes.byref(o), ctypes.byref(v),
+                                  ctypes.byref(x)), self._ctx)
+        return o.value, v.value, x.value
+
+    def add_cholesky(self, p0, p1, Lc):
+        Lc = np.ascontiguousarray(Lc, dtype=np.complex128)
+        _check(lib().cc_add_cholesky(self._ctx, p0, p1,
+                                     Lc.view(np.float64).ctypes.data_as(_D)), self._ctx)
+
+    # ---- solvers ----
+    def fns_truncate(self, threshold=None, n_keep=None):
+        if n_keep is not None:
+            _check(lib().fns_truncate_count(self._ctx, int(n_keep)), self._ctx)
+            return self.sizes()[1]
+        kept = ctypes.c_int()
+        _check(lib().fns_truncate(self._ctx, float(threshold), ctypes.byref(kept)),
+               self._ctx)
+        return kept.value
+
+    def fns_occupations(self, n):
+        out = np.empty(n)
+        _check(lib().fns_get_occupations(self._ctx, _dptr(out), n), self._ctx)
+        return out
+
+    def ccsd(self, tol=1e-8, max_iter=100, allow_unconverged=False):
+        e = np.zeros(2)
+        it = ctypes.c_int()
+        ok = (0, -5) if allow_unconverged else (0,)
+        _check(lib().ccsd_solve(self._ctx, tol, max_iter, _dptr(e), ctypes.byref(it)),
+               self._ctx, ok)
+        self.ccsd_iterations = it.value
+        return complex(e[0], e[1])
+
+    def ipeom(self, n_roots, tol=1e-7, max_iter=100, allow_unconverged=False):
+        w = np.zeros(2 * n_roots)
+        r1 = np.zeros(n_roots)
+        it = ctypes.c_int()
+        ok = (0, -5) if allow_unconverged else (0,)
+        _check(lib().ipeom_solve(self._ctx, n_roots, tol, max_iter, _dptr(w), _dptr(r1),
+                                 ctypes.byref(it)), self._ctx, ok)
+        self.davidson_iterations = it.value
+        return w[0::2] + 1j * w[1::2], r1
+
+    def get_amplitudes(self):
+        o, v, _ = self.sizes()
+        t1 = np.empty(o * v, np.complex128)
+        t2 = np.empty(o * (o - 1) // 2 * (v * (v - 1) // 2), np.complex128)
+        _check(lib().cc_get_amplitudes(self._ctx, t1.view(np.float64).ctypes.data_as(_D),
+                                       t2.view(np.float64).ctypes.data_as(_D)), self._ctx)
+        return t1.reshape(o, v), t2
+
+    def reset_amplitudes(self):
+        _check(lib().cc_reset_amplitudes(self._ctx), self._ctx)
+
+    def set_amplitudes(self, t1, t2_packed):
+        t1 = np.ascontiguousarray(t1, np.complex128)
+        t2 = np.ascontiguousarray(t2_packed, np.complex128)
+        _check(lib().cc_set_amplitudes(self._ctx, t1.view(np.float64).ctypes.data_as(_D),
+                                       t2.view(np.float64).ctypes.data_as(_D)), self._ctx)
+
+    # ---- components on device tensors (torch complex128, contiguous) ----
+    def ladder_dev(self, tau, out):
+        _check(lib().cc_ladder_dev(self._ctx, _P(tau.data_ptr()), _P(out.data_ptr())),
+               self._ctx)
+
+    def residual_dev(self, t1, t2, r1, r2):
+        _check(lib().cc_residual_dev(self._ctx, _P(t1.data_ptr()), _P(t2.data_ptr()),
+                                     _P(r1.data_ptr()), _P(r2.data_ptr())), self._ctx)
+
+    def sigma_dev(self, r, s):
+        _check(lib().ipeom_sigma_dev(self._ctx, int(r.shape[0]), _P(r.data_ptr()),
+                                     _P(s.data_ptr())), self._ctx)
+
+    def dump_integrals(self, block):
+        o, v, _ = self.sizes()
+        shapes = {0: (o, o, o, o), 1: (o, o, o, v), 2: (o, o, v, v), 3: (o, v, v, o)}
+        out = np.empty(shapes[block], np.complex128)
+        _check(lib().cc_dump_integrals(self._ctx, block,
+                                       out.view(np.float64).ctypes.data_as(_D)), self._ctx)
+        return out
+
+    def stats(self):
+        s = np.zeros(16)
+        _check(lib().cc_get_stats(self._ctx, _dptr(s), 16), self._ctx)
+        keys = ["ladder_ms", "ladder_calls", "ladder_flops", "fns_ms", "ccsd_ms",
+                "ipeom_ms", "launches", "ccsd_iter", "davidson_iter"]
+        return {k: float(s[i]) for i, k in enumerate(keys)}

@@ -1,0 +1,423 @@
+// extern "C" boundary of libcdfns.so (declared in include/cdfns.h).
+#include <cstring>
+#include <mutex>
+
+#include "solver.h"
+
+struct cc_ctx {
+  cdfns::Ctx c;
+};
+
+namespace cdfns {
+
+namespace {
+std::mutex g_mu;
+std::string g_last_error;
+Allocator g_default_alloc;
+cudaStream_t g_default_stream = nullptr;
+}  // namespace
+
+void fail(int code, const std::string &msg) { throw Error{code, msg}; }
+
+void check_cuda(cudaError_t e, const char *what, const char *file, int line) {
+  if (e == cudaSuccess) return;
+  const int code = (e == cudaErrorMemoryAllocation) ? CC_ERR_OOM : CC_ERR_CUDA;
+  fail(code, std::string(what) + ": " + cudaGetErrorString(e) + " (" + file + ":" +
+                 std::to_string(line) + ")");
+}
+
+void *Allocator::get(size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void *p = nullptr;
+  if (alloc) {
+    p = alloc(bytes, user);
+    if (!p) fail(CC_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  } else {
+    const cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      fail(CC_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+  }
+  return p;
+}
+
+void Allocator::put(void *p) {
+  if (!p) return;
+  if (free) free(p, user);
+  else cudaFree(p);
+}
+
+void Buf::reset(Allocator *a, size_t n) {
+  release();
+  al = a;
+  p = a->get(n);
+  bytes = n;
+}
+
+void Buf::release() {
+  if (p && al) al->put(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+}  // namespace cdfns
+
+using cdfns::Ctx;
+using cdfns::Error;
+
+namespace {
+
+template <class F>
+int guarded(cc_ctx *ctx, F &&f) {
+  try {
+    return f();
+  } catch (const Error &e) {
+    if (ctx) ctx->c.last_error = e.msg;
+    std::lock_guard<std::mutex> lk(cdfns::g_mu);
+    cdfns::g_last_error = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc &) {
+    if (ctx) ctx->c.last_error = "host allocation failed";
+    return CC_ERR_OOM;
+  } catch (const std::exception &e) {
+    if (ctx) ctx->c.last_error = e.what();
+    return CC_ERR_CUDA;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int cc_set_default_allocator(void *(*alloc)(size_t, void *), void (*free_fn)(void *, void *),
+                             void *user) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return CC_ERR_ARG;
+  std::lock_guard<std::mutex> lk(cdfns::g_mu);
+  cdfns::g_default_alloc.alloc = alloc;
+  cdfns::g_default_alloc.free = free_fn;
+  cdfns::g_default_alloc.user = user;
+  return CC_OK;
+}
+
+int cc_set_default_stream(void *stream) {
+  std::lock_guard<std::mutex> lk(cdfns::g_mu);
+  cdfns::g_default_stream = static_cast<cudaStream_t>(stream);
+  return CC_OK;
+}
+
+int cc_init_chunked(int n_occ, int n_virt, int n_aux, const double *eps, cc_ctx **out) {
+  if (!out) return CC_ERR_ARG;
+  *out = nullptr;
+  cc_ctx *ctx = nullptr;
+  try {
+    ctx = new cc_ctx;
+  } catch (...) {
+    return CC_ERR_OOM;
+  }
+  {
+    std::lock_guard<std::mutex> lk(cdfns::g_mu);
+    ctx->c.al = cdfns::g_default_alloc;
+    ctx->c.st = cdfns::g_default_stream;
+  }
+  const int rc = guarded(ctx, [&] {
+    ctx->c.create(n_occ, n_virt, n_aux, eps);
+    return CC_OK;
+  });
+  if (rc != CC_OK) {
+    delete ctx;
+    return rc;
+  }
+  *out = ctx;
+  return CC_OK;
+}
+
+int cc_add_cholesky(cc_ctx *ctx, int p0, int p1, const double *L_chunk) {
+  if (!ctx) return CC_ERR_ARG;
+  return guarded(ctx, [&] {
+    ctx->c.add_chunk(p0, p1, L_chunk);
+    return CC_OK;
+  });
+}
+
+int cc_init(int n_occ, int n_virt, int n_aux, const double *eps, const double *L, cc_ctx **out) {
+  if (!out) return CC_ERR_ARG;
+  *out = nullptr;
+  if (!L) return CC_ERR_ARG;
+  cc_ctx *ctx = nullptr;
+  int rc = cc_init_chunked(n_occ, n_virt, n_aux, eps, &ctx);
+  if (rc != CC_OK) return rc;
+  rc = guarded(ctx, [&] {
+    ctx->c.add_chunk(0, n_aux, L);
+    ctx->c.validate_input();
+    return CC_OK;
+  });
+  if (rc != CC_OK) {
+    delete ctx;
+    return rc;
+  }
+  *out = ctx;
+  return CC_OK;
+}
+
+int cc_set_precision(cc_ctx *ctx, int tier) {
+  if (!ctx) return CC_ERR_ARG;
+  if (tier < CC_TIER_FP64 || tier > CC_TIER_BF16X3) return CC_ERR_ARG;
+  ctx->c.tier = tier;
+  ctx->c.hbar_done = false;
+  return CC_OK;
+}
+
+int cc_set_precision_eom(cc_ctx *ctx, int tier) {
+  if (!ctx) return CC_ERR_ARG;
+  if (tier < -1 || tier > CC_TIER_BF16X3) return CC_ERR_ARG;
+  ctx->c.eom_tier = tier;
+  return CC_OK;
+}
+
+int cc_set_stream(cc_ctx *ctx, void *stream) {
+  if (!ctx) return CC_ERR_ARG;
+  ctx->c.st = static_cast<cudaStream_t>(stream);
+  ctx->c.eng.st = ctx->c.st;
+  return CC_OK;
+}
+
+int cc_set_slab_budget(cc_ctx *ctx, size_t bytes) {
+  if (!ctx || bytes < 4096) return CC_ERR_ARG;
+  ctx->c.slab_budget = bytes;
+  return CC_OK;
+}
+
+int cc_get_sizes(const cc_ctx *ctx, int *n_occ, int *n_virt, int *n_aux) {
+  if (!ctx) return CC_ERR_ARG;
+  if (n_occ) *n_occ = ctx->c.o;
+  if (n_virt) *n_virt = ctx->c.v;
+  if (n_aux) *n_aux = ctx->c.X;
+  return CC_OK;
+}
+
+int fns_truncate(cc_ctx *ctx, double threshold, int *n_virt_kept) {
+  if (!ctx) return CC_ERR_ARG;
+  if (!(threshold >= 0)) return CC_ERR_ARG;
+  return guarded(ctx, [&] {
+    const int rc = ctx->c.fns(threshold, -1);
+    if (n_virt_kept) *n_virt_kept = ctx->c.v;
+    return rc;
+  });
+}
+
+int fns_truncate_count(cc_ctx *ctx, int n_keep) {
+  if (!ctx || n_keep < 1) return CC_ERR_ARG;
+  return guarded(ctx, [&] { return ctx->c.fns(0.0, n_keep); });
+}
+
+int fns_get_occupations(const cc_ctx *ctx, double *occ, int n) {
+  if (!ctx || !occ) return CC_ERR_ARG;
+  const auto &f = ctx->c.fns_occ;
+  if (f.empty()) return CC_ERR_STATE;
+  if (n < static_cast<int>(f.size())) return CC_ERR_ARG;
+  std::memcpy(occ, f.data(), sizeof(double) * f.size());
+  return CC_OK;
+}
+
+int ccsd_solve(cc_ctx *ctx, double tol, int max_iter, double *e_corr, int *n_iter) {
+  if (!ctx || !e_corr) return CC_ERR_ARG;
+  return guarded(ctx, [&] { return ctx->c.ccsd(tol, max_iter, e_corr, n_iter); });
+}
+
+int ipeom_solve(cc_ctx *ctx, int n_roots, double tol, int max_iter, double *omega, double *r1_weight,
+                int *n_iter) {
+  if (!ctx || !omega) return CC_ERR_ARG;
+  return guarded(ctx, [&] {
+    return ctx->c.ipeom(n_roots, tol, max_iter, omega, r1_weight, n_iter);
+  });
+}
+
+int cc_get_amplitudes(const cc_ctx *cctx, double *t1_host, double *t2_host) {
+  cc_ctx *ctx = const_cast<cc_ctx *>(cctx);
+  if (!ctx || !t1_host || !t2_host) return CC_ERR_ARG;
+  return guarded(ctx, [&] {
+    Ctx &c = ctx->c;
+    if (!c.amps) cdfns::fail(CC_ERR_STATE, "no amplitudes yet");
+    const long na = c.n_amp();
+    cdfns::Buf vec(&c.al, sizeof(cdfns::cplx) * na);
+    cdfns::pack_amps(c.t1.c(), c.t2.c(), c.o, c.v, vec.c(), c.st);
+    const long n1 = static_cast<long>(c.o) * c.v;
+    CUDA_CHECK(cudaMemcpyAsync(t1_host, vec.p, sizeof(cdfns::cplx) * n1, cudaMemcpyDeviceToHost, c.st));
+    CUDA_CHECK(cudaMemcpyAsync(t2_host, vec.c() + n1, sizeof(cdfns::cplx) * (na - n1),
+                               cudaMemcpyDeviceToHost, c.st));
+    CUDA_CHECK(cudaStreamSynchronize(c.st));
+    return CC_OK;
+  });
+}
+
+int cc_reset_amplitudes(cc_ctx *ctx) {
+  if (!ctx) return CC_ERR_ARG;
+  ctx->c.amps = false;
+  ctx->c.amps_user = false;
+  ctx->c.ccsd_done = false;
+  ctx->c.hbar_done = false;
+  return CC_OK;
+}
+
+int cc_set_amplitudes(cc_ctx *ctx, const double *t1_host, const double *t2_host) {
+  if (!ctx || !t1_host || !t2_host) return CC_ERR_ARG;
+  return guarded(ctx, [&] {
+    Ctx &c = ctx->c;
+    c.ensure_ready();
+    const long na = c.n_amp();
+    const long n1 = static_cast<long>(c.o) * c.v;
+    cdfns::Buf vec(&c.al, sizeof(cdfns::cplx) * na);
+    CUDA_CHECK(cudaMemcpyAsync(vec.p, t1_host, sizeof(cdfns::cplx) * n1, cudaMemcpyHostToDevice, c.st));
+    CUDA_CHECK(cudaMemcpyAsync(vec.c() + n1, t2_host, sizeof(cdfns::cplx) * (na - n1),
+                               cudaMemcpyHostToDevice, c.st));
+    c.B(c.t1, n1);
+    c.B(c.t2, static_cast<long>(c.o) * c.o * c.v * c.v);
+    cdfns::unpack_amps(vec.c(), c.o, c.v, c.t1.c(), c.t2.c(), c.st);
+    CUDA_CHECK(cudaStreamSynchronize(c.st));
+    c.amps = true;
+    c.amps_user = true;
+    c.ccsd_done = false;
+    c.hbar_done = false;
+    return CC_OK;
+  });
+}
+
+int cc_ladder_dev(cc_ctx *ctx, const double *tau_dev, double *out_dev) {
+  if (!ctx || !tau_dev || !out_dev) return CC_ERR_ARG;
+  return guarded(ctx, [&] {
+    Ctx &c = ctx->c;
+    c.ensure_ready();
+    const size_t n = sizeof(cdfns::cplx) * c.o * c.o * c.v * c.v;
+    CUDA_CHECK(cudaMemsetAsync(out_dev, 0, n, c.st));
+    c.ladder(c.Lvv.c(), reinterpret_cast<const cdfns::cplx *>(tau_dev),
+             reinterpret_cast<cdfns::cplx *>(out_dev), c.tier);
+    CUDA_CHECK(cudaStreamSynchronize(c.st));
+    return CC_OK;
+  });
+}
+
+int cc_residual_dev(cc_ctx *ctx, const double *t1_dev, const double *t2_dev, double *r1_dev,
+                    double *r2_dev) {
+  if (!ctx || !t1_dev || !t2_dev || !r1_dev || !r2_dev) return CC_ERR_ARG;
+  return guarded(ctx, [&] {
+    Ctx &c = ctx->c;
+    c.ensure_ready();
+    c.residual(reinterpret_cast<const cdfns::cplx *>(t1_dev), reinterpret_cast<const cdfns::cplx *>(t2_dev),
+               reinterpret_cast<cdfns::cplx *>(r1_dev), reinterpret_cast<cdfns::cplx *>(r2_dev));
+    CUDA_CHECK(cudaStreamSynchronize(c.st));
+    c.check_err_flag();
+    return CC_OK;
+  });
+}
+
+int ipeom_sigma_dev(cc_ctx *ctx, int n_vec, const double *r_dev, double *s_dev) {
+  if (!ctx || !r_dev || !s_dev || n_vec < 1) return CC_ERR_ARG;
+  return guarded(ctx, [&] {
+    Ctx &c = ctx->c;
+    if (!c.ccsd_done && !c.amps) cdfns::fail(CC_ERR_STATE, "sigma needs amplitudes");
+    if (!c.hbar_done) c.build_hbar();
+    c.sigma(n_vec, reinterpret_cast<const cdfns::cplx *>(r_dev), reinterpret_cast<cdfns::cplx *>(s_dev));
+    CUDA_CHECK(cudaStreamSynchronize(c.st));
+    c.check_err_flag();
+    return CC_OK;
+  });
+}
+
+int cc_zgemm_dev(int tier, long M, long N, long K, const double *A, const double *B, double *C) {
+  if (tier < CC_TIER_FP64 || tier > CC_TIER_BF16X3 || M < 1 || N < 1 || K < 1 || !A || !B || !C)
+    return CC_ERR_ARG;
+  return guarded(nullptr, [&] {
+    static cdfns::Allocator al;
+    cdfns::Engine eng;
+    eng.al = &al;
+    eng.st = cdfns::g_default_stream;
+    int dev = 0;
+    CUDA_CHECK(cudaGetDevice(&dev));
+    CUDA_CHECK(cudaDeviceGetAttribute(&eng.num_sms, cudaDevAttrMultiProcessorCount, dev));
+    cdfns::Buf err(&al, 16);
+    CUDA_CHECK(cudaMemsetAsync(err.p, 0, 16, eng.st));
+    eng.err_flag = err.as<int>();
+    using cdfns::T;
+    eng.contract(cdfns::C1(), T(reinterpret_cast<const cdfns::cplx *>(A), "mk", {M, K}),
+                 T(reinterpret_cast<const cdfns::cplx *>(B), "nk", {N, K}), cdfns::C0(),
+                 T(reinterpret_cast<const cdfns::cplx *>(C), "mn", {M, N}), tier);
+    int e = 0;
+    CUDA_CHECK(cudaMemcpyAsync(&e, err.p, sizeof(int), cudaMemcpyDeviceToHost, eng.st));
+    CUDA_CHECK(cudaStreamSynchronize(eng.st));
+    if (e) cdfns::fail(CC_ERR_TIMEOUT, "bounded wait expired");
+    return CC_OK;
+  });
+}
+
+int cc_dump_integrals(cc_ctx *ctx, int block, double *out_host) {
+  if (!ctx || !out_host || block < 0 || block > 3) return CC_ERR_ARG;
+  return guarded(ctx, [&] {
+    Ctx &c = ctx->c;
+    c.ensure_ready();
+    const long o = c.o, v = c.v, X = c.X;
+    // strides: [P][p][q] blocks
+    const cdfns::cplx *Loo = c.Loo.c(), *Lov = c.Lov.c(), *Lvo = c.Lvo.c(), *Lvv = c.Lvv.c();
+    const long soo = o * o, sov = o * v, svv = v * v;
+    int np, nq, nr, ns;
+    cdfns::Buf out;
+    // <pq||rs> = sum_P L_pr L_qs - L_ps L_qr
+    switch (block) {
+      case 0:  // <ij||kl>
+        np = nq = nr = ns = c.o;
+        out.reset(&c.al, sizeof(cdfns::cplx) * o * o * o * o);
+        cdfns::dump_block(Loo, soo, o, 1, Loo, soo, o, 1, Loo, soo, o, 1, Loo, soo, o, 1, c.X, np, nq,
+                          nr, ns, out.c(), c.st);
+        break;
+      case 1:  // <ij||ka>: L_ik L_ja - L_ia L_jk
+        np = nq = nr = c.o;
+        ns = c.v;
+        out.reset(&c.al, sizeof(cdfns::cplx) * o * o * o * v);
+        cdfns::dump_block(Loo, soo, o, 1, Lov, sov, v, 1, Lov, sov, v, 1, Loo, soo, o, 1, c.X, np, nq,
+                          nr, ns, out.c(), c.st);
+        break;
+      case 2:  // <ij||ab>: L_ia L_jb - L_ib L_ja
+        np = nq = c.o;
+        nr = ns = c.v;
+        out.reset(&c.al, sizeof(cdfns::cplx) * o * o * v * v);
+        cdfns::dump_block(Lov, sov, v, 1, Lov, sov, v, 1, Lov, sov, v, 1, Lov, sov, v, 1, c.X, np, nq,
+                          nr, ns, out.c(), c.st);
+        break;
+      default:  // <ia||bj>: L_ib L_aj - L_ij L_ab
+        np = c.o;
+        nq = c.v;
+        nr = c.v;
+        ns = c.o;
+        out.reset(&c.al, sizeof(cdfns::cplx) * o * v * v * o);
+        cdfns::dump_block(Lov, sov, v, 1, Lvo, sov, o, 1, Loo, soo, o, 1, Lvv, svv, v, 1, c.X, np, nq,
+                          nr, ns, out.c(), c.st);
+        break;
+    }
+    (void)X;
+    CUDA_CHECK(cudaMemcpyAsync(out_host, out.p, out.bytes, cudaMemcpyDeviceToHost, c.st));
+    CUDA_CHECK(cudaStreamSynchronize(c.st));
+    return CC_OK;
+  });
+}
+
+int cc_get_stats(const cc_ctx *ctx, double *out, int n) {
+  if (!ctx || !out || n < 0 || n > 16) return CC_ERR_ARG;
+  double s[16];
+  std::memcpy(s, ctx->c.stat, sizeof(s));
+  s[6] = static_cast<double>(cdfns::g_launches);
+  std::memcpy(out, s, sizeof(double) * n);
+  return CC_OK;
+}
+
+const char *cc_last_error(const cc_ctx *ctx) {
+  if (ctx) return ctx->c.last_error.c_str();
+  return cdfns::g_last_error.c_str();
+}
+
+void cc_free(cc_ctx *ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->c.st);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Shared definitions for the CD/FNS IP-EOM-CCSD CUDA library.
+//
+// Complex numbers are stored interleaved (re, im): double2 for FP64 tensors,
+// float2 for the FP32 staging planes of the tensor-core path.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/cdfns.h"
+
+namespace cdfns {
+
+typedef double2 cplx;
+
+__host__ __device__ inline cplx mk(double r, double i) { return make_double2(r, i); }
+__host__ __device__ inline cplx cadd(cplx a, cplx b) { return mk(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline cplx csub(cplx a, cplx b) { return mk(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline cplx cmul(cplx a, cplx b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline cplx cconj(cplx a) { return mk(a.x, -a.y); }
+__host__ __device__ inline cplx cscale(double s, cplx a) { return mk(s * a.x, s * a.y); }
+__host__ __device__ inline cplx cfma(cplx a, cplx b, cplx c) {  // a*b + c
+  c.x = fma(a.x, b.x, c.x); c.x = fma(-a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y); c.y = fma(a.y, b.x, c.y);
+  return c;
+}
+
+// Error raised inside the library; carries a CC_ERR_* code.
+struct Error {
+  int code;
+  std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string &msg);
+void check_cuda(cudaError_t e, const char *what, const char *file, int line);
+#define CUDA_CHECK(x) ::cdfns::check_cuda((x), #x, __FILE__, __LINE__)
+#define LAUNCH_CHECK() ::cdfns::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+
+// Device workspace: every buffer the library owns goes through here so that
+// the caller's allocator (for example PyTorch's caching allocator) can serve
+// it. Buffers are freed when the Buf goes out of scope.
+struct Allocator {
+  void *(*alloc)(size_t, void *) = nullptr;
+  void (*free)(void *, void *) = nullptr;
+  void *user = nullptr;
+  void *get(size_t bytes);
+  void put(void *p);
+};
+
+struct Buf {
+  Allocator *al = nullptr;
+  void *p = nullptr;
+  size_t bytes = 0;
+  Buf() = default;
+  Buf(Allocator *a, size_t n) { reset(a, n); }
+  Buf(const Buf &) = delete;
+  Buf &operator=(const Buf &) = delete;
+  Buf(Buf &&o) noexcept { *this = std::move(o); }
+  Buf &operator=(Buf &&o) noexcept {
+    release();
+    al = o.al; p = o.p; bytes = o.bytes;
+    o.p = nullptr; o.bytes = 0;
+    return *this;
+  }
+  ~Buf() { release(); }
+  void reset(Allocator *a, size_t n);
+  void release();
+  template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+  cplx *c() const { return as<cplx>(); }
+};
+
+// Precision tiers of the contraction engine (CC_TIER_* in cdfns.h).
+enum Tier { TIER_FP64 = 0, TIER_TF32 = 1, TIER_TF32X3 = 2, TIER_BF16X3 = 3 };
+
+// Kernel launch counter (for reporting how many kernels ran).
+extern unsigned long long g_launches;
+inline void count_launch(unsigned long long n = 1) { g_launches += n; }
+
+}  // namespace cdfns

@@ -1,0 +1,247 @@
+#include "engine.h"
+
+#include <algorithm>
+#include <sstream>
+#include <tuple>
+
+namespace cdfns {
+
+TRef T(const cplx *p, const std::string &idx, const std::vector<long> &dims, bool cj) {
+  TRef t;
+  t.p = const_cast<cplx *>(p);
+  t.idx = idx;
+  t.dims = dims;
+  t.str.resize(dims.size());
+  long s = 1;
+  for (int i = static_cast<int>(dims.size()) - 1; i >= 0; --i) {
+    t.str[i] = s;
+    s *= dims[i];
+  }
+  t.conj = cj;
+  if (idx.size() != dims.size()) fail(CC_ERR_ARG, "tensor view: index/dims mismatch " + idx);
+  return t;
+}
+
+TRef T(const cplx *p, const char *idx, std::initializer_list<long> dims, bool cj) {
+  return T(p, std::string(idx), std::vector<long>(dims), cj);
+}
+
+TRef Tv(const cplx *p, const char *idx, std::initializer_list<long> dims,
+        std::initializer_list<long> strides, bool cj) {
+  TRef t = T(p, idx, dims, cj);
+  t.str = strides;
+  if (t.str.size() != t.dims.size()) fail(CC_ERR_ARG, "strided view: rank mismatch");
+  return t;
+}
+
+const long *Engine::table(const std::vector<long> &dims, const std::vector<long> &strides) {
+  std::ostringstream key;
+  for (size_t i = 0; i < dims.size(); ++i) key << dims[i] << ':' << strides[i] << ',';
+  auto it = cache_.find(key.str());
+  if (it != cache_.end()) return it->second.as<long>();
+  long total = 1;
+  for (long d : dims) total *= d;
+  Buf b(al, sizeof(long) * std::max<long>(total, 1));
+  make_offsets(b.as<long>(), static_cast<int>(dims.size()), dims.data(), strides.data(), st);
+  const long *p = b.as<long>();
+  cache_[key.str()] = std::move(b);
+  return p;
+}
+
+std::pair<void *, void *> Engine::packed(bool a_side, const TRef &t, const long *rt, const long *kt,
+                                         long ld, long rows, long K, long Kp, int tier) {
+  std::ostringstream key;
+  key << (a_side ? 'A' : 'B') << t.p << ':' << t.conj << ':' << rt << ':' << kt << ':' << ld << ':'
+      << rows << ':' << K << ':' << Kp << ':' << tier;
+  auto it = packs_.find(key.str());
+  if (it != packs_.end()) return {it->second.hi.p, it->second.lo.p};
+  const size_t eb = tc_elem_bytes(tier);
+  const size_t n = eb * (a_side ? 2 : 1) * rows * Kp;
+  Packed pk;
+  pk.hi.reset(al, n);
+  if (tier != TIER_TF32) pk.lo.reset(al, n);
+  if (a_side)
+    tc_pack_A(t.p, rt, kt, ld, t.conj, rows, K, Kp, tier, pk.hi.p, pk.lo.p, st);
+  else
+    tc_pack_B(t.p, rt, kt, ld, t.conj, rows, K, Kp, tier, pk.hi.p, pk.lo.p, st);
+  std::pair<void *, void *> r{pk.hi.p, pk.lo.p};
+  packs_[key.str()] = std::move(pk);
+  return r;
+}
+
+void *Engine::plane(int which, size_t bytes) {
+  Buf &b = planes_[which];
+  if (b.bytes < bytes) {
+    b.release();
+    b.reset(al, bytes + bytes / 8);
+  }
+  return b.p;
+}
+
+namespace {
+
+int find(const std::string &s, char c) {
+  const size_t p = s.find(c);
+  return p == std::string::npos ? -1 : static_cast<int>(p);
+}
+
+// A table that is a plain linear map (offset = i * step) is not needed.
+bool linear(const std::vector<long> &dims, const std::vector<long> &str, long *step) {
+  // row-major contiguous block with a uniform inner stride
+  if (dims.empty()) {
+    *step = 0;
+    return true;
+  }
+  long expect = str.back();
+  for (int i = static_cast<int>(dims.size()) - 1; i >= 0; --i) {
+    if (dims[i] == 1) continue;
+    if (str[i] != expect) return false;
+    expect *= dims[i];
+  }
+  *step = str.back();
+  // if every dim of size 1 the step is irrelevant
+  return true;
+}
+
+}  // namespace
+
+void Engine::contract(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef &C,
+                      int tier) {
+  std::vector<long> mdim, amstr, cmstr, ndim, bnstr, cnstr, kdim, akstr, bkstr;
+  for (size_t i = 0; i < C.idx.size(); ++i) {
+    const char c = C.idx[i];
+    const int ia = find(A.idx, c), ib = find(B.idx, c);
+    if (ia >= 0 && ib >= 0) fail(CC_ERR_ARG, std::string("contract: batch index ") + c);
+    if (ia >= 0) {
+      if (A.dims[ia] != C.dims[i]) fail(CC_ERR_ARG, std::string("contract: dim mismatch ") + c);
+      mdim.push_back(C.dims[i]);
+      amstr.push_back(A.str[ia]);
+      cmstr.push_back(C.str[i]);
+    } else if (ib >= 0) {
+      if (B.dims[ib] != C.dims[i]) fail(CC_ERR_ARG, std::string("contract: dim mismatch ") + c);
+      ndim.push_back(C.dims[i]);
+      bnstr.push_back(B.str[ib]);
+      cnstr.push_back(C.str[i]);
+    } else {
+      fail(CC_ERR_ARG, std::string("contract: output index not in inputs ") + c);
+    }
+  }
+  for (size_t i = 0; i < A.idx.size(); ++i) {
+    const char c = A.idx[i];
+    if (find(C.idx, c) >= 0) continue;
+    const int ib = find(B.idx, c);
+    if (ib < 0) fail(CC_ERR_ARG, std::string("contract: dangling index ") + c);
+    if (A.dims[i] != B.dims[ib]) fail(CC_ERR_ARG, std::string("contract: K dim mismatch ") + c);
+    kdim.push_back(A.dims[i]);
+    akstr.push_back(A.str[i]);
+    bkstr.push_back(B.str[ib]);
+  }
+  for (size_t i = 0; i < B.idx.size(); ++i) {
+    const char c = B.idx[i];
+    if (find(C.idx, c) < 0 && find(A.idx, c) < 0)
+      fail(CC_ERR_ARG, std::string("contract: dangling index ") + c);
+  }
+  long M = 1, N = 1, K = 1;
+  for (long d : mdim) M *= d;
+  for (long d : ndim) N *= d;
+  for (long d : kdim) K *= d;
+  if (M == 0 || N == 0) return;
+  flops += 8.0 * M * N * K;
+
+  // tables (NULL when linear)
+  long step;
+  const long *am = nullptr, *ak = nullptr, *bn = nullptr, *bk = nullptr, *cm = nullptr, *cn = nullptr;
+  long lda = 0, ldb = 0, ldc = 0;
+  if (linear(mdim, amstr, &step)) lda = step; else am = table(mdim, amstr);
+  if (linear(mdim, cmstr, &step)) ldc = step; else cm = table(mdim, cmstr);
+  if (linear(ndim, bnstr, &step)) ldb = step; else bn = table(ndim, bnstr);
+  {
+    long s2;
+    if (!(linear(ndim, cnstr, &s2) && s2 == 1 && !ndim.empty())) {
+      if (ndim.empty()) {
+        cn = nullptr;  // N = 1: offset 0
+      } else {
+        cn = table(ndim, cnstr);
+      }
+    }
+  }
+  if (!(linear(kdim, akstr, &step) && (kdim.empty() || step == 1))) ak = table(kdim, akstr);
+  if (!(linear(kdim, bkstr, &step) && (kdim.empty() || step == 1))) bk = table(kdim, bkstr);
+  if (mdim.empty()) { lda = 0; ldc = 0; }
+  if (ndim.empty()) ldb = 0;
+
+  // small or skinny products stay on the FP64 path (GEMV or a few tiles)
+  const bool tiny = static_cast<double>(M) * N * K < 2.0e6 || K < 16 || M < 8 || N < 8;
+  if (tier == TIER_FP64 || tiny) {
+    GemmDesc g;
+    g.M = M; g.N = N; g.K = K;
+    g.A = A.p; g.am = am; g.ak = ak; g.lda = lda; g.conjA = A.conj;
+    g.B = B.p; g.bn = bn; g.bk = bk; g.ldb = ldb; g.conjB = B.conj;
+    g.C = C.p; g.cm = cm; g.cn = cn; g.ldc = ldc;
+    g.alpha = alpha; g.beta = beta;
+    g.k_contig = kdim.empty() || (M == 1 ? bkstr.back() == 1 : akstr.back() == 1);
+    gemm_f64(g, st, num_sms);
+    return;
+  }
+  // fast tier: pack operands into expanded planes, tensor-core GEMM
+  const int kal = tc_k_align(tier);
+  const long Kp = ((2 * K + kal - 1) / kal) * kal;
+  const size_t eb = tc_elem_bytes(tier);
+  const bool split = tier != TIER_TF32;
+  void *Ah, *Al = nullptr, *Bh, *Bl = nullptr;
+  if (A.stable) {
+    std::tie(Ah, Al) = packed(true, A, am, ak, lda, M, K, Kp, tier);
+  } else {
+    Ah = plane(0, eb * 2 * M * Kp);
+    Al = split ? plane(1, eb * 2 * M * Kp) : nullptr;
+    tc_pack_A(A.p, am, ak, lda, A.conj, M, K, Kp, tier, Ah, Al, st);
+  }
+  if (B.stable) {
+    std::tie(Bh, Bl) = packed(false, B, bn, bk, ldb, N, K, Kp, tier);
+  } else {
+    Bh = plane(2, eb * N * Kp);
+    Bl = split ? plane(3, eb * N * Kp) : nullptr;
+    tc_pack_B(B.p, bn, bk, ldb, B.conj, N, K, Kp, tier, Bh, Bl, st);
+  }
+  TcDesc t;
+  t.M = M; t.N = N; t.Kp = Kp;
+  t.A = Ah; t.Alo = Al; t.B = Bh; t.Blo = Bl;
+  t.tier = tier;
+  t.C = C.p; t.cm = cm; t.cn = cn; t.ldc = ldc;
+  t.alpha = alpha; t.beta = beta;
+  const long bn_cols = N >= 192 ? 256 : 128;
+  const long tiles = ((2 * M + 127) / 128) * ((N + bn_cols - 1) / bn_cols);
+  const long nkb = Kp / kal;
+  int sk = 1;
+  if (tiles < num_sms && nkb >= 8) {
+    sk = static_cast<int>(std::min<long>((num_sms + tiles - 1) / tiles, nkb / 4));
+    sk = std::max(sk, 1);
+  }
+  t.split_k = sk;
+  if (sk > 1) {
+    scale_2d(C.p, cm, cn, ldc, M, N, beta, st);
+    t.out = TC_OUT_F64_ATOMIC;
+  } else {
+    t.out = TC_OUT_F64;
+  }
+  gemm_tc(t, st, err_flag);
+}
+
+void Engine::permute_into(cplx alpha, const TRef &in, cplx beta, const TRef &out) {
+  // out must be contiguous; in strides reordered to out's index order
+  std::vector<long> istr(out.idx.size());
+  for (size_t i = 0; i < out.idx.size(); ++i) {
+    const int p = find(in.idx, out.idx[i]);
+    if (p < 0 || in.dims[p] != out.dims[i]) fail(CC_ERR_ARG, "permute_into: index mismatch");
+    istr[i] = in.str[p];
+  }
+  long expect = 1;
+  for (int i = static_cast<int>(out.dims.size()) - 1; i >= 0; --i) {
+    if (out.str[i] != expect && out.dims[i] != 1) fail(CC_ERR_ARG, "permute_into: out not contiguous");
+    expect *= out.dims[i];
+  }
+  permute(out.p, in.p, static_cast<int>(out.dims.size()), out.dims.data(), istr.data(), alpha, beta,
+          in.conj != out.conj, st);
+}
+
+}  // namespace cdfns

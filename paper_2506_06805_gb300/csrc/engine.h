@@ -1,0 +1,90 @@
+// Host-side tensor contraction engine.
+//
+// contract(alpha, A, B, beta, C) computes
+//   C[c-indices] = alpha * sum_{k} opA(A)[a-indices] opB(B)[b-indices] + beta * C
+// for index strings such as "imae", "mbej" -> "ijab". Indices of C split
+// into M (found in A) and N (found in B); indices in both A and B but not in C
+// are contracted (K). The operands are addressed in place through offset
+// tables (no permutation copies) for the FP64 GEMM, or packed once into the
+// expanded real planes of the tensor-core GEMM for the fast tiers.
+#pragma once
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+
+namespace cdfns {
+
+struct TRef {
+  cplx *p = nullptr;
+  std::string idx;
+  std::vector<long> dims;
+  std::vector<long> str;  // element strides
+  bool conj = false;
+  bool stable = false;  // contents fixed until Engine::clear_pack_cache()
+  long size() const {
+    long s = 1;
+    for (long d : dims) s *= d;
+    return s;
+  }
+};
+
+// Contiguous row-major view.
+TRef T(const cplx *p, const char *idx, std::initializer_list<long> dims, bool conj = false);
+TRef T(const cplx *p, const std::string &idx, const std::vector<long> &dims, bool conj = false);
+// Strided view.
+TRef Tv(const cplx *p, const char *idx, std::initializer_list<long> dims,
+        std::initializer_list<long> strides, bool conj = false);
+inline TRef conj(TRef t) {
+  t.conj = !t.conj;
+  return t;
+}
+// Mark an operand whose contents stay fixed across calls (integrals, H-bar):
+// its packed tensor-core planes are then built once and reused.
+inline TRef stable(TRef t) {
+  t.stable = true;
+  return t;
+}
+
+class Engine {
+ public:
+  Allocator *al = nullptr;
+  cudaStream_t st = nullptr;
+  int num_sms = 148;
+  int *err_flag = nullptr;  // device int, set by bounded waits
+  // statistics
+  double flops = 0;
+
+  void contract(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef &C, int tier);
+  // out = alpha * permuted(in) + beta * out, where out's index string names
+  // the order: e.g. permute_into(T(x,"ijab"), T(y,"jiab")) copies y with i,j
+  // exchanged.
+  void permute_into(cplx alpha, const TRef &in, cplx beta, const TRef &out);
+  const long *table(const std::vector<long> &dims, const std::vector<long> &strides);
+  // growable scratch planes for the tensor-core operands
+  void *plane(int which, size_t bytes);
+  void clear_cache() {
+    cache_.clear();
+    packs_.clear();
+  }
+  void clear_pack_cache() { packs_.clear(); }
+
+ private:
+  struct Packed {
+    Buf hi, lo;
+  };
+  // returns (hi, lo) planes of a stable operand, packing it on first use
+  std::pair<void *, void *> packed(bool a_side, const TRef &t, const long *rt, const long *kt,
+                                   long ld, long rows, long K, long Kp, int tier);
+  std::map<std::string, Buf> cache_;
+  std::map<std::string, Packed> packs_;
+  Buf planes_[6];
+};
+
+inline cplx C1() { return mk(1.0, 0.0); }
+inline cplx C0() { return mk(0.0, 0.0); }
+inline cplx Cr(double r) { return mk(r, 0.0); }
+
+}  // namespace cdfns

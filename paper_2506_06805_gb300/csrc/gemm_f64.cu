@@ -1,0 +1,219 @@
+// Complex FP64 GEMM on the FP64 pipe (the plain CC_TIER_FP64 path).
+//
+// C(m, n) = alpha * sum_k A(m, k) B(n, k) + beta * C(m, n) with operands
+// gathered through offset tables (see GemmDesc). 64 x 64 complex output tile
+// per 256-thread CTA, 4 x 4 complex accumulators per thread, K staged through
+// shared memory 8 complex elements at a time. GB300's FP64 rate is low enough
+// that this register tiling keeps the FP64 pipe busy; split-K over
+// blockIdx.z (with FP64 atomics) covers tall-skinny shapes such as the
+// Davidson subspace products.
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace cdfns {
+namespace {
+
+constexpr int TM = 64, TN = 64, TK = 8;
+
+__global__ void __launch_bounds__(256)
+    zgemm_kernel(long M, long N, long K, const double2 *__restrict__ A, const long *__restrict__ am,
+                 const long *__restrict__ ak, long lda, bool conjA, const double2 *__restrict__ B,
+                 const long *__restrict__ bn, const long *__restrict__ bk, long ldb, bool conjB,
+                 double2 *C, const long *__restrict__ cm, const long *__restrict__ cn, long ldc,
+                 double2 alpha, double2 beta, long k_per_split, bool atomic) {
+  __shared__ double2 As[TK][TM + 1];
+  __shared__ double2 Bs[TK][TN + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const long m0 = static_cast<long>(blockIdx.y) * TM;
+  const long n0 = static_cast<long>(blockIdx.x) * TN;
+  const long kbeg = static_cast<long>(blockIdx.z) * k_per_split;
+  const long kend = min(K, kbeg + k_per_split);
+
+  // loader mapping: 256 threads x 2 elements = 64 rows x 8 k
+  const int lr = threadIdx.x >> 2;        // row within tile
+  const int lk = (threadIdx.x & 3) * 2;   // k pair
+  const long arow = m0 + lr, brow = n0 + lr;
+  const long aro = arow < M ? (am ? am[arow] : arow * lda) : -1;
+  const long bro = brow < N ? (bn ? bn[brow] : brow * ldb) : -1;
+
+  double2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+
+  for (long k0 = kbeg; k0 < kend; k0 += TK) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const long k = k0 + lk + u;
+      double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
+      if (k < kend) {
+        if (aro >= 0) {
+          a = A[aro + (ak ? ak[k] : k)];
+          if (conjA) a.y = -a.y;
+        }
+        if (bro >= 0) {
+          b = B[bro + (bk ? bk[k] : k)];
+          if (conjB) b.y = -b.y;
+        }
+      }
+      As[lk + u][lr] = a;
+      Bs[lk + u][lr] = b;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      double2 a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = cfma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const long m = m0 + ty + 16 * i;
+    if (m >= M) continue;
+    const long co = cm ? cm[m] : m * ldc;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const long n = n0 + tx + 16 * j;
+      if (n >= N) continue;
+      const long off = co + (cn ? cn[n] : n);
+      const double2 x = cmul(alpha, acc[i][j]);
+      if (atomic) {
+        atomicAdd(&C[off].x, x.x);
+        atomicAdd(&C[off].y, x.y);
+      } else if (beta.x == 0.0 && beta.y == 0.0) {
+        C[off] = x;
+      } else {
+        C[off] = cadd(x, cmul(beta, C[off]));
+      }
+    }
+  }
+}
+
+// y(n) = alpha sum_k A(k) B(n, k) + beta y(n): one thread per output n, the
+// loop over k walks each thread's own row (L1 absorbs the stride).
+__global__ void gemv_kernel(long N, long K, const double2 *__restrict__ A, const long *__restrict__ ak,
+                            bool conjA, const double2 *__restrict__ B, const long *__restrict__ bn,
+                            const long *__restrict__ bk, long ldb, bool conjB, double2 *C,
+                            const long *__restrict__ cn, long ldc, double2 alpha, double2 beta) {
+  for (long n = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; n < N;
+       n += static_cast<long>(gridDim.x) * blockDim.x) {
+    const long bo = bn ? bn[n] : n * ldb;
+    double2 acc = make_double2(0.0, 0.0);
+    for (long k = 0; k < K; ++k) {
+      double2 a = A[ak ? ak[k] : k];
+      double2 b = B[bo + (bk ? bk[k] : k)];
+      if (conjA) a.y = -a.y;
+      if (conjB) b.y = -b.y;
+      acc = cfma(a, b, acc);
+    }
+    const long off = cn ? cn[n] : n * ldc;
+    const double2 x = cmul(alpha, acc);
+    C[off] = (beta.x == 0.0 && beta.y == 0.0) ? x : cadd(x, cmul(beta, C[off]));
+  }
+}
+
+// Same contraction with one warp per output element and the lanes striding
+// k: coalesced when the operand's innermost K index has unit stride.
+__global__ void gemv_warp_kernel(long N, long K, const double2 *__restrict__ A,
+                                 const long *__restrict__ ak, bool conjA,
+                                 const double2 *__restrict__ B, const long *__restrict__ bn,
+                                 const long *__restrict__ bk, long ldb, bool conjB, double2 *C,
+                                 const long *__restrict__ cn, long ldc, double2 alpha,
+                                 double2 beta) {
+  const int lane = threadIdx.x & 31;
+  const long wpb = blockDim.x >> 5;
+  for (long n = blockIdx.x * wpb + (threadIdx.x >> 5); n < N; n += static_cast<long>(gridDim.x) * wpb) {
+    const long bo = bn ? bn[n] : n * ldb;
+    double2 acc = make_double2(0.0, 0.0);
+    for (long k = lane; k < K; k += 32) {
+      double2 a = A[ak ? ak[k] : k];
+      double2 b = B[bo + (bk ? bk[k] : k)];
+      if (conjA) a.y = -a.y;
+      if (conjB) b.y = -b.y;
+      acc = cfma(a, b, acc);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) {
+      const long off = cn ? cn[n] : n * ldc;
+      const double2 x = cmul(alpha, acc);
+      C[off] = (beta.x == 0.0 && beta.y == 0.0) ? x : cadd(x, cmul(beta, C[off]));
+    }
+  }
+}
+
+}  // namespace
+
+void gemm_f64(const GemmDesc &g, cudaStream_t st, int num_sms) {
+  if (g.M <= 0 || g.N <= 0) return;
+  if (g.K <= 0) {
+    scale_2d(g.C, g.cm, g.cn, g.ldc, g.M, g.N, g.beta, st);
+    return;
+  }
+  // Matrix-vector shapes are memory bound: one thread per output element.
+  // Taken when the vector side and the output's other index need no table
+  // (always the case for the engine's size-1 index sets).
+  const bool rowvec = g.M == 1 && !g.am && !g.cm;
+  const bool colvec = !rowvec && g.N == 1 && !g.bn && !g.cn;
+  if (rowvec || colvec) {
+    const long n_out = rowvec ? g.N : g.M;
+    if (g.k_contig) {
+      const unsigned wb = static_cast<unsigned>(std::min<long>((n_out + 7) / 8, 65535));
+      if (rowvec)
+        gemv_warp_kernel<<<wb, 256, 0, st>>>(n_out, g.K, g.A, g.ak, g.conjA, g.B, g.bn, g.bk, g.ldb,
+                                             g.conjB, g.C, g.cn, 1, g.alpha, g.beta);
+      else
+        gemv_warp_kernel<<<wb, 256, 0, st>>>(n_out, g.K, g.B, g.bk, g.conjB, g.A, g.am, g.ak, g.lda,
+                                             g.conjA, g.C, g.cm, g.ldc, g.alpha, g.beta);
+      LAUNCH_CHECK();
+      count_launch();
+      return;
+    }
+    const unsigned blocks = static_cast<unsigned>(std::min<long>((n_out + 255) / 256, 65535));
+    if (rowvec) {
+      gemv_kernel<<<blocks, 256, 0, st>>>(n_out, g.K, g.A, g.ak, g.conjA, g.B, g.bn, g.bk, g.ldb,
+                                          g.conjB, g.C, g.cn, 1, g.alpha, g.beta);
+    } else {
+      gemv_kernel<<<blocks, 256, 0, st>>>(n_out, g.K, g.B, g.bk, g.conjB, g.A, g.am, g.ak, g.lda,
+                                          g.conjA, g.C, g.cm, g.ldc, g.alpha, g.beta);
+    }
+    LAUNCH_CHECK();
+    count_launch();
+    return;
+  }
+  const long tiles = ((g.M + TM - 1) / TM) * ((g.N + TN - 1) / TN);
+  long split = 1;
+  const long target = 2L * num_sms;
+  if (tiles < target && g.K >= 4 * TK * 16) {
+    split = std::min<long>((target + tiles - 1) / tiles, (g.K + 255) / 256);
+    split = std::max<long>(split, 1);
+  }
+  long kps = (g.K + split - 1) / split;
+  kps = (kps + TK - 1) / TK * TK;
+  split = (g.K + kps - 1) / kps;
+  const bool atomic = split > 1;
+  if (atomic) scale_2d(g.C, g.cm, g.cn, g.ldc, g.M, g.N, g.beta, st);
+  dim3 grid(static_cast<unsigned>((g.N + TN - 1) / TN), static_cast<unsigned>((g.M + TM - 1) / TM),
+            static_cast<unsigned>(split));
+  if (grid.y > 65535) fail(CC_ERR_ARG, "gemm_f64: M too large");
+  zgemm_kernel<<<grid, 256, 0, st>>>(g.M, g.N, g.K, g.A, g.am, g.ak, g.lda, g.conjA, g.B, g.bn, g.bk,
+                                     g.ldb, g.conjB, g.C, g.cm, g.cn, g.ldc, g.alpha, g.beta, kps,
+                                     atomic);
+  LAUNCH_CHECK();
+  count_launch();
+}
+
+}  // namespace cdfns

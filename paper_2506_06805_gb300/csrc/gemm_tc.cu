@@ -1,0 +1,557 @@
+// Tensor-core complex GEMM for sm_103a: tcgen05.mma with TMEM accumulators,
+// operands staged by TMA (cp.async.bulk.tensor) into 128-byte-swizzled
+// shared memory, mbarrier pipeline, warp-specialised roles.
+//
+// The complex product is done as ONE real GEMM on an expanded operand:
+// A' (2M x 2K) holds rows (Re a, -Im a) and (Im a, Re a) interleaved over k,
+// B' (N x 2K) is the interleaved complex B. Rows 2m / 2m+1 of D = A' B'^T are
+// then Re / Im of (A B^T)(m, :), i.e. the four real products of the complex
+// product ("4M") in a single accumulator tile.
+//
+// Precision tiers: kind::tf32 with one product (TIER_TF32) or with a hi/lo
+// split and three products hi*hi + hi*lo + lo*hi (TIER_TF32X3); kind::f16
+// with bf16 hi/lo and three products (TIER_BF16X3). Accumulation is FP32 in
+// TMEM; the epilogue accumulates into FP64 (or stores FP32 for staging).
+//
+// CTA layout (192 threads): warps 0-3 epilogue (TMEM lane quadrant = warp),
+// warp 4 TMA producer, warp 5 TMEM allocator + MMA issuer. One output tile
+// of 128 real rows (64 complex rows) x BN columns per CTA; split-K over
+// blockIdx.z. Every mbarrier wait is bounded in time; on expiry the kernel
+// records an error flag, drains, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include "kernels.h"
+
+namespace cdfns {
+
+namespace {
+
+constexpr int BM = 128;            // real rows per tile (TMEM lanes)
+constexpr int ROW_BYTES = 128;     // one swizzle row: 32 fp32 or 64 bf16
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of the given parity to complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > WAIT_NS) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), version 1, tile base 1024-byte aligned.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>(1u) << 16;               // LBO (unused for SW128 K-major)
+  d |= static_cast<uint64_t>(1024u >> 4) << 32;       // SBO
+  d |= static_cast<uint64_t>(1u) << 46;               // descriptor version
+  d |= static_cast<uint64_t>(2u) << 61;               // SWIZZLE_128B
+  return d;
+}
+// Instruction descriptor for kind::tf32 / kind::f16: D f32, A/B K-major.
+__host__ __device__ constexpr uint32_t make_idesc(int m, int n, uint32_t ab_type) {
+  return (1u << 4) | (ab_type << 7) | (ab_type << 10) |
+         (static_cast<uint32_t>(n >> 3) << 17) | (static_cast<uint32_t>(m >> 4) << 24);
+}
+template <bool BF16>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t acc) {
+  if constexpr (BF16) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  }
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+struct TcArgs {
+  long M, N;        // complex rows, columns
+  int num_kb;       // K blocks of 128 bytes per row
+  int kb_per_split;
+  int chunk;        // K blocks accumulated in TMEM before promotion
+  int out;
+  void *C;
+  const long *cm, *cn;
+  long ldc;
+  double2 alpha, beta;
+  int *err;
+};
+
+// CTA: warps 0-7 epilogue (TMEM lane quadrant = warp % 4, column half =
+// warp / 4), warp 8 TMA producer, warp 9 TMEM allocator + MMA issuer.
+// TMEM holds two accumulator buffers of BN columns. The MMA warp fills one
+// buffer with a chunk of `chunk` K blocks while the epilogue warps add the
+// other buffer's partial sums into FP32 registers (round to nearest): the
+// tensor core's own accumulation only ever spans one chunk, which bounds its
+// truncation bias independently of K.
+template <int BN, int STAGES, bool SPLIT, bool BF16>
+__global__ void __launch_bounds__(320, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mAlo,
+                   const __grid_constant__ CUtensorMap mB, const __grid_constant__ CUtensorMap mBlo,
+                   const TcArgs args) {
+  constexpr int A_BYTES = BM * ROW_BYTES;
+  constexpr int B_BYTES = BN * ROW_BYTES;
+  constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * (SPLIT ? 2 : 1);
+  constexpr int K_ELEMS = BF16 ? 64 : 32;        // elements per 128-byte row
+  constexpr int MMA_K_BYTES = 32;                // K per MMA: 8 tf32 / 16 bf16
+  constexpr uint32_t IDESC = make_idesc(BM, BN, BF16 ? 1u : 2u);
+  constexpr int HALF = BN / 2;                   // columns per epilogue warp
+  constexpr uint32_t TMEM_COLS = 2 * BN;
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+  uint64_t *empty = full + STAGES;
+  uint64_t *tfull = empty + STAGES;   // [2]
+  uint64_t *tempty = tfull + 2;       // [2]
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int m_tile = blockIdx.y;
+  const int n_tile = blockIdx.x;
+  const int kb0 = blockIdx.z * args.kb_per_split;
+  const int kb1 = min(args.num_kb, kb0 + args.kb_per_split);
+  const int nkb = kb1 - kb0;
+  if (nkb <= 0) return;  // uniform over the CTA
+  const int chunk = args.chunk;
+  const int nchunks = (nkb + chunk - 1) / chunk;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 8);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 9) tmem_alloc(tmem_slot, TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 8) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      int issued = 0;
+      for (int i = 0; i < nkb; ++i) {
+        const int s = i % STAGES;
+        const uint32_t ph = (i / STAGES) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u)) {
+          atomicExch(args.err, 1);
+          break;
+        }
+        uint8_t *st = smem + s * STAGE_BYTES;
+        mbar_expect_tx(&full[s], STAGE_BYTES);
+        const int kx = (kb0 + i) * K_ELEMS;
+        tma_load_2d(st, &mA, &full[s], kx, m_tile * BM);
+        tma_load_2d(st + A_BYTES, &mB, &full[s], kx, n_tile * BN);
+        if constexpr (SPLIT) {
+          tma_load_2d(st + A_BYTES + B_BYTES, &mAlo, &full[s], kx, m_tile * BM);
+          tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mBlo, &full[s], kx, n_tile * BN);
+        }
+        issued = i + 1;
+      }
+      // the last load issued into each stage must land before the CTA exits
+      for (int i = (issued > STAGES ? issued - STAGES : 0); i < issued; ++i) {
+        if (!mbar_wait(&full[i % STAGES], (i / STAGES) & 1u)) atomicExch(args.err, 1);
+      }
+    }
+  } else if (warp == 9) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      int kb = 0;
+      bool ok = true;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        const int buf = c & 1;
+        if (c >= 2 && !mbar_wait(&tempty[buf], ((c - 2) >> 1) & 1u)) {
+          atomicExch(args.err, 1);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dt = tmem + buf * BN;
+        const int kend = min(nkb, (c + 1) * chunk);
+        for (int i = 0; kb < kend; ++i, ++kb) {
+          const int s = kb % STAGES;
+          const uint32_t ph = (kb / STAGES) & 1u;
+          if (!mbar_wait(&full[s], ph)) {
+            atomicExch(args.err, 1);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
+          const uint32_t b0 = a0 + A_BYTES;
+          const uint32_t alo = b0 + B_BYTES;
+          const uint32_t blo = alo + A_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < ROW_BYTES / MMA_K_BYTES; ++kk) {
+            const uint64_t da = sw128_desc(a0 + kk * MMA_K_BYTES);
+            const uint64_t db = sw128_desc(b0 + kk * MMA_K_BYTES);
+            mma<BF16>(dt, da, db, IDESC, (i > 0 || kk > 0) ? 1u : 0u);
+            if constexpr (SPLIT) {
+              mma<BF16>(dt, da, sw128_desc(blo + kk * MMA_K_BYTES), IDESC, 1u);
+              mma<BF16>(dt, sw128_desc(alo + kk * MMA_K_BYTES), db, IDESC, 1u);
+            }
+          }
+          mma_commit(&empty[s]);
+        }
+        mma_commit(&tfull[buf]);
+      }
+      if (!ok) {
+        // release the epilogue of every chunk it still waits for
+        for (int b = 0; b < 2; ++b) mma_commit(&tfull[b]);
+      }
+    }
+  } else {
+    // ---------------- epilogue: 8 warps ----------------
+    const int q = warp & 3;
+    const int h = warp >> 2;
+    float acc[HALF];
+#pragma unroll
+    for (int j = 0; j < HALF; ++j) acc[j] = 0.f;
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      const int buf = c & 1;
+      if (!mbar_wait(&tfull[buf], (c >> 1) & 1u)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + buf * BN + h * HALF;
+#pragma unroll
+      for (int j = 0; j < HALF; j += 16) {
+        float v[16];
+        tmem_ld16(base + j, v);
+#pragma unroll
+        for (int t = 0; t < 16; ++t) acc[j + t] += v[t];
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
+    }
+    if (!ok) {
+      if (lane == 0) atomicExch(args.err, 1);
+    } else {
+      const long mc = static_cast<long>(m_tile) * (BM / 2) + q * 16 + (lane >> 1);
+      const bool odd = lane & 1;
+      const bool row_ok = mc < args.M;
+      const long coff = row_ok ? (args.cm ? args.cm[mc] : mc * args.ldc) : 0;
+      const long nbase = static_cast<long>(n_tile) * BN + h * HALF;
+#pragma unroll
+      for (int j = 0; j < HALF; j += 16) {
+        float other[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) other[t] = __shfl_xor_sync(0xffffffffu, acc[j + t], 1);
+        // even lane: acc = Re, other = Im (writes columns j..j+7);
+        // odd lane: acc = Im, other = Re (writes columns j+8..j+15)
+        if (row_ok) {
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const long n = nbase + j + (odd ? 8 : 0) + jj;
+            if (n >= args.N) break;
+            const float re = odd ? other[8 + jj] : acc[j + jj];
+            const float im = odd ? acc[j + 8 + jj] : other[jj];
+            if (args.out == TC_OUT_F32) {
+              float2 *Cf = reinterpret_cast<float2 *>(args.C);
+              Cf[mc * args.ldc + n] = make_float2(re, im);
+            } else {
+              double2 *C = reinterpret_cast<double2 *>(args.C);
+              const long off = coff + (args.cn ? args.cn[n] : n);
+              const double dr = re, di = im;
+              const double xr = args.alpha.x * dr - args.alpha.y * di;
+              const double xi = args.alpha.x * di + args.alpha.y * dr;
+              if (args.out == TC_OUT_F64_ATOMIC) {
+                atomicAdd(&C[off].x, xr);
+                atomicAdd(&C[off].y, xi);
+              } else if (args.beta.x == 0.0 && args.beta.y == 0.0) {
+                C[off] = make_double2(xr, xi);
+              } else {
+                const double2 cv = C[off];
+                C[off] = make_double2(xr + args.beta.x * cv.x - args.beta.y * cv.y,
+                                      xi + args.beta.x * cv.y + args.beta.y * cv.x);
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 9) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void *p = nullptr;
+    CUDA_CHECK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                                cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) fail(CC_ERR_CUDA, "cuTensorMapEncodeTiled not found");
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+CUtensorMap make_map(const void *base, long rows, long kp, int box_rows, bool bf16) {
+  CUtensorMap m;
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(kp), static_cast<cuuint64_t>(rows)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(kp) * (bf16 ? 2 : 4)};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(bf16 ? 64 : 32),
+                             static_cast<cuuint32_t>(box_rows)};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = get_encoder()(&m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                             2, const_cast<void *>(base), dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) fail(CC_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(r));
+  return m;
+}
+
+template <int BN, int STAGES, bool SPLIT, bool BF16>
+void launch(const TcDesc &g, cudaStream_t st, int *err) {
+  constexpr int STAGE_BYTES = (BM * ROW_BYTES + BN * ROW_BYTES) * (SPLIT ? 2 : 1);
+  constexpr int SMEM = STAGES * STAGE_BYTES + (2 * STAGES + 4) * 8 + 16 + 1024;
+  static_assert(SMEM <= 232448, "shared memory budget");
+  auto kern = tc_gemm_kernel<BN, STAGES, SPLIT, BF16>;
+  static bool attr = false;
+  if (!attr) {
+    CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
+    attr = true;
+  }
+  const long mr = 2 * g.M;
+  CUtensorMap mA = make_map(g.A, mr, g.Kp, BM, BF16);
+  CUtensorMap mB = make_map(g.B, g.N, g.Kp, BN, BF16);
+  CUtensorMap mAlo = SPLIT ? make_map(g.Alo, mr, g.Kp, BM, BF16) : mA;
+  CUtensorMap mBlo = SPLIT ? make_map(g.Blo, g.N, g.Kp, BN, BF16) : mB;
+  TcArgs a;
+  a.M = g.M;
+  a.N = g.N;
+  a.num_kb = static_cast<int>(g.Kp / (BF16 ? 64 : 32));
+  const int sk = std::max(1, std::min(g.split_k, a.num_kb));
+  a.kb_per_split = (a.num_kb + sk - 1) / sk;
+  const int zs = (a.num_kb + a.kb_per_split - 1) / a.kb_per_split;
+  a.chunk = (g.tier == TIER_TF32) ? 8 : 4;
+  a.out = g.out;
+  a.C = g.C;
+  a.cm = g.cm;
+  a.cn = g.cn;
+  a.ldc = g.ldc;
+  a.alpha = g.alpha;
+  a.beta = g.beta;
+  a.err = err;
+  dim3 grid(static_cast<unsigned>((g.N + BN - 1) / BN), static_cast<unsigned>((mr + BM - 1) / BM),
+            static_cast<unsigned>(zs));
+  kern<<<grid, 320, SMEM, st>>>(mA, mAlo, mB, mBlo, a);
+  LAUNCH_CHECK();
+  count_launch();
+}
+
+}  // namespace
+
+int tc_k_align(int tier) { return tier == TIER_BF16X3 ? 64 : 32; }
+size_t tc_elem_bytes(int tier) { return tier == TIER_BF16X3 ? 2 : 4; }
+
+void gemm_tc(const TcDesc &g, cudaStream_t st, int *err) {
+  if (g.M <= 0 || g.N <= 0 || g.Kp <= 0) return;
+  if (g.Kp % tc_k_align(g.tier)) fail(CC_ERR_ARG, "gemm_tc: Kp not padded");
+  if ((reinterpret_cast<uintptr_t>(g.A) | reinterpret_cast<uintptr_t>(g.B)) & 15)
+    fail(CC_ERR_ARG, "gemm_tc: operands must be 16-byte aligned");
+  const bool wide = g.N >= 192;
+  switch (g.tier) {
+    case TIER_TF32:
+      if (wide) launch<256, 4, false, false>(g, st, err);
+      else launch<128, 6, false, false>(g, st, err);
+      break;
+    case TIER_TF32X3:
+      if (wide) launch<256, 2, true, false>(g, st, err);
+      else launch<128, 3, true, false>(g, st, err);
+      break;
+    case TIER_BF16X3:
+      if (wide) launch<256, 2, true, true>(g, st, err);
+      else launch<128, 3, true, true>(g, st, err);
+      break;
+    default:
+      fail(CC_ERR_ARG, "gemm_tc: bad tier");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Operand packing (FP64 complex -> expanded real planes)
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+template <bool BF16>
+__device__ __forceinline__ void split_store(void *hi, void *lo, long idx, float x) {
+  if constexpr (BF16) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    reinterpret_cast<__nv_bfloat16 *>(hi)[idx] = h;
+    if (lo) reinterpret_cast<__nv_bfloat16 *>(lo)[idx] = __float2bfloat16_rn(x - __bfloat162float(h));
+  } else {
+    const float h = to_tf32(x);
+    reinterpret_cast<float *>(hi)[idx] = h;
+    if (lo) reinterpret_cast<float *>(lo)[idx] = to_tf32(x - h);
+  }
+}
+
+// Grid: x over complex k (padded to Kp/2), y over rows (grid-stride).
+template <bool BF16, bool EXPAND>
+__global__ void pack_kernel(const double2 *__restrict__ src, const long *__restrict__ rt,
+                            const long *__restrict__ kt, long ld, bool conj, long rows, long K,
+                            long Kp, void *hi, void *lo) {
+  const long kc = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;  // complex k
+  if (kc >= Kp / 2) return;
+  for (long r = blockIdx.y; r < rows; r += gridDim.y) {
+    double2 a = make_double2(0.0, 0.0);
+    if (kc < K) {
+      const long off = (rt ? rt[r] : r * ld) + (kt ? kt[kc] : kc);
+      a = src[off];
+      if (conj) a.y = -a.y;
+    }
+    const float re = static_cast<float>(a.x), im = static_cast<float>(a.y);
+    if (EXPAND) {
+      const long r0 = (2 * r) * Kp + 2 * kc;
+      const long r1 = (2 * r + 1) * Kp + 2 * kc;
+      split_store<BF16>(hi, lo, r0, re);
+      split_store<BF16>(hi, lo, r0 + 1, -im);
+      split_store<BF16>(hi, lo, r1, im);
+      split_store<BF16>(hi, lo, r1 + 1, re);
+    } else {
+      const long r0 = r * Kp + 2 * kc;
+      split_store<BF16>(hi, lo, r0, re);
+      split_store<BF16>(hi, lo, r0 + 1, im);
+    }
+  }
+}
+
+template <bool EXPAND>
+void pack_launch(const cplx *src, const long *rt, const long *kt, long ld, bool conj, long rows,
+                 long K, long Kp, int tier, void *hi, void *lo, cudaStream_t st) {
+  if (rows <= 0) return;
+  const int threads = 256;
+  dim3 grid(static_cast<unsigned>((Kp / 2 + threads - 1) / threads),
+            static_cast<unsigned>(std::min<long>(rows, 65535)));
+  void *l = (tier == TIER_TF32) ? nullptr : lo;
+  if (tier == TIER_BF16X3)
+    pack_kernel<true, EXPAND><<<grid, threads, 0, st>>>(src, rt, kt, ld, conj, rows, K, Kp, hi, l);
+  else
+    pack_kernel<false, EXPAND><<<grid, threads, 0, st>>>(src, rt, kt, ld, conj, rows, K, Kp, hi, l);
+  LAUNCH_CHECK();
+  count_launch();
+}
+
+}  // namespace
+
+void tc_pack_A(const cplx *src, const long *am, const long *ak, long lda, bool conj, long M,
+               long K, long Kp, int tier, void *hi, void *lo, cudaStream_t st) {
+  pack_launch<true>(src, am, ak, lda, conj, M, K, Kp, tier, hi, lo, st);
+}
+void tc_pack_B(const cplx *src, const long *bn, const long *bk, long ldb, bool conj, long N,
+               long K, long Kp, int tier, void *hi, void *lo, cudaStream_t st) {
+  pack_launch<false>(src, bn, bk, ldb, conj, N, K, Kp, tier, hi, lo, st);
+}
+
+}  // namespace cdfns

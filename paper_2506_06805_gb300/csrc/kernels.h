@@ -1,0 +1,94 @@
+// Internal kernel entry points (host launchers) of the library.
+#pragma once
+
+#include "common.cuh"
+
+namespace cdfns {
+
+// ---------------------------------------------------------------------------
+// Complex GEMM  C(m, n) = alpha * sum_k opA(A)(m, k) * opB(B)(n, k) + beta * C
+//
+// Operands are addressed through offset tables (element offsets, complex
+// units): A(m, k) = A[am[m] + ak[k]], B(n, k) = B[bn[n] + bk[k]],
+// C(m, n) = C[cm[m] + cn[n]]. A NULL table means the linear map
+// (am[m] = m * lda, ak[k] = k, ... cm[m] = m * ldc, cn[n] = n), so plain
+// row-major K-major operands need no table. conj flags conjugate an operand.
+// ---------------------------------------------------------------------------
+struct GemmDesc {
+  long M = 0, N = 0, K = 0;
+  const cplx *A = nullptr; const long *am = nullptr, *ak = nullptr; long lda = 0; bool conjA = false;
+  const cplx *B = nullptr; const long *bn = nullptr, *bk = nullptr; long ldb = 0; bool conjB = false;
+  cplx *C = nullptr; const long *cm = nullptr, *cn = nullptr; long ldc = 0;
+  cplx alpha = {1.0, 0.0}, beta = {0.0, 0.0};
+  bool k_contig = false;  // the GEMV operand's innermost K index has unit stride
+};
+
+// FP64 SIMT path (CC_TIER_FP64).
+void gemm_f64(const GemmDesc &g, cudaStream_t st, int num_sms);
+
+// Real tensor-core GEMM on the expanded complex form (tcgen05, TMEM, TMA).
+//   D(r, n) = sum_k A'(r, k) B'(n, k),  r < Mr = 2 M, k < Kp (padded)
+// A' rows 2m / 2m+1 hold (Re, -Im) / (Im, Re) of A(m, :) interleaved over k,
+// B' row n holds (Re, Im) of B(n, :), so rows 2m, 2m+1 of D are Re, Im of
+// (A B^T)(m, n). Planes are fp32 (tf32 kinds) or bf16, row-major with
+// leading dimension Kp; *_lo planes hold the low parts for the 3-product
+// split tiers (NULL otherwise).
+enum TcOut {
+  TC_OUT_F64 = 0,        // C(m, n) = alpha D + beta C through tables (double2)
+  TC_OUT_F64_ATOMIC = 1, // C(m, n) += alpha D (split-K partials)
+  TC_OUT_F32 = 2,        // Cf[m * ldc + n] = D (float2, plain row-major)
+};
+struct TcDesc {
+  long M = 0, N = 0, Kp = 0;  // complex rows, columns, padded real K
+  const void *A = nullptr, *Alo = nullptr, *B = nullptr, *Blo = nullptr;
+  int tier = TIER_TF32;
+  int out = TC_OUT_F64;
+  void *C = nullptr; const long *cm = nullptr, *cn = nullptr; long ldc = 0;
+  cplx alpha = {1.0, 0.0}, beta = {0.0, 0.0};
+  int split_k = 1;
+};
+void gemm_tc(const TcDesc &g, cudaStream_t st, int *err_flag);
+// Padded K granularity (real elements) for a tier: 32 for tf32, 64 for bf16.
+int tc_k_align(int tier);
+size_t tc_elem_bytes(int tier);
+
+// Expand/convert operands for gemm_tc from FP64 tensors addressed by tables.
+// A side: rows 2m, 2m+1 (M complex rows) x Kp real columns (2 per complex k).
+void tc_pack_A(const cplx *src, const long *am, const long *ak, long lda,
+               bool conj, long M, long K, long Kp, int tier, void *hi,
+               void *lo, cudaStream_t st);
+void tc_pack_B(const cplx *src, const long *bn, const long *bk, long ldb,
+               bool conj, long N, long K, long Kp, int tier, void *hi,
+               void *lo, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Tensor helpers
+// ---------------------------------------------------------------------------
+// table[i] = sum_d digit_d(i) * stride_d over the row-major index space dims.
+void make_offsets(long *table, int nd, const long *dims, const long *strides,
+                  cudaStream_t st);
+// C(m, n) *= beta through tables (or linear when NULL).
+void scale_2d(cplx *C, const long *cm, const long *cn, long ldc, long M,
+              long N, cplx beta, cudaStream_t st);
+// y = alpha * x + beta * y (contiguous)
+void axpby(long n, cplx alpha, const cplx *x, cplx beta, cplx *y,
+           cudaStream_t st);
+// out[perm-ordered] = alpha * in + beta * out, generic rank <= 8 permutation:
+// out element with row-major index over odims reads in[sum digit * istr].
+void permute(cplx *out, const cplx *in, int nd, const long *odims,
+             const long *istr, cplx alpha, cplx beta, bool conj,
+             cudaStream_t st);
+
+// R += c (X - s_ij X(ji) - s_ab X(ba) + s_ij s_ab X(ji,ba)) on [o][o][v][v]
+// tensors, mode bit 0 = P(ij), bit 1 = P(ab); tiled through shared memory.
+void antisym_add(cplx *R, const cplx *X, int o, int v, double c, int mode, cudaStream_t st);
+
+// Deterministic FP64 reductions (two-pass, fixed order).
+// sum_i w * conj?(x_i) * y_i
+cplx dot(const cplx *x, const cplx *y, long n, bool conj_x, cudaStream_t st,
+         cplx *dev_scratch /* >= 1024 */, cplx *host_out = nullptr);
+// Same, result left on the device (no synchronisation).
+void dot_dev(const cplx *x, const cplx *y, long n, bool conj_x, cplx *res,
+             cudaStream_t st, cplx *dev_scratch);
+
+}  // namespace cdfns

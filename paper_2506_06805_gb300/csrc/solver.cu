@@ -1,0 +1,991 @@
+// Host orchestration of CD/FNS IP-EOM-CCSD on one GPU.
+//
+// Storage policy (the implementation section of the paper): integrals with
+// at most two virtual indices are stored (<ij||kl>, <ij||ka>, <ij||ab>,
+// <ia||bj>); everything with three or four virtual indices is formed from
+// the Cholesky vectors (Eq. 23) inside the contraction that needs it.
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "solver.h"
+
+namespace cdfns {
+
+namespace {
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+struct Solver {
+  cusolverDnHandle_t h = nullptr;
+  cusolverDnParams_t p = nullptr;
+  ~Solver() {
+    if (p) cusolverDnDestroyParams(p);
+    if (h) cusolverDnDestroy(h);
+  }
+};
+
+Solver &solver_for(cudaStream_t st) {
+  thread_local Solver s;
+  if (!s.h) {
+    if (cusolverDnCreate(&s.h) != CUSOLVER_STATUS_SUCCESS) fail(CC_ERR_CUDA, "cusolverDnCreate failed");
+    if (cusolverDnCreateParams(&s.p) != CUSOLVER_STATUS_SUCCESS)
+      fail(CC_ERR_CUDA, "cusolverDnCreateParams failed");
+  }
+  cusolverDnSetStream(s.h, st);
+  return s;
+}
+
+// Hermitian eigensolver on a column-major n x n matrix (in place: vectors).
+void heevd(Allocator *al, cudaStream_t st, cplx *A, int n, double *w) {
+  Solver &s = solver_for(st);
+  int lwork = 0;
+  if (cusolverDnZheevd_bufferSize(s.h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n,
+                                  reinterpret_cast<cuDoubleComplex *>(A), n, w,
+                                  &lwork) != CUSOLVER_STATUS_SUCCESS)
+    fail(CC_ERR_CUDA, "zheevd buffer size failed");
+  Buf work(al, sizeof(cuDoubleComplex) * std::max(lwork, 1));
+  Buf info(al, sizeof(int));
+  if (cusolverDnZheevd(s.h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n,
+                       reinterpret_cast<cuDoubleComplex *>(A), n, w, work.as<cuDoubleComplex>(),
+                       lwork, info.as<int>()) != CUSOLVER_STATUS_SUCCESS)
+    fail(CC_ERR_CUDA, "zheevd failed");
+  int hinfo = 0;
+  CUDA_CHECK(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  if (hinfo != 0) fail(CC_ERR_NUMERIC, "zheevd info " + std::to_string(hinfo));
+}
+
+// General complex eigensolver (right vectors) on a column-major m x m matrix.
+void geev(Allocator *al, cudaStream_t st, cplx *A, int m, cplx *w, cplx *vr) {
+  Solver &s = solver_for(st);
+  size_t dbytes = 0, hbytes = 0;
+  if (cusolverDnXgeev_bufferSize(s.h, s.p, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR, m,
+                                 CUDA_C_64F, A, m, CUDA_C_64F, w, CUDA_C_64F, nullptr, m,
+                                 CUDA_C_64F, vr, m, CUDA_C_64F, &dbytes,
+                                 &hbytes) != CUSOLVER_STATUS_SUCCESS)
+    fail(CC_ERR_CUDA, "Xgeev buffer size failed");
+  Buf dwork(al, std::max<size_t>(dbytes, 16));
+  std::vector<char> hwork(std::max<size_t>(hbytes, 16));
+  Buf info(al, sizeof(int));
+  if (cusolverDnXgeev(s.h, s.p, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR, m, CUDA_C_64F, A,
+                      m, CUDA_C_64F, w, CUDA_C_64F, nullptr, m, CUDA_C_64F, vr, m, CUDA_C_64F,
+                      dwork.p, dbytes, hwork.data(), hbytes,
+                      info.as<int>()) != CUSOLVER_STATUS_SUCCESS)
+    fail(CC_ERR_CUDA, "Xgeev failed");
+  int hinfo = 0;
+  CUDA_CHECK(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  if (hinfo != 0) fail(CC_ERR_NUMERIC, "Xgeev info " + std::to_string(hinfo));
+}
+
+void h2d(void *dst, const void *src, size_t n, cudaStream_t st) {
+  CUDA_CHECK(cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, st));
+}
+void d2h(void *dst, const void *src, size_t n, cudaStream_t st) {
+  CUDA_CHECK(cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, st));
+  CUDA_CHECK(cudaStreamSynchronize(st));
+}
+void d2d(void *dst, const void *src, size_t n, cudaStream_t st) {
+  CUDA_CHECK(cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, st));
+}
+void zero(void *dst, size_t n, cudaStream_t st) { CUDA_CHECK(cudaMemsetAsync(dst, 0, n, st)); }
+
+}  // namespace
+
+// ===========================================================================
+// lifecycle
+// ===========================================================================
+void Ctx::create(int n_occ, int n_virt, int n_aux, const double *eps_host) {
+  if (n_occ < 1 || n_virt < 1 || n_aux < 1) fail(CC_ERR_ARG, "n_occ, n_virt, n_aux must be >= 1");
+  if (!eps_host) fail(CC_ERR_ARG, "eps is NULL");
+  o = n_occ;
+  v = n_virt;
+  X = n_aux;
+  v_input = v;
+  eps.assign(eps_host, eps_host + o + v);
+  for (double e : eps)
+    if (!std::isfinite(e)) fail(CC_ERR_INPUT, "eps contains NaN or Inf");
+  int dev = 0;
+  CUDA_CHECK(cudaGetDevice(&dev));
+  CUDA_CHECK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+  eng.al = &al;
+  eng.st = st;
+  eng.num_sms = num_sms;
+  err_d.reset(&al, 64);
+  stats_d.reset(&al, 64);
+  red.reset(&al, 4096 * sizeof(cplx));
+  zero(err_d.p, 64, st);
+  zero(stats_d.p, 64, st);
+  eng.err_flag = err_d.as<int>();
+  eps_d.reset(&al, sizeof(double) * (o + v));
+  h2d(eps_d.p, eps.data(), sizeof(double) * (o + v), st);
+  const size_t cs = sizeof(cplx);
+  Loo.reset(&al, cs * X * o * o);
+  Lov.reset(&al, cs * X * o * v);
+  Lvo.reset(&al, cs * X * v * o);
+  Lvv.reset(&al, cs * X * v * v);
+  have_P.assign(X, 0);
+  n_have = 0;
+}
+
+void Ctx::add_chunk(int p0, int p1, const double *L_host) {
+  if (p0 < 0 || p1 > X || p0 >= p1) fail(CC_ERR_ARG, "cholesky chunk range");
+  if (!L_host) fail(CC_ERR_ARG, "L chunk is NULL");
+  if (ints) fail(CC_ERR_STATE, "Cholesky vectors already consumed");
+  const int n = o + v;
+  const size_t per = sizeof(cplx) * n * n;
+  const int step = static_cast<int>(std::max<size_t>(1, (size_t(256) << 20) / per));
+  Buf stage(&al, per * std::min(step, p1 - p0));
+  for (int q0 = p0; q0 < p1; q0 += step) {
+    const int q1 = std::min(p1, q0 + step);
+    h2d(stage.p, L_host + static_cast<size_t>(q0 - p0) * 2 * n * n, per * (q1 - q0), st);
+    split_cholesky(stage.c(), q1 - q0, q0, o, v, Loo.c(), Lov.c(), Lvo.c(), Lvv.c(),
+                   stats_d.as<unsigned long long>(), st);
+  }
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  for (int P = p0; P < p1; ++P)
+    if (!have_P[P]) {
+      have_P[P] = 1;
+      ++n_have;
+    }
+}
+
+void Ctx::validate_input() {
+  if (n_have < X) fail(CC_ERR_STATE, "not every Cholesky vector has been given");
+  if (input_checked) return;
+  unsigned long long s[3];
+  d2h(s, stats_d.p, sizeof(s), st);
+  double mx, asym;
+  std::memcpy(&mx, &s[0], 8);
+  std::memcpy(&asym, &s[1], 8);
+  if (s[2] != 0) fail(CC_ERR_INPUT, "L contains NaN or Inf");
+  if (asym > 1e-12 * std::max(mx, 1e-300))
+    fail(CC_ERR_INPUT, "L^P is not Hermitian (max |L_pq - conj(L_qp)| = " + std::to_string(asym) + ")");
+  input_checked = true;
+}
+
+// Integrals are built at the first solver call, in the tier current then.
+void Ctx::ensure_ready() {
+  validate_input();
+  if (!ints) build_integrals();
+}
+
+void Ctx::check_err_flag() {
+  int e = 0;
+  d2h(&e, err_d.p, sizeof(int), st);
+  if (e) {
+    zero(err_d.p, sizeof(int), st);
+    fail(CC_ERR_TIMEOUT, "a bounded device wait expired in a tensor-core kernel");
+  }
+}
+
+void Ctx::ensure_pairs() {
+  if (pairs_o == o && pairs_v == v) return;
+  ij_i.reset(&al, sizeof(int) * std::max<long>(nij(), 1));
+  ij_j.reset(&al, sizeof(int) * std::max<long>(nij(), 1));
+  ab_a.reset(&al, sizeof(int) * std::max<long>(nab(), 1));
+  ab_b.reset(&al, sizeof(int) * std::max<long>(nab(), 1));
+  make_pairs(o, ij_i.as<int>(), ij_j.as<int>(), st);
+  make_pairs(v, ab_a.as<int>(), ab_b.as<int>(), st);
+  pairs_o = o;
+  pairs_v = v;
+}
+
+// <pq||rs> = sum_P (L_pr L_qs - L_ps L_qr)  (Eq. 23), stored blocks only.
+void Ctx::build_integrals() {
+  const int tr = int_tier();
+  const long oo = static_cast<long>(o) * o, ov = static_cast<long>(o) * v;
+  B(oooo, oo * oo);
+  B(ooov, oo * ov);
+  B(oovv, oo * v * v);
+  B(ovvo, ov * v * o);
+  Buf tmp(&al, sizeof(cplx) * std::max(oo * oo, oo * v * v));
+  // <mn||ij>
+  eng.contract(C1(), T(Loo.c(), "Pmi", {X, o, o}), T(Loo.c(), "Pnj", {X, o, o}), C0(),
+               T(tmp.c(), "mnij", {o, o, o, o}), tr);
+  eng.permute_into(C1(), T(tmp.c(), "mnij", {o, o, o, o}), C0(), T(oooo.c(), "mnij", {o, o, o, o}));
+  eng.permute_into(Cr(-1), T(tmp.c(), "mnji", {o, o, o, o}), C1(), T(oooo.c(), "mnij", {o, o, o, o}));
+  // <mn||ie>
+  eng.contract(C1(), T(Loo.c(), "Pmi", {X, o, o}), T(Lov.c(), "Pne", {X, o, v}), C0(),
+               T(ooov.c(), "mnie", {o, o, o, v}), tr);
+  eng.contract(Cr(-1), T(Lov.c(), "Pme", {X, o, v}), T(Loo.c(), "Pni", {X, o, o}), C1(),
+               T(ooov.c(), "mnie", {o, o, o, v}), tr);
+  // <ij||ab>
+  eng.contract(C1(), T(Lov.c(), "Pia", {X, o, v}), T(Lov.c(), "Pjb", {X, o, v}), C0(),
+               T(tmp.c(), "ijab", {o, o, v, v}), tr);
+  eng.permute_into(C1(), T(tmp.c(), "ijab", {o, o, v, v}), C0(), T(oovv.c(), "ijab", {o, o, v, v}));
+  eng.permute_into(Cr(-1), T(tmp.c(), "ijba", {o, o, v, v}), C1(), T(oovv.c(), "ijab", {o, o, v, v}));
+  // <mb||ej>
+  eng.contract(C1(), T(Lov.c(), "Pme", {X, o, v}), T(Lvo.c(), "Pbj", {X, v, o}), C0(),
+               T(ovvo.c(), "mbej", {o, v, v, o}), tr);
+  eng.contract(Cr(-1), T(Loo.c(), "Pmj", {X, o, o}), T(Lvv.c(), "Pbe", {X, v, v}), C1(),
+               T(ovvo.c(), "mbej", {o, v, v, o}), tr);
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  check_err_flag();
+  eng.clear_pack_cache();
+  ints = true;
+}
+
+cplx Ctx::energy(const cplx *t1p, const cplx *t2p) {
+  // Eq. 15 with f_ia = 0: 1/4 <ij||ab> t_ij^ab + 1/2 <ij||ab> t_i^a t_j^b
+  const long n2 = static_cast<long>(o) * o * v * v;
+  Buf tmp(&al, sizeof(cplx) * o * v);
+  eng.contract(C1(), T(oovv.c(), "ijab", {o, o, v, v}), T(t1p, "jb", {o, v}), C0(),
+               T(tmp.c(), "ia", {o, v}), TIER_FP64);
+  cplx* r = red.c();
+  dot_dev(oovv.c(), t2p, n2, false, r + 2048, st, r);
+  dot_dev(tmp.c(), t1p, static_cast<long>(o) * v, false, r + 2049, st, r + 1024);
+  cplx h[2];
+  d2h(h, r + 2048, sizeof(h), st);
+  return mk(0.25 * h[0].x + 0.5 * h[1].x, 0.25 * h[0].y + 0.5 * h[1].y);
+}
+
+// ===========================================================================
+// frozen natural spinors (Eqs. 24-28)
+// ===========================================================================
+int Ctx::fns(double threshold, int n_keep) {
+  ensure_ready();
+  if (ccsd_done || amps_user) fail(CC_ERR_STATE, "fns_truncate must precede ccsd_solve");
+  const double t0 = now_ms();
+  const long oo = static_cast<long>(o) * o;
+  const int tr = TIER_FP64;
+  // MP2 amplitudes t_ij^ab = <ab||ij> / D
+  Buf tm1(&al, sizeof(cplx) * o * v), tm2(&al, sizeof(cplx) * oo * v * v);
+  mp2_amplitudes(oovv.c(), eps_d.as<double>(), o, v, tm1.c(), tm2.c(), st);
+  // Eq. 24: D_ab = 1/2 sum_ijc t_ij^ac conj(t_ij^bc); stored column-major
+  Buf Dm(&al, sizeof(cplx) * v * v);
+  eng.contract(Cr(0.5), T(tm2.c(), "ijac", {o, o, v, v}), conj(T(tm2.c(), "ijbc", {o, o, v, v})),
+               C0(), T(Dm.c(), "ba", {v, v}), tr);
+  tm2.release();
+  // Eq. 25
+  Buf w(&al, sizeof(double) * v);
+  heevd(&al, st, Dm.c(), v, w.as<double>());
+  std::vector<double> occ(v);
+  d2h(occ.data(), w.p, sizeof(double) * v, st);
+  std::reverse(occ.begin(), occ.end());  // descending
+  fns_occ = occ;
+  int nk = n_keep;
+  if (nk < 0) {
+    nk = 0;
+    for (double x : occ)
+      if (x >= threshold) ++nk;
+  }
+  if (nk < 1) fail(CC_ERR_STATE, "FNS threshold keeps no virtual spinor");
+  if (nk > v) fail(CC_ERR_ARG, "n_keep exceeds n_virt");
+  // V~ rows: Vt[k][a] = eigenvector of the k-th largest occupation
+  Buf Vt(&al, sizeof(cplx) * nk * v);
+  eng.permute_into(C1(), Tv(Dm.c() + static_cast<long>(v - 1) * v, "ka", {nk, v}, {-v, 1}), C0(),
+                   T(Vt.c(), "ka", {nk, v}));
+  // Eq. 26: F^NS = V~^H diag(eps_v) V~  (column-major for the eigensolver)
+  std::vector<cplx> Ed(static_cast<size_t>(v) * v, mk(0, 0));
+  for (int a = 0; a < v; ++a) Ed[static_cast<size_t>(a) * v + a] = mk(eps[o + a], 0);
+  Buf Ev(&al, sizeof(cplx) * v * v);
+  h2d(Ev.p, Ed.data(), sizeof(cplx) * v * v, st);
+  Buf EVt(&al, sizeof(cplx) * nk * v), Fm(&al, sizeof(cplx) * nk * nk);
+  eng.contract(C1(), T(Vt.c(), "kb", {nk, v}), T(Ev.c(), "ab", {v, v}), C0(),
+               T(EVt.c(), "ka", {nk, v}), tr);
+  eng.contract(C1(), conj(T(Vt.c(), "ka", {nk, v})), T(EVt.c(), "la", {nk, v}), C0(),
+               T(Fm.c(), "lk", {nk, nk}), tr);
+  // Eq. 27
+  Buf w2(&al, sizeof(double) * nk);
+  heevd(&al, st, Fm.c(), nk, w2.as<double>());
+  std::vector<double> ev(nk);
+  d2h(ev.data(), w2.p, sizeof(double) * nk, st);
+  // Eq. 28 (read as U = V~ Z~): U[a][l] = sum_k V~(a,k) Z(k,l)
+  Buf U(&al, sizeof(cplx) * v * nk);
+  eng.contract(C1(), T(Vt.c(), "ka", {nk, v}), T(Fm.c(), "lk", {nk, nk}), C0(),
+               T(U.c(), "al", {v, nk}), tr);
+  // rotate the virtual indices of L (Eq. 22 form)
+  const int rt = int_tier();
+  Buf Lov2(&al, sizeof(cplx) * X * o * nk), Lvo2(&al, sizeof(cplx) * X * nk * o);
+  Buf Lvv2(&al, sizeof(cplx) * X * nk * nk);
+  eng.contract(C1(), T(Lov.c(), "Pia", {X, o, v}), T(U.c(), "al", {v, nk}), C0(),
+               T(Lov2.c(), "Pil", {X, o, nk}), rt);
+  eng.contract(C1(), conj(T(U.c(), "al", {v, nk})), T(Lvo.c(), "Pai", {X, v, o}), C0(),
+               T(Lvo2.c(), "Pli", {X, nk, o}), rt);
+  {
+    Buf tmp(&al, sizeof(cplx) * X * v * nk);
+    eng.contract(C1(), T(Lvv.c(), "Pab", {X, v, v}), T(U.c(), "bl", {v, nk}), C0(),
+                 T(tmp.c(), "Pal", {X, v, nk}), rt);
+    eng.contract(C1(), conj(T(U.c(), "ak", {v, nk})), T(tmp.c(), "Pal", {X, v, nk}), C0(),
+                 T(Lvv2.c(), "Pkl", {X, nk, nk}), rt);
+  }
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  check_err_flag();
+  Lov = std::move(Lov2);
+  Lvo = std::move(Lvo2);
+  Lvv = std::move(Lvv2);
+  v = nk;
+  eps.resize(o + v);
+  for (int a = 0; a < v; ++a) eps[o + a] = ev[a];
+  eps_d.reset(&al, sizeof(double) * (o + v));
+  h2d(eps_d.p, eps.data(), sizeof(double) * (o + v), st);
+  ints = false;
+  hbar_done = false;
+  amps = false;
+  eng.clear_cache();
+  build_integrals();
+  fns_done = true;
+  stat[3] += now_ms() - t0;
+  return CC_OK;
+}
+
+// ===========================================================================
+// ladder: R2 += 1/2 sum_cd <ab||cd> tau_ij^cd with <ab||cd> from Lv (Eq. 23)
+// ===========================================================================
+void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr) {
+  ensure_pairs();
+  const long vv = static_cast<long>(v) * v;
+  const long n_ij = nij(), n_cd = nab(), n_ab = nab();
+  if (n_ij == 0 || n_ab == 0) return;
+  cudaEvent_t e0, e1;
+  CUDA_CHECK(cudaEventCreate(&e0));
+  CUDA_CHECK(cudaEventCreate(&e1));
+  CUDA_CHECK(cudaEventRecord(e0, st));
+  Buf Rp(&al, sizeof(cplx) * n_ij * n_ab);
+  // tau gather tables: row (i<j) -> (i*o + j)*vv, col (c<d) -> c*v + d
+  std::vector<long> rows(n_ij), cols(n_cd);
+  {
+    long q = 0;
+    for (int i = 0; i < o; ++i)
+      for (int j = i + 1; j < o; ++j) rows[q++] = (static_cast<long>(i) * o + j) * vv;
+    q = 0;
+    for (int c = 0; c < v; ++c)
+      for (int d = c + 1; d < v; ++d) cols[q++] = static_cast<long>(c) * v + d;
+  }
+  Buf rt(&al, sizeof(long) * n_ij), kt(&al, sizeof(long) * n_cd);
+  h2d(rt.p, rows.data(), sizeof(long) * n_ij, st);
+  h2d(kt.p, cols.data(), sizeof(long) * n_cd, st);
+  const long Pstride[1] = {vv};
+  const long Xd[1] = {X};
+  const long *ptab = eng.table(std::vector<long>(Xd, Xd + 1), std::vector<long>(Pstride, Pstride + 1));
+  const bool fast = tr != TIER_FP64;
+  const size_t eb = fast ? tc_elem_bytes(tr) : sizeof(cplx);
+  const size_t veb = fast ? sizeof(float2) : sizeof(cplx);
+  double tc_ms = 0;
+  (void)tc_ms;
+
+  if (!fast) {
+    // K-major copy of L: LT[(a,c)][P]
+    Buf LT(&al, sizeof(cplx) * vv * X);
+    eng.permute_into(C1(), T(Lv, "Pac", {X, v, v}), C0(), T(LT.c(), "acP", {v, v, X}));
+    long a0 = 0;
+    Buf Vs, W;
+    while (a0 < v - 1) {
+      const long per_a = static_cast<long>(v) * (v - a0) * v;
+      long nA = std::max<long>(1, static_cast<long>(slab_budget / (per_a * veb)));
+      nA = std::min<long>(nA, v - 1 - a0);
+      const long a1 = a0 + nA;
+      const long p0 = a0 * v - a0 * (a0 + 1) / 2;
+      const long p1 = a1 * v - a1 * (a1 + 1) / 2;
+      const long np = p1 - p0;
+      B(Vs, nA * per_a);
+      B(W, np * n_cd);
+      GemmDesc g1;
+      g1.M = nA * v; g1.N = (v - a0) * v; g1.K = X;
+      g1.A = LT.c() + a0 * v * X; g1.lda = X;
+      g1.B = LT.c() + a0 * v * X; g1.ldb = X;
+      g1.C = Vs.c(); g1.ldc = (v - a0) * v;
+      gemm_f64(g1, st, num_sms);
+      ladder_antisym(Vs.p, false, v, static_cast<int>(a0), static_cast<int>(nA), p0, p1,
+                     ab_a.as<int>(), ab_b.as<int>(), ab_a.as<int>(), ab_b.as<int>(), TIER_FP64,
+                     nullptr, nullptr, 0, W.c(), st);
+      GemmDesc g2;
+      g2.M = n_ij; g2.N = np; g2.K = n_cd;
+      g2.A = tau; g2.am = rt.as<long>(); g2.ak = kt.as<long>();
+      g2.B = W.c(); g2.ldb = n_cd;
+      g2.C = Rp.c() + p0; g2.ldc = n_ab;
+      gemm_f64(g2, st, num_sms);
+      a0 = a1;
+    }
+  } else {
+    const int kal = tc_k_align(tr);
+    const long Kp1 = ((2L * X + kal - 1) / kal) * kal;
+    const long Kp2 = ((2L * n_cd + kal - 1) / kal) * kal;
+    const bool split = tr != TIER_TF32;
+    Buf A1h(&al, eb * 2 * vv * Kp1), B1h(&al, eb * vv * Kp1), A2h(&al, eb * 2 * n_ij * Kp2);
+    Buf A1l, B1l, A2l;
+    if (split) {
+      A1l.reset(&al, eb * 2 * vv * Kp1);
+      B1l.reset(&al, eb * vv * Kp1);
+      A2l.reset(&al, eb * 2 * n_ij * Kp2);
+    }
+    tc_pack_A(Lv, nullptr, ptab, 1, false, vv, X, Kp1, tr, A1h.p, A1l.p, st);
+    tc_pack_B(Lv, nullptr, ptab, 1, false, vv, X, Kp1, tr, B1h.p, B1l.p, st);
+    tc_pack_A(tau, rt.as<long>(), kt.as<long>(), 0, false, n_ij, n_cd, Kp2, tr, A2h.p, A2l.p, st);
+    long a0 = 0;
+    Buf Vs, Wh, Wl;
+    auto off = [&](const Buf &b, long elems) -> const void * {
+      return b.p ? static_cast<const void *>(static_cast<const char *>(b.p) + elems * eb) : nullptr;
+    };
+    while (a0 < v - 1) {
+      const long per_a = static_cast<long>(v) * (v - a0) * v;
+      long nA = std::max<long>(1, static_cast<long>(slab_budget / (per_a * veb)));
+      nA = std::min<long>(nA, v - 1 - a0);
+      const long a1 = a0 + nA;
+      const long p0 = a0 * v - a0 * (a0 + 1) / 2;
+      const long p1 = a1 * v - a1 * (a1 + 1) / 2;
+      const long np = p1 - p0;
+      if (Vs.bytes < veb * nA * per_a) Vs.reset(&al, veb * nA * per_a);
+      if (Wh.bytes < eb * np * Kp2) {
+        Wh.reset(&al, eb * np * Kp2);
+        if (split) Wl.reset(&al, eb * np * Kp2);
+      }
+      TcDesc g1;
+      g1.M = nA * v; g1.N = (v - a0) * v; g1.Kp = Kp1;
+      g1.A = off(A1h, 2 * a0 * v * Kp1); g1.Alo = off(A1l, 2 * a0 * v * Kp1);
+      g1.B = off(B1h, a0 * v * Kp1); g1.Blo = off(B1l, a0 * v * Kp1);
+      g1.tier = tr; g1.out = TC_OUT_F32;
+      g1.C = Vs.p; g1.ldc = (v - a0) * v;
+      gemm_tc(g1, st, err_d.as<int>());
+      ladder_antisym(Vs.p, true, v, static_cast<int>(a0), static_cast<int>(nA), p0, p1,
+                     ab_a.as<int>(), ab_b.as<int>(), ab_a.as<int>(), ab_b.as<int>(), tr, Wh.p,
+                     Wl.p, Kp2, nullptr, st);
+      TcDesc g2;
+      g2.M = n_ij; g2.N = np; g2.Kp = Kp2;
+      g2.A = A2h.p; g2.Alo = A2l.p; g2.B = Wh.p; g2.Blo = Wl.p;
+      g2.tier = tr; g2.out = TC_OUT_F64;
+      g2.C = Rp.c() + p0; g2.ldc = n_ab;
+      gemm_tc(g2, st, err_d.as<int>());
+      a0 = a1;
+    }
+  }
+  unpack_pairs_add(Rp.c(), o, v, ij_i.as<int>(), ij_j.as<int>(), ab_a.as<int>(), ab_b.as<int>(), R2,
+                   st);
+  CUDA_CHECK(cudaEventRecord(e1, st));
+  CUDA_CHECK(cudaEventSynchronize(e1));
+  float ms = 0;
+  CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  stat[0] += ms;
+  stat[1] += 1;
+  stat[2] = 8.0 * (static_cast<double>(X) * v * v * v * (v - 1) / 2.0 +
+                   static_cast<double>(n_cd) * n_cd * n_ij);
+  check_err_flag();
+}
+
+// ===========================================================================
+// CCSD residual (Eqs. 13-14, spin-orbital intermediate form)
+// ===========================================================================
+void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
+  const int tr = tier;
+  const long oo = static_cast<long>(o) * o, vv = static_cast<long>(v) * v, n2 = oo * vv;
+  Buf tau(&al, sizeof(cplx) * n2), taut(&al, sizeof(cplx) * n2);
+  make_tau(t1p, t2p, tau.c(), o, v, 1.0, st);
+  make_tau(t1p, t2p, taut.c(), o, v, 0.5, st);
+  Buf Fae(&al, sizeof(cplx) * vv), Fmi(&al, sizeof(cplx) * oo), Fme(&al, sizeof(cplx) * o * v);
+  Buf cP(&al, sizeof(cplx) * X), Y(&al, sizeof(cplx) * X * v * o), Zm(&al, sizeof(cplx) * X * oo);
+  Buf Q(&al, sizeof(cplx) * X * o * v);
+  const std::vector<long> d_oo = {o, o}, d_ov = {o, v}, d_vv = {v, v};
+  auto t1 = [&](const char *ix) { return T(t1p, ix, {o, v}); };
+  auto t2 = [&](const char *ix) { return T(t2p, ix, {o, o, v, v}); };
+  auto g_oovv = [&](const char *ix) { return stable(T(oovv.c(), ix, {o, o, v, v})); };
+  auto g_ooov = [&](const char *ix) { return stable(T(ooov.c(), ix, {o, o, o, v})); };
+  auto g_ovvo = [&](const char *ix) { return stable(T(ovvo.c(), ix, {o, v, v, o})); };
+  auto Lov_ = [&](const char *ix) { return stable(T(Lov.c(), ix, {X, o, v})); };
+  auto Lvo_ = [&](const char *ix) { return stable(T(Lvo.c(), ix, {X, v, o})); };
+  auto Lvv_ = [&](const char *ix) { return stable(T(Lvv.c(), ix, {X, v, v})); };
+
+  // F_me = sum_nf t_n^f <mn||ef>
+  eng.contract(C1(), t1("nf"), g_oovv("mnef"), C0(), T(Fme.c(), "me", {o, v}), TIER_FP64);
+  // F_ae = sum_mf t_m^f <ma||fe> - 1/2 tau~_mn^af <mn||ef>; the first term
+  // through L: sum_P c_P L^P_ae - sum_Pm L^P_me Y^P_am, Y^P_am = sum_f L^P_af t_m^f
+  eng.contract(C1(), t1("mf"), Lov_("Pmf"), C0(), T(cP.c(), "P", {X}), TIER_FP64);
+  eng.contract(C1(), Lvv_("Paf"), t1("mf"), C0(), T(Y.c(), "Pam", {X, v, o}), tr);
+  eng.contract(C1(), T(cP.c(), "P", {X}), Lvv_("Pae"), C0(), T(Fae.c(), "ae", {v, v}), TIER_FP64);
+  eng.contract(Cr(-1), Lov_("Pme"), T(Y.c(), "Pam", {X, v, o}), C1(), T(Fae.c(), "ae", {v, v}), tr);
+  eng.contract(Cr(-0.5), T(taut.c(), "mnaf", {o, o, v, v}), g_oovv("mnef"), C1(),
+               T(Fae.c(), "ae", {v, v}), tr);
+  // F_mi = sum_ne t_n^e <mn||ie> + 1/2 tau~_in^ef <mn||ef>
+  eng.contract(C1(), g_ooov("mnie"), t1("ne"), C0(), T(Fmi.c(), "mi", {o, o}), TIER_FP64);
+  eng.contract(Cr(0.5), g_oovv("mnef"), T(taut.c(), "inef", {o, o, v, v}), C1(),
+               T(Fmi.c(), "mi", {o, o}), tr);
+  taut.release();
+
+  // ---------------- singles (Eq. 13) ----------------
+  eng.contract(C1(), t1("ie"), T(Fae.c(), "ae", {v, v}), C0(), T(R1, "ia", {o, v}), TIER_FP64);
+  eng.contract(Cr(-1), t1("ma"), T(Fmi.c(), "mi", {o, o}), C1(), T(R1, "ia", {o, v}), TIER_FP64);
+  eng.contract(C1(), t2("imae"), T(Fme.c(), "me", {o, v}), C1(), T(R1, "ia", {o, v}), TIER_FP64);
+  eng.contract(C1(), t1("nf"), g_ovvo("nafi"), C1(), T(R1, "ia", {o, v}), TIER_FP64);
+  // -1/2 t_im^ef <ma||ef> = -sum_Pf L^P_af Q^P_if, Q^P_if = sum_me t_im^ef L^P_me
+  eng.contract(C1(), t2("imef"), Lov_("Pme"), C0(), T(Q.c(), "Pif", {X, o, v}), tr);
+  eng.contract(Cr(-1), Lvv_("Paf"), T(Q.c(), "Pif", {X, o, v}), C1(), T(R1, "ia", {o, v}), tr);
+  // -1/2 t_mn^ae <nm||ei> = +1/2 t_mn^ae <nm||ie>
+  eng.contract(Cr(0.5), t2("mnae"), g_ooov("nmie"), C1(), T(R1, "ia", {o, v}), tr);
+  Q.release();
+
+  // ---------------- doubles (Eq. 14) ----------------
+  Buf Xb(&al, sizeof(cplx) * n2);
+  auto Xt = [&](const char *ix) { return T(Xb.c(), ix, {o, o, v, v}); };
+  auto R2t = [&](const char *ix) { return T(R2, ix, {o, o, v, v}); };
+  // driver <ab||ij> = conj(<ij||ab>)
+  eng.permute_into(C1(), conj(g_oovv("ijab")), C0(), R2t("ijab"));
+  // P(ab) t_ij^ae (F_be - 1/2 t_m^b F_me)
+  {
+    Buf Fbe(&al, sizeof(cplx) * vv);
+    d2d(Fbe.p, Fae.p, sizeof(cplx) * vv, st);
+    eng.contract(Cr(-0.5), t1("mb"), T(Fme.c(), "me", {o, v}), C1(), T(Fbe.c(), "be", {v, v}),
+                 TIER_FP64);
+    eng.contract(C1(), t2("ijae"), T(Fbe.c(), "be", {v, v}), C0(), Xt("ijab"), tr);
+    antisym_add(R2, Xb.c(), o, v, 1.0, 2, st);
+  }
+  // -P(ij) t_im^ab (F_mj + 1/2 t_j^e F_me)
+  {
+    Buf Fmj(&al, sizeof(cplx) * oo);
+    d2d(Fmj.p, Fmi.p, sizeof(cplx) * oo, st);
+    eng.contract(Cr(0.5), t1("je"), T(Fme.c(), "me", {o, v}), C1(), T(Fmj.c(), "mj", {o, o}),
+                 TIER_FP64);
+    eng.contract(C1(), t2("imab"), T(Fmj.c(), "mj", {o, o}), C0(), Xt("ijab"), tr);
+    antisym_add(R2, Xb.c(), o, v, -1.0, 1, st);
+  }
+  // hole ladder: 1/2 tau_mn^ab W'_mnij + 1/4 t_mn^ab Z_mnij, with
+  // W' = <mn||ij> + P(ij) t_j^e <mn||ie>, Z = sum_ef <mn||ef> tau_ij^ef
+  {
+    Buf Wp(&al, sizeof(cplx) * oo * oo), Zb(&al, sizeof(cplx) * oo * oo), tmp(&al, sizeof(cplx) * oo * oo);
+    const std::initializer_list<long> d4 = {o, o, o, o};
+    d2d(Wp.p, oooo.p, sizeof(cplx) * oo * oo, st);
+    eng.contract(C1(), g_ooov("mnie"), t1("je"), C0(), T(tmp.c(), "mnij", d4), tr);
+    eng.permute_into(C1(), T(tmp.c(), "mnij", d4), C1(), T(Wp.c(), "mnij", d4));
+    eng.permute_into(Cr(-1), T(tmp.c(), "mnji", d4), C1(), T(Wp.c(), "mnij", d4));
+    eng.contract(C1(), g_oovv("mnef"), T(tau.c(), "ijef", {o, o, v, v}), C0(), T(Zb.c(), "mnij", d4),
+                 tr);
+    eng.contract(Cr(0.5), T(tau.c(), "mnab", {o, o, v, v}), T(Wp.c(), "mnij", d4), C1(), R2t("ijab"),
+                 tr);
+    eng.contract(Cr(0.25), t2("mnab"), T(Zb.c(), "mnij", d4), C1(), R2t("ijab"), tr);
+  }
+  // particle ladder with T1-dressed vectors: L~^P_ac = L^P_ac - sum_m t_m^a L^P_mc
+  {
+    Buf Lt(&al, sizeof(cplx) * X * vv);
+    d2d(Lt.p, Lvv.p, sizeof(cplx) * X * vv, st);
+    eng.contract(Cr(-1), t1("ma"), Lov_("Pmc"), C1(), T(Lt.c(), "Pac", {X, v, v}), tr);
+    ladder(Lt.c(), tau.c(), R2, tr);
+  }
+  // W_mbej
+  Buf W(&al, sizeof(cplx) * n2);
+  auto Wt = [&](const char *ix) { return T(W.c(), ix, {o, v, v, o}); };
+  d2d(W.p, ovvo.p, sizeof(cplx) * n2, st);
+  //   + t_j^f <mb||ef> = sum_P L^P_me Y^P_bj - sum_P Z^P_mj L^P_be
+  eng.contract(C1(), Lov_("Pme"), T(Y.c(), "Pbj", {X, v, o}), C1(), Wt("mbej"), tr);
+  eng.contract(C1(), Lov_("Pmf"), t1("jf"), C0(), T(Zm.c(), "Pmj", {X, o, o}), tr);
+  eng.contract(Cr(-1), T(Zm.c(), "Pmj", {X, o, o}), Lvv_("Pbe"), C1(), Wt("mbej"), tr);
+  //   - t_n^b <mn||ej> = + t_n^b <mn||je>
+  eng.contract(C1(), g_ooov("mnje"), t1("nb"), C1(), Wt("mbej"), tr);
+  //   - (1/2 t_jn^fb + t_j^f t_n^b) <mn||ef>
+  {
+    Buf z(&al, sizeof(cplx) * n2);
+    make_z(t1p, t2p, z.c(), o, v, 0.5, st);
+    eng.contract(Cr(-1), T(z.c(), "jnfb", {o, o, v, v}), g_oovv("mnef"), C1(), Wt("mbej"), tr);
+  }
+  // P(ij)P(ab) [t_im^ae W_mbej - t_i^e t_m^a <mb||ej>]
+  eng.contract(C1(), t2("imae"), Wt("mbej"), C0(), Xt("ijab"), tr);
+  {
+    Buf y2(&al, sizeof(cplx) * oo * o * v);
+    eng.contract(C1(), t1("ie"), g_ovvo("mbej"), C0(), T(y2.c(), "mbij", {o, v, o, o}), tr);
+    eng.contract(Cr(-1), t1("ma"), T(y2.c(), "mbij", {o, v, o, o}), C1(), Xt("ijab"), tr);
+  }
+  antisym_add(R2, Xb.c(), o, v, 1.0, 3, st);
+  // P(ij) t_i^e <ab||ej> = P(ij) sum_P (Y^P_ai L^P_bj - L^P_aj Y^P_bi)
+  eng.contract(C1(), T(Y.c(), "Pai", {X, v, o}), Lvo_("Pbj"), C0(), Xt("ijab"), tr);
+  eng.contract(Cr(-1), Lvo_("Paj"), T(Y.c(), "Pbi", {X, v, o}), C1(), Xt("ijab"), tr);
+  antisym_add(R2, Xb.c(), o, v, 1.0, 1, st);
+  // -P(ab) t_m^a <mb||ij>, <mb||ij> = conj(<ij||mb>)
+  eng.contract(C1(), t1("ma"), conj(g_ooov("ijmb")), C0(), Xt("ijab"), tr);
+  antisym_add(R2, Xb.c(), o, v, -1.0, 2, st);
+}
+
+// ===========================================================================
+// CCSD iterations with Jacobi updates and DIIS
+// ===========================================================================
+int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
+  if (!(tol > 0) || max_iter < 1) fail(CC_ERR_ARG, "tol must be > 0 and max_iter >= 1");
+  ensure_ready();
+  eng.clear_pack_cache();
+  const double t0 = now_ms();
+  const long n1 = static_cast<long>(o) * v, n2 = static_cast<long>(o) * o * v * v;
+  const long na = n_amp();
+  B(t1, n1);
+  B(t2, n2);
+  if (!amps) {
+    mp2_amplitudes(oovv.c(), eps_d.as<double>(), o, v, t1.c(), t2.c(), st);
+    amps = true;
+  }
+  Buf R1(&al, sizeof(cplx) * n1), R2(&al, sizeof(cplx) * n2);
+  Buf tn1(&al, sizeof(cplx) * n1), tn2(&al, sizeof(cplx) * n2);
+  Buf vcur(&al, sizeof(cplx) * na), vnew(&al, sizeof(cplx) * na), step(&al, sizeof(cplx) * na);
+  const int m_max = 8, diis_start = 3;
+  std::vector<Buf> hv(m_max), he(m_max);
+  Buf Bm(&al, sizeof(cplx) * 16 * 16), coef(&al, sizeof(cplx) * 16), dstat(&al, sizeof(int) * 4);
+  int n_hist = 0, slot = 0;
+  std::vector<int> order;  // slots in age order
+  pack_amps(t1.c(), t2.c(), o, v, vcur.c(), st);
+  cplx e_old = energy(t1.c(), t2.c());
+  bool converged = false;
+  int it = 0;
+  for (it = 1; it <= max_iter; ++it) {
+    residual(t1.c(), t2.c(), R1.c(), R2.c());
+    jacobi(R1.c(), R2.c(), eps_d.as<double>(), o, v, tn1.c(), tn2.c(), st);
+    pack_amps(tn1.c(), tn2.c(), o, v, vnew.c(), st);
+    d2d(step.p, vnew.p, sizeof(cplx) * na, st);
+    axpby(na, Cr(-1), vcur.c(), C1(), step.c(), st);
+    const cplx nrm2 = dot(step.c(), step.c(), na, true, st, red.c());
+    const double dnorm = std::sqrt(std::max(nrm2.x, 0.0));
+    const cplx e_new = energy(tn1.c(), tn2.c());
+    check_err_flag();
+    if (!std::isfinite(dnorm) || !std::isfinite(e_new.x) || !std::isfinite(e_new.y))
+      fail(CC_ERR_NUMERIC, "CCSD iteration produced NaN/Inf");
+    const double de = std::hypot(e_new.x - e_old.x, e_new.y - e_old.y);
+    if (dnorm < tol && de < tol) {
+      d2d(t1.p, tn1.p, sizeof(cplx) * n1, st);
+      d2d(t2.p, tn2.p, sizeof(cplx) * n2, st);
+      e_old = e_new;
+      converged = true;
+      break;
+    }
+    if (it >= diis_start) {
+      // push (vnew, step) into the ring of m_max slots
+      if (n_hist < m_max) {
+        slot = n_hist++;
+        hv[slot].reset(&al, sizeof(cplx) * na);
+        he[slot].reset(&al, sizeof(cplx) * na);
+        order.push_back(slot);
+      } else {
+        slot = order.front();
+        order.erase(order.begin());
+        order.push_back(slot);
+      }
+      d2d(hv[slot].p, vnew.p, sizeof(cplx) * na, st);
+      d2d(he[slot].p, step.p, sizeof(cplx) * na, st);
+      // B[i][slot] = <e_i|e_slot>, B[slot][i] = conj
+      for (int k = 0; k < n_hist; ++k)
+        dot_dev(he[k].c(), he[slot].c(), na, true, Bm.c() + k * 16 + slot, st, red.c());
+      // mirror the new column into the new row (Hermitian)
+      {
+        std::vector<cplx> Bh(16 * 16);
+        d2h(Bh.data(), Bm.p, sizeof(cplx) * 256, st);
+        for (int k = 0; k < n_hist; ++k) Bh[slot * 16 + k] = cconj(Bh[k * 16 + slot]);
+        // order the system by age so the solve is independent of slot layout
+        std::vector<cplx> Bo(16 * 16);
+        for (int a = 0; a < n_hist; ++a)
+          for (int b = 0; b < n_hist; ++b) Bo[a * 16 + b] = Bh[order[a] * 16 + order[b]];
+        h2d(Bm.p, Bh.data(), sizeof(cplx) * 256, st);
+        if (n_hist >= 2) {
+          Buf Bord(&al, sizeof(cplx) * 256);
+          h2d(Bord.p, Bo.data(), sizeof(cplx) * 256, st);
+          diis_solve(Bord.c(), n_hist, 16, coef.c(), dstat.as<int>(), st);
+          int ds = 0;
+          d2h(&ds, dstat.p, sizeof(int), st);
+          if (ds == 0) {
+            std::vector<cplx *> vp(n_hist);
+            for (int a = 0; a < n_hist; ++a) vp[a] = hv[order[a]].c();
+            diis_combine(vp.data(), coef.c(), n_hist, na, vnew.c(), st);
+          }
+        }
+      }
+    }
+    unpack_amps(vnew.c(), o, v, t1.c(), t2.c(), st);
+    d2d(vcur.p, vnew.p, sizeof(cplx) * na, st);
+    e_old = energy(t1.c(), t2.c());
+  }
+  if (it > max_iter) it = max_iter;
+  e_corr = e_old;
+  if (e_out) {
+    e_out[0] = e_corr.x;
+    e_out[1] = e_corr.y;
+  }
+  if (n_iter) *n_iter = it;
+  stat[4] += now_ms() - t0;
+  stat[7] = it;
+  ccsd_done = true;
+  hbar_done = false;
+  return converged ? CC_OK : CC_ERR_NOT_CONVERGED;
+}
+
+// ===========================================================================
+// H-bar elements with at most two virtual indices (built once)
+// ===========================================================================
+void Ctx::build_hbar() {
+  eng.clear_pack_cache();
+  const int tr = int_tier() == TIER_FP64 ? TIER_FP64 : TIER_TF32X3;
+  const long oo = static_cast<long>(o) * o, vv = static_cast<long>(v) * v, ov = static_cast<long>(o) * v;
+  const long n2 = oo * vv;
+  auto a1 = [&](const char *ix) { return T(t1.c(), ix, {o, v}); };
+  auto t2t = [&](const char *ix) { return T(t2.c(), ix, {o, o, v, v}); };
+  auto g_oovv = [&](const char *ix) { return T(oovv.c(), ix, {o, o, v, v}); };
+  auto g_ooov = [&](const char *ix) { return T(ooov.c(), ix, {o, o, o, v}); };
+  auto g_ovvo = [&](const char *ix) { return T(ovvo.c(), ix, {o, v, v, o}); };
+  auto Lov_ = [&](const char *ix) { return T(Lov.c(), ix, {X, o, v}); };
+  auto Lvv_ = [&](const char *ix) { return T(Lvv.c(), ix, {X, v, v}); };
+  const std::initializer_list<long> d4 = {o, o, o, o};
+  Buf tau(&al, sizeof(cplx) * n2);
+  make_tau(t1.c(), t2.c(), tau.c(), o, v, 1.0, st);
+  B(Hov, ov);
+  B(Hoo, oo);
+  B(Hvv, vv);
+  B(Hoooo, oo * oo);
+  B(Hooov, oo * ov);
+  B(Hovvo, n2);
+  B(Hovoo, oo * ov);
+  // H_me
+  eng.contract(C1(), a1("nf"), g_oovv("mnef"), C0(), T(Hov.c(), "me", {o, v}), TIER_FP64);
+  // H_mi = f_mi + t_n^e <mn||ie> + 1/2 tau_in^ef <mn||ef>
+  eng.contract(C1(), g_ooov("mnie"), a1("ne"), C0(), T(Hoo.c(), "mi", {o, o}), TIER_FP64);
+  eng.contract(Cr(0.5), g_oovv("mnef"), T(tau.c(), "inef", {o, o, v, v}), C1(),
+               T(Hoo.c(), "mi", {o, o}), tr);
+  add_diag(Hoo.c(), eps_d.as<double>(), o, st);
+  // H_ae = f_ae + t_m^f <am||ef> - 1/2 tau_mn^af <mn||ef>
+  {
+    Buf cP(&al, sizeof(cplx) * X), Y(&al, sizeof(cplx) * X * v * o);
+    eng.contract(C1(), a1("mf"), Lov_("Pmf"), C0(), T(cP.c(), "P", {X}), TIER_FP64);
+    eng.contract(C1(), Lvv_("Paf"), a1("mf"), C0(), T(Y.c(), "Pam", {X, v, o}), tr);
+    eng.contract(C1(), T(cP.c(), "P", {X}), Lvv_("Pae"), C0(), T(Hvv.c(), "ae", {v, v}), TIER_FP64);
+    eng.contract(Cr(-1), Lov_("Pme"), T(Y.c(), "Pam", {X, v, o}), C1(), T(Hvv.c(), "ae", {v, v}), tr);
+    eng.contract(Cr(-0.5), T(tau.c(), "mnaf", {o, o, v, v}), g_oovv("mnef"), C1(),
+                 T(Hvv.c(), "ae", {v, v}), tr);
+    add_diag(Hvv.c(), eps_d.as<double>() + o, v, st);
+    // H_mbej = <mb||ej> + t_j^f <mb||ef> - t_n^b <mn||ej> - (t_jn^fb + t_j^f t_n^b) <mn||ef>
+    d2d(Hovvo.p, ovvo.p, sizeof(cplx) * n2, st);
+    auto Ht = [&](const char *ix) { return T(Hovvo.c(), ix, {o, v, v, o}); };
+    eng.contract(C1(), Lov_("Pme"), T(Y.c(), "Pbj", {X, v, o}), C1(), Ht("mbej"), tr);
+    Buf Zm(&al, sizeof(cplx) * X * oo);
+    eng.contract(C1(), Lov_("Pmf"), a1("jf"), C0(), T(Zm.c(), "Pmj", {X, o, o}), tr);
+    eng.contract(Cr(-1), T(Zm.c(), "Pmj", {X, o, o}), Lvv_("Pbe"), C1(), Ht("mbej"), tr);
+    eng.contract(C1(), g_ooov("mnje"), a1("nb"), C1(), Ht("mbej"), tr);
+    Buf z(&al, sizeof(cplx) * n2);
+    make_z(t1.c(), t2.c(), z.c(), o, v, 1.0, st);
+    eng.contract(Cr(-1), T(z.c(), "jnfb", {o, o, v, v}), g_oovv("mnef"), C1(), Ht("mbej"), tr);
+  }
+  // H_mnij = <mn||ij> + P(ij) t_j^e <mn||ie> + 1/2 tau_ij^ef <mn||ef>
+  {
+    Buf tmp(&al, sizeof(cplx) * oo * oo);
+    d2d(Hoooo.p, oooo.p, sizeof(cplx) * oo * oo, st);
+    eng.contract(C1(), g_ooov("mnie"), a1("je"), C0(), T(tmp.c(), "mnij", d4), tr);
+    eng.permute_into(C1(), T(tmp.c(), "mnij", d4), C1(), T(Hoooo.c(), "mnij", d4));
+    eng.permute_into(Cr(-1), T(tmp.c(), "mnji", d4), C1(), T(Hoooo.c(), "mnij", d4));
+    eng.contract(Cr(0.5), g_oovv("mnef"), T(tau.c(), "ijef", {o, o, v, v}), C1(),
+                 T(Hoooo.c(), "mnij", d4), tr);
+  }
+  // H_mnie = <mn||ie> + t_i^f <mn||fe>
+  d2d(Hooov.p, ooov.p, sizeof(cplx) * oo * ov, st);
+  eng.contract(C1(), g_oovv("mnfe"), a1("if"), C1(), T(Hooov.c(), "mnie", {o, o, o, v}), tr);
+  // H_mbij = <mb||ij> - H_me t_ij^be - t_n^b H_mnij + 1/2 <mb||ef> tau_ij^ef
+  //          + P(ij) [<mn||ie> t_jn^be + t_i^e (<mb||ej> - t_nj^bf <mn||ef>)]
+  {
+    auto Hb = [&](const char *ix) { return T(Hovoo.c(), ix, {o, v, o, o}); };
+    eng.permute_into(C1(), conj(g_ooov("ijmb")), C0(), Hb("mbij"));
+    eng.contract(Cr(-1), T(Hov.c(), "me", {o, v}), t2t("ijbe"), C1(), Hb("mbij"), tr);
+    eng.contract(Cr(-1), a1("nb"), T(Hoooo.c(), "mnij", d4), C1(), Hb("mbij"), tr);
+    // 1/2 <mb||ef> tau_ij^ef = sum_ef (me|bf) tau_ij^ef, (me|bf) formed from L
+    // for a block of m at a time (three-virtual integrals never stored whole)
+    const size_t per_m = sizeof(cplx) * static_cast<size_t>(v) * vv;
+    const int mb = static_cast<int>(std::max<size_t>(1, std::min<size_t>(o, slab_budget / per_m)));
+    Buf G(&al, per_m * mb);
+    for (int m0 = 0; m0 < o; m0 += mb) {
+      const int mc = std::min(mb, o - m0);
+      eng.contract(C1(), Tv(Lov.c() + static_cast<long>(m0) * v, "Pme", {X, mc, v}, {ov, v, 1}),
+                   Lvv_("Pbf"), C0(), T(G.c(), "mebf", {mc, v, v, v}), tr);
+      eng.contract(C1(), T(G.c(), "mebf", {mc, v, v, v}), T(tau.c(), "ijef", {o, o, v, v}), C1(),
+                   T(Hovoo.c() + static_cast<long>(m0) * v * oo, "mbij", {mc, v, o, o}), tr);
+    }
+    G.release();
+    Buf tW(&al, sizeof(cplx) * n2), y(&al, sizeof(cplx) * oo * ov);
+    d2d(tW.p, ovvo.p, sizeof(cplx) * n2, st);
+    eng.contract(Cr(-1), t2t("njbf"), g_oovv("mnef"), C1(), T(tW.c(), "mbej", {o, v, v, o}), tr);
+    eng.contract(C1(), g_ooov("mnie"), t2t("jnbe"), C0(), T(y.c(), "mbij", {o, v, o, o}), tr);
+    eng.contract(C1(), a1("ie"), T(tW.c(), "mbej", {o, v, v, o}), C1(), T(y.c(), "mbij", {o, v, o, o}),
+                 tr);
+    eng.permute_into(C1(), T(y.c(), "mbij", {o, v, o, o}), C1(), Hb("mbij"));
+    eng.permute_into(Cr(-1), T(y.c(), "mbji", {o, v, o, o}), C1(), Hb("mbij"));
+  }
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  check_err_flag();
+  hbar_done = true;
+}
+
+// ===========================================================================
+// IP-EOM-CCSD sigma for k packed vectors (Eqs. 17-18)
+// ===========================================================================
+void Ctx::sigma(int k, const cplx *r, cplx *s) {
+  const int tr = eom();
+  const long oo = static_cast<long>(o) * o;
+  Buf r1(&al, sizeof(cplx) * k * o), r2(&al, sizeof(cplx) * k * oo * v);
+  Buf s1(&al, sizeof(cplx) * k * o), s2(&al, sizeof(cplx) * k * oo * v);
+  Buf x(&al, sizeof(cplx) * k * oo * v), xe(&al, sizeof(cplx) * k * v);
+  ip_unpack(r, k, o, v, r1.c(), r2.c(), st);
+  auto R1 = [&](const char *ix) { return T(r1.c(), ix, {k, o}); };
+  auto R2 = [&](const char *ix) { return T(r2.c(), ix, {k, o, o, v}); };
+  auto S1 = [&](const char *ix) { return T(s1.c(), ix, {k, o}); };
+  auto S2 = [&](const char *ix) { return T(s2.c(), ix, {k, o, o, v}); };
+  auto Xt = [&](const char *ix) { return T(x.c(), ix, {k, o, o, v}); };
+  // 1h
+  eng.contract(Cr(-1), R1("Km"), T(Hoo.c(), "mi", {o, o}), C0(), S1("Ki"), TIER_FP64);
+  eng.contract(C1(), R2("Kime"), T(Hov.c(), "me", {o, v}), C1(), S1("Ki"), TIER_FP64);
+  eng.contract(Cr(-0.5), R2("Kmne"), stable(T(Hooov.c(), "mnie", {o, o, o, v})), C1(), S1("Ki"), tr);
+  // 2h1p
+  eng.contract(Cr(-1), R1("Km"), stable(T(Hovoo.c(), "mbij", {o, v, o, o})), C0(), S2("Kijb"), tr);
+  eng.contract(C1(), R2("Kije"), T(Hvv.c(), "be", {v, v}), C1(), S2("Kijb"), TIER_FP64);
+  eng.contract(C1(), T(Hoo.c(), "mi", {o, o}), R2("Kmjb"), C0(), Xt("Kijb"), TIER_FP64);
+  eng.permute_into(Cr(-1), Xt("Kijb"), C1(), S2("Kijb"));
+  eng.permute_into(C1(), Xt("Kjib"), C1(), S2("Kijb"));
+  eng.contract(Cr(0.5), R2("Kmnb"), stable(T(Hoooo.c(), "mnij", {o, o, o, o})), C1(), S2("Kijb"), tr);
+  eng.contract(C1(), R2("Kime"), stable(T(Hovvo.c(), "mbej", {o, v, v, o})), C0(), Xt("Kijb"), tr);
+  eng.permute_into(C1(), Xt("Kijb"), C1(), S2("Kijb"));
+  eng.permute_into(Cr(-1), Xt("Kjib"), C1(), S2("Kijb"));
+  // three-body part: X_e = 1/2 <mn||ef> r_mn^f ; -X_e t_ij^eb
+  eng.contract(Cr(0.5), R2("Kmnf"), stable(T(oovv.c(), "mnef", {o, o, v, v})), C0(), T(xe.c(), "Ke", {k, v}),
+               tr);
+  eng.contract(Cr(-1), T(xe.c(), "Ke", {k, v}), stable(T(t2.c(), "ijeb", {o, o, v, v})), C1(), S2("Kijb"), tr);
+  ip_pack(s1.c(), s2.c(), k, o, v, s, st);
+}
+
+// ===========================================================================
+// block Davidson (FP64) for the n_roots lowest IP roots
+// ===========================================================================
+int Ctx::ipeom(int nr, double tol, int max_iter, double *omega, double *r1w, int *n_iter) {
+  if (!ccsd_done) fail(CC_ERR_STATE, "ipeom_solve needs a converged ccsd_solve");
+  if (!(tol > 0) || max_iter < 1) fail(CC_ERR_ARG, "tol must be > 0 and max_iter >= 1");
+  const long dim = dim_ip();
+  if (nr < 1 || nr > dim || nr > 64) fail(CC_ERR_ARG, "n_roots out of range");
+  const double t0 = now_ms();
+  if (!hbar_done) build_hbar();
+  const int max_sp = static_cast<int>(std::min<long>(dim, std::max(8 * nr, 40)));
+  Buf V(&al, sizeof(cplx) * max_sp * dim), S(&al, sizeof(cplx) * max_sp * dim);
+  Buf d(&al, sizeof(cplx) * dim);
+  Buf Xr(&al, sizeof(cplx) * nr * dim), SX(&al, sizeof(cplx) * nr * dim), R(&al, sizeof(cplx) * nr * dim);
+  Buf G(&al, sizeof(cplx) * max_sp * max_sp), wv(&al, sizeof(cplx) * max_sp),
+      VR(&al, sizeof(cplx) * max_sp * max_sp);
+  Buf Ysel(&al, sizeof(cplx) * nr * max_sp), wsel(&al, sizeof(cplx) * nr), cproj(&al, sizeof(cplx) * nr * max_sp);
+  ip_diag(Hoo.c(), Hvv.c(), o, v, d.c(), st);
+  std::vector<cplx> dh(dim);
+  d2h(dh.data(), d.p, sizeof(cplx) * dim, st);
+  std::vector<long> idx(dim);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](long a, long b) { return dh[a].x < dh[b].x; });
+  zero(V.p, sizeof(cplx) * nr * dim, st);
+  const cplx one = mk(1.0, 0.0);
+  for (int r = 0; r < nr; ++r) h2d(V.c() + r * dim + idx[r], &one, sizeof(cplx), st);
+  sigma(nr, V.c(), S.c());
+  int m = nr;
+  bool converged = false;
+  int it = 0;
+  std::vector<cplx> w_out(nr);
+  std::vector<double> rn(nr);
+  auto orth_new = [&](cplx *vecs, int nnew, int mbase) -> int {
+    // orthogonalise rows vecs[0..nnew) against V[0..mbase) (two passes) and
+    // among themselves; accepted rows are appended to V at mbase
+    if (mbase > 0) {
+      for (int pass = 0; pass < 2; ++pass) {
+        eng.contract(C1(), T(vecs, "rd", {nnew, dim}), conj(T(V.c(), "ad", {mbase, dim})), C0(),
+                     T(cproj.c(), "ra", {nnew, mbase}), TIER_FP64);
+        eng.contract(Cr(-1), T(cproj.c(), "ra", {nnew, mbase}), T(V.c(), "ad", {mbase, dim}), C1(),
+                     T(vecs, "rd", {nnew, dim}), TIER_FP64);
+      }
+    }
+    int acc = 0;
+    for (int j = 0; j < nnew; ++j) {
+      cplx *x = vecs + static_cast<long>(j) * dim;
+      for (int pass = 0; pass < 2; ++pass)
+        for (int i = 0; i < acc; ++i) {
+          cplx *y = V.c() + static_cast<long>(mbase + i) * dim;
+          const cplx c = dot(y, x, dim, true, st, red.c());
+          axpby(dim, mk(-c.x, -c.y), y, C1(), x, st);
+        }
+      const cplx n2 = dot(x, x, dim, true, st, red.c());
+      const double nrm = std::sqrt(std::max(n2.x, 0.0));
+      if (nrm < 1e-10) continue;
+      cplx *dst = V.c() + static_cast<long>(mbase + acc) * dim;
+      d2d(dst, x, sizeof(cplx) * dim, st);
+      axpby(dim, mk(1.0 / nrm, 0.0), dst, C0(), dst, st);
+      ++acc;
+    }
+    return acc;
+  };
+  for (it = 1; it <= max_iter; ++it) {
+    // projected matrix, column-major: G(a, b) = <v_a | sigma_b>
+    eng.contract(C1(), T(S.c(), "bd", {m, dim}), conj(T(V.c(), "ad", {m, dim})), C0(),
+                 T(G.c(), "ba", {m, m}), TIER_FP64);
+    geev(&al, st, G.c(), m, wv.c(), VR.c());
+    std::vector<cplx> wh(m), vh(static_cast<size_t>(m) * m);
+    d2h(wh.data(), wv.p, sizeof(cplx) * m, st);
+    d2h(vh.data(), VR.p, sizeof(cplx) * m * m, st);
+    std::vector<int> ord(m);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return wh[a].x < wh[b].x; });
+    std::vector<cplx> ys(static_cast<size_t>(nr) * m);
+    for (int r = 0; r < nr; ++r) {
+      const int c = ord[r];
+      double nn = 0;
+      for (int a = 0; a < m; ++a) nn += vh[c * m + a].x * vh[c * m + a].x + vh[c * m + a].y * vh[c * m + a].y;
+      nn = 1.0 / std::sqrt(nn);
+      for (int a = 0; a < m; ++a) ys[r * m + a] = cscale(nn, vh[c * m + a]);
+      w_out[r] = wh[c];
+    }
+    h2d(Ysel.p, ys.data(), sizeof(cplx) * nr * m, st);
+    h2d(wsel.p, w_out.data(), sizeof(cplx) * nr, st);
+    eng.contract(C1(), T(Ysel.c(), "ra", {nr, m}), T(V.c(), "ad", {m, dim}), C0(),
+                 T(Xr.c(), "rd", {nr, dim}), TIER_FP64);
+    eng.contract(C1(), T(Ysel.c(), "ra", {nr, m}), T(S.c(), "ad", {m, dim}), C0(),
+                 T(SX.c(), "rd", {nr, dim}), TIER_FP64);
+    // R_r = SX_r - w_r X_r
+    d2d(R.p, SX.p, sizeof(cplx) * nr * dim, st);
+    bool all = true;
+    for (int r = 0; r < nr; ++r) {
+      axpby(dim, mk(-w_out[r].x, -w_out[r].y), Xr.c() + r * dim, C1(), R.c() + r * dim, st);
+      const cplx n2 = dot(R.c() + r * dim, R.c() + r * dim, dim, true, st, red.c());
+      rn[r] = std::sqrt(std::max(n2.x, 0.0));
+      if (!std::isfinite(rn[r])) fail(CC_ERR_NUMERIC, "Davidson residual NaN");
+      if (rn[r] >= tol) all = false;
+    }
+    if (all) {
+      converged = true;
+      break;
+    }
+    if (it == max_iter) break;
+    // correction vectors for the unconverged roots
+    std::vector<int> todo;
+    for (int r = 0; r < nr; ++r)
+      if (rn[r] >= tol) todo.push_back(r);
+    if (m + static_cast<int>(todo.size()) > max_sp) {
+      // restart from the Ritz vectors
+      Buf Xc(&al, sizeof(cplx) * nr * dim);
+      d2d(Xc.p, Xr.p, sizeof(cplx) * nr * dim, st);
+      m = orth_new(Xc.c(), nr, 0);
+      sigma(m, V.c(), S.c());
+      continue;
+    }
+    precondition(R.c(), wsel.c(), d.c(), nr, dim, SX.c(), st);  // reuse SX as scratch
+    Buf corr(&al, sizeof(cplx) * todo.size() * dim);
+    for (size_t j = 0; j < todo.size(); ++j)
+      d2d(corr.c() + j * dim, SX.c() + static_cast<long>(todo[j]) * dim, sizeof(cplx) * dim, st);
+    const int added = orth_new(corr.c(), static_cast<int>(todo.size()), m);
+    if (added == 0) break;
+    sigma(added, V.c() + static_cast<long>(m) * dim, S.c() + static_cast<long>(m) * dim);
+    m += added;
+  }
+  if (it > max_iter) it = max_iter;
+  check_err_flag();
+  for (int r = 0; r < nr; ++r) {
+    omega[2 * r] = w_out[r].x;
+    omega[2 * r + 1] = w_out[r].y;
+    if (r1w) {
+      const cplx a = dot(Xr.c() + r * dim, Xr.c() + r * dim, o, true, st, red.c());
+      const cplx b = dot(Xr.c() + r * dim, Xr.c() + r * dim, dim, true, st, red.c());
+      r1w[r] = a.x / b.x;
+    }
+  }
+  if (n_iter) *n_iter = it;
+  stat[5] += now_ms() - t0;
+  stat[8] = it;
+  return converged ? CC_OK : CC_ERR_NOT_CONVERGED;
+}
+
+}  // namespace cdfns

@@ -1,0 +1,83 @@
+// Solver state of one system and the host orchestration of the hot path.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "cc_kernels.h"
+#include "engine.h"
+
+namespace cdfns {
+
+struct Ctx {
+  int o = 0, v = 0, X = 0;  // current occupied / virtual / auxiliary sizes
+  int v_input = 0;          // virtual count given at init (before FNS)
+  std::vector<double> eps;  // host copy, occupied first
+  Allocator al;
+  cudaStream_t st = nullptr;
+  Engine eng;
+  int tier = TIER_FP64;
+  int eom_tier = -1;  // -1: same as tier
+  int num_sms = 148;
+  size_t slab_budget = size_t(4) << 30;  // bytes for ladder V slabs
+
+  // inputs
+  Buf eps_d;
+  Buf Loo, Lov, Lvo, Lvv;  // [X][o][o], [X][o][v], [X][v][o], [X][v][v]
+  std::vector<char> have_P;
+  long n_have = 0;
+  bool input_checked = false;
+  Buf stats_d, err_d, red;
+
+  // stored integrals (at most two virtual indices)
+  bool ints = false;
+  Buf oooo, ooov, oovv, ovvo;
+
+  // amplitudes
+  Buf t1, t2;
+  bool amps = false, amps_user = false, ccsd_done = false, fns_done = false;
+  cplx e_corr = {0, 0};
+
+  // H-bar
+  bool hbar_done = false;
+  Buf Hov, Hoo, Hvv, Hoooo, Hooov, Hovvo, Hovoo;
+
+  // pair tables (row-major i<j over o, a<b over v)
+  Buf ij_i, ij_j, ab_a, ab_b;
+  int pairs_o = -1, pairs_v = -1;
+
+  std::vector<double> fns_occ;
+  double stat[16] = {0};
+  std::string last_error;
+
+  // --- lifecycle ---
+  void create(int n_occ, int n_virt, int n_aux, const double *eps_host);
+  void add_chunk(int p0, int p1, const double *L_host);
+  void validate_input();
+  void ensure_ready();
+  void build_integrals();
+  // --- solvers ---
+  int fns(double threshold, int n_keep);
+  int ccsd(double tol, int max_iter, double *e_out, int *n_iter);
+  int ipeom(int n_roots, double tol, int max_iter, double *omega, double *r1w, int *n_iter);
+  // --- components ---
+  void residual(const cplx *t1, const cplx *t2, cplx *R1, cplx *R2);
+  void ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tier);
+  void build_hbar();
+  void sigma(int k, const cplx *r, cplx *s);
+  cplx energy(const cplx *t1, const cplx *t2);
+  void check_err_flag();
+  void ensure_pairs();
+  int eom() const { return eom_tier < 0 ? tier : eom_tier; }
+  int int_tier() const { return tier == TIER_FP64 ? TIER_FP64 : TIER_TF32X3; }
+  long nij() const { return static_cast<long>(o) * (o - 1) / 2; }
+  long nab() const { return static_cast<long>(v) * (v - 1) / 2; }
+  long dim_ip() const { return o + nij() * v; }
+  long n_amp() const { return static_cast<long>(o) * v + nij() * nab(); }
+  cplx *B(Buf &b, size_t n) {  // (re)allocate n complex elements
+    if (b.bytes < n * sizeof(cplx)) b.reset(&al, n * sizeof(cplx));
+    return b.c();
+  }
+};
+
+}  // namespace cdfns

@@ -62,6 +62,8 @@ def _spec(n_occ, n_virt, n_aux, seed=0, kramers=False, **extra):
 CONFIGS = {
     "tiny": _spec(10, 30, 120, n_roots=4, ccsd_tol=1e-8, eom_tol=1e-7),
     "mid": _spec(12, 72, 288, n_roots=4, ccsd_tol=1e-8, eom_tol=1e-7),
+    "small": _spec(20, 160, 640, kramers=True, n_roots=8, ccsd_tol=1e-8,
+                   eom_tol=1e-7),
     "medium": _spec(40, 300, 1200, kramers=True, n_roots=8, ccsd_tol=1e-8,
                     eom_tol=1e-7),
     "fns": _spec(40, 800, 2400, n_roots=8, fns_threshold=1e-5,

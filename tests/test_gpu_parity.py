@@ -1,0 +1,246 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Every input is seeded and synthetic. Sizes are chosen so that the oracle
+finishes in seconds while the kernels still see several tiles and ragged
+tails (tile rows 128 real = 64 complex, columns 128/256, K blocks of 32).
+
+Tolerances (relative to the largest magnitude of the compared quantity):
+FP64 tier 1e-11 (differences in summation order only); TF32 (10-bit
+mantissa operands, FP32 accumulate) 4e-3; the 3-product split tiers
+(TF32X3 ~ 2^-21, BF16X3 ~ 2^-16 per product) 2e-6 and 1e-4. End-to-end IPs
+are compared in Hartree against the 1e-5 Eh target, and tighter for FP64.
+"""
+import numpy as np
+import pytest
+
+from paper_2506_06805_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL = {"fp64": 1e-11, "tf32": 4e-3, "tf32x3": 2e-6, "bf16x3": 1e-4}
+
+
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2506_06805_gb300 as P
+    P.lib()
+    return P
+
+
+def _system(o, v, X, seed=1, scale=1.0, kramers=False):
+    rng = np.random.default_rng(seed)
+    eps = synth.make_eps(rng, o, v, kramers)
+    L = synth.make_cholesky(rng, o + v, X, kramers) * scale
+    return eps, L
+
+
+def _amps(rng, o, v, s=0.05):
+    t1 = s * (rng.standard_normal((o, v)) + 1j * rng.standard_normal((o, v)))
+    t2 = s * (rng.standard_normal((o, o, v, v)) + 1j * rng.standard_normal((o, o, v, v)))
+    t2 = t2 - t2.transpose(1, 0, 2, 3)
+    t2 = 0.5 * (t2 - t2.transpose(0, 1, 3, 2))
+    return t1, t2
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _relerr(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+# --- integrals: bit-exact ----------------------------------------------------
+
+def test_integral_dump_bit_exact():
+    P = _gpu()
+    from oracle import integrals
+    o, v, X = 10, 30, 120
+    c, eps, L = synth.make_config("tiny")
+    with P.System(eps, L, n_occ=o) as s:
+        O, V = slice(0, o), slice(o, o + v)
+        for block, sl in ((0, (O, O, O, O)), (1, (O, O, O, V)), (2, (O, O, V, V)),
+                          (3, (O, V, V, O))):
+            got = s.dump_integrals(block)
+            ref = integrals.antisym_fixed_order(L, *sl)
+            assert got.shape == ref.shape
+            assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), block
+
+
+# --- the ladder (spec kernel) ---------------------------------------------
+
+@pytest.mark.parametrize("tier", ["fp64", "tf32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("o,v,X,budget", [(10, 30, 120, None), (6, 71, 97, 3 << 20)])
+def test_ladder_matches_oracle(tier, o, v, X, budget):
+    """1/2 sum_cd <ab||cd> tau_ij^cd with <ab||cd> built from L (Eq. 23);
+    the second case forces many a-blocks (small slab budget) with ragged
+    M, N and K everywhere (v = 71, X = 97)."""
+    P = _gpu()
+    from oracle import ccsd, integrals
+    eps, L = _system(o, v, X, seed=3, scale=4.0)
+    rng = np.random.default_rng(7)
+    _, tau = _amps(rng, o, v)
+    ref = ccsd.ladder_term(integrals.antisym_block(
+        L, *(slice(o, o + v),) * 4), tau)
+    with P.System(eps, L, n_occ=o, tier=tier) as s:
+        if budget:
+            s.set_slab_budget(budget)
+        out = torch.zeros((o, o, v, v), dtype=torch.complex128, device="cuda")
+        s.ladder_dev(_dev(tau), out)
+        got = out.cpu().numpy()
+    assert _relerr(got, ref) <= REL[tier]
+
+
+# --- CCSD residual at arbitrary amplitudes -----------------------------------
+
+@pytest.mark.parametrize("tier", ["fp64", "tf32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("o,v,X", [(10, 30, 120), (7, 45, 66)])
+def test_ccsd_residual_matches_oracle(tier, o, v, X):
+    P = _gpu()
+    from oracle import ccsd, integrals
+    eps, L = _system(o, v, X, seed=4, scale=4.0)
+    g = integrals.blocks_from_cholesky(L, o)
+    rng = np.random.default_rng(11)
+    t1, t2 = _amps(rng, o, v, 0.02)
+    R1, R2 = ccsd.residuals(g, eps, t1, t2)
+    with P.System(eps, L, n_occ=o, tier=tier) as s:
+        r1 = torch.zeros((o, v), dtype=torch.complex128, device="cuda")
+        r2 = torch.zeros((o, o, v, v), dtype=torch.complex128, device="cuda")
+        s.residual_dev(_dev(t1), _dev(t2), r1, r2)
+        g1, g2 = r1.cpu().numpy(), r2.cpu().numpy()
+    # TF32 noise scales with the magnitudes that enter the products
+    assert _relerr(g1, R1) <= 4 * REL[tier]
+    assert _relerr(g2, R2) <= 4 * REL[tier]
+
+
+# --- IP-EOM sigma at the oracle's amplitudes --------------------------------------
+
+@pytest.mark.parametrize("tier", ["fp64", "tf32x3"])
+def test_sigma_matches_oracle(tier):
+    P = _gpu()
+    from oracle import ccsd, integrals, ipeom
+    o, v, X = 8, 26, 80
+    eps, L = _system(o, v, X, seed=5, scale=4.0)
+    g = integrals.blocks_from_cholesky(L, o)
+    res = ccsd.solve(g, eps, tol=1e-11, max_iter=200)
+    H = ipeom.hbar(g, eps, res["t1"], res["t2"])
+    rng = np.random.default_rng(3)
+    dim = ipeom.dim(o, v)
+    k = 5
+    R = rng.standard_normal((k, dim)) + 1j * rng.standard_normal((k, dim))
+    ref = np.stack([ipeom.sigma(H, R[i], o, v) for i in range(k)])
+    io, jo = np.triu_indices(o, 1)
+    av, bv = np.triu_indices(v, 1)
+    t2p = res["t2"][io, jo][:, av, bv].ravel()
+    with P.System(eps, L, n_occ=o, tier=tier) as s:
+        s.set_amplitudes(res["t1"], t2p)
+        out = torch.zeros((k, dim), dtype=torch.complex128, device="cuda")
+        s.sigma_dev(_dev(R), out)
+        got = out.cpu().numpy()
+    assert _relerr(got, ref) <= 10 * REL[tier]
+
+
+# --- end to end ------------------------------------------------------------------
+
+def _oracle_roots(eps, L, o, n_roots, tol=1e-10):
+    from oracle import ccsd, davidson, integrals, ipeom
+    g = integrals.blocks_from_cholesky(L, o)
+    res = ccsd.solve(g, eps, tol=tol, max_iter=200)
+    H = ipeom.hbar(g, eps, res["t1"], res["t2"])
+    v = L.shape[1] - o
+    w, _, _, conv = davidson.davidson(lambda x: ipeom.sigma(H, x, o, v),
+                                      ipeom.diagonal(H, o, v), n_roots, tol=1e-9)
+    assert conv
+    return res["e_corr"], np.sort_complex(w)
+
+
+@pytest.mark.parametrize("tier,tol_e", [("fp64", 1e-9), ("tf32", 1e-5),
+                                        ("tf32x3", 1e-7), ("bf16x3", 1e-6)])
+@pytest.mark.parametrize("scale", [1.0, 4.0])
+def test_end_to_end_tiny(tier, tol_e, scale):
+    """The tiny workload (o=10, v=30, X=120, seed 0) as specified (scale 1) and
+    with 4x stronger Cholesky vectors so correlation shifts the IPs well
+    beyond the 1e-5 Eh target."""
+    P = _gpu()
+    c, eps, L = synth.make_config("tiny")
+    L = L * scale
+    o = c.n_occ
+    e_ref, w_ref = _oracle_roots(eps, L, o, 4)
+    eom = "tf32x3" if tier == "tf32" else None
+    # TF32 (10-bit operands) cannot resolve steps below ~1e-8 at 4x coupling
+    ctol = {"fp64": 1e-10, "tf32x3": 1e-9, "bf16x3": 1e-8}.get(tier, 1e-7)
+    with P.System(eps, L, n_occ=o, tier=tier, eom_tier=eom) as s:
+        e = s.ccsd(tol=ctol, max_iter=100)
+        w, r1 = s.ipeom(4, tol=1e-8 if tier != "bf16x3" else 1e-7, max_iter=200)
+    assert abs(e - e_ref) <= tol_e
+    assert np.abs(np.sort_complex(w) - w_ref).max() <= max(tol_e, 1e-9)
+    assert np.all((r1 > 0) & (r1 <= 1))
+
+
+def test_kramers_pairs_on_gpu():
+    P = _gpu()
+    o, v, X = 8, 40, 120
+    eps, L = _system(o, v, X, seed=2, scale=4.0, kramers=True)
+    with P.System(eps, L, n_occ=o, tier="fp64") as s:
+        e = s.ccsd(tol=1e-10)
+        w, _ = s.ipeom(6, tol=1e-8)
+    w = np.sort(w.real)
+    assert abs(e.imag) < 1e-12
+    assert np.abs(w[0::2] - w[1::2]).max() < 1e-7
+
+
+def test_fns_matches_oracle():
+    P = _gpu()
+    from oracle import ccsd, fns, integrals
+    o, v, X = 8, 40, 120
+    eps, L = _system(o, v, X, seed=6, scale=4.0)
+    out = fns.frozen_natural_spinors(L, eps, o, n_keep=18)
+    thr = 0.5 * (out["occupations"][17] + out["occupations"][18])
+    g = integrals.blocks_from_cholesky(out["L"], o)
+    e_ref = ccsd.solve(g, out["eps"], tol=1e-11)["e_corr"]
+    with P.System(eps, L, n_occ=o) as s:
+        kept = s.fns_truncate(threshold=thr)
+        occ = s.fns_occupations(v)
+        e = s.ccsd(tol=1e-11)
+    assert kept == 18
+    assert np.abs(occ - out["occupations"]).max() <= 1e-12 * out["occupations"][0]
+    assert abs(e - e_ref) <= 1e-10
+
+
+# --- boundary behaviour on a live device --------------------------------------------
+
+def test_rejects_non_hermitian_and_nan():
+    P = _gpu()
+    eps, L = _system(3, 5, 4)
+    bad = L.copy()
+    bad[1, 0, 2] += 1e-3
+    with pytest.raises(P.CCError) as e:
+        P.System(eps, bad, n_occ=3)
+    assert e.value.code == -2
+    bad = L.copy()
+    bad[0, 1, 1] = np.nan
+    with pytest.raises(P.CCError) as e:
+        P.System(eps, bad, n_occ=3)
+    assert e.value.code == -2
+
+
+def test_call_order_and_chunked_init():
+    P = _gpu()
+    eps, L = _system(4, 10, 12, scale=4.0)
+    with P.System(eps, L, n_occ=4) as s:
+        with pytest.raises(P.CCError) as e:
+            s.ipeom(2)
+        assert e.value.code == -8
+        e_full = s.ccsd(tol=1e-10)
+    # chunked, out of order: identical integrals, identical energy
+    with P.System(eps, None, n_occ=4, n_aux=12,
+                  chunks=[(6, 12, L[6:]), (0, 6, L[:6])]) as s:
+        e_chunk = s.ccsd(tol=1e-10)
+    assert e_chunk == e_full
+    # missing chunk -> state error
+    with P.System(eps, None, n_occ=4, n_aux=12, chunks=[(0, 6, L[:6])]) as s:
+        with pytest.raises(P.CCError) as e:
+            s.ccsd(tol=1e-8)
+        assert e.value.code == -8
