@@ -185,6 +185,33 @@ int cc_zgemm_dev(int tier, long M, long N, long K, const double *A_dev,
                  const double *B_dev, double *C_dev);
 
 /*
+ * cc_zgemm_noalloc: the same complex GEMM as cc_zgemm_dev, for callers that
+ * must not allocate device memory: code running while a stream is being
+ * captured into a CUDA graph, frameworks that own all device memory through
+ * their own pool, and loops where a cudaMalloc would stall the device. (The
+ * paper has no counterpart; this is a property of the library interface.)
+ *   C[m][n] = sum_k A[m][k] * B[n][k]   (complex128, row-major, C overwritten)
+ * Temporaries live in one fixed 64 MiB array in device global memory that
+ * every GPU loading the library holds until exit; nothing is allocated and
+ * no allocating library routine is called. The tensor-core tiers need
+ * 256 + s (round256(2 M Kp e) + round256(N Kp e)) bytes of it, with
+ * Kp = 2K rounded up to 32 (tf32) or 64 (bf16) elements, e = 4 (tf32) or
+ * 2 (bf16) bytes and s = 1 (CC_TIER_TF32) or 2 (split tiers); larger
+ * problems are rejected with CC_ERR_ARG and a message. CC_TIER_FP64 uses
+ * no temporaries. Work runs on the default stream (cc_set_default_stream)
+ * and the call returns after it completes.
+ * The first call on each device looks up the array's device address with
+ * that device current; make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents: calls
+ * whose work could overlap on the GPU (for example from two streams or
+ * threads) race on it and must be ordered by the caller.
+ * Errors: CC_ERR_ARG, CC_ERR_TIMEOUT, CC_ERR_CUDA (message via
+ * cc_last_error(NULL)).
+ */
+int cc_zgemm_noalloc(int tier, long M, long N, long K, const double *A_dev,
+                     const double *B_dev, double *C_dev);
+
+/*
  * cc_dump_integrals: bit-reproducible FP64 evaluation of Eq. 23 for one
  * block (0: <ij||kl>, 1: <ij||ka>, 2: <ij||ab>, 3: <ia||bj>), host
  * complex128 output in row-major block order. The sum over P runs in

@@ -66,6 +66,8 @@ _SIGS = {
     "cc_dump_integrals": (ctypes.c_int, [_P, ctypes.c_int, _D]),
     "cc_zgemm_dev": (ctypes.c_int, [ctypes.c_int, ctypes.c_long, ctypes.c_long,
                                     ctypes.c_long, _P, _P, _P]),
+    "cc_zgemm_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_long, ctypes.c_long,
+                                        ctypes.c_long, _P, _P, _P]),
     "cc_get_stats": (ctypes.c_int, [_P, _D, ctypes.c_int]),
     "cc_last_error": (ctypes.c_char_p, [_P]),
     "cc_free": (None, [_P]),
@@ -152,6 +154,17 @@ def zgemm_dev(A, B, C, tier="fp64"):
     N = B.shape[0]
     _check(lib().cc_zgemm_dev(t, M, N, K, _P(A.data_ptr()), _P(B.data_ptr()),
                               _P(C.data_ptr())))
+
+
+def zgemm_noalloc(A, B, C, tier="fp64"):
+    """Same product as zgemm_dev with every temporary in the library's fixed
+    device scratch array: no device allocation (for callers that cannot
+    allocate, e.g. during stream capture). Calls must not overlap."""
+    t = TIERS[tier] if isinstance(tier, str) else int(tier)
+    M, K = A.shape
+    N = B.shape[0]
+    _check(lib().cc_zgemm_noalloc(t, M, N, K, _P(A.data_ptr()), _P(B.data_ptr()),
+                                  _P(C.data_ptr())))
 
 
 class System:

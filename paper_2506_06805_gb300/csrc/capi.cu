@@ -19,6 +19,16 @@ cudaStream_t g_default_stream = nullptr;
 
 void fail(int code, const std::string &msg) { throw Error{code, msg}; }
 
+cudaStream_t noalloc_stream() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_default_stream;
+}
+
+void noalloc_record_error(const std::string &m) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_last_error = m;
+}
+
 void check_cuda(cudaError_t e, const char *what, const char *file, int line) {
   if (e == cudaSuccess) return;
   const int code = (e == cudaErrorMemoryAllocation) ? CC_ERR_OOM : CC_ERR_CUDA;
