@@ -251,7 +251,9 @@ int cc_get_amplitudes(const cc_ctx *cctx, double *t1_host, double *t2_host) {
     if (!c.amps) cdfns::fail(CC_ERR_STATE, "no amplitudes yet");
     const long na = c.n_amp();
     cdfns::Buf vec(&c.al, sizeof(cdfns::cplx) * na);
-    cdfns::pack_amps(c.t1.c(), c.t2.c(), c.o, c.v, vec.c(), c.st);
+    c.ensure_pairs();
+    cdfns::pack_amps(c.t1.c(), c.t2.c(), c.o, c.v, c.ij_i.as<int>(), c.ij_j.as<int>(), c.ab_a.as<int>(),
+                     c.ab_b.as<int>(), vec.c(), c.st);
     const long n1 = static_cast<long>(c.o) * c.v;
     CUDA_CHECK(cudaMemcpyAsync(t1_host, vec.p, sizeof(cdfns::cplx) * n1, cudaMemcpyDeviceToHost, c.st));
     CUDA_CHECK(cudaMemcpyAsync(t2_host, vec.c() + n1, sizeof(cdfns::cplx) * (na - n1),

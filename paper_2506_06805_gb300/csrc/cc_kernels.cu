@@ -68,50 +68,80 @@ __global__ void split_kernel(const double2 *chunk, int np, int p0, int o, int v,
   }
 }
 
+// Elementwise kernels over [o][o][v][v] use a 2D grid: blockIdx.y walks the
+// (i, j) planes, threads walk (a, b) inside a plane (32-bit index math).
 __global__ void tau_kernel(const double2 *t1, const double2 *t2, double2 *out, int o, int v,
                            double f) {
-  const long total = static_cast<long>(o) * o * v * v;
-  GRID_STRIDE(idx, total) {
-    const int b = static_cast<int>(idx % v);
-    const int a = static_cast<int>((idx / v) % v);
-    const int j = static_cast<int>((idx / (static_cast<long>(v) * v)) % o);
-    const int i = static_cast<int>(idx / (static_cast<long>(v) * v * o));
-    const double2 x = csub(cmul(t1[i * v + a], t1[j * v + b]), cmul(t1[i * v + b], t1[j * v + a]));
-    out[idx] = cadd(t2[idx], cscale(f, x));
+  const int vv = v * v;
+  for (int ij = blockIdx.y; ij < o * o; ij += gridDim.y) {
+    const int i = ij / o, j = ij - (ij / o) * o;
+    const long base = static_cast<long>(ij) * vv;
+    for (int ab = blockIdx.x * blockDim.x + threadIdx.x; ab < vv; ab += gridDim.x * blockDim.x) {
+      const int a = ab / v, b = ab - (ab / v) * v;
+      const double2 x = csub(cmul(t1[i * v + a], t1[j * v + b]), cmul(t1[i * v + b], t1[j * v + a]));
+      out[base + ab] = cadd(t2[base + ab], cscale(f, x));
+    }
+  }
+}
+
+// Same with the t1 t1 part formed in FP32 (for the tensor-core tiers, whose
+// GEMMs round these operands to TF32/BF16 anyway; GB300's FP64 rate is low).
+__global__ void tau32_kernel(const double2 *t1, const double2 *t2, double2 *out, int o, int v,
+                             float f) {
+  const int vv = v * v;
+  for (int ij = blockIdx.y; ij < o * o; ij += gridDim.y) {
+    const int i = ij / o, j = ij - (ij / o) * o;
+    const long base = static_cast<long>(ij) * vv;
+    for (int ab = blockIdx.x * blockDim.x + threadIdx.x; ab < vv; ab += gridDim.x * blockDim.x) {
+      const int a = ab / v, b = ab - (ab / v) * v;
+      const double2 p = t1[i * v + a], q = t1[j * v + b], r = t1[i * v + b], s = t1[j * v + a];
+      const float2 pf = make_float2(static_cast<float>(p.x), static_cast<float>(p.y));
+      const float2 qf = make_float2(static_cast<float>(q.x), static_cast<float>(q.y));
+      const float2 rf = make_float2(static_cast<float>(r.x), static_cast<float>(r.y));
+      const float2 sf = make_float2(static_cast<float>(s.x), static_cast<float>(s.y));
+      const float xr = (pf.x * qf.x - pf.y * qf.y) - (rf.x * sf.x - rf.y * sf.y);
+      const float xi = (pf.x * qf.y + pf.y * qf.x) - (rf.x * sf.y + rf.y * sf.x);
+      const double2 t = t2[base + ab];
+      out[base + ab] = make_double2(t.x + static_cast<double>(f * xr), t.y + static_cast<double>(f * xi));
+    }
   }
 }
 
 __global__ void z_kernel(const double2 *t1, const double2 *t2, double2 *out, int o, int v,
                          double c2) {
-  const long total = static_cast<long>(o) * o * v * v;
-  GRID_STRIDE(idx, total) {
-    const int b = static_cast<int>(idx % v);
-    const int f = static_cast<int>((idx / v) % v);
-    const int n = static_cast<int>((idx / (static_cast<long>(v) * v)) % o);
-    const int j = static_cast<int>(idx / (static_cast<long>(v) * v * o));
-    out[idx] = cadd(cscale(c2, t2[idx]), cmul(t1[j * v + f], t1[n * v + b]));
+  // out[j][n][f][b] = c2 t2[j][n][f][b] + t1[j][f] t1[n][b]
+  const int vv = v * v;
+  for (int jn = blockIdx.y; jn < o * o; jn += gridDim.y) {
+    const int j = jn / o, n = jn - (jn / o) * o;
+    const long base = static_cast<long>(jn) * vv;
+    for (int fb = blockIdx.x * blockDim.x + threadIdx.x; fb < vv; fb += gridDim.x * blockDim.x) {
+      const int f = fb / v, b = fb - (fb / v) * v;
+      out[base + fb] = cadd(cscale(c2, t2[base + fb]), cmul(t1[j * v + f], t1[n * v + b]));
+    }
   }
 }
 
 __global__ void jacobi_kernel(const double2 *R1, const double2 *R2, const double *eps, int o, int v,
                               double2 *t1, double2 *t2) {
-  const long n1 = static_cast<long>(o) * v;
-  const long total = static_cast<long>(o) * o * v * v;
-  GRID_STRIDE(idx, total) {
-    const int b = static_cast<int>(idx % v);
-    const int a = static_cast<int>((idx / v) % v);
-    const int j = static_cast<int>((idx / (static_cast<long>(v) * v)) % o);
-    const int i = static_cast<int>(idx / (static_cast<long>(v) * v * o));
-    if (i == j || a == b) {
-      t2[idx] = make_double2(0.0, 0.0);
-    } else {
-      const double d = eps[i] + eps[j] - eps[o + a] - eps[o + b];
-      t2[idx] = make_double2(R2[idx].x / d, R2[idx].y / d);
-    }
-    if (idx < n1) {
-      const int ii = static_cast<int>(idx / v), aa = static_cast<int>(idx % v);
-      const double d = eps[ii] - eps[o + aa];
-      t1[idx] = make_double2(R1[idx].x / d, R1[idx].y / d);
+  const int vv = v * v;
+  for (int ij = blockIdx.y; ij < o * o; ij += gridDim.y) {
+    const int i = ij / o, j = ij - (ij / o) * o;
+    const long base = static_cast<long>(ij) * vv;
+    const double eij = eps[i] + eps[j];
+    for (int ab = blockIdx.x * blockDim.x + threadIdx.x; ab < vv; ab += gridDim.x * blockDim.x) {
+      const int a = ab / v, b = ab - (ab / v) * v;
+      if (i == j || a == b) {
+        t2[base + ab] = make_double2(0.0, 0.0);
+      } else {
+        const double inv = 1.0 / (eij - eps[o + a] - eps[o + b]);
+        const double2 r = R2[base + ab];
+        t2[base + ab] = make_double2(r.x * inv, r.y * inv);
+      }
+      if (ij == 0 && ab < o * v) {
+        const int ii = ab / v, aa = ab - (ab / v) * v;
+        const double d = eps[ii] - eps[o + aa];
+        t1[ab] = make_double2(R1[ab].x / d, R1[ab].y / d);
+      }
     }
   }
 }
@@ -136,7 +166,8 @@ __global__ void mp2_kernel(const double2 *oovv, const double *eps, int o, int v,
 }
 
 __global__ void pack_amps_kernel(const double2 *t1, const double2 *t2, int o, int v,
-                                 double2 *vec) {
+                                 const int *ij_i, const int *ij_j, const int *ab_a,
+                                 const int *ab_b, double2 *vec) {
   const long n1 = static_cast<long>(o) * v;
   const long nab = static_cast<long>(v) * (v - 1) / 2;
   const long nij = static_cast<long>(o) * (o - 1) / 2;
@@ -146,9 +177,8 @@ __global__ void pack_amps_kernel(const double2 *t1, const double2 *t2, int o, in
       vec[idx] = t1[idx];
     } else {
       const long q = idx - n1;
-      int i, j, a, b;
-      pair_decode(q / nab, o, &i, &j);
-      pair_decode(q % nab, v, &a, &b);
+      const long pij = q / nab, pab = q - (q / nab) * nab;
+      const int i = ij_i[pij], j = ij_j[pij], a = ab_a[pab], b = ab_b[pab];
       vec[idx] = t2[((static_cast<long>(i) * o + j) * v + a) * v + b];
     }
   }
@@ -390,6 +420,29 @@ __global__ void ip_diag_kernel(const double2 *Hoo, const double2 *Hvv, int o, in
   }
 }
 
+__global__ void ip_diag_apply_kernel(const double2 *r1, const double2 *r2, const double2 *doo,
+                                     const double2 *dvv, int k, int o, int v, double2 *s1,
+                                     double2 *s2) {
+  const long per = static_cast<long>(o) * o * v;
+  GRID_STRIDE(idx, static_cast<long>(k) * per) {
+    const long kk = idx / per, rem = idx % per;
+    const int b = static_cast<int>(rem % v);
+    const int j = static_cast<int>((rem / v) % o);
+    const int i = static_cast<int>(rem / (static_cast<long>(v) * o));
+    const double2 d = csub(csub(dvv[b], doo[i]), doo[j]);
+    s2[idx] = cadd(s2[idx], cmul(d, r2[idx]));
+    if (rem < o) s1[kk * o + rem] = csub(s1[kk * o + rem], cmul(doo[rem], r1[kk * o + rem]));
+  }
+}
+
+__global__ void split_diag_kernel(const double2 *A, int n, double2 *off, double2 *diag) {
+  GRID_STRIDE(idx, static_cast<long>(n) * n) {
+    const long r = idx / n, c = idx % n;
+    off[idx] = (r == c) ? make_double2(0.0, 0.0) : A[idx];
+    if (r == c) diag[r] = A[idx];
+  }
+}
+
 __global__ void precond_kernel(const double2 *R, const double2 *w, const double2 *d, int nr,
                                long dim, double2 *x) {
   GRID_STRIDE(idx, static_cast<long>(nr) * dim) {
@@ -450,21 +503,34 @@ void split_cholesky(const cplx *chunk, int np, int p0, int o, int v, cplx *Loo, 
   count_launch();
 }
 
-void make_tau(const cplx *t1, const cplx *t2, cplx *out, int o, int v, double f, cudaStream_t st) {
-  tau_kernel<<<grid_for(static_cast<long>(o) * o * v * v), 256, 0, st>>>(t1, t2, out, o, v, f);
+inline dim3 grid2d(int o, int v) {
+  const int vv = v * v;
+  const unsigned gx = static_cast<unsigned>(std::min((vv + 255) / 256, 64));
+  const unsigned gy = static_cast<unsigned>(std::min(o * o, 65535));
+  return dim3(gx, gy);
+}
+
+void make_tau(const cplx *t1, const cplx *t2, cplx *out, int o, int v, double f, cudaStream_t st,
+              bool fp32_t1) {
+  if (fp32_t1)
+    tau32_kernel<<<grid2d(o, v), 256, 0, st>>>(t1, t2, out, o, v, static_cast<float>(f));
+  else
+    tau_kernel<<<grid2d(o, v), 256, 0, st>>>(t1, t2, out, o, v, f);
   LAUNCH_CHECK();
   count_launch();
 }
 
 void make_z(const cplx *t1, const cplx *t2, cplx *out, int o, int v, double c2, cudaStream_t st) {
-  z_kernel<<<grid_for(static_cast<long>(o) * o * v * v), 256, 0, st>>>(t1, t2, out, o, v, c2);
+  z_kernel<<<grid2d(o, v), 256, 0, st>>>(t1, t2, out, o, v, c2);
   LAUNCH_CHECK();
   count_launch();
 }
 
 void jacobi(const cplx *R1, const cplx *R2, const double *eps, int o, int v, cplx *t1, cplx *t2,
             cudaStream_t st) {
-  jacobi_kernel<<<grid_for(static_cast<long>(o) * o * v * v), 256, 0, st>>>(R1, R2, eps, o, v, t1, t2);
+  if (static_cast<long>(o) * v > static_cast<long>(v) * v)
+    fail(CC_ERR_UNSUPPORTED, "jacobi: n_occ > n_virt is not supported");
+  jacobi_kernel<<<grid2d(o, v), 256, 0, st>>>(R1, R2, eps, o, v, t1, t2);
   LAUNCH_CHECK();
   count_launch();
 }
@@ -476,10 +542,11 @@ void mp2_amplitudes(const cplx *oovv, const double *eps, int o, int v, cplx *t1,
   count_launch();
 }
 
-void pack_amps(const cplx *t1, const cplx *t2, int o, int v, cplx *vec, cudaStream_t st) {
+void pack_amps(const cplx *t1, const cplx *t2, int o, int v, const int *ij_i, const int *ij_j,
+               const int *ab_a, const int *ab_b, cplx *vec, cudaStream_t st) {
   const long n = static_cast<long>(o) * v +
                  static_cast<long>(o) * (o - 1) / 2 * (static_cast<long>(v) * (v - 1) / 2);
-  pack_amps_kernel<<<grid_for(n), 256, 0, st>>>(t1, t2, o, v, vec);
+  pack_amps_kernel<<<grid_for(n), 256, 0, st>>>(t1, t2, o, v, ij_i, ij_j, ab_a, ab_b, vec);
   LAUNCH_CHECK();
   count_launch();
 }
@@ -577,6 +644,20 @@ void ip_pack(const cplx *r1, const cplx *r2, int k, int o, int v, cplx *vec, cud
 void ip_diag(const cplx *Hoo, const cplx *Hvv, int o, int v, cplx *d, cudaStream_t st) {
   const long dim = o + static_cast<long>(o) * (o - 1) / 2 * v;
   ip_diag_kernel<<<grid_for(dim), 256, 0, st>>>(Hoo, Hvv, o, v, d);
+  LAUNCH_CHECK();
+  count_launch();
+}
+
+void ip_diag_apply(const cplx *r1, const cplx *r2, const cplx *doo, const cplx *dvv, int k, int o,
+                   int v, cplx *s1, cplx *s2, cudaStream_t st) {
+  ip_diag_apply_kernel<<<grid_for(static_cast<long>(k) * o * o * v), 256, 0, st>>>(r1, r2, doo, dvv, k,
+                                                                                  o, v, s1, s2);
+  LAUNCH_CHECK();
+  count_launch();
+}
+
+void split_diag(const cplx *A, int n, cplx *off, cplx *diag, cudaStream_t st) {
+  split_diag_kernel<<<grid_for(static_cast<long>(n) * n), 256, 0, st>>>(A, n, off, diag);
   LAUNCH_CHECK();
   count_launch();
 }

@@ -15,8 +15,9 @@ void split_cholesky(const cplx *chunk, int np, int p0, int o, int v, cplx *Loo, 
 
 // --- amplitudes ----------------------------------------------------------------
 // out[ijab] = t2[ijab] + f * (t1[ia] t1[jb] - t1[ib] t1[ja])
+// fp32_t1: form the t1 t1 part in FP32 (tensor-core tiers only)
 void make_tau(const cplx *t1, const cplx *t2, cplx *out, int o, int v, double f,
-              cudaStream_t st);
+              cudaStream_t st, bool fp32_t1 = false);
 // out[jnfb] = c2 * t2[jnfb] + t1[jf] t1[nb]
 void make_z(const cplx *t1, const cplx *t2, cplx *out, int o, int v, double c2,
             cudaStream_t st);
@@ -27,7 +28,8 @@ void jacobi(const cplx *R1, const cplx *R2, const double *eps, int o, int v, cpl
 void mp2_amplitudes(const cplx *oovv, const double *eps, int o, int v, cplx *t1, cplx *t2,
                     cudaStream_t st);
 // Unique amplitudes: [t1 (o*v)] + [t2 i<j, a<b (row-major pairs)].
-void pack_amps(const cplx *t1, const cplx *t2, int o, int v, cplx *vec, cudaStream_t st);
+void pack_amps(const cplx *t1, const cplx *t2, int o, int v, const int *ij_i, const int *ij_j,
+               const int *ab_a, const int *ab_b, cplx *vec, cudaStream_t st);
 void unpack_amps(const cplx *vec, int o, int v, cplx *t1, cplx *t2, cudaStream_t st);
 // Weighted squared norm helpers are done with dot() on packed vectors.
 
@@ -62,6 +64,12 @@ void ip_unpack(const cplx *vec, int k, int o, int v, cplx *r1, cplx *r2, cudaStr
 void ip_pack(const cplx *r1, const cplx *r2, int k, int o, int v, cplx *vec, cudaStream_t st);
 // d[o + pairs*v]: -Hoo_ii and Hvv_bb - Hoo_ii - Hoo_jj
 void ip_diag(const cplx *Hoo, const cplx *Hvv, int o, int v, cplx *d, cudaStream_t st);
+// s2[K][i][j][b] += (dvv_b - doo_i - doo_j) r2, s1[K][i] -= doo_i r1 (the
+// diagonal one-body part of sigma, exact in FP64)
+void ip_diag_apply(const cplx *r1, const cplx *r2, const cplx *doo, const cplx *dvv, int k, int o,
+                   int v, cplx *s1, cplx *s2, cudaStream_t st);
+// off = A with zero diagonal, diag = diagonal of A (n x n)
+void split_diag(const cplx *A, int n, cplx *off, cplx *diag, cudaStream_t st);
 // x[r] = R[r] / (w[r] - d) with |den| floored at 1e-8
 void precondition(const cplx *R, const cplx *w, const cplx *d, int nr, long dim, cplx *x,
                   cudaStream_t st);

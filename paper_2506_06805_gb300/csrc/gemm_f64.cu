@@ -109,16 +109,63 @@ __global__ void gemv_kernel(long N, long K, const double2 *__restrict__ A, const
   for (long n = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; n < N;
        n += static_cast<long>(gridDim.x) * blockDim.x) {
     const long bo = bn ? bn[n] : n * ldb;
-    double2 acc = make_double2(0.0, 0.0);
-    for (long k = 0; k < K; ++k) {
+    double2 acc[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
+                      make_double2(0.0, 0.0)};
+    long k = 0;
+    for (; k + 4 <= K; k += 4) {  // four independent loads in flight
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        double2 a = A[ak ? ak[k + u] : k + u];
+        double2 b = B[bo + (bk ? bk[k + u] : k + u)];
+        if (conjA) a.y = -a.y;
+        if (conjB) b.y = -b.y;
+        acc[u] = cfma(a, b, acc[u]);
+      }
+    }
+    for (; k < K; ++k) {
+      double2 a = A[ak ? ak[k] : k];
+      double2 b = B[bo + (bk ? bk[k] : k)];
+      if (conjA) a.y = -a.y;
+      if (conjB) b.y = -b.y;
+      acc[0] = cfma(a, b, acc[0]);
+    }
+    const double2 accs = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
+    const long off = cn ? cn[n] : n * ldc;
+    const double2 x = cmul(alpha, accs);
+    C[off] = (beta.x == 0.0 && beta.y == 0.0) ? x : cadd(x, cmul(beta, C[off]));
+  }
+}
+
+// Thread-per-output with the K range split over 8 thread rows of the block
+// (blockDim 32 x 8) and summed through shared memory: 8x the loads in
+// flight of gemv_kernel for long K with a strided operand.
+__global__ void gemv_kt_kernel(long N, long K, const double2 *__restrict__ A,
+                               const long *__restrict__ ak, bool conjA,
+                               const double2 *__restrict__ B, const long *__restrict__ bn,
+                               const long *__restrict__ bk, long ldb, bool conjB, double2 *C,
+                               const long *__restrict__ cn, long ldc, double2 alpha, double2 beta) {
+  __shared__ double2 red[8][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const long n = blockIdx.x * 32L + tx;
+  double2 acc = make_double2(0.0, 0.0);
+  if (n < N) {
+    const long bo = bn ? bn[n] : n * ldb;
+    for (long k = ty; k < K; k += 8) {
       double2 a = A[ak ? ak[k] : k];
       double2 b = B[bo + (bk ? bk[k] : k)];
       if (conjA) a.y = -a.y;
       if (conjB) b.y = -b.y;
       acc = cfma(a, b, acc);
     }
+  }
+  red[ty][tx] = acc;
+  __syncthreads();
+  if (ty == 0 && n < N) {
+    double2 s = red[0][tx];
+#pragma unroll
+    for (int y = 1; y < 8; ++y) s = cadd(s, red[y][tx]);
     const long off = cn ? cn[n] : n * ldc;
-    const double2 x = cmul(alpha, acc);
+    const double2 x = cmul(alpha, s);
     C[off] = (beta.x == 0.0 && beta.y == 0.0) ? x : cadd(x, cmul(beta, C[off]));
   }
 }
@@ -178,6 +225,18 @@ void gemm_f64(const GemmDesc &g, cudaStream_t st, int num_sms) {
       else
         gemv_warp_kernel<<<wb, 256, 0, st>>>(n_out, g.K, g.B, g.bk, g.conjB, g.A, g.am, g.ak, g.lda,
                                              g.conjA, g.C, g.cm, g.ldc, g.alpha, g.beta);
+      LAUNCH_CHECK();
+      count_launch();
+      return;
+    }
+    if (g.K >= 64 && n_out <= 65535L * 32) {
+      const unsigned kb = static_cast<unsigned>((n_out + 31) / 32);
+      if (rowvec)
+        gemv_kt_kernel<<<kb, dim3(32, 8), 0, st>>>(n_out, g.K, g.A, g.ak, g.conjA, g.B, g.bn, g.bk,
+                                                   g.ldb, g.conjB, g.C, g.cn, 1, g.alpha, g.beta);
+      else
+        gemv_kt_kernel<<<kb, dim3(32, 8), 0, st>>>(n_out, g.K, g.B, g.bk, g.conjB, g.A, g.am, g.ak,
+                                                   g.lda, g.conjA, g.C, g.cm, g.ldc, g.alpha, g.beta);
       LAUNCH_CHECK();
       count_launch();
       return;

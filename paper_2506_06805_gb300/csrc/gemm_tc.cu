@@ -153,6 +153,8 @@ struct TcArgs {
   int num_kb;       // K blocks of 128 bytes per row
   int kb_per_split;
   int chunk;        // K blocks accumulated in TMEM before promotion
+  int m_tiles, n_tiles, k_splits;
+  int group_m;      // m tiles per raster group (A panels kept in L2)
   int out;
   void *C;
   const long *cm, *cn;
@@ -161,13 +163,31 @@ struct TcArgs {
   int *err;
 };
 
-// CTA: warps 0-7 epilogue (TMEM lane quadrant = warp % 4, column half =
-// warp / 4), warp 8 TMA producer, warp 9 TMEM allocator + MMA issuer.
-// TMEM holds two accumulator buffers of BN columns. The MMA warp fills one
-// buffer with a chunk of `chunk` K blocks while the epilogue warps add the
-// other buffer's partial sums into FP32 registers (round to nearest): the
-// tensor core's own accumulation only ever spans one chunk, which bounds its
-// truncation bias independently of K.
+// Linear tile index -> (m tile, n tile, k split): groups of group_m m-tiles,
+// n-tiles swept inside a group, so a wave of CTAs shares a few A panels and a
+// few B panels in L2.
+__device__ __forceinline__ void tile_coords(const TcArgs &a, int t, int &m, int &n, int &z) {
+  const int mn = a.m_tiles * a.n_tiles;
+  z = t / mn;
+  const int r0 = t - z * mn;
+  const int per_group = a.group_m * a.n_tiles;
+  const int g = r0 / per_group;
+  const int first_m = g * a.group_m;
+  const int gsize = min(a.group_m, a.m_tiles - first_m);
+  const int r = r0 - g * per_group;
+  m = first_m + r % gsize;
+  n = r / gsize;
+}
+
+// Persistent CTA (one per SM): warps 0-7 epilogue (TMEM lane quadrant =
+// warp % 4, column half = warp / 4), warp 8 TMA producer, warp 9 TMEM
+// allocator + MMA issuer, all walking the same tile sequence. TMEM holds two
+// accumulator buffers of BN columns. The MMA warp fills one buffer with a
+// chunk of `chunk` K blocks while the epilogue warps add the other buffer's
+// partial sums into FP32 registers (round to nearest): the tensor core's own
+// accumulation only ever spans one chunk, which bounds its truncation bias
+// independently of K. Chunk and stage counters run on across tiles, so the
+// MMA of the next tile overlaps the epilogue stores of the previous one.
 template <int BN, int STAGES, bool SPLIT, bool BF16>
 __global__ void __launch_bounds__(320, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mAlo,
@@ -190,17 +210,12 @@ __global__ void __launch_bounds__(320, 1)
   uint64_t *tfull = empty + STAGES;   // [2]
   uint64_t *tempty = tfull + 2;       // [2]
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+  float *stage = reinterpret_cast<float *>(smem + STAGES * STAGE_BYTES + 256);  // 8 x 4 KB
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int m_tile = blockIdx.y;
-  const int n_tile = blockIdx.x;
-  const int kb0 = blockIdx.z * args.kb_per_split;
-  const int kb1 = min(args.num_kb, kb0 + args.kb_per_split);
-  const int nkb = kb1 - kb0;
-  if (nkb <= 0) return;  // uniform over the CTA
+  const int n_tiles_total = args.m_tiles * args.n_tiles * args.k_splits;
   const int chunk = args.chunk;
-  const int nchunks = (nkb + chunk - 1) / chunk;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -223,71 +238,87 @@ __global__ void __launch_bounds__(320, 1)
   if (warp == 8) {
     if (lane == 0) {
       // ---------------- TMA producer ----------------
-      int issued = 0;
-      for (int i = 0; i < nkb; ++i) {
-        const int s = i % STAGES;
-        const uint32_t ph = (i / STAGES) & 1u;
-        if (!mbar_wait(&empty[s], ph ^ 1u)) {
-          atomicExch(args.err, 1);
-          break;
+      long it = 0;  // k blocks issued so far (all tiles)
+      bool ok = true;
+      for (int t = blockIdx.x; t < n_tiles_total && ok; t += gridDim.x) {
+        int m_tile, n_tile, z;
+        tile_coords(args, t, m_tile, n_tile, z);
+        const int kb0 = z * args.kb_per_split;
+        const int kb1 = min(args.num_kb, kb0 + args.kb_per_split);
+        for (int kb = kb0; kb < kb1; ++kb, ++it) {
+          const int s = static_cast<int>(it % STAGES);
+          const uint32_t ph = static_cast<uint32_t>(it / STAGES) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u)) {
+            atomicExch(args.err, 1);
+            ok = false;
+            break;
+          }
+          uint8_t *st = smem + s * STAGE_BYTES;
+          mbar_expect_tx(&full[s], STAGE_BYTES);
+          const int kx = kb * K_ELEMS;
+          tma_load_2d(st, &mA, &full[s], kx, m_tile * BM);
+          tma_load_2d(st + A_BYTES, &mB, &full[s], kx, n_tile * BN);
+          if constexpr (SPLIT) {
+            tma_load_2d(st + A_BYTES + B_BYTES, &mAlo, &full[s], kx, m_tile * BM);
+            tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mBlo, &full[s], kx, n_tile * BN);
+          }
         }
-        uint8_t *st = smem + s * STAGE_BYTES;
-        mbar_expect_tx(&full[s], STAGE_BYTES);
-        const int kx = (kb0 + i) * K_ELEMS;
-        tma_load_2d(st, &mA, &full[s], kx, m_tile * BM);
-        tma_load_2d(st + A_BYTES, &mB, &full[s], kx, n_tile * BN);
-        if constexpr (SPLIT) {
-          tma_load_2d(st + A_BYTES + B_BYTES, &mAlo, &full[s], kx, m_tile * BM);
-          tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mBlo, &full[s], kx, n_tile * BN);
-        }
-        issued = i + 1;
       }
       // the last load issued into each stage must land before the CTA exits
-      for (int i = (issued > STAGES ? issued - STAGES : 0); i < issued; ++i) {
-        if (!mbar_wait(&full[i % STAGES], (i / STAGES) & 1u)) atomicExch(args.err, 1);
+      for (long i = (it > STAGES ? it - STAGES : 0); i < it; ++i) {
+        if (!mbar_wait(&full[i % STAGES], static_cast<uint32_t>(i / STAGES) & 1u))
+          atomicExch(args.err, 1);
       }
     }
   } else if (warp == 9) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
-      int kb = 0;
+      long it = 0;  // k blocks consumed (all tiles)
+      long c = 0;   // chunks issued (all tiles)
       bool ok = true;
-      for (int c = 0; c < nchunks && ok; ++c) {
-        const int buf = c & 1;
-        if (c >= 2 && !mbar_wait(&tempty[buf], ((c - 2) >> 1) & 1u)) {
-          atomicExch(args.err, 1);
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t dt = tmem + buf * BN;
-        const int kend = min(nkb, (c + 1) * chunk);
-        for (int i = 0; kb < kend; ++i, ++kb) {
-          const int s = kb % STAGES;
-          const uint32_t ph = (kb / STAGES) & 1u;
-          if (!mbar_wait(&full[s], ph)) {
+      for (int t = blockIdx.x; t < n_tiles_total && ok; t += gridDim.x) {
+        int m_tile, n_tile, z;
+        tile_coords(args, t, m_tile, n_tile, z);
+        const int kb0 = z * args.kb_per_split;
+        const int nkb = min(args.num_kb, kb0 + args.kb_per_split) - kb0;
+        const int nch = (nkb + chunk - 1) / chunk;
+        for (int cc = 0; cc < nch && ok; ++cc, ++c) {
+          const int buf = static_cast<int>(c & 1);
+          if (c >= 2 && !mbar_wait(&tempty[buf], static_cast<uint32_t>((c - 2) >> 1) & 1u)) {
             atomicExch(args.err, 1);
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
-          const uint32_t b0 = a0 + A_BYTES;
-          const uint32_t alo = b0 + B_BYTES;
-          const uint32_t blo = alo + A_BYTES;
-#pragma unroll
-          for (int kk = 0; kk < ROW_BYTES / MMA_K_BYTES; ++kk) {
-            const uint64_t da = sw128_desc(a0 + kk * MMA_K_BYTES);
-            const uint64_t db = sw128_desc(b0 + kk * MMA_K_BYTES);
-            mma<BF16>(dt, da, db, IDESC, (i > 0 || kk > 0) ? 1u : 0u);
-            if constexpr (SPLIT) {
-              mma<BF16>(dt, da, sw128_desc(blo + kk * MMA_K_BYTES), IDESC, 1u);
-              mma<BF16>(dt, sw128_desc(alo + kk * MMA_K_BYTES), db, IDESC, 1u);
+          const uint32_t dt = tmem + buf * BN;
+          const int kend = min(nkb, (cc + 1) * chunk);
+          for (int i = 0, kb = cc * chunk; kb < kend; ++i, ++kb, ++it) {
+            const int s = static_cast<int>(it % STAGES);
+            const uint32_t ph = static_cast<uint32_t>(it / STAGES) & 1u;
+            if (!mbar_wait(&full[s], ph)) {
+              atomicExch(args.err, 1);
+              ok = false;
+              break;
             }
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
+            const uint32_t b0 = a0 + A_BYTES;
+            const uint32_t alo = b0 + B_BYTES;
+            const uint32_t blo = alo + A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < ROW_BYTES / MMA_K_BYTES; ++kk) {
+              const uint64_t da = sw128_desc(a0 + kk * MMA_K_BYTES);
+              const uint64_t db = sw128_desc(b0 + kk * MMA_K_BYTES);
+              mma<BF16>(dt, da, db, IDESC, (i > 0 || kk > 0) ? 1u : 0u);
+              if constexpr (SPLIT) {
+                mma<BF16>(dt, da, sw128_desc(blo + kk * MMA_K_BYTES), IDESC, 1u);
+                mma<BF16>(dt, sw128_desc(alo + kk * MMA_K_BYTES), db, IDESC, 1u);
+              }
+            }
+            mma_commit(&empty[s]);
           }
-          mma_commit(&empty[s]);
+          mma_commit(&tfull[buf]);
         }
-        mma_commit(&tfull[buf]);
       }
       if (!ok) {
         // release the epilogue of every chunk it still waits for
@@ -298,75 +329,83 @@ __global__ void __launch_bounds__(320, 1)
     // ---------------- epilogue: 8 warps ----------------
     const int q = warp & 3;
     const int h = warp >> 2;
-    float acc[HALF];
-#pragma unroll
-    for (int j = 0; j < HALF; ++j) acc[j] = 0.f;
+    long c = 0;
     bool ok = true;
-    for (int c = 0; c < nchunks; ++c) {
-      const int buf = c & 1;
-      if (!mbar_wait(&tfull[buf], (c >> 1) & 1u)) {
-        ok = false;
-        break;
-      }
-      tc_fence_after();
-      const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + buf * BN + h * HALF;
+    for (int t = blockIdx.x; t < n_tiles_total && ok; t += gridDim.x) {
+      int m_tile, n_tile, z;
+      tile_coords(args, t, m_tile, n_tile, z);
+      const int kb0 = z * args.kb_per_split;
+      const int nkb = min(args.num_kb, kb0 + args.kb_per_split) - kb0;
+      const int nch = (nkb + chunk - 1) / chunk;
+      float acc[HALF];
 #pragma unroll
-      for (int j = 0; j < HALF; j += 16) {
-        float v[16];
-        tmem_ld16(base + j, v);
+      for (int j = 0; j < HALF; ++j) acc[j] = 0.f;
+      for (int cc = 0; cc < nch; ++cc, ++c) {
+        const int buf = static_cast<int>(c & 1);
+        if (!mbar_wait(&tfull[buf], static_cast<uint32_t>(c >> 1) & 1u)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + buf * BN + h * HALF;
 #pragma unroll
-        for (int t = 0; t < 16; ++t) acc[j + t] += v[t];
+        for (int j = 0; j < HALF; j += 16) {
+          float v[16];
+          tmem_ld16(base + j, v);
+#pragma unroll
+          for (int u = 0; u < 16; ++u) acc[j + u] += v[u];
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[buf]);
-    }
-    if (!ok) {
-      if (lane == 0) atomicExch(args.err, 1);
-    } else {
-      const long mc = static_cast<long>(m_tile) * (BM / 2) + q * 16 + (lane >> 1);
-      const bool odd = lane & 1;
-      const bool row_ok = mc < args.M;
-      const long coff = row_ok ? (args.cm ? args.cm[mc] : mc * args.ldc) : 0;
+      if (!ok) break;
+      // Write-out through a per-warp 32 x 32 float staging block (XOR
+      // swizzled, conflict free): lane = TMEM row (Re/Im of complex row
+      // lane/2) on the way in, lane = output column on the way out, so each
+      // store instruction writes 32 consecutive complex values of one row.
+      float *stg = stage + warp * 1024;
       const long nbase = static_cast<long>(n_tile) * BN + h * HALF;
+      const long mbase = static_cast<long>(m_tile) * (BM / 2) + q * 16;
 #pragma unroll
-      for (int j = 0; j < HALF; j += 16) {
-        float other[16];
+      for (int j = 0; j < HALF; j += 32) {
 #pragma unroll
-        for (int t = 0; t < 16; ++t) other[t] = __shfl_xor_sync(0xffffffffu, acc[j + t], 1);
-        // even lane: acc = Re, other = Im (writes columns j..j+7);
-        // odd lane: acc = Im, other = Re (writes columns j+8..j+15)
-        if (row_ok) {
-#pragma unroll
-          for (int jj = 0; jj < 8; ++jj) {
-            const long n = nbase + j + (odd ? 8 : 0) + jj;
-            if (n >= args.N) break;
-            const float re = odd ? other[8 + jj] : acc[j + jj];
-            const float im = odd ? acc[j + 8 + jj] : other[jj];
-            if (args.out == TC_OUT_F32) {
-              float2 *Cf = reinterpret_cast<float2 *>(args.C);
-              Cf[mc * args.ldc + n] = make_float2(re, im);
+        for (int u = 0; u < 32; ++u) stg[lane * 32 + (u ^ lane)] = acc[j + u];
+        __syncwarp();
+        const long n = nbase + j + lane;
+        const bool col_ok = n < args.N;
+        const long cno = col_ok ? (args.cn ? args.cn[n] : n) : 0;
+#pragma unroll 4
+        for (int rr = 0; rr < 16; ++rr) {
+          const float re = stg[(2 * rr) * 32 + (lane ^ (2 * rr))];
+          const float im = stg[(2 * rr + 1) * 32 + (lane ^ (2 * rr + 1))];
+          const long mc = mbase + rr;
+          if (!col_ok || mc >= args.M) continue;
+          if (args.out == TC_OUT_F32) {
+            float2 *Cf = reinterpret_cast<float2 *>(args.C);
+            Cf[mc * args.ldc + n] = make_float2(re, im);
+          } else {
+            double2 *C = reinterpret_cast<double2 *>(args.C);
+            const long off = (args.cm ? args.cm[mc] : mc * args.ldc) + cno;
+            const double dr = re, di = im;
+            const double xr = args.alpha.x * dr - args.alpha.y * di;
+            const double xi = args.alpha.x * di + args.alpha.y * dr;
+            if (args.out == TC_OUT_F64_ATOMIC) {
+              atomicAdd(&C[off].x, xr);
+              atomicAdd(&C[off].y, xi);
+            } else if (args.beta.x == 0.0 && args.beta.y == 0.0) {
+              C[off] = make_double2(xr, xi);
             } else {
-              double2 *C = reinterpret_cast<double2 *>(args.C);
-              const long off = coff + (args.cn ? args.cn[n] : n);
-              const double dr = re, di = im;
-              const double xr = args.alpha.x * dr - args.alpha.y * di;
-              const double xi = args.alpha.x * di + args.alpha.y * dr;
-              if (args.out == TC_OUT_F64_ATOMIC) {
-                atomicAdd(&C[off].x, xr);
-                atomicAdd(&C[off].y, xi);
-              } else if (args.beta.x == 0.0 && args.beta.y == 0.0) {
-                C[off] = make_double2(xr, xi);
-              } else {
-                const double2 cv = C[off];
-                C[off] = make_double2(xr + args.beta.x * cv.x - args.beta.y * cv.y,
-                                      xi + args.beta.x * cv.y + args.beta.y * cv.x);
-              }
+              const double2 cv = C[off];
+              C[off] = make_double2(xr + args.beta.x * cv.x - args.beta.y * cv.y,
+                                    xi + args.beta.x * cv.y + args.beta.y * cv.x);
             }
           }
         }
+        __syncwarp();
       }
     }
+    if (!ok && lane == 0) atomicExch(args.err, 1);
   }
   tc_fence_before();
   __syncthreads();
@@ -408,7 +447,9 @@ CUtensorMap make_map(const void *base, long rows, long kp, int box_rows, bool bf
 template <int BN, int STAGES, bool SPLIT, bool BF16>
 void launch(const TcDesc &g, cudaStream_t st, int *err) {
   constexpr int STAGE_BYTES = (BM * ROW_BYTES + BN * ROW_BYTES) * (SPLIT ? 2 : 1);
-  constexpr int SMEM = STAGES * STAGE_BYTES + (2 * STAGES + 4) * 8 + 16 + 1024;
+  // stages + barrier block (256 B) + 8 warps x 4 KB staging + alignment slack
+  constexpr int SMEM = STAGES * STAGE_BYTES + 256 + 8 * 4096 + 1024;
+  static_assert((2 * STAGES + 4) * 8 + 8 <= 256, "barrier block");
   static_assert(SMEM <= 232448, "shared memory budget");
   auto kern = tc_gemm_kernel<BN, STAGES, SPLIT, BF16>;
   static bool attr = false;
@@ -427,7 +468,13 @@ void launch(const TcDesc &g, cudaStream_t st, int *err) {
   a.num_kb = static_cast<int>(g.Kp / (BF16 ? 64 : 32));
   const int sk = std::max(1, std::min(g.split_k, a.num_kb));
   a.kb_per_split = (a.num_kb + sk - 1) / sk;
-  const int zs = (a.num_kb + a.kb_per_split - 1) / a.kb_per_split;
+  a.k_splits = (a.num_kb + a.kb_per_split - 1) / a.kb_per_split;
+  a.m_tiles = static_cast<int>((mr + BM - 1) / BM);
+  a.n_tiles = static_cast<int>((g.N + BN - 1) / BN);
+  // raster groups: as many A panels (128 rows x the K range of a split) as
+  // fit in ~24 MB of L2 share each B panel while it is resident
+  const double panel = static_cast<double>(BM) * a.kb_per_split * ROW_BYTES * (SPLIT ? 2 : 1);
+  a.group_m = static_cast<int>(std::max(1.0, std::min<double>(a.m_tiles, 24.0e6 / panel)));
   a.chunk = (g.tier == TIER_TF32) ? 8 : 4;
   a.out = g.out;
   a.C = g.C;
@@ -437,8 +484,15 @@ void launch(const TcDesc &g, cudaStream_t st, int *err) {
   a.alpha = g.alpha;
   a.beta = g.beta;
   a.err = err;
-  dim3 grid(static_cast<unsigned>((g.N + BN - 1) / BN), static_cast<unsigned>((mr + BM - 1) / BM),
-            static_cast<unsigned>(zs));
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    CUDA_CHECK(cudaGetDevice(&dev));
+    CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const long total = static_cast<long>(a.m_tiles) * a.n_tiles * a.k_splits;
+  if (total > 0x7fffffffL) fail(CC_ERR_ARG, "gemm_tc: too many tiles");
+  dim3 grid(static_cast<unsigned>(std::min<long>(total, sms)));
   kern<<<grid, 320, SMEM, st>>>(mA, mAlo, mB, mBlo, a);
   LAUNCH_CHECK();
   count_launch();

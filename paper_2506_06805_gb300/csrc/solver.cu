@@ -263,8 +263,11 @@ int Ctx::fns(double threshold, int n_keep) {
   mp2_amplitudes(oovv.c(), eps_d.as<double>(), o, v, tm1.c(), tm2.c(), st);
   // Eq. 24: D_ab = 1/2 sum_ijc t_ij^ac conj(t_ij^bc); stored column-major
   Buf Dm(&al, sizeof(cplx) * v * v);
+  // the o^2 v^3 density GEMM runs in the 3-product split tier when a
+  // tensor-core tier is selected (relative error ~1e-6, far below the
+  // spacing of occupations near any threshold)
   eng.contract(Cr(0.5), T(tm2.c(), "ijac", {o, o, v, v}), conj(T(tm2.c(), "ijbc", {o, o, v, v})),
-               C0(), T(Dm.c(), "ba", {v, v}), tr);
+               C0(), T(Dm.c(), "ba", {v, v}), int_tier());
   tm2.release();
   // Eq. 25
   Buf w(&al, sizeof(double) * v);
@@ -481,8 +484,8 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
   const int tr = tier;
   const long oo = static_cast<long>(o) * o, vv = static_cast<long>(v) * v, n2 = oo * vv;
   Buf tau(&al, sizeof(cplx) * n2), taut(&al, sizeof(cplx) * n2);
-  make_tau(t1p, t2p, tau.c(), o, v, 1.0, st);
-  make_tau(t1p, t2p, taut.c(), o, v, 0.5, st);
+  make_tau(t1p, t2p, tau.c(), o, v, 1.0, st, tr != TIER_FP64);
+  make_tau(t1p, t2p, taut.c(), o, v, 0.5, st, tr != TIER_FP64);
   Buf Fae(&al, sizeof(cplx) * vv), Fmi(&al, sizeof(cplx) * oo), Fme(&al, sizeof(cplx) * o * v);
   Buf cP(&al, sizeof(cplx) * X), Y(&al, sizeof(cplx) * X * v * o), Zm(&al, sizeof(cplx) * X * oo);
   Buf Q(&al, sizeof(cplx) * X * o * v);
@@ -615,6 +618,7 @@ int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
   const long na = n_amp();
   B(t1, n1);
   B(t2, n2);
+  ensure_pairs();
   if (!amps) {
     mp2_amplitudes(oovv.c(), eps_d.as<double>(), o, v, t1.c(), t2.c(), st);
     amps = true;
@@ -627,14 +631,14 @@ int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
   Buf Bm(&al, sizeof(cplx) * 16 * 16), coef(&al, sizeof(cplx) * 16), dstat(&al, sizeof(int) * 4);
   int n_hist = 0, slot = 0;
   std::vector<int> order;  // slots in age order
-  pack_amps(t1.c(), t2.c(), o, v, vcur.c(), st);
+  pack_amps(t1.c(), t2.c(), o, v, ij_i.as<int>(), ij_j.as<int>(), ab_a.as<int>(), ab_b.as<int>(), vcur.c(), st);
   cplx e_old = energy(t1.c(), t2.c());
   bool converged = false;
   int it = 0;
   for (it = 1; it <= max_iter; ++it) {
     residual(t1.c(), t2.c(), R1.c(), R2.c());
     jacobi(R1.c(), R2.c(), eps_d.as<double>(), o, v, tn1.c(), tn2.c(), st);
-    pack_amps(tn1.c(), tn2.c(), o, v, vnew.c(), st);
+    pack_amps(tn1.c(), tn2.c(), o, v, ij_i.as<int>(), ij_j.as<int>(), ab_a.as<int>(), ab_b.as<int>(), vnew.c(), st);
     d2d(step.p, vnew.p, sizeof(cplx) * na, st);
     axpby(na, Cr(-1), vcur.c(), C1(), step.c(), st);
     const cplx nrm2 = dot(step.c(), step.c(), na, true, st, red.c());
@@ -806,6 +810,12 @@ void Ctx::build_hbar() {
     eng.permute_into(C1(), T(y.c(), "mbij", {o, v, o, o}), C1(), Hb("mbij"));
     eng.permute_into(Cr(-1), T(y.c(), "mbji", {o, v, o, o}), C1(), Hb("mbij"));
   }
+  B(Hoo_off, oo);
+  B(Hvv_off, vv);
+  B(doo, o);
+  B(dvv, v);
+  split_diag(Hoo.c(), o, Hoo_off.c(), doo.c(), st);
+  split_diag(Hvv.c(), v, Hvv_off.c(), dvv.c(), st);
   CUDA_CHECK(cudaStreamSynchronize(st));
   check_err_flag();
   hbar_done = true;
@@ -826,14 +836,15 @@ void Ctx::sigma(int k, const cplx *r, cplx *s) {
   auto S1 = [&](const char *ix) { return T(s1.c(), ix, {k, o}); };
   auto S2 = [&](const char *ix) { return T(s2.c(), ix, {k, o, o, v}); };
   auto Xt = [&](const char *ix) { return T(x.c(), ix, {k, o, o, v}); };
-  // 1h
-  eng.contract(Cr(-1), R1("Km"), T(Hoo.c(), "mi", {o, o}), C0(), S1("Ki"), TIER_FP64);
+  // 1h (the diagonal of H_oo is applied exactly below)
+  eng.contract(Cr(-1), R1("Km"), T(Hoo_off.c(), "mi", {o, o}), C0(), S1("Ki"), TIER_FP64);
   eng.contract(C1(), R2("Kime"), T(Hov.c(), "me", {o, v}), C1(), S1("Ki"), TIER_FP64);
   eng.contract(Cr(-0.5), R2("Kmne"), stable(T(Hooov.c(), "mnie", {o, o, o, v})), C1(), S1("Ki"), tr);
-  // 2h1p
+  // 2h1p; the one-body terms use the off-diagonal parts of H_vv and H_oo,
+  // whose elements are correlation-sized, and their diagonals in FP64 below
   eng.contract(Cr(-1), R1("Km"), stable(T(Hovoo.c(), "mbij", {o, v, o, o})), C0(), S2("Kijb"), tr);
-  eng.contract(C1(), R2("Kije"), T(Hvv.c(), "be", {v, v}), C1(), S2("Kijb"), TIER_FP64);
-  eng.contract(C1(), T(Hoo.c(), "mi", {o, o}), R2("Kmjb"), C0(), Xt("Kijb"), TIER_FP64);
+  eng.contract(C1(), R2("Kije"), stable(T(Hvv_off.c(), "be", {v, v})), C1(), S2("Kijb"), tr);
+  eng.contract(C1(), stable(T(Hoo_off.c(), "mi", {o, o})), R2("Kmjb"), C0(), Xt("Kijb"), tr);
   eng.permute_into(Cr(-1), Xt("Kijb"), C1(), S2("Kijb"));
   eng.permute_into(C1(), Xt("Kjib"), C1(), S2("Kijb"));
   eng.contract(Cr(0.5), R2("Kmnb"), stable(T(Hoooo.c(), "mnij", {o, o, o, o})), C1(), S2("Kijb"), tr);
@@ -844,6 +855,7 @@ void Ctx::sigma(int k, const cplx *r, cplx *s) {
   eng.contract(Cr(0.5), R2("Kmnf"), stable(T(oovv.c(), "mnef", {o, o, v, v})), C0(), T(xe.c(), "Ke", {k, v}),
                tr);
   eng.contract(Cr(-1), T(xe.c(), "Ke", {k, v}), stable(T(t2.c(), "ijeb", {o, o, v, v})), C1(), S2("Kijb"), tr);
+  ip_diag_apply(r1.c(), r2.c(), doo.c(), dvv.c(), k, o, v, s1.c(), s2.c(), st);
   ip_pack(s1.c(), s2.c(), k, o, v, s, st);
 }
 
@@ -861,7 +873,8 @@ int Ctx::ipeom(int nr, double tol, int max_iter, double *omega, double *r1w, int
   Buf V(&al, sizeof(cplx) * max_sp * dim), S(&al, sizeof(cplx) * max_sp * dim);
   Buf d(&al, sizeof(cplx) * dim);
   Buf Xr(&al, sizeof(cplx) * nr * dim), SX(&al, sizeof(cplx) * nr * dim), R(&al, sizeof(cplx) * nr * dim);
-  Buf G(&al, sizeof(cplx) * max_sp * max_sp), wv(&al, sizeof(cplx) * max_sp),
+  Buf G(&al, sizeof(cplx) * max_sp * max_sp), Gm(&al, sizeof(cplx) * max_sp * max_sp),
+      wv(&al, sizeof(cplx) * max_sp),
       VR(&al, sizeof(cplx) * max_sp * max_sp);
   Buf Ysel(&al, sizeof(cplx) * nr * max_sp), wsel(&al, sizeof(cplx) * nr), cproj(&al, sizeof(cplx) * nr * max_sp);
   ip_diag(Hoo.c(), Hvv.c(), o, v, d.c(), st);
@@ -875,6 +888,15 @@ int Ctx::ipeom(int nr, double tol, int max_iter, double *omega, double *r1w, int
   for (int r = 0; r < nr; ++r) h2d(V.c() + r * dim + idx[r], &one, sizeof(cplx), st);
   sigma(nr, V.c(), S.c());
   int m = nr;
+  const long ld = max_sp;
+  // Gm holds G(a, b) = <v_a | sigma_b> column-major (Gm[b * ld + a]); only the
+  // rows and columns of newly added vectors are computed each iteration
+  auto g_block = [&](int b0, int nb, int a0, int na) {
+    eng.contract(C1(), T(S.c() + static_cast<long>(b0) * dim, "bd", {nb, dim}),
+                 conj(T(V.c() + static_cast<long>(a0) * dim, "ad", {na, dim})), C0(),
+                 Tv(Gm.c() + static_cast<long>(b0) * ld + a0, "ba", {nb, na}, {ld, 1}), TIER_FP64);
+  };
+  g_block(0, m, 0, m);
   bool converged = false;
   int it = 0;
   std::vector<cplx> w_out(nr);
@@ -911,8 +933,7 @@ int Ctx::ipeom(int nr, double tol, int max_iter, double *omega, double *r1w, int
   };
   for (it = 1; it <= max_iter; ++it) {
     // projected matrix, column-major: G(a, b) = <v_a | sigma_b>
-    eng.contract(C1(), T(S.c(), "bd", {m, dim}), conj(T(V.c(), "ad", {m, dim})), C0(),
-                 T(G.c(), "ba", {m, m}), TIER_FP64);
+    eng.permute_into(C1(), Tv(Gm.c(), "ba", {m, m}, {ld, 1}), C0(), T(G.c(), "ba", {m, m}));
     geev(&al, st, G.c(), m, wv.c(), VR.c());
     std::vector<cplx> wh(m), vh(static_cast<size_t>(m) * m);
     d2h(wh.data(), wv.p, sizeof(cplx) * m, st);
@@ -960,6 +981,7 @@ int Ctx::ipeom(int nr, double tol, int max_iter, double *omega, double *r1w, int
       d2d(Xc.p, Xr.p, sizeof(cplx) * nr * dim, st);
       m = orth_new(Xc.c(), nr, 0);
       sigma(m, V.c(), S.c());
+      g_block(0, m, 0, m);
       continue;
     }
     precondition(R.c(), wsel.c(), d.c(), nr, dim, SX.c(), st);  // reuse SX as scratch
@@ -969,6 +991,8 @@ int Ctx::ipeom(int nr, double tol, int max_iter, double *omega, double *r1w, int
     const int added = orth_new(corr.c(), static_cast<int>(todo.size()), m);
     if (added == 0) break;
     sigma(added, V.c() + static_cast<long>(m) * dim, S.c() + static_cast<long>(m) * dim);
+    g_block(m, added, 0, m + added);  // new columns
+    g_block(0, m, m, added);          // new rows
     m += added;
   }
   if (it > max_iter) it = max_iter;

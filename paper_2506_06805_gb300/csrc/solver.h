@@ -41,6 +41,7 @@ struct Ctx {
   // H-bar
   bool hbar_done = false;
   Buf Hov, Hoo, Hvv, Hoooo, Hooov, Hovvo, Hovoo;
+  Buf Hoo_off, Hvv_off, doo, dvv;  // one-body H-bar split into diagonal + rest
 
   // pair tables (row-major i<j over o, a<b over v)
   Buf ij_i, ij_j, ab_a, ab_b;

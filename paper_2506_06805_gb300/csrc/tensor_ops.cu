@@ -60,8 +60,15 @@ __global__ void permute_kernel(double2 *out, const double2 *in, long total, Dims
     }
     double2 x = in[off];
     if (conj) x.y = -x.y;
-    x = cmul(alpha, x);
-    if (!(beta.x == 0.0 && beta.y == 0.0)) x = cadd(x, cmul(beta, out[i]));
+    // +-1 scalings and beta in {0, 1} without FP64 multiplies (GB300's FP64
+    // rate makes them the cost of this memory-bound kernel)
+    if (alpha.y == 0.0 && (alpha.x == 1.0 || alpha.x == -1.0)) {
+      if (alpha.x < 0) x = make_double2(-x.x, -x.y);
+    } else {
+      x = cmul(alpha, x);
+    }
+    if (beta.x == 1.0 && beta.y == 0.0) x = cadd(x, out[i]);
+    else if (!(beta.x == 0.0 && beta.y == 0.0)) x = cadd(x, cmul(beta, out[i]));
     out[i] = x;
   }
 }
@@ -135,7 +142,9 @@ __global__ void antisym_add_kernel(double2 *R, const double2 *X, int o, int v, d
     x = csub(x, t1[tx][ty]);
     if (mode & 1) x = cadd(x, t2[tx][ty]);
   }
-  R[ij + e] = cadd(R[ij + e], cscale(c, x));
+  if (c == 1.0) R[ij + e] = cadd(R[ij + e], x);
+  else if (c == -1.0) R[ij + e] = csub(R[ij + e], x);
+  else R[ij + e] = cadd(R[ij + e], cscale(c, x));
 }
 
 inline unsigned grid_for(long n, int threads = 256) {

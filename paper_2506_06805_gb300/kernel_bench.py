@@ -2,11 +2,16 @@
 
     python -m paper_2506_06805_gb300.kernel_bench ladder --o 20 --v 160 --X 640
     python -m paper_2506_06805_gb300.kernel_bench gemm --M 4096 --N 4096 --K 4096
+    python -m paper_2506_06805_gb300.kernel_bench fns --config fns --keep-frac 0.4
 
 ``ladder`` times cc_ladder_dev (1/2 sum_cd <ab||cd> tau_ij^cd with <ab||cd>
 formed from Cholesky vectors) and reports algorithmic TFLOP/s with the
 symmetry-reduced count 8 [X v^3 (v-1)/2 + (v(v-1)/2)^2 o(o-1)/2].
 ``gemm`` times the complex GEMM entry point (8 M N K flops).
+``fns`` feeds a configured system's Cholesky vectors in chunks of 200
+(cc_add_cholesky), reports the natural-spinor occupations and the count
+kept at the literal threshold, then runs FNS with the kept fraction,
+CCSD and IP-EOM in two tier pairs and compares their IPs.
 One JSON line per run.
 """
 from __future__ import annotations
@@ -22,7 +27,9 @@ def main():
 
     from . import System, synth, use_torch_memory, zgemm_dev
     p = argparse.ArgumentParser()
-    p.add_argument("what", choices=["ladder", "gemm"])
+    p.add_argument("what", choices=["ladder", "gemm", "fns"])
+    p.add_argument("--config", default="fns")
+    p.add_argument("--keep-frac", type=float, default=0.4)
     p.add_argument("--o", type=int, default=20)
     p.add_argument("--v", type=int, default=160)
     p.add_argument("--X", type=int, default=640)
@@ -36,6 +43,8 @@ def main():
     use_torch_memory()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    if a.what == "fns":
+        return fns_run(a)
     if a.what == "ladder":
         eps, L = synth.make_system(a.o, a.v, a.X, seed=0, kramers=False)
         rng = np.random.default_rng(1)
@@ -75,6 +84,57 @@ def main():
         ms = ev0.elapsed_time(ev1) / a.reps
         print(json.dumps({"kernel": "zgemm", "M": a.M, "N": a.N, "K": a.K, "tier": a.tier,
                           "ms": ms, "tflops": 8.0 * a.M * a.N * a.K / ms / 1e9}))
+
+
+def fns_run(a):
+    import time
+
+    import torch
+
+    from . import System, synth
+    c = synth.CONFIGS[a.config]
+    o, v, X = c.n_occ, c.n_virt, c.n_aux
+    out = {"config": a.config, "o": o, "v": v, "X": X}
+
+    def make(tier, eom):
+        rng = np.random.default_rng(c.seed)
+        eps = synth.make_eps(rng, o, v, c.kramers)
+        s = System(eps, None, n_occ=o, n_aux=X, tier=tier, eom_tier=eom)
+        for p0 in range(0, X, 200):
+            p1 = min(X, p0 + 200)
+            s.add_cholesky(p0, p1, synth.cholesky_chunks(rng, o + v, X, p0, p1, c.kramers))
+        return s
+
+    thr = c.get("fns_threshold", 1e-5)
+    with make("tf32", "tf32x3") as s:
+        t0 = time.perf_counter()
+        out["kept_at_threshold"] = s.fns_truncate(threshold=thr)
+        torch.cuda.synchronize()
+        out["fns_s"] = time.perf_counter() - t0
+        occ = s.fns_occupations(v)
+        out["threshold"] = thr
+        out["occ_max"] = float(occ[0])
+        out["n_ge"] = {f"{t:.3g}": int((occ >= t).sum()) for t in (1e-4, 10 ** -4.5, 1e-5, 1e-6)}
+    n_keep = max(1, int(round(a.keep_frac * v)))
+    res = {}
+    for tier, eom in (("tf32", "tf32x3"), ("tf32x3", "tf32x3")):
+        with make(tier, eom) as s:
+            t0 = time.perf_counter()
+            s.fns_truncate(n_keep=n_keep)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            e = s.ccsd(tol=c.ccsd_tol, max_iter=60)
+            t2 = time.perf_counter()
+            w, _ = s.ipeom(c.n_roots, tol=c.eom_tol, max_iter=100)
+            t3 = time.perf_counter()
+            res[tier] = {"fns_s": t1 - t0, "ccsd_s": t2 - t1, "ipeom_s": t3 - t2,
+                         "e_corr": [e.real, e.imag], "ccsd_iter": s.ccsd_iterations,
+                         "ips": [float(x) for x in np.sort(w.real)]}
+    out["n_keep"] = n_keep
+    out["runs"] = res
+    out["max_dIP_tf32_vs_tf32x3"] = float(np.abs(np.array(res["tf32"]["ips"])
+                                                 - np.array(res["tf32x3"]["ips"])).max())
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":

@@ -52,6 +52,28 @@ def _relerr(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
+# --- the tensor-core GEMM ----------------------------------------------------
+
+@pytest.mark.parametrize("tier", ["tf32", "tf32x3", "bf16x3"])
+def test_gemm_accumulation_bias_flat_in_k(tier):
+    """Same-sign products expose any systematic rounding of the tensor-core
+    accumulation: without promotion from TMEM every few K blocks the
+    relative bias grew linearly with K (about -2e-5 at K = 32768 in TF32x3).
+    With promotion it must stay at the per-chunk level for any K."""
+    P = _gpu()
+    rng = np.random.default_rng(0)
+    M, N, K = 192, 320, 32768
+    A = rng.uniform(0.5, 1.0, (M, K)) + 0j
+    B = rng.uniform(0.5, 1.0, (N, K)) + 0j
+    ref = A.real @ B.real.T
+    C = torch.zeros((M, N), dtype=torch.complex128, device="cuda")
+    P.zgemm_dev(_dev(A), _dev(B), C, tier)
+    got = C.cpu().numpy().real
+    bias = float(np.mean((got - ref) / ref))
+    assert abs(bias) < 3e-6, bias
+    assert float(np.abs(got - ref).max() / ref.max()) < {"tf32": 5e-5}.get(tier, 5e-6)
+
+
 # --- integrals: bit-exact ----------------------------------------------------
 
 def test_integral_dump_bit_exact():
