@@ -230,6 +230,45 @@ int cc_dump_integrals(cc_ctx *ctx, int block, double *out_host);
  * launches inside the ladder. */
 int cc_get_stats(const cc_ctx *ctx, double *out_host, int n);
 
+/*
+ * Learned warm start (the benchmark spec's learned part; the paper has none).
+ * A per-element MLP maps gauge-invariant features of each unique doubles
+ * element (i<j, a<b) -- log10|t_MP2|, D_ij^ab, <ij||ij>, <ab||ab>, sum and
+ * spread of <ia||ia>+<jb||jb> and <ib||ib>+<ja||ja>, eps_i+eps_j, |<ij||ab>|,
+ * integrals scaled by the system's rms <ij||ij> and energies by its mean
+ * |eps| -- to rho = t_CCSD / t_MP2. Network 8 -> 64 -> 64 -> 2 (ReLU) with
+ * FP16 weights and FP32 accumulation; parameters are W1[64][8], b1[64],
+ * W2[64][64], b2[64], W3[2][64], b3[2] in that order (host float arrays).
+ * The network outputs rho - 1. Training minimises the mean of
+ * w |rho_pred - rho|^2 with w = |t_MP2|^2 normalised to mean 1 (the amplitude
+ * error), by Adam (beta 0.9/0.999, eps 1e-8) on the GPU.
+ */
+typedef struct cc_mlp cc_mlp;
+int cc_mlp_num_params(void);
+int cc_mlp_create(cc_mlp **out);
+void cc_mlp_free(cc_mlp *mlp);
+const char *cc_mlp_last_error(const cc_mlp *mlp);
+int cc_mlp_set_params(cc_mlp *mlp, const float *params_host, int n);
+int cc_mlp_get_params(const cc_mlp *mlp, float *params_host, int n);
+/* Append up to max_samples evenly strided unique elements of a context with
+ * converged CCSD amplitudes to the training set (features and targets). */
+int cc_mlp_add_samples(cc_mlp *mlp, cc_ctx *ctx, long max_samples);
+int cc_mlp_num_samples(const cc_mlp *mlp, long *n);
+/* steps Adam steps on contiguous minibatches of the training set in the
+ * order perm_host (perm_len indices, NULL = stored order), wrapping around;
+ * final_loss (may be NULL) gets the last minibatch loss. */
+int cc_mlp_train(cc_mlp *mlp, int steps, int batch, float lr,
+                 const int *perm_host, long perm_len, double *final_loss);
+/* Loss and gradient for a given batch: X_host [n][8], Y_host [n][3] holding
+ * (Re, Im of the target rho - 1, weight); grad_host [num_params]. */
+int cc_mlp_loss_grad(cc_mlp *mlp, long n, const float *X_host,
+                     const float *Y_host, double *loss, float *grad_host);
+/* Features of the first n unique elements of a context (host [n][8]). */
+int cc_mlp_features(cc_ctx *ctx, long n, float *X_host);
+/* Set the context's starting amplitudes t1 = 0, t2 = rho(MLP) * t_MP2; the
+ * next ccsd_solve starts from them. Errors: CC_ERR_STATE after ccsd_solve. */
+int cc_mlp_warm_start(cc_mlp *mlp, cc_ctx *ctx);
+
 const char *cc_last_error(const cc_ctx *ctx); /* NULL ctx: last global */
 void cc_free(cc_ctx *ctx);
 

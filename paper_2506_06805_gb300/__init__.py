@@ -21,7 +21,7 @@ import os
 
 import numpy as np
 
-__all__ = ["lib", "System", "CCError", "TIERS", "LIB_PATH"]
+__all__ = ["lib", "System", "Mlp", "CCError", "TIERS", "LIB_PATH"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcdfns.so")
 
@@ -70,6 +70,21 @@ _SIGS = {
                                         ctypes.c_long, _P, _P, _P]),
     "cc_get_stats": (ctypes.c_int, [_P, _D, ctypes.c_int]),
     "cc_last_error": (ctypes.c_char_p, [_P]),
+    "cc_mlp_num_params": (ctypes.c_int, []),
+    "cc_mlp_create": (ctypes.c_int, [ctypes.POINTER(_P)]),
+    "cc_mlp_free": (None, [_P]),
+    "cc_mlp_last_error": (ctypes.c_char_p, [_P]),
+    "cc_mlp_set_params": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
+    "cc_mlp_get_params": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
+    "cc_mlp_add_samples": (ctypes.c_int, [_P, _P, ctypes.c_long]),
+    "cc_mlp_num_samples": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_long)]),
+    "cc_mlp_train": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                    ctypes.POINTER(ctypes.c_int), ctypes.c_long, _D]),
+    "cc_mlp_loss_grad": (ctypes.c_int, [_P, ctypes.c_long, ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(ctypes.c_float), _D,
+                                        ctypes.POINTER(ctypes.c_float)]),
+    "cc_mlp_features": (ctypes.c_int, [_P, ctypes.c_long, ctypes.POINTER(ctypes.c_float)]),
+    "cc_mlp_warm_start": (ctypes.c_int, [_P, _P]),
     "cc_free": (None, [_P]),
 }
 
@@ -322,3 +337,98 @@ class System:
         keys = ["ladder_ms", "ladder_calls", "ladder_flops", "fns_ms", "ccsd_ms",
                 "ipeom_ms", "launches", "ccsd_iter", "davidson_iter"]
         return {k: float(s[i]) for i, k in enumerate(keys)}
+
+
+_FP = ctypes.POINTER(ctypes.c_float)
+
+
+def _fptr(a):
+    return a.ctypes.data_as(_FP)
+
+
+class Mlp:
+    """The learned warm start (8 -> 64 -> 64 -> 2 MLP, FP16 weights).
+
+    Parameters are a flat float32 array (W1, b1, W2, b2, W3, b3); see
+    cc_mlp_* in cdfns.h for the features and the loss.
+    """
+
+    def __init__(self, params=None, seed=0):
+        self._h = _P()
+        _check(lib().cc_mlp_create(ctypes.byref(self._h)))
+        self.n_params = lib().cc_mlp_num_params()
+        if params is None:
+            params = self.init_params(seed)
+        self.set_params(params)
+
+    @staticmethod
+    def init_params(seed=0):
+        """He-uniform weights, zero biases (the last layer starts small)."""
+        rng = np.random.default_rng(seed)
+        parts = []
+        for fan_in, fan_out, scale in ((8, 64, 1.0), (64, 64, 1.0), (64, 2, 0.01)):
+            lim = scale * np.sqrt(6.0 / fan_in)
+            parts.append(rng.uniform(-lim, lim, (fan_out, fan_in)).ravel())
+            parts.append(np.zeros(fan_out))
+        return np.concatenate(parts).astype(np.float32)
+
+    def _err(self, rc, ok=(0,)):
+        if rc not in ok:
+            raise CCError(rc, lib().cc_mlp_last_error(self._h).decode())
+
+    def close(self):
+        if self._h:
+            lib().cc_mlp_free(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._err(lib().cc_mlp_set_params(self._h, _fptr(p), p.size))
+
+    def params(self):
+        out = np.empty(self.n_params, np.float32)
+        self._err(lib().cc_mlp_get_params(self._h, _fptr(out), out.size))
+        return out
+
+    def add_samples(self, system, max_samples):
+        self._err(lib().cc_mlp_add_samples(self._h, system._ctx, int(max_samples)))
+
+    def num_samples(self):
+        n = ctypes.c_long()
+        self._err(lib().cc_mlp_num_samples(self._h, ctypes.byref(n)))
+        return n.value
+
+    def train(self, steps, batch=4096, lr=1e-3, perm=None):
+        loss = ctypes.c_double()
+        if perm is not None:
+            perm = np.ascontiguousarray(perm, dtype=np.int32)
+            pp, pl = perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), perm.size
+        else:
+            pp, pl = None, 0
+        self._err(lib().cc_mlp_train(self._h, int(steps), int(batch), float(lr), pp, pl,
+                                     ctypes.byref(loss)))
+        return loss.value
+
+    def loss_grad(self, X, Y):
+        X = np.ascontiguousarray(X, np.float32)
+        Y = np.ascontiguousarray(Y, np.float32)
+        g = np.empty(self.n_params, np.float32)
+        loss = ctypes.c_double()
+        self._err(lib().cc_mlp_loss_grad(self._h, X.shape[0], _fptr(X), _fptr(Y),
+                                         ctypes.byref(loss), _fptr(g)))
+        return loss.value, g
+
+    def warm_start(self, system):
+        self._err(lib().cc_mlp_warm_start(self._h, system._ctx))
+
+    @staticmethod
+    def features(system, n):
+        out = np.empty((n, 8), np.float32)
+        _check(lib().cc_mlp_features(system._ctx, int(n), _fptr(out)), system._ctx)
+        return out

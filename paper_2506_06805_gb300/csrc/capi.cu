@@ -4,10 +4,6 @@
 
 #include "solver.h"
 
-struct cc_ctx {
-  cdfns::Ctx c;
-};
-
 namespace cdfns {
 
 namespace {

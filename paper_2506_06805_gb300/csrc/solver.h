@@ -82,3 +82,8 @@ struct Ctx {
 };
 
 }  // namespace cdfns
+
+// The opaque handle of the C ABI wraps one solver state.
+struct cc_ctx {
+  cdfns::Ctx c;
+};

@@ -329,3 +329,32 @@ def test_davidson_matches_dense():
         tol=1e-9)
     assert conv
     assert np.abs(w - w_dense).max() <= 1e-9
+
+
+# --- warm-start network (oracle side) ------------------------------------------
+
+def test_mlp_oracle_gradient_matches_finite_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(0)
+    p = rng.standard_normal(mlp.N_PARAMS) * 0.3
+    X = rng.standard_normal((17, mlp.F))
+    Y = np.column_stack([rng.standard_normal((17, 2)), rng.uniform(0.5, 2, 17)])
+    loss, g = mlp.loss_grad(p, X, Y)
+    idx = rng.choice(mlp.N_PARAMS, 60, replace=False)
+    for k in idx:
+        h = 1e-6
+        pp, pm = p.copy(), p.copy()
+        pp[k] += h
+        pm[k] -= h
+        fd = (mlp.loss_grad(pp, X, Y)[0] - mlp.loss_grad(pm, X, Y)[0]) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(g[k])), (k, fd, g[k])
+
+
+def test_mlp_features_are_gauge_invariant():
+    from oracle import mlp
+    o, v, X = 3, 6, 10
+    eps, L = _system(o, v, X, seed=3, scale=5.0)
+    theta = np.random.default_rng(1).uniform(0, 2 * np.pi, o + v)
+    f1 = mlp.features(L, eps, o, 20)
+    f2 = mlp.features(synth.gauge_transform(L, theta), eps, o, 20)
+    assert np.abs(f1 - f2).max() <= 1e-10
