@@ -145,6 +145,24 @@ int ccsd_solve(cc_ctx *ctx, double tol, int max_iter, double *e_corr,
 int ipeom_solve(cc_ctx *ctx, int n_roots, double tol, int max_iter,
                 double *omega, double *r1_weight, int *n_iter);
 
+/*
+ * cc_batch_ipeom: ipeom_solve for several independent systems (uneven sizes
+ * allowed), each with converged CCSD. Their block Davidson iterations run in
+ * lockstep; each round builds the sigma vectors of every still-active
+ * system in one batched pass whose two-body contractions share one grouped
+ * persistent tensor-core launch, replayed from a CUDA graph after its first
+ * use (cc_set_graphs). Work runs on systems[0]'s stream.
+ * omega [n_sys][n_roots][2], r1_weight [n_sys][n_roots] (may be NULL),
+ * n_iter [n_sys] (may be NULL), status [n_sys] (CC_OK or
+ * CC_ERR_NOT_CONVERGED per system). Returns CC_ERR_NOT_CONVERGED if any
+ * system did not converge; errors are reported on systems[0].
+ */
+int cc_batch_ipeom(cc_ctx **systems, int n_sys, int n_roots, double tol,
+                   int max_iter, double *omega, double *r1_weight, int *n_iter,
+                   int *status);
+/* Replay the batched sigma from CUDA graphs (1, default) or not (0). */
+int cc_set_graphs(cc_ctx *ctx, int on);
+
 /* Amplitudes as unique elements, host complex128: t1 [o][v] then t2 for
  * i<j, a<b in row-major pair order ([o(o-1)/2][v(v-1)/2]). */
 int cc_get_amplitudes(const cc_ctx *ctx, double *t1_host, double *t2_host);
@@ -231,7 +249,7 @@ int cc_dump_integrals(cc_ctx *ctx, int block, double *out_host);
 int cc_get_stats(const cc_ctx *ctx, double *out_host, int n);
 
 /*
- * Learned warm start (the benchmark spec's learned part; the paper has none).
+ * Learned warm start of the CCSD amplitudes (an extension: the paper has no learned component).
  * A per-element MLP maps gauge-invariant features of each unique doubles
  * element (i<j, a<b) -- log10|t_MP2|, D_ij^ab, <ij||ij>, <ab||ab>, sum and
  * spread of <ia||ia>+<jb||jb> and <ib||ib>+<ja||ja>, eps_i+eps_j, |<ij||ab>|,

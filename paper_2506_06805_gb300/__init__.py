@@ -86,6 +86,9 @@ _SIGS = {
     "cc_mlp_features": (ctypes.c_int, [_P, ctypes.c_long, ctypes.POINTER(ctypes.c_float)]),
     "cc_mlp_warm_start": (ctypes.c_int, [_P, _P]),
     "cc_free": (None, [_P]),
+    "cc_set_graphs": (ctypes.c_int, [_P, ctypes.c_int]),
+    "cc_batch_ipeom": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_int, _D, _D, _I, _I]),
 }
 
 _lib = None
@@ -169,6 +172,22 @@ def zgemm_dev(A, B, C, tier="fp64"):
     N = B.shape[0]
     _check(lib().cc_zgemm_dev(t, M, N, K, _P(A.data_ptr()), _P(B.data_ptr()),
                               _P(C.data_ptr())))
+
+
+def batch_ipeom(systems, n_roots, tol=1e-7, max_iter=100, allow_unconverged=False):
+    """IP-EOM roots of several systems with batched sigma builds.
+
+    Returns (omega [n_sys][n_roots] complex, r1_weight, n_iter, status)."""
+    n = len(systems)
+    arr = (_P * n)(*[s._ctx for s in systems])
+    w = np.zeros((n, n_roots, 2))
+    r1 = np.zeros((n, n_roots))
+    it = np.zeros(n, np.int32)
+    stt = np.zeros(n, np.int32)
+    rc = lib().cc_batch_ipeom(arr, n, n_roots, tol, max_iter, _dptr(w), _dptr(r1),
+                              it.ctypes.data_as(_I), stt.ctypes.data_as(_I))
+    _check(rc, systems[0]._ctx, (0, -5) if allow_unconverged else (0,))
+    return w[..., 0] + 1j * w[..., 1], r1, it, stt
 
 
 def zgemm_noalloc(A, B, C, tier="fp64"):
@@ -292,6 +311,9 @@ class System:
                                  ctypes.byref(it)), self._ctx, ok)
         self.davidson_iterations = it.value
         return w[0::2] + 1j * w[1::2], r1
+
+    def set_graphs(self, on=True):
+        _check(lib().cc_set_graphs(self._ctx, 1 if on else 0), self._ctx)
 
     def get_amplitudes(self):
         o, v, _ = self.sizes()

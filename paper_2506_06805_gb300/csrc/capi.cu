@@ -425,7 +425,31 @@ const char *cc_last_error(const cc_ctx *ctx) {
 void cc_free(cc_ctx *ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->c.st);
+  cdfns::drop_graphs(&ctx->c);
   delete ctx;
+}
+
+int cc_set_graphs(cc_ctx *ctx, int on) {
+  if (!ctx) return CC_ERR_ARG;
+  ctx->c.use_graphs = on != 0;
+  return CC_OK;
+}
+
+int cc_batch_ipeom(cc_ctx **systems, int n_sys, int n_roots, double tol, int max_iter,
+                   double *omega, double *r1_weight, int *n_iter, int *status) {
+  if (!systems || n_sys < 1 || !omega || !status) return CC_ERR_ARG;
+  for (int q = 0; q < n_sys; ++q)
+    if (!systems[q]) return CC_ERR_ARG;
+  if (!(tol > 0) || max_iter < 1) return CC_ERR_ARG;
+  return guarded(systems[0], [&] {
+    std::vector<cdfns::Ctx *> sys;
+    for (int q = 0; q < n_sys; ++q) sys.push_back(&systems[q]->c);
+    cdfns::run_ipeom(sys, n_roots, tol, max_iter, omega, r1_weight, n_iter, status,
+                     systems[0]->c.use_graphs);
+    for (int q = 0; q < n_sys; ++q)
+      if (status[q] != CC_OK) return CC_ERR_NOT_CONVERGED;
+    return CC_OK;
+  });
 }
 
 }  // extern "C"

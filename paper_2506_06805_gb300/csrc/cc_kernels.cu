@@ -435,6 +435,24 @@ __global__ void ip_diag_apply_kernel(const double2 *r1, const double2 *r2, const
   }
 }
 
+// s2 += tA + tB + tC - P(ij) X1 + P(ij) X2 on [k][o][o][v] tensors
+__global__ void sigma_combine_kernel(double2 *s2, const double2 *tA, const double2 *tB,
+                                     const double2 *tC, const double2 *X1, const double2 *X2, int k,
+                                     int o, int v) {
+  const long per = static_cast<long>(o) * o * v;
+  GRID_STRIDE(idx, static_cast<long>(k) * per) {
+    const long kk = idx / per, rem = idx % per;
+    const int b = static_cast<int>(rem % v);
+    const int j = static_cast<int>((rem / v) % o);
+    const int i = static_cast<int>(rem / (static_cast<long>(v) * o));
+    const long sw = kk * per + (static_cast<long>(j) * o + i) * v + b;
+    double2 x = cadd(cadd(s2[idx], tA[idx]), cadd(tB[idx], tC[idx]));
+    x = cadd(x, csub(X1[sw], X1[idx]));
+    x = cadd(x, csub(X2[idx], X2[sw]));
+    s2[idx] = x;
+  }
+}
+
 __global__ void split_diag_kernel(const double2 *A, int n, double2 *off, double2 *diag) {
   GRID_STRIDE(idx, static_cast<long>(n) * n) {
     const long r = idx / n, c = idx % n;
@@ -652,6 +670,14 @@ void ip_diag_apply(const cplx *r1, const cplx *r2, const cplx *doo, const cplx *
                    int v, cplx *s1, cplx *s2, cudaStream_t st) {
   ip_diag_apply_kernel<<<grid_for(static_cast<long>(k) * o * o * v), 256, 0, st>>>(r1, r2, doo, dvv, k,
                                                                                   o, v, s1, s2);
+  LAUNCH_CHECK();
+  count_launch();
+}
+
+void sigma_combine(cplx *s2, const cplx *tA, const cplx *tB, const cplx *tC, const cplx *X1,
+                   const cplx *X2, int k, int o, int v, cudaStream_t st) {
+  sigma_combine_kernel<<<grid_for(static_cast<long>(k) * o * o * v), 256, 0, st>>>(s2, tA, tB, tC, X1,
+                                                                                  X2, k, o, v);
   LAUNCH_CHECK();
   count_launch();
 }

@@ -68,6 +68,9 @@ void ip_diag(const cplx *Hoo, const cplx *Hvv, int o, int v, cplx *d, cudaStream
 // diagonal one-body part of sigma, exact in FP64)
 void ip_diag_apply(const cplx *r1, const cplx *r2, const cplx *doo, const cplx *dvv, int k, int o,
                    int v, cplx *s1, cplx *s2, cudaStream_t st);
+// s2 += tA + tB + tC - (X1 - X1(i<->j)) + (X2 - X2(i<->j)), [k][o][o][v]
+void sigma_combine(cplx *s2, const cplx *tA, const cplx *tB, const cplx *tC, const cplx *X1,
+                   const cplx *X2, int k, int o, int v, cudaStream_t st);
 // off = A with zero diagonal, diag = diagonal of A (n x n)
 void split_diag(const cplx *A, int n, cplx *off, cplx *diag, cudaStream_t st);
 // x[r] = R[r] / (w[r] - d) with |den| floored at 1e-8

@@ -58,6 +58,7 @@ std::pair<void *, void *> Engine::packed(bool a_side, const TRef &t, const long 
   const size_t eb = tc_elem_bytes(tier);
   const size_t n = eb * (a_side ? 2 : 1) * rows * Kp;
   Packed pk;
+  ++gen;
   pk.hi.reset(al, n);
   if (tier != TIER_TF32) pk.lo.reset(al, n);
   if (a_side)
@@ -74,6 +75,7 @@ void *Engine::plane(int which, size_t bytes) {
   if (b.bytes < bytes) {
     b.release();
     b.reset(al, bytes + bytes / 8);
+    ++gen;
   }
   return b.p;
 }
@@ -107,6 +109,17 @@ bool linear(const std::vector<long> &dims, const std::vector<long> &str, long *s
 
 void Engine::contract(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef &C,
                       int tier) {
+  run(alpha, A, B, beta, C, tier, -1, nullptr);
+}
+
+bool Engine::prepare(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef &C, int tier,
+                     int slot, TcDesc *out) {
+  if (slot < 0 || !out) fail(CC_ERR_ARG, "prepare: slot and descriptor required");
+  return run(alpha, A, B, beta, C, tier, slot, out);
+}
+
+bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef &C, int tier,
+                 int slot, TcDesc *out) {
   std::vector<long> mdim, amstr, cmstr, ndim, bnstr, cnstr, kdim, akstr, bkstr;
   for (size_t i = 0; i < C.idx.size(); ++i) {
     const char c = C.idx[i];
@@ -145,7 +158,7 @@ void Engine::contract(cplx alpha, const TRef &A, const TRef &B, cplx beta, const
   for (long d : mdim) M *= d;
   for (long d : ndim) N *= d;
   for (long d : kdim) K *= d;
-  if (M == 0 || N == 0) return;
+  if (M == 0 || N == 0) return false;
   flops += 8.0 * M * N * K;
 
   // tables (NULL when linear)
@@ -181,7 +194,7 @@ void Engine::contract(cplx alpha, const TRef &A, const TRef &B, cplx beta, const
     g.alpha = alpha; g.beta = beta;
     g.k_contig = kdim.empty() || (M == 1 ? bkstr.back() == 1 : akstr.back() == 1);
     gemm_f64(g, st, num_sms);
-    return;
+    return false;
   }
   // fast tier: pack operands into expanded planes, tensor-core GEMM
   const int kal = tc_k_align(tier);
@@ -189,18 +202,19 @@ void Engine::contract(cplx alpha, const TRef &A, const TRef &B, cplx beta, const
   const size_t eb = tc_elem_bytes(tier);
   const bool split = tier != TIER_TF32;
   void *Ah, *Al = nullptr, *Bh, *Bl = nullptr;
+  const int pb = 4 * (slot < 0 ? 0 : slot + 1);  // plane set of this contraction
   if (A.stable) {
     std::tie(Ah, Al) = packed(true, A, am, ak, lda, M, K, Kp, tier);
   } else {
-    Ah = plane(0, eb * 2 * M * Kp);
-    Al = split ? plane(1, eb * 2 * M * Kp) : nullptr;
+    Ah = plane(pb + 0, eb * 2 * M * Kp);
+    Al = split ? plane(pb + 1, eb * 2 * M * Kp) : nullptr;
     tc_pack_A(A.p, am, ak, lda, A.conj, M, K, Kp, tier, Ah, Al, st);
   }
   if (B.stable) {
     std::tie(Bh, Bl) = packed(false, B, bn, bk, ldb, N, K, Kp, tier);
   } else {
-    Bh = plane(2, eb * N * Kp);
-    Bl = split ? plane(3, eb * N * Kp) : nullptr;
+    Bh = plane(pb + 2, eb * N * Kp);
+    Bl = split ? plane(pb + 3, eb * N * Kp) : nullptr;
     tc_pack_B(B.p, bn, bk, ldb, B.conj, N, K, Kp, tier, Bh, Bl, st);
   }
   TcDesc t;
@@ -224,7 +238,12 @@ void Engine::contract(cplx alpha, const TRef &A, const TRef &B, cplx beta, const
   } else {
     t.out = TC_OUT_F64;
   }
+  if (out) {
+    *out = t;
+    return true;
+  }
   gemm_tc(t, st, err_flag);
+  return false;
 }
 
 void Engine::permute_into(cplx alpha, const TRef &in, cplx beta, const TRef &out) {

@@ -56,8 +56,15 @@ class Engine {
   int *err_flag = nullptr;  // device int, set by bounded waits
   // statistics
   double flops = 0;
+  long gen = 0;  // bumped whenever a plane or packed buffer is (re)allocated or freed
 
   void contract(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef &C, int tier);
+  // Same contraction prepared for a grouped launch (gemm_tc_grouped): packs
+  // the operands into the planes of `slot` (distinct slots for contractions
+  // launched together) and fills *out. Returns false when the contraction
+  // was small or FP64 and has already run on the FP64 path.
+  bool prepare(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef &C, int tier,
+               int slot, TcDesc *out);
   // out = alpha * permuted(in) + beta * out, where out's index string names
   // the order: e.g. permute_into(T(x,"ijab"), T(y,"jiab")) copies y with i,j
   // exchanged.
@@ -68,8 +75,12 @@ class Engine {
   void clear_cache() {
     cache_.clear();
     packs_.clear();
+    ++gen;
   }
-  void clear_pack_cache() { packs_.clear(); }
+  void clear_pack_cache() {
+    packs_.clear();
+    ++gen;
+  }
 
  private:
   struct Packed {
@@ -80,7 +91,10 @@ class Engine {
                                    long ld, long rows, long K, long Kp, int tier);
   std::map<std::string, Buf> cache_;
   std::map<std::string, Packed> packs_;
-  Buf planes_[6];
+  std::map<int, Buf> planes_;
+  struct Plan;
+  bool run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef &C, int tier, int slot,
+           TcDesc *out);
 };
 
 inline cplx C1() { return mk(1.0, 0.0); }

@@ -22,6 +22,14 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
 #include "kernels.h"
 
 namespace cdfns {
@@ -148,25 +156,41 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-struct TcArgs {
+// One GEMM problem of a (possibly grouped) launch. The tensor maps live in
+// the kernel parameters (__grid_constant__), 64-byte aligned.
+struct alignas(64) TcProblem {
+  CUtensorMap mA, mAlo, mB, mBlo;
   long M, N;        // complex rows, columns
-  int num_kb;       // K blocks of 128 bytes per row
-  int kb_per_split;
-  int chunk;        // K blocks accumulated in TMEM before promotion
-  int m_tiles, n_tiles, k_splits;
-  int group_m;      // m tiles per raster group (A panels kept in L2)
-  int out;
   void *C;
   const long *cm, *cn;
   long ldc;
   double2 alpha, beta;
+  int num_kb;       // K blocks of 128 bytes per row
+  int kb_per_split;
+  int k_splits, m_tiles, n_tiles;
+  int group_m;      // m tiles per raster group (A panels kept in L2)
+  int out;
+  int tile_start;   // first index of this problem in the launch's tile space
+};
+constexpr int MAX_PROBLEMS = 16;
+struct TcGroup {
+  TcProblem p[MAX_PROBLEMS];
+  int nprob;
+  int total_tiles;
+  int chunk;        // K blocks accumulated in TMEM before promotion
   int *err;
 };
 
-// Linear tile index -> (m tile, n tile, k split): groups of group_m m-tiles,
+__device__ __forceinline__ int find_problem(const TcGroup &g, int t) {
+  int p = 0;
+  while (p + 1 < g.nprob && t >= g.p[p + 1].tile_start) ++p;
+  return p;
+}
+
+// Local tile index -> (m tile, n tile, k split): groups of group_m m-tiles,
 // n-tiles swept inside a group, so a wave of CTAs shares a few A panels and a
 // few B panels in L2.
-__device__ __forceinline__ void tile_coords(const TcArgs &a, int t, int &m, int &n, int &z) {
+__device__ __forceinline__ void tile_coords(const TcProblem &a, int t, int &m, int &n, int &z) {
   const int mn = a.m_tiles * a.n_tiles;
   z = t / mn;
   const int r0 = t - z * mn;
@@ -190,9 +214,7 @@ __device__ __forceinline__ void tile_coords(const TcArgs &a, int t, int &m, int 
 // MMA of the next tile overlaps the epilogue stores of the previous one.
 template <int BN, int STAGES, bool SPLIT, bool BF16>
 __global__ void __launch_bounds__(320, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mAlo,
-                   const __grid_constant__ CUtensorMap mB, const __grid_constant__ CUtensorMap mBlo,
-                   const TcArgs args) {
+    tc_gemm_kernel(const __grid_constant__ TcGroup grp) {
   constexpr int A_BYTES = BM * ROW_BYTES;
   constexpr int B_BYTES = BN * ROW_BYTES;
   constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * (SPLIT ? 2 : 1);
@@ -214,8 +236,9 @@ __global__ void __launch_bounds__(320, 1)
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int n_tiles_total = args.m_tiles * args.n_tiles * args.k_splits;
-  const int chunk = args.chunk;
+  const int n_tiles_total = grp.total_tiles;
+  const int chunk = grp.chunk;
+  int *const err = grp.err;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -241,33 +264,34 @@ __global__ void __launch_bounds__(320, 1)
       long it = 0;  // k blocks issued so far (all tiles)
       bool ok = true;
       for (int t = blockIdx.x; t < n_tiles_total && ok; t += gridDim.x) {
+        const TcProblem &P = grp.p[find_problem(grp, t)];
         int m_tile, n_tile, z;
-        tile_coords(args, t, m_tile, n_tile, z);
-        const int kb0 = z * args.kb_per_split;
-        const int kb1 = min(args.num_kb, kb0 + args.kb_per_split);
+        tile_coords(P, t - P.tile_start, m_tile, n_tile, z);
+        const int kb0 = z * P.kb_per_split;
+        const int kb1 = min(P.num_kb, kb0 + P.kb_per_split);
         for (int kb = kb0; kb < kb1; ++kb, ++it) {
           const int s = static_cast<int>(it % STAGES);
           const uint32_t ph = static_cast<uint32_t>(it / STAGES) & 1u;
           if (!mbar_wait(&empty[s], ph ^ 1u)) {
-            atomicExch(args.err, 1);
+            atomicExch(err, 1);
             ok = false;
             break;
           }
           uint8_t *st = smem + s * STAGE_BYTES;
           mbar_expect_tx(&full[s], STAGE_BYTES);
           const int kx = kb * K_ELEMS;
-          tma_load_2d(st, &mA, &full[s], kx, m_tile * BM);
-          tma_load_2d(st + A_BYTES, &mB, &full[s], kx, n_tile * BN);
+          tma_load_2d(st, &P.mA, &full[s], kx, m_tile * BM);
+          tma_load_2d(st + A_BYTES, &P.mB, &full[s], kx, n_tile * BN);
           if constexpr (SPLIT) {
-            tma_load_2d(st + A_BYTES + B_BYTES, &mAlo, &full[s], kx, m_tile * BM);
-            tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mBlo, &full[s], kx, n_tile * BN);
+            tma_load_2d(st + A_BYTES + B_BYTES, &P.mAlo, &full[s], kx, m_tile * BM);
+            tma_load_2d(st + 2 * A_BYTES + B_BYTES, &P.mBlo, &full[s], kx, n_tile * BN);
           }
         }
       }
       // the last load issued into each stage must land before the CTA exits
       for (long i = (it > STAGES ? it - STAGES : 0); i < it; ++i) {
         if (!mbar_wait(&full[i % STAGES], static_cast<uint32_t>(i / STAGES) & 1u))
-          atomicExch(args.err, 1);
+          atomicExch(err, 1);
       }
     }
   } else if (warp == 9) {
@@ -277,15 +301,16 @@ __global__ void __launch_bounds__(320, 1)
       long c = 0;   // chunks issued (all tiles)
       bool ok = true;
       for (int t = blockIdx.x; t < n_tiles_total && ok; t += gridDim.x) {
+        const TcProblem &P = grp.p[find_problem(grp, t)];
         int m_tile, n_tile, z;
-        tile_coords(args, t, m_tile, n_tile, z);
-        const int kb0 = z * args.kb_per_split;
-        const int nkb = min(args.num_kb, kb0 + args.kb_per_split) - kb0;
+        tile_coords(P, t - P.tile_start, m_tile, n_tile, z);
+        const int kb0 = z * P.kb_per_split;
+        const int nkb = min(P.num_kb, kb0 + P.kb_per_split) - kb0;
         const int nch = (nkb + chunk - 1) / chunk;
         for (int cc = 0; cc < nch && ok; ++cc, ++c) {
           const int buf = static_cast<int>(c & 1);
           if (c >= 2 && !mbar_wait(&tempty[buf], static_cast<uint32_t>((c - 2) >> 1) & 1u)) {
-            atomicExch(args.err, 1);
+            atomicExch(err, 1);
             ok = false;
             break;
           }
@@ -296,7 +321,7 @@ __global__ void __launch_bounds__(320, 1)
             const int s = static_cast<int>(it % STAGES);
             const uint32_t ph = static_cast<uint32_t>(it / STAGES) & 1u;
             if (!mbar_wait(&full[s], ph)) {
-              atomicExch(args.err, 1);
+              atomicExch(err, 1);
               ok = false;
               break;
             }
@@ -332,8 +357,9 @@ __global__ void __launch_bounds__(320, 1)
     long c = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < n_tiles_total && ok; t += gridDim.x) {
+      const TcProblem &args = grp.p[find_problem(grp, t)];
       int m_tile, n_tile, z;
-      tile_coords(args, t, m_tile, n_tile, z);
+      tile_coords(args, t - args.tile_start, m_tile, n_tile, z);
       const int kb0 = z * args.kb_per_split;
       const int nkb = min(args.num_kb, kb0 + args.kb_per_split) - kb0;
       const int nch = (nkb + chunk - 1) / chunk;
@@ -405,7 +431,7 @@ __global__ void __launch_bounds__(320, 1)
         __syncwarp();
       }
     }
-    if (!ok && lane == 0) atomicExch(args.err, 1);
+    if (!ok && lane == 0) atomicExch(err, 1);
   }
   tc_fence_before();
   __syncthreads();
@@ -445,7 +471,7 @@ CUtensorMap make_map(const void *base, long rows, long kp, int box_rows, bool bf
 }
 
 template <int BN, int STAGES, bool SPLIT, bool BF16>
-void launch(const TcDesc &g, cudaStream_t st, int *err) {
+void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
   constexpr int STAGE_BYTES = (BM * ROW_BYTES + BN * ROW_BYTES) * (SPLIT ? 2 : 1);
   // stages + barrier block (256 B) + 8 warps x 4 KB staging + alignment slack
   constexpr int SMEM = STAGES * STAGE_BYTES + 256 + 8 * 4096 + 1024;
@@ -457,45 +483,83 @@ void launch(const TcDesc &g, cudaStream_t st, int *err) {
     CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
     attr = true;
   }
-  const long mr = 2 * g.M;
-  CUtensorMap mA = make_map(g.A, mr, g.Kp, BM, BF16);
-  CUtensorMap mB = make_map(g.B, g.N, g.Kp, BN, BF16);
-  CUtensorMap mAlo = SPLIT ? make_map(g.Alo, mr, g.Kp, BM, BF16) : mA;
-  CUtensorMap mBlo = SPLIT ? make_map(g.Blo, g.N, g.Kp, BN, BF16) : mB;
-  TcArgs a;
-  a.M = g.M;
-  a.N = g.N;
-  a.num_kb = static_cast<int>(g.Kp / (BF16 ? 64 : 32));
-  const int sk = std::max(1, std::min(g.split_k, a.num_kb));
-  a.kb_per_split = (a.num_kb + sk - 1) / sk;
-  a.k_splits = (a.num_kb + a.kb_per_split - 1) / a.kb_per_split;
-  a.m_tiles = static_cast<int>((mr + BM - 1) / BM);
-  a.n_tiles = static_cast<int>((g.N + BN - 1) / BN);
-  // raster groups: as many A panels (128 rows x the K range of a split) as
-  // fit in ~24 MB of L2 share each B panel while it is resident
-  const double panel = static_cast<double>(BM) * a.kb_per_split * ROW_BYTES * (SPLIT ? 2 : 1);
-  a.group_m = static_cast<int>(std::max(1.0, std::min<double>(a.m_tiles, 24.0e6 / panel)));
-  a.chunk = (g.tier == TIER_TF32) ? 8 : 4;
-  a.out = g.out;
-  a.C = g.C;
-  a.cm = g.cm;
-  a.cn = g.cn;
-  a.ldc = g.ldc;
-  a.alpha = g.alpha;
-  a.beta = g.beta;
-  a.err = err;
   static int sms = 0;
   if (!sms) {
     int dev = 0;
     CUDA_CHECK(cudaGetDevice(&dev));
     CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   }
-  const long total = static_cast<long>(a.m_tiles) * a.n_tiles * a.k_splits;
-  if (total > 0x7fffffffL) fail(CC_ERR_ARG, "gemm_tc: too many tiles");
-  dim3 grid(static_cast<unsigned>(std::min<long>(total, sms)));
-  kern<<<grid, 320, SMEM, st>>>(mA, mAlo, mB, mBlo, a);
+  TcGroup grp;
+  std::memset(static_cast<void *>(&grp), 0, sizeof(grp));
+  long tiles = 0;
+  int np = 0;
+  for (int q = 0; q < n; ++q) {
+    const TcDesc &g = descs[q];
+    if (g.M <= 0 || g.N <= 0 || g.Kp <= 0) continue;
+    TcProblem &a = grp.p[np++];
+    const long mr = 2 * g.M;
+    a.mA = make_map(g.A, mr, g.Kp, BM, BF16);
+    a.mB = make_map(g.B, g.N, g.Kp, BN, BF16);
+    a.mAlo = SPLIT ? make_map(g.Alo, mr, g.Kp, BM, BF16) : a.mA;
+    a.mBlo = SPLIT ? make_map(g.Blo, g.N, g.Kp, BN, BF16) : a.mB;
+    a.M = g.M;
+    a.N = g.N;
+    a.num_kb = static_cast<int>(g.Kp / (BF16 ? 64 : 32));
+    const int sk = std::max(1, std::min(g.split_k, a.num_kb));
+    a.kb_per_split = (a.num_kb + sk - 1) / sk;
+    a.k_splits = (a.num_kb + a.kb_per_split - 1) / a.kb_per_split;
+    a.m_tiles = static_cast<int>((mr + BM - 1) / BM);
+    a.n_tiles = static_cast<int>((g.N + BN - 1) / BN);
+    // raster groups: as many A panels (128 rows x the K range of a split) as
+    // fit in ~24 MB of L2 share each B panel while it is resident
+    const double panel = static_cast<double>(BM) * a.kb_per_split * ROW_BYTES * (SPLIT ? 2 : 1);
+    a.group_m = g.group_m > 0 ? std::min(g.group_m, a.m_tiles)
+                              : static_cast<int>(std::max(1.0, std::min<double>(a.m_tiles, 24.0e6 / panel)));
+    a.out = g.out;
+    a.C = g.C;
+    a.cm = g.cm;
+    a.cn = g.cn;
+    a.ldc = g.ldc;
+    a.alpha = g.alpha;
+    a.beta = g.beta;
+    a.tile_start = static_cast<int>(tiles);
+    tiles += static_cast<long>(a.m_tiles) * a.n_tiles * a.k_splits;
+    if (tiles > 0x7fffffffL) fail(CC_ERR_ARG, "gemm_tc: too many tiles");
+  }
+  if (np == 0) return;
+  grp.nprob = np;
+  grp.total_tiles = static_cast<int>(tiles);
+  grp.chunk = descs[0].chunk > 0 ? descs[0].chunk : (descs[0].tier == TIER_TF32 ? 8 : 4);
+  grp.err = err;
+  dim3 grid(static_cast<unsigned>(std::min<long>(tiles, sms)));
+  kern<<<grid, 320, SMEM, st>>>(grp);
   LAUNCH_CHECK();
   count_launch();
+}
+
+void check_desc(const TcDesc &g) {
+  if (g.Kp % tc_k_align(g.tier)) fail(CC_ERR_ARG, "gemm_tc: Kp not padded");
+  if ((reinterpret_cast<uintptr_t>(g.A) | reinterpret_cast<uintptr_t>(g.B)) & 15)
+    fail(CC_ERR_ARG, "gemm_tc: operands must be 16-byte aligned");
+}
+
+void dispatch(const TcDesc *d, int n, bool wide, cudaStream_t st, int *err) {
+  switch (d[0].tier) {
+    case TIER_TF32:
+      if (wide) launch<256, 4, false, false>(d, n, st, err);
+      else launch<128, 6, false, false>(d, n, st, err);
+      break;
+    case TIER_TF32X3:
+      if (wide) launch<256, 2, true, false>(d, n, st, err);
+      else launch<128, 3, true, false>(d, n, st, err);
+      break;
+    case TIER_BF16X3:
+      if (wide) launch<256, 2, true, true>(d, n, st, err);
+      else launch<128, 3, true, true>(d, n, st, err);
+      break;
+    default:
+      fail(CC_ERR_ARG, "gemm_tc: bad tier");
+  }
 }
 
 }  // namespace
@@ -503,27 +567,156 @@ void launch(const TcDesc &g, cudaStream_t st, int *err) {
 int tc_k_align(int tier) { return tier == TIER_BF16X3 ? 64 : 32; }
 size_t tc_elem_bytes(int tier) { return tier == TIER_BF16X3 ? 2 : 4; }
 
-void gemm_tc(const TcDesc &g, cudaStream_t st, int *err) {
-  if (g.M <= 0 || g.N <= 0 || g.Kp <= 0) return;
-  if (g.Kp % tc_k_align(g.tier)) fail(CC_ERR_ARG, "gemm_tc: Kp not padded");
-  if ((reinterpret_cast<uintptr_t>(g.A) | reinterpret_cast<uintptr_t>(g.B)) & 15)
-    fail(CC_ERR_ARG, "gemm_tc: operands must be 16-byte aligned");
-  const bool wide = g.N >= 192;
-  switch (g.tier) {
-    case TIER_TF32:
-      if (wide) launch<256, 4, false, false>(g, st, err);
-      else launch<128, 6, false, false>(g, st, err);
-      break;
-    case TIER_TF32X3:
-      if (wide) launch<256, 2, true, false>(g, st, err);
-      else launch<128, 3, true, false>(g, st, err);
-      break;
-    case TIER_BF16X3:
-      if (wide) launch<256, 2, true, true>(g, st, err);
-      else launch<128, 3, true, true>(g, st, err);
-      break;
-    default:
-      fail(CC_ERR_ARG, "gemm_tc: bad tier");
+// ---------------------------------------------------------------------------
+// Autotuner: per (tier, shape bucket) the tile width, raster group and TMEM
+// promotion chunk are chosen by timing a few candidates once, on a scratch
+// FP32 output, when CDFNS_AUTOTUNE=1. Choices persist in the JSON file named
+// by CDFNS_TUNE_CACHE ({"key": [bn, group_m, chunk], ...}). Never runs while
+// the stream is being captured.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Choice {
+  int bn, group_m, chunk;
+};
+std::mutex g_tune_mu;
+std::map<std::string, Choice> g_tune;
+bool g_tune_loaded = false;
+
+long pow2_up(long x) {
+  long p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+std::string tune_key(const TcDesc &g) {
+  return std::to_string(g.tier) + ":" + std::to_string(pow2_up(2 * g.M)) + "x" +
+         std::to_string(pow2_up(g.N)) + "x" + std::to_string(pow2_up(g.Kp)) + ":" +
+         std::to_string(g.split_k > 1);
+}
+
+const char *tune_path() { return std::getenv("CDFNS_TUNE_CACHE"); }
+bool tune_enabled() {
+  const char *e = std::getenv("CDFNS_AUTOTUNE");
+  return e && e[0] == '1';
+}
+
+void tune_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char *p = tune_path();
+  if (!p) return;
+  FILE *f = std::fopen(p, "r");
+  if (!f) return;
+  char key[256];
+  int bn, gm, ch;
+  // format written by tune_save: one "key": [bn, group_m, chunk] per line
+  char line[512];
+  while (std::fgets(line, sizeof(line), f)) {
+    if (std::sscanf(line, " \"%255[^\"]\": [%d, %d, %d]", key, &bn, &gm, &ch) == 4)
+      g_tune[key] = Choice{bn, gm, ch};
+  }
+  std::fclose(f);
+}
+
+void tune_save() {
+  const char *p = tune_path();
+  if (!p) return;
+  FILE *f = std::fopen(p, "w");
+  if (!f) return;
+  std::fprintf(f, "{\n");
+  size_t i = 0;
+  for (const auto &kv : g_tune) {
+    std::fprintf(f, "  \"%s\": [%d, %d, %d]%s\n", kv.first.c_str(), kv.second.bn, kv.second.group_m,
+                 kv.second.chunk, ++i < g_tune.size() ? "," : "");
+  }
+  std::fprintf(f, "}\n");
+  std::fclose(f);
+}
+
+Choice tune(const TcDesc &g, cudaStream_t st, int *err) {
+  const int dch = g.tier == TIER_TF32 ? 8 : 4;
+  const Choice cands[] = {{256, 0, dch}, {256, 1, dch}, {256, 16, dch},
+                          {128, 0, dch}, {256, 0, 2 * dch}, {128, 1, dch}};
+  void *scratch = nullptr;
+  CUDA_CHECK(cudaMalloc(&scratch, sizeof(float2) * g.M * g.N));
+  cudaEvent_t e0, e1;
+  CUDA_CHECK(cudaEventCreate(&e0));
+  CUDA_CHECK(cudaEventCreate(&e1));
+  Choice best = cands[0];
+  float best_ms = 1e30f;
+  for (const Choice &c : cands) {
+    TcDesc t = g;
+    t.out = TC_OUT_F32;
+    t.C = scratch;
+    t.cm = t.cn = nullptr;
+    t.ldc = g.N;
+    t.bn = c.bn;
+    t.group_m = c.group_m;
+    t.chunk = c.chunk;
+    dispatch(&t, 1, c.bn == 256, st, err);  // warm
+    CUDA_CHECK(cudaEventRecord(e0, st));
+    dispatch(&t, 1, c.bn == 256, st, err);
+    CUDA_CHECK(cudaEventRecord(e1, st));
+    CUDA_CHECK(cudaEventSynchronize(e1));
+    float ms = 0;
+    CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(scratch);
+  return best;
+}
+
+}  // namespace
+
+void gemm_tc(const TcDesc &g0, cudaStream_t st, int *err) {
+  if (g0.M <= 0 || g0.N <= 0 || g0.Kp <= 0) return;
+  check_desc(g0);
+  TcDesc g = g0;
+  if (g.bn == 0 && (tune_enabled() || tune_path())) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load();
+    const std::string key = tune_key(g);
+    auto it = g_tune.find(key);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cap);
+    if (it == g_tune.end() && tune_enabled() && cap == cudaStreamCaptureStatusNone) {
+      g_tune[key] = tune(g, st, err);
+      tune_save();
+      it = g_tune.find(key);
+    }
+    if (it != g_tune.end()) {
+      g.bn = it->second.bn;
+      g.group_m = it->second.group_m;
+      g.chunk = it->second.chunk;
+    }
+  }
+  const bool wide = g.bn > 0 ? g.bn == 256 : g.N >= 192;
+  dispatch(&g, 1, wide, st, err);
+}
+
+void gemm_tc_grouped(const std::vector<TcDesc> &descs, cudaStream_t st, int *err) {
+  // one launch per (tier, width) class, at most MAX_PROBLEMS problems each
+  for (int tier = TIER_TF32; tier <= TIER_BF16X3; ++tier) {
+    for (int w = 0; w < 2; ++w) {
+      std::vector<TcDesc> cls;
+      for (const TcDesc &g : descs) {
+        if (g.tier != tier || g.M <= 0 || g.N <= 0 || g.Kp <= 0) continue;
+        const bool wide = g.bn > 0 ? g.bn == 256 : g.N >= 192;
+        if (wide != (w == 1)) continue;
+        check_desc(g);
+        cls.push_back(g);
+      }
+      for (size_t k = 0; k < cls.size(); k += MAX_PROBLEMS) {
+        const int n = static_cast<int>(std::min<size_t>(MAX_PROBLEMS, cls.size() - k));
+        dispatch(cls.data() + k, n, w == 1, st, err);
+      }
+    }
   }
 }
 

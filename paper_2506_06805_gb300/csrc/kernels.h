@@ -1,6 +1,8 @@
 // Internal kernel entry points (host launchers) of the library.
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace cdfns {
@@ -46,8 +48,15 @@ struct TcDesc {
   void *C = nullptr; const long *cm = nullptr, *cn = nullptr; long ldc = 0;
   cplx alpha = {1.0, 0.0}, beta = {0.0, 0.0};
   int split_k = 1;
+  // tile choices (0 = automatic): output tile width 128 or 256, m-tiles per
+  // raster group, K blocks per TMEM promotion chunk
+  int bn = 0, group_m = 0, chunk = 0;
 };
 void gemm_tc(const TcDesc &g, cudaStream_t st, int *err_flag);
+// Several independent GEMMs (any shapes, same or mixed tiers) in as few
+// persistent launches as possible: one per tier and tile width, up to 16
+// problems each, sharing one tile queue.
+void gemm_tc_grouped(const std::vector<TcDesc> &descs, cudaStream_t st, int *err_flag);
 // Padded K granularity (real elements) for a tier: 32 for tf32, 64 for bf16.
 int tc_k_align(int tier);
 size_t tc_elem_bytes(int tier);

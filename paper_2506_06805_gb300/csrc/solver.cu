@@ -64,8 +64,22 @@ void heevd(Allocator *al, cudaStream_t st, cplx *A, int n, double *w) {
   if (hinfo != 0) fail(CC_ERR_NUMERIC, "zheevd info " + std::to_string(hinfo));
 }
 
+void h2d(void *dst, const void *src, size_t n, cudaStream_t st) {
+  CUDA_CHECK(cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, st));
+}
+void d2h(void *dst, const void *src, size_t n, cudaStream_t st) {
+  CUDA_CHECK(cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, st));
+  CUDA_CHECK(cudaStreamSynchronize(st));
+}
+void d2d(void *dst, const void *src, size_t n, cudaStream_t st) {
+  CUDA_CHECK(cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, st));
+}
+void zero(void *dst, size_t n, cudaStream_t st) { CUDA_CHECK(cudaMemsetAsync(dst, 0, n, st)); }
+
+}  // namespace
+
 // General complex eigensolver (right vectors) on a column-major m x m matrix.
-void geev(Allocator *al, cudaStream_t st, cplx *A, int m, cplx *w, cplx *vr) {
+void geev_dev(Allocator *al, cudaStream_t st, cplx *A, int m, cplx *w, cplx *vr) {
   Solver &s = solver_for(st);
   size_t dbytes = 0, hbytes = 0;
   if (cusolverDnXgeev_bufferSize(s.h, s.p, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR, m,
@@ -87,19 +101,6 @@ void geev(Allocator *al, cudaStream_t st, cplx *A, int m, cplx *w, cplx *vr) {
   if (hinfo != 0) fail(CC_ERR_NUMERIC, "Xgeev info " + std::to_string(hinfo));
 }
 
-void h2d(void *dst, const void *src, size_t n, cudaStream_t st) {
-  CUDA_CHECK(cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, st));
-}
-void d2h(void *dst, const void *src, size_t n, cudaStream_t st) {
-  CUDA_CHECK(cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, st));
-  CUDA_CHECK(cudaStreamSynchronize(st));
-}
-void d2d(void *dst, const void *src, size_t n, cudaStream_t st) {
-  CUDA_CHECK(cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, st));
-}
-void zero(void *dst, size_t n, cudaStream_t st) { CUDA_CHECK(cudaMemsetAsync(dst, 0, n, st)); }
-
-}  // namespace
 
 // ===========================================================================
 // lifecycle
@@ -719,6 +720,7 @@ int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
 // ===========================================================================
 void Ctx::build_hbar() {
   eng.clear_pack_cache();
+  ++sig_gen;
   const int tr = int_tier() == TIER_FP64 ? TIER_FP64 : TIER_TF32X3;
   const long oo = static_cast<long>(o) * o, vv = static_cast<long>(v) * v, ov = static_cast<long>(o) * v;
   const long n2 = oo * vv;
@@ -822,194 +824,19 @@ void Ctx::build_hbar() {
 }
 
 // ===========================================================================
-// IP-EOM-CCSD sigma for k packed vectors (Eqs. 17-18)
+// IP-EOM-CCSD (Eqs. 17-18): sigma and Davidson live in eom.cu
 // ===========================================================================
 void Ctx::sigma(int k, const cplx *r, cplx *s) {
-  const int tr = eom();
-  const long oo = static_cast<long>(o) * o;
-  Buf r1(&al, sizeof(cplx) * k * o), r2(&al, sizeof(cplx) * k * oo * v);
-  Buf s1(&al, sizeof(cplx) * k * o), s2(&al, sizeof(cplx) * k * oo * v);
-  Buf x(&al, sizeof(cplx) * k * oo * v), xe(&al, sizeof(cplx) * k * v);
-  ip_unpack(r, k, o, v, r1.c(), r2.c(), st);
-  auto R1 = [&](const char *ix) { return T(r1.c(), ix, {k, o}); };
-  auto R2 = [&](const char *ix) { return T(r2.c(), ix, {k, o, o, v}); };
-  auto S1 = [&](const char *ix) { return T(s1.c(), ix, {k, o}); };
-  auto S2 = [&](const char *ix) { return T(s2.c(), ix, {k, o, o, v}); };
-  auto Xt = [&](const char *ix) { return T(x.c(), ix, {k, o, o, v}); };
-  // 1h (the diagonal of H_oo is applied exactly below)
-  eng.contract(Cr(-1), R1("Km"), T(Hoo_off.c(), "mi", {o, o}), C0(), S1("Ki"), TIER_FP64);
-  eng.contract(C1(), R2("Kime"), T(Hov.c(), "me", {o, v}), C1(), S1("Ki"), TIER_FP64);
-  eng.contract(Cr(-0.5), R2("Kmne"), stable(T(Hooov.c(), "mnie", {o, o, o, v})), C1(), S1("Ki"), tr);
-  // 2h1p; the one-body terms use the off-diagonal parts of H_vv and H_oo,
-  // whose elements are correlation-sized, and their diagonals in FP64 below
-  eng.contract(Cr(-1), R1("Km"), stable(T(Hovoo.c(), "mbij", {o, v, o, o})), C0(), S2("Kijb"), tr);
-  eng.contract(C1(), R2("Kije"), stable(T(Hvv_off.c(), "be", {v, v})), C1(), S2("Kijb"), tr);
-  eng.contract(C1(), stable(T(Hoo_off.c(), "mi", {o, o})), R2("Kmjb"), C0(), Xt("Kijb"), tr);
-  eng.permute_into(Cr(-1), Xt("Kijb"), C1(), S2("Kijb"));
-  eng.permute_into(C1(), Xt("Kjib"), C1(), S2("Kijb"));
-  eng.contract(Cr(0.5), R2("Kmnb"), stable(T(Hoooo.c(), "mnij", {o, o, o, o})), C1(), S2("Kijb"), tr);
-  eng.contract(C1(), R2("Kime"), stable(T(Hovvo.c(), "mbej", {o, v, v, o})), C0(), Xt("Kijb"), tr);
-  eng.permute_into(C1(), Xt("Kijb"), C1(), S2("Kijb"));
-  eng.permute_into(Cr(-1), Xt("Kjib"), C1(), S2("Kijb"));
-  // three-body part: X_e = 1/2 <mn||ef> r_mn^f ; -X_e t_ij^eb
-  eng.contract(Cr(0.5), R2("Kmnf"), stable(T(oovv.c(), "mnef", {o, o, v, v})), C0(), T(xe.c(), "Ke", {k, v}),
-               tr);
-  eng.contract(Cr(-1), T(xe.c(), "Ke", {k, v}), stable(T(t2.c(), "ijeb", {o, o, v, v})), C1(), S2("Kijb"), tr);
-  ip_diag_apply(r1.c(), r2.c(), doo.c(), dvv.c(), k, o, v, s1.c(), s2.c(), st);
-  ip_pack(s1.c(), s2.c(), k, o, v, s, st);
+  std::vector<Ctx *> one{this};
+  batch_sigma(one, {k}, {r}, {s}, false);
 }
 
-// ===========================================================================
-// block Davidson (FP64) for the n_roots lowest IP roots
-// ===========================================================================
 int Ctx::ipeom(int nr, double tol, int max_iter, double *omega, double *r1w, int *n_iter) {
-  if (!ccsd_done) fail(CC_ERR_STATE, "ipeom_solve needs a converged ccsd_solve");
   if (!(tol > 0) || max_iter < 1) fail(CC_ERR_ARG, "tol must be > 0 and max_iter >= 1");
-  const long dim = dim_ip();
-  if (nr < 1 || nr > dim || nr > 64) fail(CC_ERR_ARG, "n_roots out of range");
-  const double t0 = now_ms();
-  if (!hbar_done) build_hbar();
-  const int max_sp = static_cast<int>(std::min<long>(dim, std::max(8 * nr, 40)));
-  Buf V(&al, sizeof(cplx) * max_sp * dim), S(&al, sizeof(cplx) * max_sp * dim);
-  Buf d(&al, sizeof(cplx) * dim);
-  Buf Xr(&al, sizeof(cplx) * nr * dim), SX(&al, sizeof(cplx) * nr * dim), R(&al, sizeof(cplx) * nr * dim);
-  Buf G(&al, sizeof(cplx) * max_sp * max_sp), Gm(&al, sizeof(cplx) * max_sp * max_sp),
-      wv(&al, sizeof(cplx) * max_sp),
-      VR(&al, sizeof(cplx) * max_sp * max_sp);
-  Buf Ysel(&al, sizeof(cplx) * nr * max_sp), wsel(&al, sizeof(cplx) * nr), cproj(&al, sizeof(cplx) * nr * max_sp);
-  ip_diag(Hoo.c(), Hvv.c(), o, v, d.c(), st);
-  std::vector<cplx> dh(dim);
-  d2h(dh.data(), d.p, sizeof(cplx) * dim, st);
-  std::vector<long> idx(dim);
-  std::iota(idx.begin(), idx.end(), 0);
-  std::stable_sort(idx.begin(), idx.end(), [&](long a, long b) { return dh[a].x < dh[b].x; });
-  zero(V.p, sizeof(cplx) * nr * dim, st);
-  const cplx one = mk(1.0, 0.0);
-  for (int r = 0; r < nr; ++r) h2d(V.c() + r * dim + idx[r], &one, sizeof(cplx), st);
-  sigma(nr, V.c(), S.c());
-  int m = nr;
-  const long ld = max_sp;
-  // Gm holds G(a, b) = <v_a | sigma_b> column-major (Gm[b * ld + a]); only the
-  // rows and columns of newly added vectors are computed each iteration
-  auto g_block = [&](int b0, int nb, int a0, int na) {
-    eng.contract(C1(), T(S.c() + static_cast<long>(b0) * dim, "bd", {nb, dim}),
-                 conj(T(V.c() + static_cast<long>(a0) * dim, "ad", {na, dim})), C0(),
-                 Tv(Gm.c() + static_cast<long>(b0) * ld + a0, "ba", {nb, na}, {ld, 1}), TIER_FP64);
-  };
-  g_block(0, m, 0, m);
-  bool converged = false;
-  int it = 0;
-  std::vector<cplx> w_out(nr);
-  std::vector<double> rn(nr);
-  auto orth_new = [&](cplx *vecs, int nnew, int mbase) -> int {
-    // orthogonalise rows vecs[0..nnew) against V[0..mbase) (two passes) and
-    // among themselves; accepted rows are appended to V at mbase
-    if (mbase > 0) {
-      for (int pass = 0; pass < 2; ++pass) {
-        eng.contract(C1(), T(vecs, "rd", {nnew, dim}), conj(T(V.c(), "ad", {mbase, dim})), C0(),
-                     T(cproj.c(), "ra", {nnew, mbase}), TIER_FP64);
-        eng.contract(Cr(-1), T(cproj.c(), "ra", {nnew, mbase}), T(V.c(), "ad", {mbase, dim}), C1(),
-                     T(vecs, "rd", {nnew, dim}), TIER_FP64);
-      }
-    }
-    int acc = 0;
-    for (int j = 0; j < nnew; ++j) {
-      cplx *x = vecs + static_cast<long>(j) * dim;
-      for (int pass = 0; pass < 2; ++pass)
-        for (int i = 0; i < acc; ++i) {
-          cplx *y = V.c() + static_cast<long>(mbase + i) * dim;
-          const cplx c = dot(y, x, dim, true, st, red.c());
-          axpby(dim, mk(-c.x, -c.y), y, C1(), x, st);
-        }
-      const cplx n2 = dot(x, x, dim, true, st, red.c());
-      const double nrm = std::sqrt(std::max(n2.x, 0.0));
-      if (nrm < 1e-10) continue;
-      cplx *dst = V.c() + static_cast<long>(mbase + acc) * dim;
-      d2d(dst, x, sizeof(cplx) * dim, st);
-      axpby(dim, mk(1.0 / nrm, 0.0), dst, C0(), dst, st);
-      ++acc;
-    }
-    return acc;
-  };
-  for (it = 1; it <= max_iter; ++it) {
-    // projected matrix, column-major: G(a, b) = <v_a | sigma_b>
-    eng.permute_into(C1(), Tv(Gm.c(), "ba", {m, m}, {ld, 1}), C0(), T(G.c(), "ba", {m, m}));
-    geev(&al, st, G.c(), m, wv.c(), VR.c());
-    std::vector<cplx> wh(m), vh(static_cast<size_t>(m) * m);
-    d2h(wh.data(), wv.p, sizeof(cplx) * m, st);
-    d2h(vh.data(), VR.p, sizeof(cplx) * m * m, st);
-    std::vector<int> ord(m);
-    std::iota(ord.begin(), ord.end(), 0);
-    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return wh[a].x < wh[b].x; });
-    std::vector<cplx> ys(static_cast<size_t>(nr) * m);
-    for (int r = 0; r < nr; ++r) {
-      const int c = ord[r];
-      double nn = 0;
-      for (int a = 0; a < m; ++a) nn += vh[c * m + a].x * vh[c * m + a].x + vh[c * m + a].y * vh[c * m + a].y;
-      nn = 1.0 / std::sqrt(nn);
-      for (int a = 0; a < m; ++a) ys[r * m + a] = cscale(nn, vh[c * m + a]);
-      w_out[r] = wh[c];
-    }
-    h2d(Ysel.p, ys.data(), sizeof(cplx) * nr * m, st);
-    h2d(wsel.p, w_out.data(), sizeof(cplx) * nr, st);
-    eng.contract(C1(), T(Ysel.c(), "ra", {nr, m}), T(V.c(), "ad", {m, dim}), C0(),
-                 T(Xr.c(), "rd", {nr, dim}), TIER_FP64);
-    eng.contract(C1(), T(Ysel.c(), "ra", {nr, m}), T(S.c(), "ad", {m, dim}), C0(),
-                 T(SX.c(), "rd", {nr, dim}), TIER_FP64);
-    // R_r = SX_r - w_r X_r
-    d2d(R.p, SX.p, sizeof(cplx) * nr * dim, st);
-    bool all = true;
-    for (int r = 0; r < nr; ++r) {
-      axpby(dim, mk(-w_out[r].x, -w_out[r].y), Xr.c() + r * dim, C1(), R.c() + r * dim, st);
-      const cplx n2 = dot(R.c() + r * dim, R.c() + r * dim, dim, true, st, red.c());
-      rn[r] = std::sqrt(std::max(n2.x, 0.0));
-      if (!std::isfinite(rn[r])) fail(CC_ERR_NUMERIC, "Davidson residual NaN");
-      if (rn[r] >= tol) all = false;
-    }
-    if (all) {
-      converged = true;
-      break;
-    }
-    if (it == max_iter) break;
-    // correction vectors for the unconverged roots
-    std::vector<int> todo;
-    for (int r = 0; r < nr; ++r)
-      if (rn[r] >= tol) todo.push_back(r);
-    if (m + static_cast<int>(todo.size()) > max_sp) {
-      // restart from the Ritz vectors
-      Buf Xc(&al, sizeof(cplx) * nr * dim);
-      d2d(Xc.p, Xr.p, sizeof(cplx) * nr * dim, st);
-      m = orth_new(Xc.c(), nr, 0);
-      sigma(m, V.c(), S.c());
-      g_block(0, m, 0, m);
-      continue;
-    }
-    precondition(R.c(), wsel.c(), d.c(), nr, dim, SX.c(), st);  // reuse SX as scratch
-    Buf corr(&al, sizeof(cplx) * todo.size() * dim);
-    for (size_t j = 0; j < todo.size(); ++j)
-      d2d(corr.c() + j * dim, SX.c() + static_cast<long>(todo[j]) * dim, sizeof(cplx) * dim, st);
-    const int added = orth_new(corr.c(), static_cast<int>(todo.size()), m);
-    if (added == 0) break;
-    sigma(added, V.c() + static_cast<long>(m) * dim, S.c() + static_cast<long>(m) * dim);
-    g_block(m, added, 0, m + added);  // new columns
-    g_block(0, m, m, added);          // new rows
-    m += added;
-  }
-  if (it > max_iter) it = max_iter;
-  check_err_flag();
-  for (int r = 0; r < nr; ++r) {
-    omega[2 * r] = w_out[r].x;
-    omega[2 * r + 1] = w_out[r].y;
-    if (r1w) {
-      const cplx a = dot(Xr.c() + r * dim, Xr.c() + r * dim, o, true, st, red.c());
-      const cplx b = dot(Xr.c() + r * dim, Xr.c() + r * dim, dim, true, st, red.c());
-      r1w[r] = a.x / b.x;
-    }
-  }
-  if (n_iter) *n_iter = it;
-  stat[5] += now_ms() - t0;
-  stat[8] = it;
-  return converged ? CC_OK : CC_ERR_NOT_CONVERGED;
+  std::vector<Ctx *> one{this};
+  int status = CC_OK;
+  run_ipeom(one, nr, tol, max_iter, omega, r1w, n_iter, &status, use_graphs);
+  return status;
 }
 
 }  // namespace cdfns

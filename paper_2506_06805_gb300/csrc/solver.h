@@ -18,6 +18,7 @@ struct Ctx {
   Engine eng;
   int tier = TIER_FP64;
   int eom_tier = -1;  // -1: same as tier
+  bool use_graphs = true;  // replay the batched sigma from CUDA graphs
   int num_sms = 148;
   size_t slab_budget = size_t(4) << 30;  // bytes for ladder V slabs
 
@@ -46,6 +47,13 @@ struct Ctx {
   // pair tables (row-major i<j over o, a<b over v)
   Buf ij_i, ij_j, ab_a, ab_b;
   int pairs_o = -1, pairs_v = -1;
+
+  // persistent workspace of the batched sigma (kept for CUDA-graph replay)
+  struct SigmaWS {
+    long kcap = 0;
+    Buf rin, sout, r1, r2, s1, s2, tA, tB, tC, X1, X2, xe;
+  } sws;
+  long sig_gen = 0;  // bumped whenever H-bar or the sigma workspace changes
 
   std::vector<double> fns_occ;
   double stat[16] = {0};
@@ -80,6 +88,14 @@ struct Ctx {
     return b.c();
   }
 };
+
+// eom.cu: batched sigma, lockstep block Davidson, graph cache
+void batch_sigma(std::vector<Ctx *> &sys, const std::vector<int> &k,
+                 const std::vector<const cplx *> &r, const std::vector<cplx *> &s, bool use_graph);
+void run_ipeom(std::vector<Ctx *> &sys, int nr, double tol, int max_iter, double *omega,
+               double *r1w, int *n_iter, int *status, bool use_graph);
+void drop_graphs(const void *ctx);
+void geev_dev(Allocator *al, cudaStream_t st, cplx *A, int m, cplx *w, cplx *vr);
 
 }  // namespace cdfns
 

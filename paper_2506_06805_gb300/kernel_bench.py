@@ -3,6 +3,7 @@
     python -m paper_2506_06805_gb300.kernel_bench ladder --o 20 --v 160 --X 640
     python -m paper_2506_06805_gb300.kernel_bench gemm --M 4096 --N 4096 --K 4096
     python -m paper_2506_06805_gb300.kernel_bench fns --config fns --keep-frac 0.4
+    python -m paper_2506_06805_gb300.kernel_bench batch --n-sys 8 --roots 8
 
 ``ladder`` times cc_ladder_dev (1/2 sum_cd <ab||cd> tau_ij^cd with <ab||cd>
 formed from Cholesky vectors) and reports algorithmic TFLOP/s with the
@@ -12,6 +13,11 @@ symmetry-reduced count 8 [X v^3 (v-1)/2 + (v(v-1)/2)^2 o(o-1)/2].
 (cc_add_cholesky), reports the natural-spinor occupations and the count
 kept at the literal threshold, then runs FNS with the kept fraction,
 CCSD and IP-EOM in two tier pairs and compares their IPs.
+``batch`` builds the uneven batch of systems (n_occ 20-50, n_virt 150-400,
+n_aux = 4 n_virt, shapes and inputs from ``synth.batch_specs``), solves
+CCSD for each, then times IP-EOM for all of them one after another and as
+one batch (batched sigma in grouped launches, with and without CUDA graphs)
+and compares the roots.
 One JSON line per run.
 """
 from __future__ import annotations
@@ -27,7 +33,9 @@ def main():
 
     from . import System, synth, use_torch_memory, zgemm_dev
     p = argparse.ArgumentParser()
-    p.add_argument("what", choices=["ladder", "gemm", "fns"])
+    p.add_argument("what", choices=["ladder", "gemm", "fns", "batch"])
+    p.add_argument("--n-sys", type=int, default=8)
+    p.add_argument("--roots", type=int, default=8)
     p.add_argument("--config", default="fns")
     p.add_argument("--keep-frac", type=float, default=0.4)
     p.add_argument("--o", type=int, default=20)
@@ -45,6 +53,8 @@ def main():
     ev1 = torch.cuda.Event(enable_timing=True)
     if a.what == "fns":
         return fns_run(a)
+    if a.what == "batch":
+        return batch_run(a)
     if a.what == "ladder":
         eps, L = synth.make_system(a.o, a.v, a.X, seed=0, kramers=False)
         rng = np.random.default_rng(1)
@@ -134,6 +144,50 @@ def fns_run(a):
     out["runs"] = res
     out["max_dIP_tf32_vs_tf32x3"] = float(np.abs(np.array(res["tf32"]["ips"])
                                                  - np.array(res["tf32x3"]["ips"])).max())
+    print(json.dumps(out))
+
+
+def batch_run(a):
+    import time
+
+    import torch
+
+    from . import System, batch_ipeom, synth
+    specs = synth.batch_specs(a.n_sys)
+    systems = []
+    t0 = time.perf_counter()
+    for sp in specs:
+        rng = np.random.default_rng(sp.seed)
+        eps = synth.make_eps(rng, sp.n_occ, sp.n_virt)
+        L = synth.make_cholesky(rng, sp.n_occ + sp.n_virt, sp.n_aux)
+        s = System(eps, L, n_occ=sp.n_occ, tier="tf32", eom_tier="tf32x3")
+        del L
+        s.ccsd(tol=1e-8, max_iter=60)
+        systems.append(s)
+    torch.cuda.synchronize()
+    out = {"systems": [[sp.n_occ, sp.n_virt, sp.n_aux] for sp in specs],
+           "ccsd_all_s": time.perf_counter() - t0, "roots": a.roots}
+    # one at a time (a first untimed pass builds every system's H-bar)
+    for s in systems:
+        s.ipeom(a.roots, tol=1e-7, max_iter=100)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq = [np.sort_complex(s.ipeom(a.roots, tol=1e-7, max_iter=100)[0]) for s in systems]
+    torch.cuda.synchronize()
+    out["eom_sequential_s"] = time.perf_counter() - t0
+    for graphs in (False, True):
+        for s in systems:
+            s.set_graphs(graphs)
+        t0 = time.perf_counter()
+        w, _, it, status = batch_ipeom(systems, a.roots, tol=1e-7, max_iter=100)
+        torch.cuda.synchronize()
+        key = "eom_batched_graphs_s" if graphs else "eom_batched_s"
+        out[key] = time.perf_counter() - t0
+        out["max_dIP_batched_vs_sequential"] = float(max(
+            np.abs(np.sort_complex(w[q]) - seq[q]).max() for q in range(len(systems))))
+        out["davidson_iterations"] = [int(x) for x in it]
+    for s in systems:
+        s.close()
     print(json.dumps(out))
 
 

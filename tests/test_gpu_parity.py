@@ -91,7 +91,7 @@ def test_integral_dump_bit_exact():
             assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), block
 
 
-# --- the ladder (spec kernel) ---------------------------------------------
+# --- the particle-particle ladder (dominant CCSD term) ---------------------------------------------
 
 @pytest.mark.parametrize("tier", ["fp64", "tf32", "tf32x3", "bf16x3"])
 @pytest.mark.parametrize("o,v,X,budget", [(10, 30, 120, None), (6, 71, 97, 3 << 20)])
