@@ -230,6 +230,18 @@ int cc_zgemm_noalloc(int tier, long M, long N, long K, const double *A_dev,
                      const double *B_dev, double *C_dev);
 
 /*
+ * cc_selftest_conversions: checks, on the device, the library's integer-pipe
+ * FP64 -> FP32 narrowing (IEEE 754 round-to-nearest-even) and FP32 -> FP64
+ * widening against the hardware conversion instructions, for every value of
+ * x_dev[0..n) (device doubles, not modified). mismatches[0] receives the
+ * count of narrowing mismatches, mismatches[1] that of widening mismatches
+ * (host array of 2). NaN results compare as equal when both are NaN.
+ * Runs on the default stream and returns after it completes.
+ * Errors: CC_ERR_ARG (null pointer, n < 0), CC_ERR_CUDA.
+ */
+int cc_selftest_conversions(const double *x_dev, long n, long long *mismatches);
+
+/*
  * cc_dump_integrals: bit-reproducible FP64 evaluation of Eq. 23 for one
  * block (0: <ij||kl>, 1: <ij||ka>, 2: <ij||ab>, 3: <ia||bj>), host
  * complex128 output in row-major block order. The sum over P runs in

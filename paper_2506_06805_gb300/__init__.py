@@ -64,6 +64,8 @@ _SIGS = {
     "cc_residual_dev": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "ipeom_sigma_dev": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "cc_dump_integrals": (ctypes.c_int, [_P, ctypes.c_int, _D]),
+    "cc_selftest_conversions": (ctypes.c_int, [_P, ctypes.c_long,
+                                               ctypes.POINTER(ctypes.c_longlong)]),
     "cc_zgemm_dev": (ctypes.c_int, [ctypes.c_int, ctypes.c_long, ctypes.c_long,
                                     ctypes.c_long, _P, _P, _P]),
     "cc_zgemm_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_long, ctypes.c_long,
@@ -188,6 +190,15 @@ def batch_ipeom(systems, n_roots, tol=1e-7, max_iter=100, allow_unconverged=Fals
                               it.ctypes.data_as(_I), stt.ctypes.data_as(_I))
     _check(rc, systems[0]._ctx, (0, -5) if allow_unconverged else (0,))
     return w[..., 0] + 1j * w[..., 1], r1, it, stt
+
+
+def selftest_conversions(x):
+    """Mismatch counts (narrowing, widening) of the library's integer-pipe
+    FP64/FP32 conversions against the hardware ones over a device float64
+    tensor x."""
+    out = (ctypes.c_longlong * 2)()
+    _check(lib().cc_selftest_conversions(_P(x.data_ptr()), x.numel(), out))
+    return int(out[0]), int(out[1])
 
 
 def zgemm_noalloc(A, B, C, tier="fp64"):

@@ -346,6 +346,7 @@ int cc_zgemm_dev(int tier, long M, long N, long K, const double *A, const double
     cdfns::Buf err(&al, 16);
     CUDA_CHECK(cudaMemsetAsync(err.p, 0, 16, eng.st));
     eng.err_flag = err.as<int>();
+    eng.trace_init();
     using cdfns::T;
     eng.contract(cdfns::C1(), T(reinterpret_cast<const cdfns::cplx *>(A), "mk", {M, K}),
                  T(reinterpret_cast<const cdfns::cplx *>(B), "nk", {N, K}), cdfns::C0(),
@@ -354,6 +355,21 @@ int cc_zgemm_dev(int tier, long M, long N, long K, const double *A, const double
     CUDA_CHECK(cudaMemcpyAsync(&e, err.p, sizeof(int), cudaMemcpyDeviceToHost, eng.st));
     CUDA_CHECK(cudaStreamSynchronize(eng.st));
     if (e) cdfns::fail(CC_ERR_TIMEOUT, "bounded wait expired");
+    return CC_OK;
+  });
+}
+
+int cc_selftest_conversions(const double *x_dev, long n, long long *mismatches) {
+  if (!x_dev || n < 0 || !mismatches) return CC_ERR_ARG;
+  return guarded(nullptr, [&] {
+    cdfns::Buf bad(&cdfns::g_default_alloc, 2 * sizeof(unsigned long long));
+    const cudaStream_t st = cdfns::noalloc_stream();
+    cdfns::conversion_check(x_dev, n, bad.as<unsigned long long>(), st);
+    unsigned long long h[2];
+    CUDA_CHECK(cudaMemcpyAsync(h, bad.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    mismatches[0] = static_cast<long long>(h[0]);
+    mismatches[1] = static_cast<long long>(h[1]);
     return CC_OK;
   });
 }

@@ -17,6 +17,27 @@ inline unsigned grid_for(long n, int threads = 256) {
   for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < (n); \
        i += static_cast<long>(gridDim.x) * blockDim.x)
 
+// Sum over a block of 256 threads (deterministic order); the result is in
+// thread 0.
+__device__ double2 block_sum_cc(double2 v) {
+  __shared__ double2 sh[8];
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = l < 8 ? sh[l] : make_double2(0.0, 0.0);
+    for (int o = 4; o > 0; o >>= 1) {
+      v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+      v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+    }
+  }
+  return v;
+}
+
 // Row-major pair index of (i < j) among n items and its inverse.
 __host__ __device__ inline long pair_index(long i, long j, long n) {
   return i * (2 * n - i - 1) / 2 + (j - i - 1);
@@ -70,56 +91,88 @@ __global__ void split_kernel(const double2 *chunk, int np, int p0, int o, int v,
 
 // Elementwise kernels over [o][o][v][v] use a 2D grid: blockIdx.y walks the
 // (i, j) planes, threads walk (a, b) inside a plane (32-bit index math).
-__global__ void tau_kernel(const double2 *t1, const double2 *t2, double2 *out, int o, int v,
-                           double f) {
-  const int vv = v * v;
-  for (int ij = blockIdx.y; ij < o * o; ij += gridDim.y) {
-    const int i = ij / o, j = ij - (ij / o) * o;
-    const long base = static_cast<long>(ij) * vv;
-    for (int ab = blockIdx.x * blockDim.x + threadIdx.x; ab < vv; ab += gridDim.x * blockDim.x) {
-      const int a = ab / v, b = ab - (ab / v) * v;
-      const double2 x = csub(cmul(t1[i * v + a], t1[j * v + b]), cmul(t1[i * v + b], t1[j * v + a]));
-      out[base + ab] = cadd(t2[base + ab], cscale(f, x));
+// Doubles-sized forms built from t2 and a product of two t1 rows. One block
+// per (i, j) and 32 rows a; the rows t1[i][:], t1[j][:] sit in shared memory.
+//   ANTI: x_ab = t_ia t_jb - t_ib t_ja (tau), else x_ab = t_ia t_jb (Z)
+//   out0 = c0 t2 + f0 x, and out1 = t2 + f1 x when out1 is given.
+// F32 (tensor-core tiers, whose GEMMs round these operands to TF32/BF16 or
+// split them at FP32 level): the t1 products in FP32, converted on the
+// integer pipes, so each element costs only its FP64 additions.
+template <typename R>
+struct RowT;
+template <>
+struct RowT<float2> {
+  __device__ static float2 load(double2 x) { return make_float2(f64_to_f32(x.x), f64_to_f32(x.y)); }
+};
+template <>
+struct RowT<double2> {
+  __device__ static double2 load(double2 x) { return x; }
+};
+
+__device__ __forceinline__ float2 tmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 tmul(double2 a, double2 b) { return cmul(a, b); }
+__device__ __forceinline__ float2 tsub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 tsub(double2 a, double2 b) { return csub(a, b); }
+__device__ __forceinline__ double2 widen_scaled(float2 x, float f) {
+  return make_double2(f32_to_f64(f * x.x), f32_to_f64(f * x.y));
+}
+__device__ __forceinline__ double2 widen_scaled(double2 x, float f) { return cscale(f, x); }
+
+// exact c * x for c in {1, 1/2}: the halving lowers the exponent of a normal
+// number (integer pipes); zeros and values near the bottom of the range use
+// the FP64 multiply
+__device__ __forceinline__ double scale_c(double x, int half) {
+  if (!half) return x;
+  const long long b = __double_as_longlong(x);
+  const unsigned e = static_cast<unsigned>(b >> 52) & 0x7ffu;
+  if (e - 2u <= 0x7feu - 2u) return __longlong_as_double(b - (1LL << 52));
+  if ((static_cast<unsigned long long>(b) << 1) == 0ull) return x;
+  return 0.5 * x;
+}
+
+template <typename T, bool ANTI>
+__global__ void __launch_bounds__(256) t1t1_kernel(const double2 *__restrict__ t1,
+                                                   const double2 *__restrict__ t2, double2 *out0,
+                                                   double2 *out1, int o, int v, int c0_half,
+                                                   double c0, float f0, float f1) {
+  extern __shared__ __align__(16) unsigned char t1t1_sm[];
+  T *ti = reinterpret_cast<T *>(t1t1_sm);
+  T *tj = ti + v;
+  const int ij = blockIdx.y;
+  const int i = ij / o, j = ij - (ij / o) * o;
+  for (int b = threadIdx.x; b < v; b += blockDim.x) {
+    ti[b] = RowT<T>::load(t1[static_cast<long>(i) * v + b]);
+    tj[b] = RowT<T>::load(t1[static_cast<long>(j) * v + b]);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long base = static_cast<long>(ij) * v * v;
+  const int a_end = min(v, static_cast<int>(blockIdx.x) * 32 + 32);
+  for (int a = blockIdx.x * 32 + warp; a < a_end; a += 8) {
+    const T tia = ti[a], tja = tj[a];
+    const long row = base + static_cast<long>(a) * v;
+    for (int b = lane; b < v; b += 32) {
+      T x = tmul(tia, tj[b]);
+      if (ANTI) x = tsub(x, tmul(ti[b], tja));
+      const double2 t = t2[row + b];
+      const double2 p0 = widen_scaled(x, f0);
+      double2 r0;
+      if (c0_half >= 0) {
+        r0 = make_double2(scale_c(t.x, c0_half) + p0.x, scale_c(t.y, c0_half) + p0.y);
+      } else {
+        r0 = make_double2(c0 * t.x + p0.x, c0 * t.y + p0.y);
+      }
+      out0[row + b] = r0;
+      if (out1) {
+        const double2 p1 = widen_scaled(x, f1);
+        out1[row + b] = make_double2(t.x + p1.x, t.y + p1.y);
+      }
     }
   }
 }
 
-// Same with the t1 t1 part formed in FP32 (for the tensor-core tiers, whose
-// GEMMs round these operands to TF32/BF16 anyway; GB300's FP64 rate is low).
-__global__ void tau32_kernel(const double2 *t1, const double2 *t2, double2 *out, int o, int v,
-                             float f) {
-  const int vv = v * v;
-  for (int ij = blockIdx.y; ij < o * o; ij += gridDim.y) {
-    const int i = ij / o, j = ij - (ij / o) * o;
-    const long base = static_cast<long>(ij) * vv;
-    for (int ab = blockIdx.x * blockDim.x + threadIdx.x; ab < vv; ab += gridDim.x * blockDim.x) {
-      const int a = ab / v, b = ab - (ab / v) * v;
-      const double2 p = t1[i * v + a], q = t1[j * v + b], r = t1[i * v + b], s = t1[j * v + a];
-      const float2 pf = make_float2(static_cast<float>(p.x), static_cast<float>(p.y));
-      const float2 qf = make_float2(static_cast<float>(q.x), static_cast<float>(q.y));
-      const float2 rf = make_float2(static_cast<float>(r.x), static_cast<float>(r.y));
-      const float2 sf = make_float2(static_cast<float>(s.x), static_cast<float>(s.y));
-      const float xr = (pf.x * qf.x - pf.y * qf.y) - (rf.x * sf.x - rf.y * sf.y);
-      const float xi = (pf.x * qf.y + pf.y * qf.x) - (rf.x * sf.y + rf.y * sf.x);
-      const double2 t = t2[base + ab];
-      out[base + ab] = make_double2(t.x + static_cast<double>(f * xr), t.y + static_cast<double>(f * xi));
-    }
-  }
-}
-
-__global__ void z_kernel(const double2 *t1, const double2 *t2, double2 *out, int o, int v,
-                         double c2) {
-  // out[j][n][f][b] = c2 t2[j][n][f][b] + t1[j][f] t1[n][b]
-  const int vv = v * v;
-  for (int jn = blockIdx.y; jn < o * o; jn += gridDim.y) {
-    const int j = jn / o, n = jn - (jn / o) * o;
-    const long base = static_cast<long>(jn) * vv;
-    for (int fb = blockIdx.x * blockDim.x + threadIdx.x; fb < vv; fb += gridDim.x * blockDim.x) {
-      const int f = fb / v, b = fb - (fb / v) * v;
-      out[base + fb] = cadd(cscale(c2, t2[base + fb]), cmul(t1[j * v + f], t1[n * v + b]));
-    }
-  }
-}
 
 __global__ void jacobi_kernel(const double2 *R1, const double2 *R2, const double *eps, int o, int v,
                               double2 *t1, double2 *t2) {
@@ -184,24 +237,135 @@ __global__ void pack_amps_kernel(const double2 *t1, const double2 *t2, int o, in
   }
 }
 
-__global__ void unpack_amps_kernel(const double2 *vec, int o, int v, double2 *t1, double2 *t2) {
+// Full t1, t2 from the packed unique amplitudes. Block: one (i, j) row and
+// 8 rows a; lanes run along b. The four images of a unique element differ
+// by sign only, applied to the sign bits.
+__device__ __forceinline__ double2 neg_if(double2 x, bool neg) {
+  if (!neg) return x;
+  return make_double2(__longlong_as_double(__double_as_longlong(x.x) ^ (1LL << 63)),
+                      __longlong_as_double(__double_as_longlong(x.y) ^ (1LL << 63)));
+}
+
+__global__ void __launch_bounds__(256) unpack_amps_kernel(const double2 *__restrict__ vec, int o,
+                                                          int v, double2 *t1, double2 *t2) {
   const long n1 = static_cast<long>(o) * v;
   const long nab = static_cast<long>(v) * (v - 1) / 2;
-  const long total = static_cast<long>(o) * o * v * v;
-  GRID_STRIDE(idx, total) {
-    const int b = static_cast<int>(idx % v);
-    const int a = static_cast<int>((idx / v) % v);
-    const int j = static_cast<int>((idx / (static_cast<long>(v) * v)) % o);
-    const int i = static_cast<int>(idx / (static_cast<long>(v) * v * o));
-    double2 x = make_double2(0.0, 0.0);
-    if (i != j && a != b) {
-      const int ii = min(i, j), jj = max(i, j), aa = min(a, b), bb = max(a, b);
-      const double s = ((i < j) == (a < b)) ? 1.0 : -1.0;
-      x = cscale(s, vec[n1 + pair_index(ii, jj, o) * nab + pair_index(aa, bb, v)]);
-    }
-    t2[idx] = x;
-    if (idx < n1) t1[idx] = vec[idx];
+  const int ij = blockIdx.y;
+  const int i = ij / o, j = ij - (ij / o) * o;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int a = blockIdx.x * 8 + warp;
+  if (blockIdx.x == 0 && ij == 0)
+    for (long k = threadIdx.x; k < n1; k += blockDim.x) t1[k] = vec[k];
+  if (a >= v) return;
+  double2 *out = t2 + (static_cast<long>(ij) * v + a) * v;
+  if (i == j) {
+    for (int b = lane; b < v; b += 32) out[b] = make_double2(0.0, 0.0);
+    return;
   }
+  const int ii = min(i, j), jj = max(i, j);
+  const double2 *row = vec + n1 + pair_index(ii, jj, o) * nab;
+  for (int b = lane; b < v; b += 32) {
+    double2 x = make_double2(0.0, 0.0);
+    if (a != b) {
+      const int aa = min(a, b), bb = max(a, b);
+      x = neg_if(row[pair_index(aa, bb, v)], (i < j) != (a < b));
+    }
+    out[b] = x;
+  }
+}
+
+// 1 / D for every packed amplitude: e_i - e_a (singles), e_i + e_j - e_a -
+// e_b (doubles); computed once per solve, in FP64.
+__global__ void amp_denoms_kernel(const double *eps, int o, int v, const int *ij_i, const int *ij_j,
+                                  const int *ab_a, const int *ab_b, double *inv) {
+  const long n1 = static_cast<long>(o) * v;
+  const long nab = static_cast<long>(v) * (v - 1) / 2;
+  const long nij = static_cast<long>(o) * (o - 1) / 2;
+  const long total = n1 + nij * nab;
+  GRID_STRIDE(idx, total) {
+    double d;
+    if (idx < n1) {
+      const int i = static_cast<int>(idx / v), a = static_cast<int>(idx - (idx / v) * v);
+      d = eps[i] - eps[o + a];
+    } else {
+      const long q = idx - n1;
+      const long pij = q / nab, pab = q - pij * nab;
+      d = eps[ij_i[pij]] + eps[ij_j[pij]] - eps[o + ab_a[pab]] - eps[o + ab_b[pab]];
+    }
+    inv[idx] = 1.0 / d;
+  }
+}
+
+// Jacobi step straight into the packed vector: vec = R * (1/D) over the
+// unique amplitudes. Grid (pab chunks, pij) for the doubles; the first row
+// of blocks also does the singles.
+__global__ void __launch_bounds__(256) jacobi_packed_kernel(
+    const double2 *__restrict__ R1, const double2 *__restrict__ R2, const double *__restrict__ inv,
+    int o, int v, const int *__restrict__ ij_i, const int *__restrict__ ij_j,
+    const int *__restrict__ ab_a, const int *__restrict__ ab_b, double2 *vec) {
+  const long n1 = static_cast<long>(o) * v;
+  const long nab = static_cast<long>(v) * (v - 1) / 2;
+  const int pij = blockIdx.y;
+  if (pij == 0)
+    for (long k = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; k < n1;
+         k += static_cast<long>(gridDim.x) * blockDim.x) {
+      const double2 r = R1[k];
+      vec[k] = make_double2(r.x * inv[k], r.y * inv[k]);
+    }
+  const int i = ij_i[pij], j = ij_j[pij];
+  const double2 *Rij = R2 + (static_cast<long>(i) * o + j) * v * v;
+  const long base = n1 + pij * nab;
+  for (long pab = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; pab < nab;
+       pab += static_cast<long>(gridDim.x) * blockDim.x) {
+    const double2 r = Rij[static_cast<long>(ab_a[pab]) * v + ab_b[pab]];
+    const double w = inv[base + pab];
+    vec[base + pab] = make_double2(r.x * w, r.y * w);
+  }
+}
+
+// E = sum over i<j, a<b of <ij||ab> (t_ij^ab + t_i^a t_j^b - t_i^b t_j^a)
+// from the packed amplitudes (Eq. 15 restricted to unique elements: the
+// four images of each give the 1/4 and 1/2 prefactors); FP64 sums, block
+// partials in partial[blockIdx.y * gridDim.x + blockIdx.x]. F32: the small
+// t1 t1 products in FP32.
+template <bool F32>
+__global__ void __launch_bounds__(256) energy_packed_kernel(
+    const double2 *__restrict__ oovv, const double2 *__restrict__ vec, int o, int v,
+    const int *__restrict__ ij_i, const int *__restrict__ ij_j, const int *__restrict__ ab_a,
+    const int *__restrict__ ab_b, double2 *partial) {
+  const long n1 = static_cast<long>(o) * v;
+  const long nab = static_cast<long>(v) * (v - 1) / 2;
+  const int pij = blockIdx.y;
+  const int i = ij_i[pij], j = ij_j[pij];
+  const double2 *g = oovv + (static_cast<long>(i) * o + j) * v * v;
+  const double2 *tp = vec + n1 + pij * nab;
+  const double2 *ti = vec + static_cast<long>(i) * v, *tj = vec + static_cast<long>(j) * v;
+  double2 acc = make_double2(0.0, 0.0);
+  for (long pab = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; pab < nab;
+       pab += static_cast<long>(gridDim.x) * blockDim.x) {
+    const int a = ab_a[pab], b = ab_b[pab];
+    double2 tau = tp[pab];
+    if (F32) {
+      const double2 p = ti[a], q = tj[b], r = ti[b], u = tj[a];
+      const float px = f64_to_f32(p.x), py = f64_to_f32(p.y), qx = f64_to_f32(q.x),
+                  qy = f64_to_f32(q.y), rx = f64_to_f32(r.x), ry = f64_to_f32(r.y),
+                  ux = f64_to_f32(u.x), uy = f64_to_f32(u.y);
+      tau.x += f32_to_f64((px * qx - py * qy) - (rx * ux - ry * uy));
+      tau.y += f32_to_f64((px * qy + py * qx) - (rx * uy + ry * ux));
+    } else {
+      tau = cadd(tau, csub(cmul(ti[a], tj[b]), cmul(ti[b], tj[a])));
+    }
+    acc = cfma(g[static_cast<long>(a) * v + b], tau, acc);
+  }
+  acc = block_sum_cc(acc);
+  if (threadIdx.x == 0) partial[static_cast<long>(blockIdx.y) * gridDim.x + blockIdx.x] = acc;
+}
+
+__global__ void sum_partials_kernel(const double2 *partial, long np, double2 *res) {
+  double2 acc = make_double2(0.0, 0.0);
+  for (long k = threadIdx.x; k < np; k += blockDim.x) acc = cadd(acc, partial[k]);
+  acc = block_sum_cc(acc);
+  if (threadIdx.x == 0) *res = acc;
 }
 
 __global__ void diis_solve_kernel(const double2 *B, int m, int ldb, double2 *coef, int *status) {
@@ -528,20 +692,45 @@ inline dim3 grid2d(int o, int v) {
   return dim3(gx, gy);
 }
 
-void make_tau(const cplx *t1, const cplx *t2, cplx *out, int o, int v, double f, cudaStream_t st,
-              bool fp32_t1) {
-  if (fp32_t1)
-    tau32_kernel<<<grid2d(o, v), 256, 0, st>>>(t1, t2, out, o, v, static_cast<float>(f));
+namespace {
+template <bool ANTI>
+void t1t1_launch(const cplx *t1, const cplx *t2, cplx *out0, cplx *out1, int o, int v, double c0,
+                 double f0, double f1, bool f32, cudaStream_t st) {
+  if (o <= 0 || v <= 0) return;
+  if (static_cast<long>(o) * o > 65535) fail(CC_ERR_ARG, "t1t1: n_occ too large");
+  const int c0_half = c0 == 1.0 ? 0 : (c0 == 0.5 ? 1 : -1);
+  dim3 grid(static_cast<unsigned>((v + 31) / 32), static_cast<unsigned>(o * o));
+  const size_t sm = 2 * static_cast<size_t>(v) * (f32 ? sizeof(float2) : sizeof(double2));
+  if (sm > 48 * 1024) {
+    CUDA_CHECK(cudaFuncSetAttribute(f32 ? t1t1_kernel<float2, ANTI> : t1t1_kernel<double2, ANTI>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(sm)));
+  }
+  if (f32)
+    t1t1_kernel<float2, ANTI><<<grid, 256, sm, st>>>(t1, t2, out0, out1, o, v, c0_half, c0,
+                                                     static_cast<float>(f0), static_cast<float>(f1));
   else
-    tau_kernel<<<grid2d(o, v), 256, 0, st>>>(t1, t2, out, o, v, f);
+    t1t1_kernel<double2, ANTI><<<grid, 256, sm, st>>>(t1, t2, out0, out1, o, v, c0_half, c0,
+                                                      static_cast<float>(f0), static_cast<float>(f1));
   LAUNCH_CHECK();
   count_launch();
 }
+}  // namespace
 
-void make_z(const cplx *t1, const cplx *t2, cplx *out, int o, int v, double c2, cudaStream_t st) {
-  z_kernel<<<grid2d(o, v), 256, 0, st>>>(t1, t2, out, o, v, c2);
-  LAUNCH_CHECK();
-  count_launch();
+void make_tau(const cplx *t1, const cplx *t2, cplx *out, int o, int v, double f, cudaStream_t st,
+              bool fp32_t1) {
+  if (!fp32_t1 && f != 1.0 && f != 0.5) fail(CC_ERR_ARG, "make_tau: f must be 1 or 1/2");
+  t1t1_launch<true>(t1, t2, out, nullptr, o, v, 1.0, f, 0.0, fp32_t1, st);
+}
+
+void make_tau_pair(const cplx *t1, const cplx *t2, cplx *tau, cplx *taut, int o, int v,
+                   cudaStream_t st, bool fp32_t1) {
+  t1t1_launch<true>(t1, t2, tau, taut, o, v, 1.0, 1.0, 0.5, fp32_t1, st);
+}
+
+void make_z(const cplx *t1, const cplx *t2, cplx *out, int o, int v, double c2, cudaStream_t st,
+            bool fp32_t1) {
+  t1t1_launch<false>(t1, t2, out, nullptr, o, v, c2, 1.0, 0.0, fp32_t1, st);
 }
 
 void jacobi(const cplx *R1, const cplx *R2, const double *eps, int o, int v, cplx *t1, cplx *t2,
@@ -570,9 +759,66 @@ void pack_amps(const cplx *t1, const cplx *t2, int o, int v, const int *ij_i, co
 }
 
 void unpack_amps(const cplx *vec, int o, int v, cplx *t1, cplx *t2, cudaStream_t st) {
-  unpack_amps_kernel<<<grid_for(static_cast<long>(o) * o * v * v), 256, 0, st>>>(vec, o, v, t1, t2);
+  if (o <= 0 || v <= 0) return;
+  if (static_cast<long>(o) * o > 65535) fail(CC_ERR_ARG, "unpack_amps: n_occ too large");
+  dim3 grid(static_cast<unsigned>((v + 7) / 8), static_cast<unsigned>(o * o));
+  unpack_amps_kernel<<<grid, 256, 0, st>>>(vec, o, v, t1, t2);
   LAUNCH_CHECK();
   count_launch();
+}
+
+void amp_denoms(const double *eps, int o, int v, const int *ij_i, const int *ij_j, const int *ab_a,
+                const int *ab_b, double *inv, cudaStream_t st) {
+  const long n = static_cast<long>(o) * v +
+                 static_cast<long>(o) * (o - 1) / 2 * (static_cast<long>(v) * (v - 1) / 2);
+  amp_denoms_kernel<<<grid_for(n), 256, 0, st>>>(eps, o, v, ij_i, ij_j, ab_a, ab_b, inv);
+  LAUNCH_CHECK();
+  count_launch();
+}
+
+namespace {
+dim3 pair_grid(int o, int v) {
+  const long nij = static_cast<long>(o) * (o - 1) / 2;
+  const long nab = static_cast<long>(v) * (v - 1) / 2;
+  if (nij > 65535) fail(CC_ERR_ARG, "packed amplitudes: n_occ too large");
+  const long gx = std::max<long>(1, std::min<long>((nab + 255) / 256, std::max<long>(1, 4096 / std::max<long>(nij, 1))));
+  return dim3(static_cast<unsigned>(gx), static_cast<unsigned>(std::max<long>(nij, 1)));
+}
+}  // namespace
+
+void jacobi_packed(const cplx *R1, const cplx *R2, const double *inv, int o, int v, const int *ij_i,
+                   const int *ij_j, const int *ab_a, const int *ab_b, cplx *vec, cudaStream_t st) {
+  if (o <= 0 || v <= 0) return;
+  jacobi_packed_kernel<<<pair_grid(o, v), 256, 0, st>>>(R1, R2, inv, o, v, ij_i, ij_j, ab_a, ab_b,
+                                                       vec);
+  LAUNCH_CHECK();
+  count_launch();
+}
+
+long energy_scratch_len(int o, int v) {
+  const dim3 g = pair_grid(o, v);
+  return static_cast<long>(g.x) * g.y;
+}
+
+void energy_packed(const cplx *oovv, const cplx *vec, int o, int v, const int *ij_i,
+                   const int *ij_j, const int *ab_a, const int *ab_b, bool f32, cplx *scratch,
+                   long scratch_len, cplx *res, cudaStream_t st) {
+  const long nij = static_cast<long>(o) * (o - 1) / 2;
+  if (nij == 0 || v < 2) {
+    CUDA_CHECK(cudaMemsetAsync(res, 0, sizeof(cplx), st));
+    return;
+  }
+  dim3 grid = pair_grid(o, v);
+  while (static_cast<long>(grid.x) * grid.y > scratch_len && grid.x > 1) grid.x = (grid.x + 1) / 2;
+  if (static_cast<long>(grid.x) * grid.y > scratch_len) fail(CC_ERR_ARG, "energy: scratch too small");
+  if (f32)
+    energy_packed_kernel<true><<<grid, 256, 0, st>>>(oovv, vec, o, v, ij_i, ij_j, ab_a, ab_b, scratch);
+  else
+    energy_packed_kernel<false><<<grid, 256, 0, st>>>(oovv, vec, o, v, ij_i, ij_j, ab_a, ab_b, scratch);
+  LAUNCH_CHECK();
+  sum_partials_kernel<<<1, 256, 0, st>>>(scratch, static_cast<long>(grid.x) * grid.y, res);
+  LAUNCH_CHECK();
+  count_launch(2);
 }
 
 void diis_solve(const cplx *B, int m, int ldb, cplx *coef, int *status, cudaStream_t st) {

@@ -18,9 +18,12 @@ void split_cholesky(const cplx *chunk, int np, int p0, int o, int v, cplx *Loo, 
 // fp32_t1: form the t1 t1 part in FP32 (tensor-core tiers only)
 void make_tau(const cplx *t1, const cplx *t2, cplx *out, int o, int v, double f,
               cudaStream_t st, bool fp32_t1 = false);
+// tau (f = 1) and tau~ (f = 1/2) in one pass over t2
+void make_tau_pair(const cplx *t1, const cplx *t2, cplx *tau, cplx *taut, int o, int v,
+                   cudaStream_t st, bool fp32_t1 = false);
 // out[jnfb] = c2 * t2[jnfb] + t1[jf] t1[nb]
 void make_z(const cplx *t1, const cplx *t2, cplx *out, int o, int v, double c2,
-            cudaStream_t st);
+            cudaStream_t st, bool fp32_t1 = false);
 // t_new = R / D with D from eps (FP64); exact zeros on i=j or a=b.
 void jacobi(const cplx *R1, const cplx *R2, const double *eps, int o, int v, cplx *t1,
             cplx *t2, cudaStream_t st);
@@ -31,6 +34,18 @@ void mp2_amplitudes(const cplx *oovv, const double *eps, int o, int v, cplx *t1,
 void pack_amps(const cplx *t1, const cplx *t2, int o, int v, const int *ij_i, const int *ij_j,
                const int *ab_a, const int *ab_b, cplx *vec, cudaStream_t st);
 void unpack_amps(const cplx *vec, int o, int v, cplx *t1, cplx *t2, cudaStream_t st);
+// inv[k] = 1 / D_k for the packed amplitudes (FP64)
+void amp_denoms(const double *eps, int o, int v, const int *ij_i, const int *ij_j, const int *ab_a,
+                const int *ab_b, double *inv, cudaStream_t st);
+// vec = packed(R) * inv (the Jacobi step, unique amplitudes only)
+void jacobi_packed(const cplx *R1, const cplx *R2, const double *inv, int o, int v, const int *ij_i,
+                   const int *ij_j, const int *ab_a, const int *ab_b, cplx *vec, cudaStream_t st);
+long energy_scratch_len(int o, int v);
+// *res = sum_{i<j,a<b} <ij||ab> (t_ij^ab + t_i^a t_j^b - t_i^b t_j^a) from a
+// packed vector (the CCSD energy, Eq. 15); scratch holds block partials.
+void energy_packed(const cplx *oovv, const cplx *vec, int o, int v, const int *ij_i,
+                   const int *ij_j, const int *ab_a, const int *ab_b, bool f32, cplx *scratch,
+                   long scratch_len, cplx *res, cudaStream_t st);
 // Weighted squared norm helpers are done with dot() on packed vectors.
 
 // --- DIIS ------------------------------------------------------------------------

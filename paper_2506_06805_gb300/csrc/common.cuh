@@ -30,6 +30,44 @@ __host__ __device__ inline cplx cfma(cplx a, cplx b, cplx c) {  // a*b + c
   return c;
 }
 
+// FP64 <-> FP32 conversions on the integer pipes. On GB300 the hardware
+// conversion instructions run at the FP64 rate (about 2 per SM clock,
+// measured), some 60x slower than FP32 or INT32 arithmetic, so every kernel
+// that narrows FP64 operands or widens FP32 results uses these instead.
+//
+// Narrowing with round-to-nearest-even, bit-identical to __double2float_rn:
+// the 52-bit mantissa keeps its top 23 bits and the 29 dropped bits decide
+// the rounding (a carry out of the mantissa increments the exponent, and
+// out of the largest exponent gives infinity, as IEEE 754 rounding does).
+// Zeros are handled in place; results outside the FP32 normal range
+// (denormals, infinities, NaN) take the hardware instruction.
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const unsigned hi = static_cast<unsigned>(b >> 32), lo = static_cast<unsigned>(b);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  if (e - 897u <= 1150u - 897u) {
+    unsigned f = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1fffffffu;
+    f += (rest > 0x10000000u || (rest == 0x10000000u && (f & 1u))) ? 1u : 0u;
+    return __uint_as_float(f);
+  }
+  if (((hi & 0x7fffffffu) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
+  return __double2float_rn(x);
+}
+
+// Widening (exact): exponent rebiased by 1023 - 127, mantissa shifted into
+// place. Zeros in place; FP32 denormals, infinities and NaN in hardware.
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e - 1u <= 253u) {
+    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+    return __hiloint2double(static_cast<int>(hi), static_cast<int>(u << 29));
+  }
+  if ((u & 0x7fffffffu) == 0u) return __hiloint2double(static_cast<int>(u & 0x80000000u), 0);
+  return static_cast<double>(x);
+}
+
 // Error raised inside the library; carries a CC_ERR_* code.
 struct Error {
   int code;

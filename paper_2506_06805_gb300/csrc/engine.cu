@@ -1,5 +1,8 @@
 #include "engine.h"
 
+#include <cstdio>
+#include <cstdlib>
+
 #include <algorithm>
 #include <sstream>
 #include <tuple>
@@ -118,6 +121,59 @@ bool Engine::prepare(cplx alpha, const TRef &A, const TRef &B, cplx beta, const 
   return run(alpha, A, B, beta, C, tier, slot, out);
 }
 
+void Engine::trace_init() {
+  const char *p = std::getenv("CDFNS_TRACE");
+  trace_on_ = p && p[0];
+  if (trace_on_) trace_path_ = p;
+}
+
+int Engine::trace_open(const std::string &label, long M, long N, long K, int tier) {
+  if (!trace_on_) return -1;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cap);
+  if (cap != cudaStreamCaptureStatusNone) return -1;
+  TraceRec r{label, M, N, K, tier, nullptr, nullptr, false};
+  CUDA_CHECK(cudaEventCreate(&r.e0));
+  CUDA_CHECK(cudaEventCreate(&r.e1));
+  CUDA_CHECK(cudaEventRecord(r.e0, st));
+  trace_.push_back(r);
+  return static_cast<int>(trace_.size()) - 1;
+}
+
+void Engine::trace_close(int rec) {
+  if (rec < 0 || rec >= static_cast<int>(trace_.size())) return;
+  CUDA_CHECK(cudaEventRecord(trace_[rec].e1, st));
+  trace_[rec].closed = true;
+}
+
+Engine::Region Engine::region(const std::string &label) {
+  return Region{this, trace_open(label, 0, 0, 0, -1), trace_epoch_};
+}
+
+Engine::Region::~Region() {
+  if (rec >= 0 && epoch == e->trace_epoch_) e->trace_close(rec);
+}
+
+void Engine::trace_flush() {
+  if (!trace_on_ || trace_.empty()) return;
+  FILE *f = std::fopen(trace_path_.c_str(), "a");
+  for (TraceRec &r : trace_) {
+    float ms = -1.0f;
+    if (r.closed && cudaEventSynchronize(r.e1) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, r.e0, r.e1) != cudaSuccess)
+      ms = -1.0f;
+    if (f && r.closed)
+      std::fprintf(f, "%s,%ld,%ld,%ld,%d,%.4f\n", r.label.c_str(), r.M, r.N, r.K, r.tier,
+                   static_cast<double>(ms));
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+  }
+  if (f) std::fclose(f);
+  cudaGetLastError();
+  trace_.clear();
+  ++trace_epoch_;
+}
+
 bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef &C, int tier,
                  int slot, TcDesc *out) {
   std::vector<long> mdim, amstr, cmstr, ndim, bnstr, cnstr, kdim, akstr, bkstr;
@@ -160,6 +216,13 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
   for (long d : kdim) K *= d;
   if (M == 0 || N == 0) return false;
   flops += 8.0 * M * N * K;
+  const bool tiny = static_cast<double>(M) * N * K < 2.0e6 || K < 16 || M < 8 || N < 8;
+  const int trec =
+      trace_on_ ? trace_open((out ? "prep " : "") + A.idx + (A.conj ? "*" : "") + "," + B.idx +
+                                 (B.conj ? "*" : "") + "->" + C.idx,
+                             M, N, K, tiny ? 0 : tier)
+                : -1;
+  Region closer{this, trec, trace_epoch_};
 
   // tables (NULL when linear)
   long step;
@@ -184,7 +247,6 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
   if (ndim.empty()) ldb = 0;
 
   // small or skinny products stay on the FP64 path (GEMV or a few tiles)
-  const bool tiny = static_cast<double>(M) * N * K < 2.0e6 || K < 16 || M < 8 || N < 8;
   if (tier == TIER_FP64 || tiny) {
     GemmDesc g;
     g.M = M; g.N = N; g.K = K;
@@ -194,6 +256,28 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
     g.alpha = alpha; g.beta = beta;
     g.k_contig = kdim.empty() || (M == 1 ? bkstr.back() == 1 : akstr.back() == 1);
     gemm_f64(g, st, num_sms);
+    return false;
+  }
+  // short contracted index with one short free side: FP32 on the CUDA cores
+  if (K <= SKINNY_MAX_K && std::min(M, N) <= 1024 && std::max(M, N) >= 2048) {
+    SkinnyDesc d;
+    d.K = static_cast<int>(K);
+    d.alpha = alpha;
+    d.beta = beta;
+    d.C = C.p;
+    const long *ak_ = kdim.empty() ? nullptr : ak, *bk_ = kdim.empty() ? nullptr : bk;
+    if (N <= M) {  // long side A (rows m), short side B (rows n)
+      d.Mb = M; d.Ns = static_cast<int>(N);
+      d.G = A.p; d.gr = am; d.ldg = lda; d.gk = ak_; d.conjG = A.conj;
+      d.S = B.p; d.sr = bn; d.lds = ldb; d.sk = bk_; d.conjS = B.conj;
+      d.cb = cm; d.ldcb = ldc; d.cs = cn; d.ldcs = 1;
+    } else {       // long side B (rows n), short side A (rows m)
+      d.Mb = N; d.Ns = static_cast<int>(M);
+      d.G = B.p; d.gr = bn; d.ldg = ldb; d.gk = bk_; d.conjG = B.conj;
+      d.S = A.p; d.sr = am; d.lds = lda; d.sk = ak_; d.conjS = A.conj;
+      d.cb = cn; d.ldcb = 1; d.cs = cm; d.ldcs = ldc;
+    }
+    gemm_skinny(d, st);
     return false;
   }
   // fast tier: pack operands into expanded planes, tensor-core GEMM
@@ -247,6 +331,7 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
 }
 
 void Engine::permute_into(cplx alpha, const TRef &in, cplx beta, const TRef &out) {
+  Region r = region("permute " + in.idx + "->" + out.idx);
   // out must be contiguous; in strides reordered to out's index order
   std::vector<long> istr(out.idx.size());
   for (size_t i = 0; i < out.idx.size(); ++i) {

@@ -82,6 +82,23 @@ class Engine {
     ++gen;
   }
 
+  // Optional device-time trace, on when the environment variable
+  // CDFNS_TRACE names a file: every contraction (operand packing and GEMM)
+  // and every region() scope is bracketed by CUDA events on the engine's
+  // stream; trace_flush() waits for them and appends one CSV line per record
+  // (label,M,N,K,tier,ms) to that file. Recording adds two event records per
+  // contraction and nothing else.
+  bool tracing() const { return trace_on_; }
+  void trace_init();
+  void trace_flush();
+  struct Region {
+    Engine *e;
+    int rec;
+    long epoch;  // records opened before a flush are not closed after it
+    ~Region();
+  };
+  Region region(const std::string &label);
+
  private:
   struct Packed {
     Buf hi, lo;
@@ -92,6 +109,19 @@ class Engine {
   std::map<std::string, Buf> cache_;
   std::map<std::string, Packed> packs_;
   std::map<int, Buf> planes_;
+  struct TraceRec {
+    std::string label;
+    long M, N, K;
+    int tier;
+    cudaEvent_t e0, e1;
+    bool closed;
+  };
+  bool trace_on_ = false;
+  std::string trace_path_;
+  std::vector<TraceRec> trace_;
+  long trace_epoch_ = 0;
+  int trace_open(const std::string &label, long M, long N, long K, int tier);
+  void trace_close(int rec);
   struct Plan;
   bool run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef &C, int tier, int slot,
            TcDesc *out);

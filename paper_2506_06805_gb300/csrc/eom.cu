@@ -466,6 +466,7 @@ void run_ipeom(std::vector<Ctx *> &sys, int nr, double tol, int max_iter, double
   }
   const double dt = now_ms() - t0;
   for (Ctx *c : sys) c->stat[5] += dt / sys.size();
+  for (Ctx *c : sys) c->eng.trace_flush();
 }
 
 }  // namespace cdfns

@@ -182,14 +182,38 @@ __global__ void gemv_warp_kernel(long N, long K, const double2 *__restrict__ A,
   const long wpb = blockDim.x >> 5;
   for (long n = blockIdx.x * wpb + (threadIdx.x >> 5); n < N; n += static_cast<long>(gridDim.x) * wpb) {
     const long bo = bn ? bn[n] : n * ldb;
-    double2 acc = make_double2(0.0, 0.0);
-    for (long k = lane; k < K; k += 32) {
+    // four independent loads per lane in flight (offset tables resolve first)
+    double2 ac[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
+                     make_double2(0.0, 0.0)};
+    long k = lane;
+    for (; k + 96 < K; k += 128) {
+      long ia[4], ib[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        ia[u] = ak ? ak[k + 32 * u] : k + 32 * u;
+        ib[u] = bo + (bk ? bk[k + 32 * u] : k + 32 * u);
+      }
+      double2 a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = A[ia[u]];
+        b[u] = B[ib[u]];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (conjA) a[u].y = -a[u].y;
+        if (conjB) b[u].y = -b[u].y;
+        ac[u] = cfma(a[u], b[u], ac[u]);
+      }
+    }
+    for (; k < K; k += 32) {
       double2 a = A[ak ? ak[k] : k];
       double2 b = B[bo + (bk ? bk[k] : k)];
       if (conjA) a.y = -a.y;
       if (conjB) b.y = -b.y;
-      acc = cfma(a, b, acc);
+      ac[0] = cfma(a, b, ac[0]);
     }
+    double2 acc = cadd(cadd(ac[0], ac[1]), cadd(ac[2], ac[3]));
     for (int o = 16; o > 0; o >>= 1) {
       acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
       acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);

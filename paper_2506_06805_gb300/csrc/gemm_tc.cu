@@ -165,6 +165,7 @@ struct alignas(64) TcProblem {
   const long *cm, *cn;
   long ldc;
   double2 alpha, beta;
+  float2 alpha_f;   // alpha rounded to FP32 (applied to the FP32 tile)
   int num_kb;       // K blocks of 128 bytes per row
   int kb_per_split;
   int k_splits, m_tiles, n_tiles;
@@ -413,14 +414,18 @@ __global__ void __launch_bounds__(320, 1)
           } else {
             double2 *C = reinterpret_cast<double2 *>(args.C);
             const long off = (args.cm ? args.cm[mc] : mc * args.ldc) + cno;
-            const double dr = re, di = im;
-            const double xr = args.alpha.x * dr - args.alpha.y * di;
-            const double xi = args.alpha.x * di + args.alpha.y * dr;
+            // alpha in FP32 (the product carries FP32 rounding already),
+            // widened on the integer pipes; FP64 arithmetic only for beta
+            const double xr = f32_to_f64(args.alpha_f.x * re - args.alpha_f.y * im);
+            const double xi = f32_to_f64(args.alpha_f.x * im + args.alpha_f.y * re);
             if (args.out == TC_OUT_F64_ATOMIC) {
               atomicAdd(&C[off].x, xr);
               atomicAdd(&C[off].y, xi);
             } else if (args.beta.x == 0.0 && args.beta.y == 0.0) {
               C[off] = make_double2(xr, xi);
+            } else if (args.beta.x == 1.0 && args.beta.y == 0.0) {
+              const double2 cv = C[off];
+              C[off] = make_double2(cv.x + xr, cv.y + xi);
             } else {
               const double2 cv = C[off];
               C[off] = make_double2(xr + args.beta.x * cv.x - args.beta.y * cv.y,
@@ -522,6 +527,7 @@ void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
     a.ldc = g.ldc;
     a.alpha = g.alpha;
     a.beta = g.beta;
+    a.alpha_f = make_float2(static_cast<float>(g.alpha.x), static_cast<float>(g.alpha.y));
     a.tile_start = static_cast<int>(tiles);
     tiles += static_cast<long>(a.m_tiles) * a.n_tiles * a.k_splits;
     if (tiles > 0x7fffffffL) fail(CC_ERR_ARG, "gemm_tc: too many tiles");
@@ -731,46 +737,81 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
+// Two adjacent elements (idx even) as one 8-byte (fp32) or 4-byte (bf16)
+// store; the split is the same as element by element.
 template <bool BF16>
-__device__ __forceinline__ void split_store(void *hi, void *lo, long idx, float x) {
+__device__ __forceinline__ void split_store2(void *hi, void *lo, long idx, float x, float y) {
   if constexpr (BF16) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    reinterpret_cast<__nv_bfloat16 *>(hi)[idx] = h;
-    if (lo) reinterpret_cast<__nv_bfloat16 *>(lo)[idx] = __float2bfloat16_rn(x - __bfloat162float(h));
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+    reinterpret_cast<__nv_bfloat162 *>(hi)[idx >> 1] = h;
+    if (lo) {
+      const float2 hf = __bfloat1622float2(h);
+      reinterpret_cast<__nv_bfloat162 *>(lo)[idx >> 1] = __floats2bfloat162_rn(x - hf.x, y - hf.y);
+    }
   } else {
-    const float h = to_tf32(x);
-    reinterpret_cast<float *>(hi)[idx] = h;
-    if (lo) reinterpret_cast<float *>(lo)[idx] = to_tf32(x - h);
+    const float hx = to_tf32(x), hy = to_tf32(y);
+    reinterpret_cast<float2 *>(hi)[idx >> 1] = make_float2(hx, hy);
+    if (lo) reinterpret_cast<float2 *>(lo)[idx >> 1] = make_float2(to_tf32(x - hx), to_tf32(y - hy));
   }
 }
 
-// Grid: x over complex k (padded to Kp/2), y over rows (grid-stride).
 template <bool BF16, bool EXPAND>
-__global__ void pack_kernel(const double2 *__restrict__ src, const long *__restrict__ rt,
-                            const long *__restrict__ kt, long ld, bool conj, long rows, long K,
-                            long Kp, void *hi, void *lo) {
+__device__ __forceinline__ void pack_store(void *hi, void *lo, long r, long kc, long Kp, double2 a,
+                                           bool conj) {
+  const float re = f64_to_f32(a.x), im = conj ? -f64_to_f32(a.y) : f64_to_f32(a.y);
+  if (EXPAND) {
+    split_store2<BF16>(hi, lo, (2 * r) * Kp + 2 * kc, re, -im);
+    split_store2<BF16>(hi, lo, (2 * r + 1) * Kp + 2 * kc, im, re);
+  } else {
+    split_store2<BF16>(hi, lo, r * Kp + 2 * kc, re, im);
+  }
+}
+
+// Block (BX, BY): x over complex k (padded to Kp/2), y over rows
+// (grid-stride); BX shrinks to the row length so short rows keep every
+// thread busy.
+template <bool BF16, bool EXPAND>
+__global__ void __launch_bounds__(256) pack_kernel(const double2 *__restrict__ src,
+                                                   const long *__restrict__ rt,
+                                                   const long *__restrict__ kt, long ld, bool conj,
+                                                   long rows, long K, long Kp, void *hi, void *lo) {
   const long kc = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;  // complex k
   if (kc >= Kp / 2) return;
-  for (long r = blockIdx.y; r < rows; r += gridDim.y) {
+  const long kof = kc < K ? (kt ? kt[kc] : kc) : 0;
+  const long step = static_cast<long>(gridDim.y) * blockDim.y;
+  for (long r = blockIdx.y * static_cast<long>(blockDim.y) + threadIdx.y; r < rows; r += step) {
     double2 a = make_double2(0.0, 0.0);
-    if (kc < K) {
-      const long off = (rt ? rt[r] : r * ld) + (kt ? kt[kc] : kc);
-      a = src[off];
-      if (conj) a.y = -a.y;
+    if (kc < K) a = src[(rt ? rt[r] : r * ld) + kof];
+    pack_store<BF16, EXPAND>(hi, lo, r, kc, Kp, a, conj);
+  }
+}
+
+// Rows contiguous in the source (unit row stride, k through a table or a
+// large stride): 32 x 32 tiles transposed through shared memory so that the
+// loads run along rows and the stores along k. Block (32, 8).
+template <bool BF16, bool EXPAND>
+__global__ void __launch_bounds__(256) pack_t_kernel(const double2 *__restrict__ src,
+                                                     const long *__restrict__ kt, bool conj, long rows, long K, long Kp,
+                                                     void *hi, void *lo) {
+  __shared__ double2 tile[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const long k0 = blockIdx.x * 32L;
+  for (long r0 = blockIdx.y * 32L; r0 < rows; r0 += gridDim.y * 32L) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const long k = k0 + ty + 8 * j, r = r0 + tx;
+      double2 a = make_double2(0.0, 0.0);
+      if (k < K && r < rows) a = src[r + kt[k]];
+      tile[ty + 8 * j][tx] = a;
     }
-    const float re = static_cast<float>(a.x), im = static_cast<float>(a.y);
-    if (EXPAND) {
-      const long r0 = (2 * r) * Kp + 2 * kc;
-      const long r1 = (2 * r + 1) * Kp + 2 * kc;
-      split_store<BF16>(hi, lo, r0, re);
-      split_store<BF16>(hi, lo, r0 + 1, -im);
-      split_store<BF16>(hi, lo, r1, im);
-      split_store<BF16>(hi, lo, r1 + 1, re);
-    } else {
-      const long r0 = r * Kp + 2 * kc;
-      split_store<BF16>(hi, lo, r0, re);
-      split_store<BF16>(hi, lo, r0 + 1, im);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const long r = r0 + ty + 8 * j, kc = k0 + tx;
+      if (r < rows && kc < Kp / 2)
+        pack_store<BF16, EXPAND>(hi, lo, r, kc, Kp, tile[tx][ty + 8 * j], conj);
     }
+    __syncthreads();
   }
 }
 
@@ -778,14 +819,27 @@ template <bool EXPAND>
 void pack_launch(const cplx *src, const long *rt, const long *kt, long ld, bool conj, long rows,
                  long K, long Kp, int tier, void *hi, void *lo, cudaStream_t st) {
   if (rows <= 0) return;
-  const int threads = 256;
-  dim3 grid(static_cast<unsigned>((Kp / 2 + threads - 1) / threads),
-            static_cast<unsigned>(std::min<long>(rows, 65535)));
   void *l = (tier == TIER_TF32) ? nullptr : lo;
-  if (tier == TIER_BF16X3)
-    pack_kernel<true, EXPAND><<<grid, threads, 0, st>>>(src, rt, kt, ld, conj, rows, K, Kp, hi, l);
-  else
-    pack_kernel<false, EXPAND><<<grid, threads, 0, st>>>(src, rt, kt, ld, conj, rows, K, Kp, hi, l);
+  const long kh = Kp / 2;
+  if (!rt && ld == 1 && kt && rows > 1 && K > 1) {
+    dim3 block(32, 8);
+    dim3 grid(static_cast<unsigned>((kh + 31) / 32),
+              static_cast<unsigned>(std::min<long>((rows + 31) / 32, 65535)));
+    if (tier == TIER_BF16X3)
+      pack_t_kernel<true, EXPAND><<<grid, block, 0, st>>>(src, kt, conj, rows, K, Kp, hi, l);
+    else
+      pack_t_kernel<false, EXPAND><<<grid, block, 0, st>>>(src, kt, conj, rows, K, Kp, hi, l);
+  } else {
+    const int bx = static_cast<int>(std::min<long>(256, std::max<long>(32, (kh + 31) / 32 * 32)));
+    const int by = 256 / bx;
+    dim3 block(bx, by);
+    dim3 grid(static_cast<unsigned>((kh + bx - 1) / bx),
+              static_cast<unsigned>(std::min<long>((rows + by - 1) / by, 65535)));
+    if (tier == TIER_BF16X3)
+      pack_kernel<true, EXPAND><<<grid, block, 0, st>>>(src, rt, kt, ld, conj, rows, K, Kp, hi, l);
+    else
+      pack_kernel<false, EXPAND><<<grid, block, 0, st>>>(src, rt, kt, ld, conj, rows, K, Kp, hi, l);
+  }
   LAUNCH_CHECK();
   count_launch();
 }

@@ -28,6 +28,23 @@ struct GemmDesc {
 // FP64 SIMT path (CC_TIER_FP64).
 void gemm_f64(const GemmDesc &g, cudaStream_t st, int num_sms);
 
+// Skinny complex product in FP32 on the CUDA cores, for the tensor-core
+// tiers: C[cb(r) + cs(s)] = alpha sum_k G[r][k] S[s][k] + beta C for
+// r < Mb (long side), s < Ns (short side), k < K <= SKINNY_MAX_K. Offsets
+// are table[i] when the table is given, else i * ld; G and S are FP64
+// complex (conjugated on request), C is FP64 complex and must not overlap
+// G or S. beta is applied in FP64, alpha and the products in FP32.
+constexpr int SKINNY_MAX_K = 48;
+struct SkinnyDesc {
+  long Mb = 0;
+  int Ns = 0, K = 0;
+  const cplx *G = nullptr; const long *gr = nullptr, *gk = nullptr; long ldg = 0; bool conjG = false;
+  const cplx *S = nullptr; const long *sr = nullptr, *sk = nullptr; long lds = 0; bool conjS = false;
+  cplx *C = nullptr; const long *cb = nullptr, *cs = nullptr; long ldcb = 0, ldcs = 0;
+  cplx alpha = {1.0, 0.0}, beta = {0.0, 0.0};
+};
+void gemm_skinny(const SkinnyDesc &d, cudaStream_t st);
+
 // Real tensor-core GEMM on the expanded complex form (tcgen05, TMEM, TMA).
 //   D(r, n) = sum_k A'(r, k) B'(n, k),  r < Mr = 2 M, k < Kp (padded)
 // A' rows 2m / 2m+1 hold (Re, -Im) / (Im, Re) of A(m, :) interleaved over k,
@@ -97,6 +114,15 @@ void antisym_add(cplx *R, const cplx *X, int o, int v, double c, int mode, cudaS
 cplx dot(const cplx *x, const cplx *y, long n, bool conj_x, cudaStream_t st,
          cplx *dev_scratch /* >= 1024 */, cplx *host_out = nullptr);
 // Same, result left on the device (no synchronisation).
+// Counts, over x[0..n), the values whose integer-pipe narrowing differs
+// from __double2float_rn (bad[0]) and whose widening of that FP32 value
+// differs from the hardware conversion (bad[1]); bad is 2 device counters.
+void conversion_check(const double *x, long n, unsigned long long *bad, cudaStream_t st);
+// res[k * res_stride] = sum_i conj(xs[k][i]) y[i] for k < m <= 16, one pass
+// over y; f32: FP32 products and per-thread sums (block sums in FP64).
+// scratch: at least m device cplx, more for more blocks.
+void dot_multi(const cplx *const *xs, int m, const cplx *y, long n, bool f32, cplx *res,
+               long res_stride, cplx *scratch, long scratch_len, cudaStream_t st);
 void dot_dev(const cplx *x, const cplx *y, long n, bool conj_x, cplx *res,
              cudaStream_t st, cplx *dev_scratch);
 

@@ -121,6 +121,7 @@ void Ctx::create(int n_occ, int n_virt, int n_aux, const double *eps_host) {
   eng.al = &al;
   eng.st = st;
   eng.num_sms = num_sms;
+  eng.trace_init();
   err_d.reset(&al, 64);
   stats_d.reset(&al, 64);
   red.reset(&al, 4096 * sizeof(cplx));
@@ -375,8 +376,6 @@ void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr) {
   const bool fast = tr != TIER_FP64;
   const size_t eb = fast ? tc_elem_bytes(tr) : sizeof(cplx);
   const size_t veb = fast ? sizeof(float2) : sizeof(cplx);
-  double tc_ms = 0;
-  (void)tc_ms;
 
   if (!fast) {
     // K-major copy of L: LT[(a,c)][P]
@@ -423,9 +422,13 @@ void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr) {
       B1l.reset(&al, eb * vv * Kp1);
       A2l.reset(&al, eb * 2 * n_ij * Kp2);
     }
-    tc_pack_A(Lv, nullptr, ptab, 1, false, vv, X, Kp1, tr, A1h.p, A1l.p, st);
-    tc_pack_B(Lv, nullptr, ptab, 1, false, vv, X, Kp1, tr, B1h.p, B1l.p, st);
-    tc_pack_A(tau, rt.as<long>(), kt.as<long>(), 0, false, n_ij, n_cd, Kp2, tr, A2h.p, A2l.p, st);
+    {
+      Engine::Region r = eng.region("ladder pack");
+      tc_pack_A(Lv, nullptr, ptab, 1, false, vv, X, Kp1, tr, A1h.p, A1l.p, st);
+      tc_pack_B(Lv, nullptr, ptab, 1, false, vv, X, Kp1, tr, B1h.p, B1l.p, st);
+      tc_pack_A(tau, rt.as<long>(), kt.as<long>(), 0, false, n_ij, n_cd, Kp2, tr, A2h.p, A2l.p,
+                st);
+    }
     long a0 = 0;
     Buf Vs, Wh, Wl;
     auto off = [&](const Buf &b, long elems) -> const void * {
@@ -450,16 +453,25 @@ void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr) {
       g1.B = off(B1h, a0 * v * Kp1); g1.Blo = off(B1l, a0 * v * Kp1);
       g1.tier = tr; g1.out = TC_OUT_F32;
       g1.C = Vs.p; g1.ldc = (v - a0) * v;
-      gemm_tc(g1, st, err_d.as<int>());
-      ladder_antisym(Vs.p, true, v, static_cast<int>(a0), static_cast<int>(nA), p0, p1,
-                     ab_a.as<int>(), ab_b.as<int>(), ab_a.as<int>(), ab_b.as<int>(), tr, Wh.p,
-                     Wl.p, Kp2, nullptr, st);
+      {
+        Engine::Region r = eng.region("ladder gemm1");
+        gemm_tc(g1, st, err_d.as<int>());
+      }
+      {
+        Engine::Region r = eng.region("ladder antisym");
+        ladder_antisym(Vs.p, true, v, static_cast<int>(a0), static_cast<int>(nA), p0, p1,
+                       ab_a.as<int>(), ab_b.as<int>(), ab_a.as<int>(), ab_b.as<int>(), tr, Wh.p,
+                       Wl.p, Kp2, nullptr, st);
+      }
       TcDesc g2;
       g2.M = n_ij; g2.N = np; g2.Kp = Kp2;
       g2.A = A2h.p; g2.Alo = A2l.p; g2.B = Wh.p; g2.Blo = Wl.p;
       g2.tier = tr; g2.out = TC_OUT_F64;
       g2.C = Rp.c() + p0; g2.ldc = n_ab;
-      gemm_tc(g2, st, err_d.as<int>());
+      {
+        Engine::Region r = eng.region("ladder gemm2");
+        gemm_tc(g2, st, err_d.as<int>());
+      }
       a0 = a1;
     }
   }
@@ -485,8 +497,10 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
   const int tr = tier;
   const long oo = static_cast<long>(o) * o, vv = static_cast<long>(v) * v, n2 = oo * vv;
   Buf tau(&al, sizeof(cplx) * n2), taut(&al, sizeof(cplx) * n2);
-  make_tau(t1p, t2p, tau.c(), o, v, 1.0, st, tr != TIER_FP64);
-  make_tau(t1p, t2p, taut.c(), o, v, 0.5, st, tr != TIER_FP64);
+  {
+    Engine::Region r = eng.region("make_tau x2");
+    make_tau_pair(t1p, t2p, tau.c(), taut.c(), o, v, st, tr != TIER_FP64);
+  }
   Buf Fae(&al, sizeof(cplx) * vv), Fmi(&al, sizeof(cplx) * oo), Fme(&al, sizeof(cplx) * o * v);
   Buf cP(&al, sizeof(cplx) * X), Y(&al, sizeof(cplx) * X * v * o), Zm(&al, sizeof(cplx) * X * oo);
   Buf Q(&al, sizeof(cplx) * X * o * v);
@@ -541,7 +555,7 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
     eng.contract(Cr(-0.5), t1("mb"), T(Fme.c(), "me", {o, v}), C1(), T(Fbe.c(), "be", {v, v}),
                  TIER_FP64);
     eng.contract(C1(), t2("ijae"), T(Fbe.c(), "be", {v, v}), C0(), Xt("ijab"), tr);
-    antisym_add(R2, Xb.c(), o, v, 1.0, 2, st);
+    { Engine::Region r_ = eng.region("antisym_add"); antisym_add(R2, Xb.c(), o, v, 1.0, 2, st); }
   }
   // -P(ij) t_im^ab (F_mj + 1/2 t_j^e F_me)
   {
@@ -550,7 +564,7 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
     eng.contract(Cr(0.5), t1("je"), T(Fme.c(), "me", {o, v}), C1(), T(Fmj.c(), "mj", {o, o}),
                  TIER_FP64);
     eng.contract(C1(), t2("imab"), T(Fmj.c(), "mj", {o, o}), C0(), Xt("ijab"), tr);
-    antisym_add(R2, Xb.c(), o, v, -1.0, 1, st);
+    { Engine::Region r_ = eng.region("antisym_add"); antisym_add(R2, Xb.c(), o, v, -1.0, 1, st); }
   }
   // hole ladder: 1/2 tau_mn^ab W'_mnij + 1/4 t_mn^ab Z_mnij, with
   // W' = <mn||ij> + P(ij) t_j^e <mn||ie>, Z = sum_ef <mn||ef> tau_ij^ef
@@ -563,15 +577,17 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
     eng.permute_into(Cr(-1), T(tmp.c(), "mnji", d4), C1(), T(Wp.c(), "mnij", d4));
     eng.contract(C1(), g_oovv("mnef"), T(tau.c(), "ijef", {o, o, v, v}), C0(), T(Zb.c(), "mnij", d4),
                  tr);
-    eng.contract(Cr(0.5), T(tau.c(), "mnab", {o, o, v, v}), T(Wp.c(), "mnij", d4), C1(), R2t("ijab"),
+    // (i,j) as the GEMM rows so the output rows (a,b) are contiguous
+    eng.contract(Cr(0.5), T(Wp.c(), "mnij", d4), T(tau.c(), "mnab", {o, o, v, v}), C1(), R2t("ijab"),
                  tr);
-    eng.contract(Cr(0.25), t2("mnab"), T(Zb.c(), "mnij", d4), C1(), R2t("ijab"), tr);
+    eng.contract(Cr(0.25), T(Zb.c(), "mnij", d4), t2("mnab"), C1(), R2t("ijab"), tr);
   }
   // particle ladder with T1-dressed vectors: L~^P_ac = L^P_ac - sum_m t_m^a L^P_mc
   {
     Buf Lt(&al, sizeof(cplx) * X * vv);
     d2d(Lt.p, Lvv.p, sizeof(cplx) * X * vv, st);
     eng.contract(Cr(-1), t1("ma"), Lov_("Pmc"), C1(), T(Lt.c(), "Pac", {X, v, v}), tr);
+    Engine::Region r = eng.region("ladder total");
     ladder(Lt.c(), tau.c(), R2, tr);
   }
   // W_mbej
@@ -587,7 +603,10 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
   //   - (1/2 t_jn^fb + t_j^f t_n^b) <mn||ef>
   {
     Buf z(&al, sizeof(cplx) * n2);
-    make_z(t1p, t2p, z.c(), o, v, 0.5, st);
+    {
+      Engine::Region r = eng.region("make_z");
+      make_z(t1p, t2p, z.c(), o, v, 0.5, st, tr != TIER_FP64);
+    }
     eng.contract(Cr(-1), T(z.c(), "jnfb", {o, o, v, v}), g_oovv("mnef"), C1(), Wt("mbej"), tr);
   }
   // P(ij)P(ab) [t_im^ae W_mbej - t_i^e t_m^a <mb||ej>]
@@ -597,14 +616,14 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
     eng.contract(C1(), t1("ie"), g_ovvo("mbej"), C0(), T(y2.c(), "mbij", {o, v, o, o}), tr);
     eng.contract(Cr(-1), t1("ma"), T(y2.c(), "mbij", {o, v, o, o}), C1(), Xt("ijab"), tr);
   }
-  antisym_add(R2, Xb.c(), o, v, 1.0, 3, st);
+  { Engine::Region r_ = eng.region("antisym_add"); antisym_add(R2, Xb.c(), o, v, 1.0, 3, st); }
   // P(ij) t_i^e <ab||ej> = P(ij) sum_P (Y^P_ai L^P_bj - L^P_aj Y^P_bi)
   eng.contract(C1(), T(Y.c(), "Pai", {X, v, o}), Lvo_("Pbj"), C0(), Xt("ijab"), tr);
   eng.contract(Cr(-1), Lvo_("Paj"), T(Y.c(), "Pbi", {X, v, o}), C1(), Xt("ijab"), tr);
-  antisym_add(R2, Xb.c(), o, v, 1.0, 1, st);
+  { Engine::Region r_ = eng.region("antisym_add"); antisym_add(R2, Xb.c(), o, v, 1.0, 1, st); }
   // -P(ab) t_m^a <mb||ij>, <mb||ij> = conj(<ij||mb>)
   eng.contract(C1(), t1("ma"), conj(g_ooov("ijmb")), C0(), Xt("ijab"), tr);
-  antisym_add(R2, Xb.c(), o, v, -1.0, 2, st);
+  { Engine::Region r_ = eng.region("antisym_add"); antisym_add(R2, Xb.c(), o, v, -1.0, 2, st); }
 }
 
 // ===========================================================================
@@ -625,33 +644,48 @@ int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
     amps = true;
   }
   Buf R1(&al, sizeof(cplx) * n1), R2(&al, sizeof(cplx) * n2);
-  Buf tn1(&al, sizeof(cplx) * n1), tn2(&al, sizeof(cplx) * n2);
   Buf vcur(&al, sizeof(cplx) * na), vnew(&al, sizeof(cplx) * na), step(&al, sizeof(cplx) * na);
+  Buf invd(&al, sizeof(double) * na);
+  amp_denoms(eps_d.as<double>(), o, v, ij_i.as<int>(), ij_j.as<int>(), ab_a.as<int>(),
+             ab_b.as<int>(), invd.as<double>(), st);
+  const long esl = energy_scratch_len(o, v);
+  Buf escr(&al, sizeof(cplx) * (esl + 1));
+  const bool e32 = tier != TIER_FP64;
+  auto energy_of = [&](const Buf &vec) {
+    energy_packed(oovv.c(), vec.c(), o, v, ij_i.as<int>(), ij_j.as<int>(), ab_a.as<int>(),
+                  ab_b.as<int>(), e32, escr.c(), esl, escr.c() + esl, st);
+    cplx h;
+    d2h(&h, escr.c() + esl, sizeof(cplx), st);
+    return h;
+  };
   const int m_max = 8, diis_start = 3;
   std::vector<Buf> hv(m_max), he(m_max);
   Buf Bm(&al, sizeof(cplx) * 16 * 16), coef(&al, sizeof(cplx) * 16), dstat(&al, sizeof(int) * 4);
   int n_hist = 0, slot = 0;
   std::vector<int> order;  // slots in age order
   pack_amps(t1.c(), t2.c(), o, v, ij_i.as<int>(), ij_j.as<int>(), ab_a.as<int>(), ab_b.as<int>(), vcur.c(), st);
-  cplx e_old = energy(t1.c(), t2.c());
+  cplx e_old = energy_of(vcur);
   bool converged = false;
   int it = 0;
   for (it = 1; it <= max_iter; ++it) {
-    residual(t1.c(), t2.c(), R1.c(), R2.c());
-    jacobi(R1.c(), R2.c(), eps_d.as<double>(), o, v, tn1.c(), tn2.c(), st);
-    pack_amps(tn1.c(), tn2.c(), o, v, ij_i.as<int>(), ij_j.as<int>(), ab_a.as<int>(), ab_b.as<int>(), vnew.c(), st);
+    {
+      Engine::Region r = eng.region("residual total");
+      residual(t1.c(), t2.c(), R1.c(), R2.c());
+    }
+    Engine::Region r_upd = eng.region("update+diis");
+    jacobi_packed(R1.c(), R2.c(), invd.as<double>(), o, v, ij_i.as<int>(), ij_j.as<int>(),
+                  ab_a.as<int>(), ab_b.as<int>(), vnew.c(), st);
     d2d(step.p, vnew.p, sizeof(cplx) * na, st);
     axpby(na, Cr(-1), vcur.c(), C1(), step.c(), st);
     const cplx nrm2 = dot(step.c(), step.c(), na, true, st, red.c());
     const double dnorm = std::sqrt(std::max(nrm2.x, 0.0));
-    const cplx e_new = energy(tn1.c(), tn2.c());
+    const cplx e_new = energy_of(vnew);
     check_err_flag();
     if (!std::isfinite(dnorm) || !std::isfinite(e_new.x) || !std::isfinite(e_new.y))
       fail(CC_ERR_NUMERIC, "CCSD iteration produced NaN/Inf");
     const double de = std::hypot(e_new.x - e_old.x, e_new.y - e_old.y);
     if (dnorm < tol && de < tol) {
-      d2d(t1.p, tn1.p, sizeof(cplx) * n1, st);
-      d2d(t2.p, tn2.p, sizeof(cplx) * n2, st);
+      unpack_amps(vnew.c(), o, v, t1.c(), t2.c(), st);
       e_old = e_new;
       converged = true;
       break;
@@ -671,8 +705,12 @@ int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
       d2d(hv[slot].p, vnew.p, sizeof(cplx) * na, st);
       d2d(he[slot].p, step.p, sizeof(cplx) * na, st);
       // B[i][slot] = <e_i|e_slot>, B[slot][i] = conj
-      for (int k = 0; k < n_hist; ++k)
-        dot_dev(he[k].c(), he[slot].c(), na, true, Bm.c() + k * 16 + slot, st, red.c());
+      {
+        std::vector<const cplx *> xs(n_hist);
+        for (int k = 0; k < n_hist; ++k) xs[k] = he[k].c();
+        dot_multi(xs.data(), n_hist, he[slot].c(), na, tier != TIER_FP64, Bm.c() + slot, 16,
+                  red.c(), 4096, st);
+      }
       // mirror the new column into the new row (Hermitian)
       {
         std::vector<cplx> Bh(16 * 16);
@@ -699,7 +737,7 @@ int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
     }
     unpack_amps(vnew.c(), o, v, t1.c(), t2.c(), st);
     d2d(vcur.p, vnew.p, sizeof(cplx) * na, st);
-    e_old = energy(t1.c(), t2.c());
+    e_old = energy_of(vnew);
   }
   if (it > max_iter) it = max_iter;
   e_corr = e_old;
@@ -708,6 +746,7 @@ int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
     e_out[1] = e_corr.y;
   }
   if (n_iter) *n_iter = it;
+  eng.trace_flush();
   stat[4] += now_ms() - t0;
   stat[7] = it;
   ccsd_done = true;
@@ -719,6 +758,7 @@ int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
 // H-bar elements with at most two virtual indices (built once)
 // ===========================================================================
 void Ctx::build_hbar() {
+  Engine::Region rg = eng.region("hbar total");
   eng.clear_pack_cache();
   ++sig_gen;
   const int tr = int_tier() == TIER_FP64 ? TIER_FP64 : TIER_TF32X3;

@@ -3,6 +3,8 @@
 
 #include "kernels.h"
 
+#include <type_traits>
+
 namespace cdfns {
 
 unsigned long long g_launches = 0;
@@ -109,6 +111,67 @@ __global__ void dot_partial(const double2 *x, const double2 *y, long n, bool con
   if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
 
+// m dot products <x_k|y> (k < m <= 16) in one pass over y. F32: products
+// and per-thread sums in FP32 (operands narrowed on the integer pipes), block
+// sums in FP64; for the tensor-core tiers, whose B matrices only steer DIIS.
+struct PtrList {
+  const double2 *p[16];
+};
+template <bool F32>
+__global__ void __launch_bounds__(256) dot_multi_partial(PtrList xs, int m, const double2 *y, long n,
+                                                         double2 *partial) {
+  using A = typename std::conditional<F32, float, double>::type;
+  A ar[16], ai[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) ar[k] = ai[k] = A(0);
+  for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long>(gridDim.x) * blockDim.x) {
+    const double2 yv = y[i];
+    A yr, yi;
+    if (F32) {
+      yr = f64_to_f32(yv.x);
+      yi = f64_to_f32(yv.y);
+    } else {
+      yr = yv.x;
+      yi = yv.y;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      if (k < m) {
+        const double2 xv = xs.p[k][i];
+        A xr, xi;
+        if (F32) {
+          xr = f64_to_f32(xv.x);
+          xi = f64_to_f32(xv.y);
+        } else {
+          xr = xv.x;
+          xi = xv.y;
+        }
+        // conj(x) y
+        ar[k] = fma(xr, yr, fma(xi, yi, ar[k]));
+        ai[k] = fma(xr, yi, fma(-xi, yr, ai[k]));
+      }
+    }
+  }
+  for (int k = 0; k < m; ++k) {
+    double2 v = make_double2(F32 ? f32_to_f64(static_cast<float>(ar[k])) : static_cast<double>(ar[k]),
+                             F32 ? f32_to_f64(static_cast<float>(ai[k])) : static_cast<double>(ai[k]));
+    v = block_sum(v);
+    if (threadIdx.x == 0) partial[static_cast<long>(k) * gridDim.x + blockIdx.x] = v;
+    __syncthreads();
+  }
+}
+
+__global__ void dot_multi_final(const double2 *partial, int np, int m, double2 *res, long stride) {
+  for (int k = 0; k < m; ++k) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int i = threadIdx.x; i < np; i += blockDim.x) acc = cadd(acc, partial[static_cast<long>(k) * np + i]);
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) res[k * stride] = acc;
+    __syncthreads();
+  }
+}
+
 __global__ void dot_final(const double2 *partial, int np, double2 *res) {
   double2 acc = make_double2(0.0, 0.0);
   for (int i = threadIdx.x; i < np; i += blockDim.x) acc = cadd(acc, partial[i]);
@@ -116,35 +179,86 @@ __global__ void dot_final(const double2 *partial, int np, double2 *res) {
   if (threadIdx.x == 0) *res = acc;
 }
 
-__global__ void antisym_add_kernel(double2 *R, const double2 *X, int o, int v, double c, int mode) {
-  __shared__ double2 t1[16][17];
-  __shared__ double2 t2[16][17];
-  const int i = blockIdx.z / o, j = blockIdx.z % o;
-  const int a0 = blockIdx.y * 16, b0 = blockIdx.x * 16;
+// R += c * P(X) for P = P(ij) (mode 1), P(ab) (mode 2) or P(ij)P(ab)
+// (mode 3), X and R [o][o][v][v]. One block owns every image of its 16 x 16
+// (a, b) tile: the pairs (i,j)/(j,i) for modes 1 and 3 and the tiles
+// (A,B)/(B,A) for modes 2 and 3. It reads each X element once and reads and
+// writes each R element once; transposed tiles go through shared memory so
+// all global accesses run along b.
+__global__ void antisym_add_kernel(double2 *R, const double2 *X, int o, int v, double c, int mode,
+                                   int ntile) {
+  __shared__ double2 sx[4][16][17];
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const long vv = static_cast<long>(v) * v;
-  const long ij = (static_cast<long>(i) * o + j) * vv;
-  const long ji = (static_cast<long>(j) * o + i) * vv;
+  // (i, j): i < j for modes 1 and 3 (i == j adds nothing), all pairs for mode 2
+  int i, j;
+  if (mode & 1) {
+    int p = blockIdx.z;
+    i = 0;
+    while (p >= o - 1 - i) {
+      p -= o - 1 - i;
+      ++i;
+    }
+    j = i + 1 + p;
+  } else {
+    i = blockIdx.z / o;
+    j = blockIdx.z - i * o;
+  }
+  // (A, B) tiles: A <= B for modes 2 and 3, all tiles for mode 1
+  int ta, tb;
   if (mode & 2) {
-    // tiles of X[..][b][a] read along a (coalesced) and used transposed
-    const int bb = b0 + ty, aa = a0 + tx;
-    const bool in = bb < v && aa < v;
-    t1[ty][tx] = in ? X[ij + static_cast<long>(bb) * v + aa] : make_double2(0.0, 0.0);
-    if (mode & 1) t2[ty][tx] = in ? X[ji + static_cast<long>(bb) * v + aa] : make_double2(0.0, 0.0);
+    int p = blockIdx.x;
+    ta = 0;
+    while (p >= ntile - ta) {
+      p -= ntile - ta;
+      ++ta;
+    }
+    tb = ta + p;
+  } else {
+    ta = blockIdx.x / ntile;
+    tb = blockIdx.x - ta * ntile;
+  }
+  const long vv = static_cast<long>(v) * v;
+  const long bij = (static_cast<long>(i) * o + j) * vv, bji = (static_cast<long>(j) * o + i) * vv;
+  const int a0 = ta * 16, b0 = tb * 16;
+  // direct tile (row a0 + ty, column b0 + tx) and transposed tile (row b0 + ty, column a0 + tx)
+  const int ra = a0 + ty, cb = b0 + tx, rb = b0 + ty, ca = a0 + tx;
+  const bool in_d = ra < v && cb < v, in_t = rb < v && ca < v;
+  const long ed = static_cast<long>(ra) * v + cb, et = static_cast<long>(rb) * v + ca;
+  const double2 z = make_double2(0.0, 0.0);
+  // sx[0]: X[ij] direct, sx[1]: X[ji] direct, sx[2]: X[ij] transposed, sx[3]: X[ji] transposed
+  const double2 x_ij = in_d ? X[bij + ed] : z;
+  const double2 x_ji = (mode & 1) && in_d ? X[bji + ed] : z;
+  if (mode & 2) {
+    sx[2][ty][tx] = in_t ? X[bij + et] : z;
+    if (mode & 1) sx[3][ty][tx] = in_t ? X[bji + et] : z;
   }
   __syncthreads();
-  const int a = a0 + ty, b = b0 + tx;
-  if (a >= v || b >= v) return;
-  const long e = static_cast<long>(a) * v + b;
-  double2 x = X[ij + e];
-  if (mode & 1) x = csub(x, X[ji + e]);
+  // Y(a, b) for a = ra, b = cb
+  double2 y = x_ij;
+  if (mode & 1) y = csub(y, x_ji);
   if (mode & 2) {
-    x = csub(x, t1[tx][ty]);
-    if (mode & 1) x = cadd(x, t2[tx][ty]);
+    y = csub(y, sx[2][tx][ty]);                 // X[ij][b][a]
+    if (mode & 1) y = cadd(y, sx[3][tx][ty]);   // X[ji][b][a]
   }
-  if (c == 1.0) R[ij + e] = cadd(R[ij + e], x);
-  else if (c == -1.0) R[ij + e] = csub(R[ij + e], x);
-  else R[ij + e] = cadd(R[ij + e], cscale(c, x));
+  y = cscale(c, y);
+  const bool diag_tile = (mode & 2) && ta == tb;
+  // direct images: R[ij][ab] += Y, R[ji][ab] -= Y (mode 1/3)
+  // (on a diagonal tile only a < b is handled here; a == b adds nothing)
+  if (in_d && !(diag_tile && ra >= cb)) {
+    R[bij + ed] = cadd(R[bij + ed], y);
+    if (mode & 1) R[bji + ed] = csub(R[bji + ed], y);
+  }
+  if (!(mode & 2)) return;
+  // transposed images: R[ij][ba] -= Y, R[ji][ba] += Y, written along a
+  sx[0][ty][tx] = y;
+  __syncthreads();
+  if (in_t) {
+    const double2 yt = sx[0][tx][ty];  // Y(a = ca, b = rb)
+    if (!(diag_tile && ca >= rb)) {
+      R[bij + et] = csub(R[bij + et], yt);
+      if (mode & 1) R[bji + et] = cadd(R[bji + et], yt);
+    }
+  }
 }
 
 inline unsigned grid_for(long n, int threads = 256) {
@@ -207,11 +321,35 @@ void permute(cplx *out, const cplx *in, int nd, const long *odims, const long *i
 
 void antisym_add(cplx *R, const cplx *X, int o, int v, double c, int mode, cudaStream_t st) {
   if (o <= 0 || v <= 0) return;
-  if (static_cast<long>(o) * o > 65535) fail(CC_ERR_ARG, "antisym_add: n_occ too large");
-  dim3 grid((v + 15) / 16, (v + 15) / 16, o * o);
-  antisym_add_kernel<<<grid, dim3(16, 16), 0, st>>>(R, X, o, v, c, mode);
+  if (mode < 1 || mode > 3) fail(CC_ERR_ARG, "antisym_add: bad mode");
+  const long pairs = (mode & 1) ? static_cast<long>(o) * (o - 1) / 2 : static_cast<long>(o) * o;
+  if (pairs == 0) return;
+  if (pairs > 65535) fail(CC_ERR_ARG, "antisym_add: n_occ too large");
+  const int nt = (v + 15) / 16;
+  const long tiles = (mode & 2) ? static_cast<long>(nt) * (nt + 1) / 2 : static_cast<long>(nt) * nt;
+  dim3 grid(static_cast<unsigned>(tiles), 1, static_cast<unsigned>(pairs));
+  antisym_add_kernel<<<grid, dim3(16, 16), 0, st>>>(R, X, o, v, c, mode, nt);
   LAUNCH_CHECK();
   count_launch();
+}
+
+void dot_multi(const cplx *const *xs, int m, const cplx *y, long n, bool f32, cplx *res,
+               long res_stride, cplx *scratch, long scratch_len, cudaStream_t st) {
+  if (m <= 0) return;
+  if (m > 16) fail(CC_ERR_ARG, "dot_multi: at most 16 vectors");
+  PtrList pl;
+  for (int k = 0; k < 16; ++k) pl.p[k] = k < m ? xs[k] : nullptr;
+  int nb = static_cast<int>(std::max<long>(1, std::min<long>(RED_BLOCKS, (n + 255) / 256)));
+  nb = static_cast<int>(std::min<long>(nb, scratch_len / m));
+  if (nb < 1) fail(CC_ERR_ARG, "dot_multi: scratch too small");
+  if (f32)
+    dot_multi_partial<true><<<nb, RED_THREADS, 0, st>>>(pl, m, y, n, scratch);
+  else
+    dot_multi_partial<false><<<nb, RED_THREADS, 0, st>>>(pl, m, y, n, scratch);
+  LAUNCH_CHECK();
+  dot_multi_final<<<1, RED_THREADS, 0, st>>>(scratch, nb, m, res, res_stride);
+  LAUNCH_CHECK();
+  count_launch(2);
 }
 
 void dot_dev(const cplx *x, const cplx *y, long n, bool conj_x, cplx *res, cudaStream_t st,

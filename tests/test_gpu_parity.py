@@ -115,18 +115,45 @@ def test_ladder_matches_oracle(tier, o, v, X, budget):
     assert _relerr(got, ref) <= REL[tier]
 
 
+@pytest.mark.parametrize("M,N,K", [(20000, 37, 40), (33, 5000, 17), (3000, 1024, 48)])
+@pytest.mark.parametrize("tier", ["tf32", "tf32x3"])
+def test_skinny_products_fp32(M, N, K, tier):
+    """Short contracted index with one short side: FP32 on the CUDA cores,
+    so the error is FP32's in both tensor-core tiers."""
+    P = _gpu()
+    rng = np.random.default_rng(M + N + K)
+    A = rng.standard_normal((M, K)) + 1j * rng.standard_normal((M, K))
+    B = rng.standard_normal((N, K)) + 1j * rng.standard_normal((N, K))
+    C = torch.zeros((M, N), dtype=torch.complex128, device="cuda")
+    P.zgemm_dev(_dev(A), _dev(B), C, tier)
+    ref = A @ B.T
+    assert _relerr(C.cpu().numpy(), ref) <= 2e-6
+
+
 # --- CCSD residual at arbitrary amplitudes -----------------------------------
 
+_RESIDUAL_REF = {}
+
+
+def _residual_ref(o, v, X):
+    """Oracle residual at seeded amplitudes (cached across tiers)."""
+    if (o, v, X) not in _RESIDUAL_REF:
+        from oracle import ccsd, integrals
+        eps, L = _system(o, v, X, seed=4, scale=4.0)
+        g = integrals.blocks_from_cholesky(L, o)
+        rng = np.random.default_rng(11)
+        t1, t2 = _amps(rng, o, v, 0.02)
+        _RESIDUAL_REF[(o, v, X)] = (eps, L, t1, t2) + tuple(ccsd.residuals(g, eps, t1, t2))
+    return _RESIDUAL_REF[(o, v, X)]
+
+
+# (16, 36, 150): o >= 16 sends the contractions over one occupied index
+# with a t1- or Fock-sized partner to the FP32 skinny kernel
 @pytest.mark.parametrize("tier", ["fp64", "tf32", "tf32x3", "bf16x3"])
-@pytest.mark.parametrize("o,v,X", [(10, 30, 120), (7, 45, 66)])
+@pytest.mark.parametrize("o,v,X", [(10, 30, 120), (7, 45, 66), (16, 36, 150)])
 def test_ccsd_residual_matches_oracle(tier, o, v, X):
     P = _gpu()
-    from oracle import ccsd, integrals
-    eps, L = _system(o, v, X, seed=4, scale=4.0)
-    g = integrals.blocks_from_cholesky(L, o)
-    rng = np.random.default_rng(11)
-    t1, t2 = _amps(rng, o, v, 0.02)
-    R1, R2 = ccsd.residuals(g, eps, t1, t2)
+    eps, L, t1, t2, R1, R2 = _residual_ref(o, v, X)
     with P.System(eps, L, n_occ=o, tier=tier) as s:
         r1 = torch.zeros((o, v), dtype=torch.complex128, device="cuda")
         r2 = torch.zeros((o, o, v, v), dtype=torch.complex128, device="cuda")
@@ -266,3 +293,29 @@ def test_call_order_and_chunked_init():
         with pytest.raises(P.CCError) as e:
             s.ccsd(tol=1e-8)
         assert e.value.code == -8
+
+
+# --- integer-pipe FP64 <-> FP32 conversions ------------------------------------------
+
+def test_conversions_match_hardware():
+    """The integer-pipe narrowing must be bit-identical to __double2float_rn
+    (round to nearest even) and the widening exact, over random values across
+    the whole exponent range, ties, the FP32 overflow and underflow borders,
+    zeros, infinities and NaN."""
+    P = _gpu()
+    rng = np.random.default_rng(7)
+    vals = [rng.standard_normal(200000) * np.exp2(rng.integers(-160, 160, 200000)),
+            rng.standard_normal(50000)]
+    # exact ties and near-ties of the 29 dropped mantissa bits
+    base = rng.integers(1, 1 << 23, 20000).astype(np.float64)
+    for off in (0.5, 0.5 - 2.0 ** -29, 0.5 + 2.0 ** -29, 1.5, 0.0):
+        vals.append((base + off) * np.exp2(rng.integers(-140, 128, 20000) - 23.0))
+    f32max = float(np.finfo(np.float32).max)
+    tiny = float(np.finfo(np.float32).tiny)
+    vals.append(np.array([0.0, -0.0, np.inf, -np.inf, np.nan, f32max, -f32max,
+                          f32max * (1 + 2.0 ** -25), f32max * (1 + 2.0 ** -24),
+                          f32max * (1 + 2.0 ** -23), tiny, tiny * (1 - 2.0 ** -30),
+                          tiny * 0.5, 2.0 ** -149, 2.0 ** -150, 2.0 ** -151, 1e-300,
+                          -1e-300, 1e300, 5e-324]))
+    x = torch.from_numpy(np.concatenate(vals)).cuda()
+    assert P.selftest_conversions(x) == (0, 0)
