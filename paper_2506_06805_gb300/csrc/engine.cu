@@ -292,6 +292,7 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
   } else {
     Ah = plane(pb + 0, eb * 2 * M * Kp);
     Al = split ? plane(pb + 1, eb * 2 * M * Kp) : nullptr;
+    Region r = region("pack A " + A.idx);
     tc_pack_A(A.p, am, ak, lda, A.conj, M, K, Kp, tier, Ah, Al, st);
   }
   if (B.stable) {
@@ -299,6 +300,7 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
   } else {
     Bh = plane(pb + 2, eb * N * Kp);
     Bl = split ? plane(pb + 3, eb * N * Kp) : nullptr;
+    Region r = region("pack B " + B.idx);
     tc_pack_B(B.p, bn, bk, ldb, B.conj, N, K, Kp, tier, Bh, Bl, st);
   }
   TcDesc t;
@@ -326,6 +328,7 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
     *out = t;
     return true;
   }
+  Region r = region("gemm " + A.idx + "," + B.idx + "->" + C.idx);
   gemm_tc(t, st, err_flag);
   return false;
 }

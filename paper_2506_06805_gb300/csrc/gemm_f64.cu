@@ -226,6 +226,67 @@ __global__ void gemv_warp_kernel(long N, long K, const double2 *__restrict__ A,
   }
 }
 
+// Few outputs over a long K (Davidson subspace overlaps): one warp per
+// output element and a K range per blockIdx.y; partial sums are added
+// atomically when K is split (C scaled by beta beforehand).
+__global__ void __launch_bounds__(256) dots_kernel(long M, long N, long K,
+                                                   const double2 *__restrict__ A,
+                                                   const long *__restrict__ am,
+                                                   const long *__restrict__ ak, long lda, bool conjA,
+                                                   const double2 *__restrict__ B,
+                                                   const long *__restrict__ bn,
+                                                   const long *__restrict__ bk, long ldb, bool conjB,
+                                                   double2 *C, const long *__restrict__ cm,
+                                                   const long *__restrict__ cn, long ldc,
+                                                   double2 alpha, double2 beta, long kchunk,
+                                                   bool atomic) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long p = blockIdx.x * 8L + warp;
+  if (p >= M * N) return;
+  const long m = p / N, n = p - m * N;
+  const long k0 = blockIdx.y * kchunk, k1 = min(K, k0 + kchunk);
+  const long ao = am ? am[m] : m * lda, bo = bn ? bn[n] : n * ldb;
+  double2 ac[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
+                   make_double2(0.0, 0.0)};
+  long k = k0 + lane;
+  for (; k + 96 < k1; k += 128) {
+    double2 a[4], b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long kk = k + 32 * u;
+      a[u] = A[ao + (ak ? ak[kk] : kk)];
+      b[u] = B[bo + (bk ? bk[kk] : kk)];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (conjA) a[u].y = -a[u].y;
+      if (conjB) b[u].y = -b[u].y;
+      ac[u] = cfma(a[u], b[u], ac[u]);
+    }
+  }
+  for (; k < k1; k += 32) {
+    double2 a = A[ao + (ak ? ak[k] : k)], b = B[bo + (bk ? bk[k] : k)];
+    if (conjA) a.y = -a.y;
+    if (conjB) b.y = -b.y;
+    ac[0] = cfma(a, b, ac[0]);
+  }
+  double2 acc = cadd(cadd(ac[0], ac[1]), cadd(ac[2], ac[3]));
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
+  }
+  if (lane == 0) {
+    const long off = (cm ? cm[m] : m * ldc) + (cn ? cn[n] : n);
+    const double2 x = cmul(alpha, acc);
+    if (atomic) {
+      atomicAdd(&C[off].x, x.x);
+      atomicAdd(&C[off].y, x.y);
+    } else {
+      C[off] = (beta.x == 0.0 && beta.y == 0.0) ? x : cadd(x, cmul(beta, C[off]));
+    }
+  }
+}
+
 }  // namespace
 
 void gemm_f64(const GemmDesc &g, cudaStream_t st, int num_sms) {
@@ -273,6 +334,44 @@ void gemm_f64(const GemmDesc &g, cudaStream_t st, int num_sms) {
       gemv_kernel<<<blocks, 256, 0, st>>>(n_out, g.K, g.B, g.bk, g.conjB, g.A, g.am, g.ak, g.lda,
                                           g.conjA, g.C, g.cm, g.ldc, g.alpha, g.beta);
     }
+    LAUNCH_CHECK();
+    count_launch();
+    return;
+  }
+  // short K with one short side: FP64 skinny kernel (no tile padding)
+  if (g.K <= SKINNY64_MAX_K && std::min(g.M, g.N) <= 256 && std::max(g.M, g.N) >= 1024) {
+    SkinnyDesc d;
+    d.f64 = true;
+    d.K = static_cast<int>(g.K);
+    d.alpha = g.alpha;
+    d.beta = g.beta;
+    d.C = g.C;
+    if (g.N <= g.M) {
+      d.Mb = g.M; d.Ns = static_cast<int>(g.N);
+      d.G = g.A; d.gr = g.am; d.ldg = g.lda; d.gk = g.ak; d.conjG = g.conjA;
+      d.S = g.B; d.sr = g.bn; d.lds = g.ldb; d.sk = g.bk; d.conjS = g.conjB;
+      d.cb = g.cm; d.ldcb = g.ldc; d.cs = g.cn; d.ldcs = 1;
+    } else {
+      d.Mb = g.N; d.Ns = static_cast<int>(g.M);
+      d.G = g.B; d.gr = g.bn; d.ldg = g.ldb; d.gk = g.bk; d.conjG = g.conjB;
+      d.S = g.A; d.sr = g.am; d.lds = g.lda; d.sk = g.ak; d.conjS = g.conjA;
+      d.cb = g.cn; d.ldcb = 1; d.cs = g.cm; d.ldcs = g.ldc;
+    }
+    gemm_skinny(d, st);
+    return;
+  }
+  // few outputs over a long K
+  if (g.M * g.N <= 4096 && g.K >= 1024) {
+    const long gx = (g.M * g.N + 7) / 8;
+    long split = std::max<long>(1, std::min<long>(g.K / 1024, (4L * num_sms + gx - 1) / gx));
+    const long kchunk = (g.K + split - 1) / split;
+    split = (g.K + kchunk - 1) / kchunk;
+    const bool atomic = split > 1;
+    if (atomic) scale_2d(g.C, g.cm, g.cn, g.ldc, g.M, g.N, g.beta, st);
+    dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(split));
+    dots_kernel<<<grid, 256, 0, st>>>(g.M, g.N, g.K, g.A, g.am, g.ak, g.lda, g.conjA, g.B, g.bn,
+                                      g.bk, g.ldb, g.conjB, g.C, g.cm, g.cn, g.ldc, g.alpha, g.beta,
+                                      kchunk, atomic);
     LAUNCH_CHECK();
     count_launch();
     return;

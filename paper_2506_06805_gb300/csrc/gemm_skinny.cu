@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(SK_THREADS) skinny_kernel(const SkinnyDesc d, 
 #pragma unroll
     for (int k = 0; k < KM; ++k) {
       double2 x = make_double2(0.0, 0.0);
-      if (live && k < d.K) x = d.G[go + (d.gk ? d.gk[k] : k)];
+      if (live && k < d.K) x = d.G[go + (d.gk ? d.gk[k] : k * d.gks)];
       const float im = f64_to_f32(x.y);
       g[k] = make_float2(f64_to_f32(x.x), d.conjG ? -im : im);
     }
@@ -56,8 +56,8 @@ __global__ void __launch_bounds__(SK_THREADS) skinny_kernel(const SkinnyDesc d, 
       const long so = d.sr ? d.sr[s0 + s] : static_cast<long>(s0 + s) * d.lds;
       const int k0 = 2 * kp, k1 = 2 * kp + 1;
       double2 x0 = make_double2(0.0, 0.0), x1 = make_double2(0.0, 0.0);
-      if (k0 < d.K) x0 = d.S[so + (d.sk ? d.sk[k0] : k0)];
-      if (k1 < d.K) x1 = d.S[so + (d.sk ? d.sk[k1] : k1)];
+      if (k0 < d.K) x0 = d.S[so + (d.sk ? d.sk[k0] : k0 * d.sks)];
+      if (k1 < d.K) x1 = d.S[so + (d.sk ? d.sk[k1] : k1 * d.sks)];
       const float sg = d.conjS ? -1.0f : 1.0f;
       s_sm[i] = make_float4(f64_to_f32(x0.x), sg * f64_to_f32(x0.y), f64_to_f32(x1.x),
                             sg * f64_to_f32(x1.y));
@@ -107,6 +107,52 @@ __global__ void __launch_bounds__(SK_THREADS) skinny_kernel(const SkinnyDesc d, 
   }
 }
 
+// FP64 variant (the FP64 tier and the Davidson subspace products): the
+// same layout with FP64 operands and sums.
+template <int KM>
+__global__ void __launch_bounds__(SK_THREADS) skinny64_kernel(const SkinnyDesc d, int chunk) {
+  extern __shared__ double2 s_sm64[];  // [chunk][KM]
+  const long r = blockIdx.x * static_cast<long>(SK_THREADS) + threadIdx.x;
+  const bool live = r < d.Mb;
+  double2 g[KM];
+  {
+    const long go = live ? (d.gr ? d.gr[r] : r * d.ldg) : 0;
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+      double2 x = make_double2(0.0, 0.0);
+      if (live && k < d.K) x = d.G[go + (d.gk ? d.gk[k] : k * d.gks)];
+      if (d.conjG) x.y = -x.y;
+      g[k] = x;
+    }
+  }
+  const long cb = live ? (d.cb ? d.cb[r] : r * d.ldcb) : 0;
+  const bool b0 = d.beta.x == 0.0 && d.beta.y == 0.0;
+  for (int s0 = 0; s0 < d.Ns; s0 += chunk) {
+    const int ns = min(chunk, d.Ns - s0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < ns * KM; i += SK_THREADS) {
+      const int s = i / KM, k = i - s * KM;
+      const long so = d.sr ? d.sr[s0 + s] : static_cast<long>(s0 + s) * d.lds;
+      double2 x = make_double2(0.0, 0.0);
+      if (k < d.K) x = d.S[so + (d.sk ? d.sk[k] : k * d.sks)];
+      if (d.conjS) x.y = -x.y;
+      s_sm64[i] = x;
+    }
+    __syncthreads();
+    if (!live) continue;
+    for (int s = 0; s < ns; ++s) {
+      const long co = cb + (d.cs ? d.cs[s0 + s] : static_cast<long>(s0 + s) * d.ldcs);
+      const double2 old = b0 ? make_double2(0.0, 0.0) : d.C[co];
+      const double2 *q = s_sm64 + s * KM;
+      double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int k = 0; k < KM; ++k) acc = cfma(g[k], q[k], acc);
+      const double2 x = cmul(d.alpha, acc);
+      d.C[co] = b0 ? x : cadd(x, cmul(d.beta, old));
+    }
+  }
+}
+
 template <int KM>
 void skinny_launch(const SkinnyDesc &d, cudaStream_t st) {
   static bool attr = false;
@@ -128,12 +174,36 @@ void skinny_launch(const SkinnyDesc &d, cudaStream_t st) {
   count_launch();
 }
 
+template <int KM>
+void skinny64_launch(const SkinnyDesc &d, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    CUDA_CHECK(cudaFuncSetAttribute(skinny64_kernel<KM>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, SK_SMEM));
+    attr = true;
+  }
+  const int per_s = KM * static_cast<int>(sizeof(double2));
+  const int chunk = std::max(1, std::min(d.Ns, SK_SMEM / per_s));
+  const long blocks = (d.Mb + SK_THREADS - 1) / SK_THREADS;
+  skinny64_kernel<KM><<<static_cast<unsigned>(blocks), SK_THREADS, chunk * per_s, st>>>(d, chunk);
+  LAUNCH_CHECK();
+  count_launch();
+}
+
 }  // namespace
 
 void gemm_skinny(const SkinnyDesc &d, cudaStream_t st) {
   if (d.Mb <= 0 || d.Ns <= 0) return;
   if (d.K < 0 || d.K > SKINNY_MAX_K) fail(CC_ERR_ARG, "gemm_skinny: K out of range");
   if (d.Mb > 0x7fffffffL * SK_THREADS) fail(CC_ERR_ARG, "gemm_skinny: too many rows");
+  if (d.f64) {
+    if (d.K > SKINNY64_MAX_K) fail(CC_ERR_ARG, "gemm_skinny: K out of range (FP64)");
+    if (d.K <= 8) skinny64_launch<8>(d, st);
+    else if (d.K <= 16) skinny64_launch<16>(d, st);
+    else if (d.K <= 24) skinny64_launch<24>(d, st);
+    else skinny64_launch<32>(d, st);
+    return;
+  }
   if (d.K <= 16) skinny_launch<16>(d, st);
   else if (d.K <= 24) skinny_launch<24>(d, st);
   else if (d.K <= 32) skinny_launch<32>(d, st);

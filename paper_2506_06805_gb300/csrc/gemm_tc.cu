@@ -424,8 +424,10 @@ __global__ void __launch_bounds__(320, 1)
             } else if (args.beta.x == 0.0 && args.beta.y == 0.0) {
               C[off] = make_double2(xr, xi);
             } else if (args.beta.x == 1.0 && args.beta.y == 0.0) {
-              const double2 cv = C[off];
-              C[off] = make_double2(cv.x + xr, cv.y + xi);
+              // one writer per element: the addition runs in L2 (no read
+              // round trip, no FP64 work on the SM)
+              atomicAdd(&C[off].x, xr);
+              atomicAdd(&C[off].y, xi);
             } else {
               const double2 cv = C[off];
               C[off] = make_double2(xr + args.beta.x * cv.x - args.beta.y * cv.y,

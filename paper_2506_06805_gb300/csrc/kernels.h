@@ -28,20 +28,26 @@ struct GemmDesc {
 // FP64 SIMT path (CC_TIER_FP64).
 void gemm_f64(const GemmDesc &g, cudaStream_t st, int num_sms);
 
-// Skinny complex product in FP32 on the CUDA cores, for the tensor-core
-// tiers: C[cb(r) + cs(s)] = alpha sum_k G[r][k] S[s][k] + beta C for
-// r < Mb (long side), s < Ns (short side), k < K <= SKINNY_MAX_K. Offsets
-// are table[i] when the table is given, else i * ld; G and S are FP64
-// complex (conjugated on request), C is FP64 complex and must not overlap
-// G or S. beta is applied in FP64, alpha and the products in FP32.
+// Skinny complex product on the CUDA cores:
+//   C[cb(r) + cs(s)] = alpha sum_k G[r][k] S[s][k] + beta C
+// for r < Mb (long side), s < Ns (short side), k < K. Row offsets are
+// table[i] when the table is given, else i * ld; k offsets gk[k] / sk[k],
+// else k * gks / k * sks. G and S are FP64 complex (conjugated on request),
+// C is FP64 complex and must not overlap G or S. f64 = false (tensor-core
+// tiers, K <= SKINNY_MAX_K): products and sums in FP32, alpha in FP32, beta
+// in FP64. f64 = true (K <= SKINNY64_MAX_K): everything in FP64.
 constexpr int SKINNY_MAX_K = 48;
+constexpr int SKINNY64_MAX_K = 32;
 struct SkinnyDesc {
   long Mb = 0;
   int Ns = 0, K = 0;
-  const cplx *G = nullptr; const long *gr = nullptr, *gk = nullptr; long ldg = 0; bool conjG = false;
-  const cplx *S = nullptr; const long *sr = nullptr, *sk = nullptr; long lds = 0; bool conjS = false;
+  const cplx *G = nullptr; const long *gr = nullptr, *gk = nullptr; long ldg = 0, gks = 1;
+  bool conjG = false;
+  const cplx *S = nullptr; const long *sr = nullptr, *sk = nullptr; long lds = 0, sks = 1;
+  bool conjS = false;
   cplx *C = nullptr; const long *cb = nullptr, *cs = nullptr; long ldcb = 0, ldcs = 0;
   cplx alpha = {1.0, 0.0}, beta = {0.0, 0.0};
+  bool f64 = false;
 };
 void gemm_skinny(const SkinnyDesc &d, cudaStream_t st);
 

@@ -319,3 +319,17 @@ def test_conversions_match_hardware():
                           -1e-300, 1e300, 5e-324]))
     x = torch.from_numpy(np.concatenate(vals)).cuda()
     assert P.selftest_conversions(x) == (0, 0)
+
+
+@pytest.mark.parametrize("M,N,K", [(8, 50000, 24), (37, 3000, 7), (8, 8, 234040),
+                                   (24, 8, 100000), (3, 5, 3000)])
+def test_fp64_short_and_dot_shaped_products(M, N, K):
+    """FP64 products with a short K and a short side (skinny kernel) or with
+    few outputs over a long K (warp-per-output kernel, K split with atomics)."""
+    P = _gpu()
+    rng = np.random.default_rng(M * 7 + N + K)
+    A = rng.standard_normal((M, K)) + 1j * rng.standard_normal((M, K))
+    B = rng.standard_normal((N, K)) + 1j * rng.standard_normal((N, K))
+    C = torch.zeros((M, N), dtype=torch.complex128, device="cuda")
+    P.zgemm_dev(_dev(A), _dev(B), C, "fp64")
+    assert _relerr(C.cpu().numpy(), A @ B.T) <= 1e-12
