@@ -309,14 +309,9 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
   t.tier = tier;
   t.C = C.p; t.cm = cm; t.cn = cn; t.ldc = ldc;
   t.alpha = alpha; t.beta = beta;
-  const long bn_cols = N >= 192 ? 256 : 128;
-  const long tiles = ((2 * M + 127) / 128) * ((N + bn_cols - 1) / bn_cols);
-  const long nkb = Kp / kal;
-  int sk = 1;
-  if (tiles < num_sms && nkb >= 8) {
-    sk = static_cast<int>(std::min<long>((num_sms + tiles - 1) / tiles, nkb / 4));
-    sk = std::max(sk, 1);
-  }
+  t.bn = tc_pick_bn(N);
+  const long tiles = ((2 * M + 127) / 128) * ((N + t.bn - 1) / t.bn);
+  const int sk = tc_pick_split(tiles, Kp / kal, num_sms);
   t.split_k = sk;
   if (sk > 1) {
     scale_2d(C.p, cm, cn, ldc, M, N, beta, st);

@@ -573,6 +573,32 @@ void dispatch(const TcDesc *d, int n, bool wide, cudaStream_t st, int *err) {
 }  // namespace
 
 int tc_k_align(int tier) { return tier == TIER_BF16X3 ? 64 : 32; }
+
+int tc_pick_bn(long N) {
+  const double u256 = static_cast<double>(N) / (((N + 255) / 256) * 256);
+  const double u128 = static_cast<double>(N) / (((N + 127) / 128) * 128);
+  return u128 > u256 + 0.08 ? 128 : 256;
+}
+
+int tc_pick_split(long tiles, long nkb, int num_sms) {
+  int sk = 1;
+  if (tiles <= 0 || tiles >= 8L * num_sms || nkb < 8) return sk;
+  const long P = num_sms;
+  auto eff = [&](long sp) {
+    const long tt = tiles * sp;
+    return static_cast<double>(tt) / (static_cast<double>((tt + P - 1) / P) * P);
+  };
+  double best = eff(1);
+  const long smax = std::min<long>(32, nkb / 4);
+  for (long sp = 2; sp <= smax; ++sp) {
+    const double e = eff(sp) * (1.0 - 0.005 * static_cast<double>(sp - 1));
+    if (e > best + 0.02) {
+      best = e;
+      sk = static_cast<int>(sp);
+    }
+  }
+  return sk;
+}
 size_t tc_elem_bytes(int tier) { return tier == TIER_BF16X3 ? 2 : 4; }
 
 // ---------------------------------------------------------------------------
@@ -686,7 +712,7 @@ void gemm_tc(const TcDesc &g0, cudaStream_t st, int *err) {
   if (g0.M <= 0 || g0.N <= 0 || g0.Kp <= 0) return;
   check_desc(g0);
   TcDesc g = g0;
-  if (g.bn == 0 && (tune_enabled() || tune_path())) {
+  if (tune_enabled() || tune_path()) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     tune_load();
     const std::string key = tune_key(g);

@@ -81,6 +81,14 @@ void gemm_tc(const TcDesc &g, cudaStream_t st, int *err_flag);
 // problems each, sharing one tile queue.
 void gemm_tc_grouped(const std::vector<TcDesc> &descs, cudaStream_t st, int *err_flag);
 // Padded K granularity (real elements) for a tier: 32 for tf32, 64 for bf16.
+// Tile width for N columns: 256 unless 128-wide tiles waste clearly less
+// to padding.
+int tc_pick_bn(long N);
+// K split count for a GEMM of `tiles` output tiles and nkb K blocks: the
+// count (<= 32, >= 4 K blocks per split) that best fills whole waves of
+// num_sms persistent CTAs, slightly favouring fewer splits; 1 when the
+// tiles already make 8 or more waves.
+int tc_pick_split(long tiles, long nkb, int num_sms);
 int tc_k_align(int tier);
 size_t tc_elem_bytes(int tier);
 

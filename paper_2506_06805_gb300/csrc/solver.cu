@@ -468,6 +468,14 @@ void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr) {
       g2.A = A2h.p; g2.Alo = A2l.p; g2.B = Wh.p; g2.Blo = Wl.p;
       g2.tier = tr; g2.out = TC_OUT_F64;
       g2.C = Rp.c() + p0; g2.ldc = n_ab;
+      g2.bn = tc_pick_bn(np);
+      g2.split_k = tc_pick_split(((2 * n_ij + 127) / 128) * ((np + g2.bn - 1) / g2.bn), Kp2 / kal,
+                                 num_sms);
+      if (g2.split_k > 1) {
+        // partial sums accumulate atomically into this block's zeroed columns
+        scale_2d(static_cast<cplx *>(g2.C), nullptr, nullptr, n_ab, n_ij, np, C0(), st);
+        g2.out = TC_OUT_F64_ATOMIC;
+      }
       {
         Engine::Region r = eng.region("ladder gemm2");
         gemm_tc(g2, st, err_d.as<int>());
@@ -590,16 +598,17 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
     Engine::Region r = eng.region("ladder total");
     ladder(Lt.c(), tau.c(), R2, tr);
   }
-  // W_mbej
+  // W_mbej, stored as W[j][b][m][e]: its producers then write rows of
+  // contiguous (m, e) and the ring contraction below reads contiguous K
   Buf W(&al, sizeof(cplx) * n2);
-  auto Wt = [&](const char *ix) { return T(W.c(), ix, {o, v, v, o}); };
-  d2d(W.p, ovvo.p, sizeof(cplx) * n2, st);
+  auto Wt = [&](const char *ix) { return T(W.c(), ix, {o, v, o, v}); };  // "jbme" order
+  eng.permute_into(C1(), g_ovvo("mbej"), C0(), Wt("jbme"));
   //   + t_j^f <mb||ef> = sum_P L^P_me Y^P_bj - sum_P Z^P_mj L^P_be
-  eng.contract(C1(), Lov_("Pme"), T(Y.c(), "Pbj", {X, v, o}), C1(), Wt("mbej"), tr);
+  eng.contract(C1(), T(Y.c(), "Pbj", {X, v, o}), Lov_("Pme"), C1(), Wt("jbme"), tr);
   eng.contract(C1(), Lov_("Pmf"), t1("jf"), C0(), T(Zm.c(), "Pmj", {X, o, o}), tr);
-  eng.contract(Cr(-1), T(Zm.c(), "Pmj", {X, o, o}), Lvv_("Pbe"), C1(), Wt("mbej"), tr);
+  eng.contract(Cr(-1), T(Zm.c(), "Pmj", {X, o, o}), Lvv_("Pbe"), C1(), Wt("jbme"), tr);
   //   - t_n^b <mn||ej> = + t_n^b <mn||je>
-  eng.contract(C1(), g_ooov("mnje"), t1("nb"), C1(), Wt("mbej"), tr);
+  eng.contract(C1(), g_ooov("mnje"), t1("nb"), C1(), Wt("jbme"), tr);
   //   - (1/2 t_jn^fb + t_j^f t_n^b) <mn||ef>
   {
     Buf z(&al, sizeof(cplx) * n2);
@@ -607,10 +616,10 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
       Engine::Region r = eng.region("make_z");
       make_z(t1p, t2p, z.c(), o, v, 0.5, st, tr != TIER_FP64);
     }
-    eng.contract(Cr(-1), T(z.c(), "jnfb", {o, o, v, v}), g_oovv("mnef"), C1(), Wt("mbej"), tr);
+    eng.contract(Cr(-1), T(z.c(), "jnfb", {o, o, v, v}), g_oovv("mnef"), C1(), Wt("jbme"), tr);
   }
   // P(ij)P(ab) [t_im^ae W_mbej - t_i^e t_m^a <mb||ej>]
-  eng.contract(C1(), t2("imae"), Wt("mbej"), C0(), Xt("ijab"), tr);
+  eng.contract(C1(), t2("imae"), Wt("jbme"), C0(), Xt("ijab"), tr);
   {
     Buf y2(&al, sizeof(cplx) * oo * o * v);
     eng.contract(C1(), t1("ie"), g_ovvo("mbej"), C0(), T(y2.c(), "mbij", {o, v, o, o}), tr);
