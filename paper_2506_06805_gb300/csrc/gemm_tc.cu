@@ -584,6 +584,8 @@ int tc_pick_split(long tiles, long nkb, int num_sms) {
   int sk = 1;
   if (tiles <= 0 || tiles >= 8L * num_sms || nkb < 8) return sk;
   const long P = num_sms;
+  // a handful of tiles over a long K: one split per free SM
+  if (tiles * 32 < P) return static_cast<int>(std::max<long>(1, std::min<long>(nkb / 4, P / tiles)));
   auto eff = [&](long sp) {
     const long tt = tiles * sp;
     return static_cast<double>(tt) / (static_cast<double>((tt + P - 1) / P) * P);

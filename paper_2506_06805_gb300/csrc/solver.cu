@@ -556,23 +556,29 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
   auto R2t = [&](const char *ix) { return T(R2, ix, {o, o, v, v}); };
   // driver <ab||ij> = conj(<ij||ab>)
   eng.permute_into(C1(), conj(g_oovv("ijab")), C0(), R2t("ijab"));
-  // P(ab) t_ij^ae (F_be - 1/2 t_m^b F_me)
+  // Terms sharing one antisymmetriser are summed into X first, so each
+  // symmetry class costs one pass over R2.
+  // P(ab) [t_ij^ae (F_be - 1/2 t_m^b F_me) - t_m^a <mb||ij>], <mb||ij> = conj(<ij||mb>)
   {
     Buf Fbe(&al, sizeof(cplx) * vv);
     d2d(Fbe.p, Fae.p, sizeof(cplx) * vv, st);
     eng.contract(Cr(-0.5), t1("mb"), T(Fme.c(), "me", {o, v}), C1(), T(Fbe.c(), "be", {v, v}),
                  TIER_FP64);
     eng.contract(C1(), t2("ijae"), T(Fbe.c(), "be", {v, v}), C0(), Xt("ijab"), tr);
+    eng.contract(Cr(-1), t1("ma"), conj(g_ooov("ijmb")), C1(), Xt("ijab"), tr);
     { Engine::Region r_ = eng.region("antisym_add"); antisym_add(R2, Xb.c(), o, v, 1.0, 2, st); }
   }
-  // -P(ij) t_im^ab (F_mj + 1/2 t_j^e F_me)
+  // P(ij) [-t_im^ab (F_mj + 1/2 t_j^e F_me) + t_i^e <ab||ej>], the second as
+  // sum_P (Y^P_ai L^P_bj - L^P_aj Y^P_bi)
   {
     Buf Fmj(&al, sizeof(cplx) * oo);
     d2d(Fmj.p, Fmi.p, sizeof(cplx) * oo, st);
     eng.contract(Cr(0.5), t1("je"), T(Fme.c(), "me", {o, v}), C1(), T(Fmj.c(), "mj", {o, o}),
                  TIER_FP64);
-    eng.contract(C1(), t2("imab"), T(Fmj.c(), "mj", {o, o}), C0(), Xt("ijab"), tr);
-    { Engine::Region r_ = eng.region("antisym_add"); antisym_add(R2, Xb.c(), o, v, -1.0, 1, st); }
+    eng.contract(Cr(-1), t2("imab"), T(Fmj.c(), "mj", {o, o}), C0(), Xt("ijab"), tr);
+    eng.contract(C1(), T(Y.c(), "Pai", {X, v, o}), Lvo_("Pbj"), C1(), Xt("ijab"), tr);
+    eng.contract(Cr(-1), Lvo_("Paj"), T(Y.c(), "Pbi", {X, v, o}), C1(), Xt("ijab"), tr);
+    { Engine::Region r_ = eng.region("antisym_add"); antisym_add(R2, Xb.c(), o, v, 1.0, 1, st); }
   }
   // hole ladder: 1/2 tau_mn^ab W'_mnij + 1/4 t_mn^ab Z_mnij, with
   // W' = <mn||ij> + P(ij) t_j^e <mn||ie>, Z = sum_ef <mn||ef> tau_ij^ef
@@ -602,7 +608,10 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
   // contiguous (m, e) and the ring contraction below reads contiguous K
   Buf W(&al, sizeof(cplx) * n2);
   auto Wt = [&](const char *ix) { return T(W.c(), ix, {o, v, o, v}); };  // "jbme" order
-  eng.permute_into(C1(), g_ovvo("mbej"), C0(), Wt("jbme"));
+  if (ovvo_jbme.p)
+    d2d(W.p, ovvo_jbme.p, sizeof(cplx) * n2, st);
+  else
+    eng.permute_into(C1(), g_ovvo("mbej"), C0(), Wt("jbme"));
   //   + t_j^f <mb||ef> = sum_P L^P_me Y^P_bj - sum_P Z^P_mj L^P_be
   eng.contract(C1(), T(Y.c(), "Pbj", {X, v, o}), Lov_("Pme"), C1(), Wt("jbme"), tr);
   eng.contract(C1(), Lov_("Pmf"), t1("jf"), C0(), T(Zm.c(), "Pmj", {X, o, o}), tr);
@@ -626,13 +635,6 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
     eng.contract(Cr(-1), t1("ma"), T(y2.c(), "mbij", {o, v, o, o}), C1(), Xt("ijab"), tr);
   }
   { Engine::Region r_ = eng.region("antisym_add"); antisym_add(R2, Xb.c(), o, v, 1.0, 3, st); }
-  // P(ij) t_i^e <ab||ej> = P(ij) sum_P (Y^P_ai L^P_bj - L^P_aj Y^P_bi)
-  eng.contract(C1(), T(Y.c(), "Pai", {X, v, o}), Lvo_("Pbj"), C0(), Xt("ijab"), tr);
-  eng.contract(Cr(-1), Lvo_("Paj"), T(Y.c(), "Pbi", {X, v, o}), C1(), Xt("ijab"), tr);
-  { Engine::Region r_ = eng.region("antisym_add"); antisym_add(R2, Xb.c(), o, v, 1.0, 1, st); }
-  // -P(ab) t_m^a <mb||ij>, <mb||ij> = conj(<ij||mb>)
-  eng.contract(C1(), t1("ma"), conj(g_ooov("ijmb")), C0(), Xt("ijab"), tr);
-  { Engine::Region r_ = eng.region("antisym_add"); antisym_add(R2, Xb.c(), o, v, -1.0, 2, st); }
 }
 
 // ===========================================================================
@@ -654,6 +656,13 @@ int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
   }
   Buf R1(&al, sizeof(cplx) * n1), R2(&al, sizeof(cplx) * n2);
   Buf vcur(&al, sizeof(cplx) * na), vnew(&al, sizeof(cplx) * na), step(&al, sizeof(cplx) * na);
+  ovvo_jbme.reset(&al, sizeof(cplx) * n2);
+  eng.permute_into(C1(), T(ovvo.c(), "mbej", {o, v, v, o}), C0(),
+                   T(ovvo_jbme.c(), "jbme", {o, v, o, v}));
+  struct Release {
+    Buf &b;
+    ~Release() { b.release(); }
+  } release_jbme{ovvo_jbme};
   Buf invd(&al, sizeof(double) * na);
   amp_denoms(eps_d.as<double>(), o, v, ij_i.as<int>(), ij_j.as<int>(), ab_a.as<int>(),
              ab_b.as<int>(), invd.as<double>(), st);
@@ -781,7 +790,7 @@ void Ctx::build_hbar() {
   auto Lov_ = [&](const char *ix) { return T(Lov.c(), ix, {X, o, v}); };
   auto Lvv_ = [&](const char *ix) { return T(Lvv.c(), ix, {X, v, v}); };
   const std::initializer_list<long> d4 = {o, o, o, o};
-  Buf tau(&al, sizeof(cplx) * n2);
+  Buf tau(&al, sizeof(cplx) * n2), Qh;
   make_tau(t1.c(), t2.c(), tau.c(), o, v, 1.0, st);
   B(Hov, ov);
   B(Hoo, oo);
@@ -815,9 +824,15 @@ void Ctx::build_hbar() {
     eng.contract(C1(), Lov_("Pmf"), a1("jf"), C0(), T(Zm.c(), "Pmj", {X, o, o}), tr);
     eng.contract(Cr(-1), T(Zm.c(), "Pmj", {X, o, o}), Lvv_("Pbe"), C1(), Ht("mbej"), tr);
     eng.contract(C1(), g_ooov("mnje"), a1("nb"), C1(), Ht("mbej"), tr);
-    Buf z(&al, sizeof(cplx) * n2);
-    make_z(t1.c(), t2.c(), z.c(), o, v, 1.0, st);
-    eng.contract(Cr(-1), T(z.c(), "jnfb", {o, o, v, v}), g_oovv("mnef"), C1(), Ht("mbej"), tr);
+    // - (t_jn^fb + t_j^f t_n^b) <mn||ef> = - Q_mbej - t_n^b u_mnej with
+    // Q_mbej = sum_nf t_jn^fb <mn||ef> (also used for H_mbij below) and
+    // u_mnej = sum_f <mn||ef> t_j^f
+    Qh.reset(&al, sizeof(cplx) * n2);
+    eng.contract(C1(), g_oovv("mnef"), t2t("jnfb"), C0(), T(Qh.c(), "mbej", {o, v, v, o}), tr);
+    axpby(n2, Cr(-1), Qh.c(), C1(), Hovvo.c(), st);
+    Buf u(&al, sizeof(cplx) * oo * ov);
+    eng.contract(C1(), g_oovv("mnef"), a1("jf"), C0(), T(u.c(), "mnej", {o, o, v, o}), tr);
+    eng.contract(Cr(-1), a1("nb"), T(u.c(), "mnej", {o, o, v, o}), C1(), Ht("mbej"), tr);
   }
   // H_mnij = <mn||ij> + P(ij) t_j^e <mn||ie> + 1/2 tau_ij^ef <mn||ef>
   {
@@ -853,8 +868,10 @@ void Ctx::build_hbar() {
     }
     G.release();
     Buf tW(&al, sizeof(cplx) * n2), y(&al, sizeof(cplx) * oo * ov);
+    // <mb||ej> - t_nj^bf <mn||ef> = <mb||ej> - Q_mbej
     d2d(tW.p, ovvo.p, sizeof(cplx) * n2, st);
-    eng.contract(Cr(-1), t2t("njbf"), g_oovv("mnef"), C1(), T(tW.c(), "mbej", {o, v, v, o}), tr);
+    axpby(n2, Cr(-1), Qh.c(), C1(), tW.c(), st);
+    Qh.release();
     eng.contract(C1(), g_ooov("mnie"), t2t("jnbe"), C0(), T(y.c(), "mbij", {o, v, o, o}), tr);
     eng.contract(C1(), a1("ie"), T(tW.c(), "mbej", {o, v, v, o}), C1(), T(y.c(), "mbij", {o, v, o, o}),
                  tr);

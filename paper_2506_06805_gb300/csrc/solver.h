@@ -33,6 +33,7 @@ struct Ctx {
   // stored integrals (at most two virtual indices)
   bool ints = false;
   Buf oooo, ooov, oovv, ovvo;
+  Buf ovvo_jbme;  // <mb||ej> as [j][b][m][e], held during ccsd_solve
 
   // amplitudes
   Buf t1, t2;
