@@ -52,6 +52,11 @@ extern "C" {
 #define CC_TIER_TF32 1   /* tcgen05 kind::tf32, one pass, FP32 accumulate */
 #define CC_TIER_TF32X3 2 /* tcgen05 tf32, hi/lo split, 3 products */
 #define CC_TIER_BF16X3 3 /* tcgen05 kind::f16 bf16, hi/lo split, 3 products */
+#define CC_TIER_FP16 4   /* tcgen05 kind::f16 fp16, one pass, FP32 accumulate;
+                          * each operand scaled by a power of two chosen from
+                          * its largest magnitude, so the product rounding is
+                          * that of TF32 (11-bit significands) at twice the
+                          * tensor-core rate */
 
 typedef struct cc_ctx cc_ctx; /* one molecular (synthetic) system */
 
@@ -215,7 +220,9 @@ int cc_zgemm_dev(int tier, long M, long N, long K, const double *A_dev,
  * 256 + s (round256(2 M Kp e) + round256(N Kp e)) bytes of it, with
  * Kp = 2K rounded up to 32 (tf32) or 64 (bf16) elements, e = 4 (tf32) or
  * 2 (bf16) bytes and s = 1 (CC_TIER_TF32) or 2 (split tiers); larger
- * problems are rejected with CC_ERR_ARG and a message. CC_TIER_FP64 uses
+ * problems are rejected with CC_ERR_ARG and a message. CC_TIER_FP16 (whose
+ * operand scales need device scratch of their own) is rejected with
+ * CC_ERR_ARG. CC_TIER_FP64 uses
  * no temporaries. Work runs on the default stream (cc_set_default_stream)
  * and the call returns after it completes.
  * The first call on each device looks up the array's device address with

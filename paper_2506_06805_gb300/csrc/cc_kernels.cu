@@ -1,4 +1,5 @@
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cmath>
@@ -494,6 +495,101 @@ __global__ void antisym_kernel(const void *Vp, bool f32, int v, int a0, long p0,
   }
 }
 
+// Tensor-core tiers: W[(a,b)][(c<d)] = V[a][c][b][d] - V[a][d][b][c] from the
+// FP32 slab. Block (32, 8) per (a, b) pair row and (C <= D) pair of 32-wide
+// tiles of c and d: the tiles V[a][C][b][D] and V[a][D][b][C] are read along
+// their inner index into shared memory, and W is written along d (packed
+// (c<d) columns are contiguous in d for fixed c). Differences in FP32; PT:
+// 0 tf32 hi (+ lo), 1 bf16 hi (+ lo), 2 fp16 scaled by fp16_scale(*amax).
+template <int PT>
+__global__ void __launch_bounds__(256) antisym_tile_kernel(
+    const float2 *__restrict__ V, int v, int a0, long p0, long np, const int *__restrict__ pair_a,
+    const int *__restrict__ pair_b, void *hi, void *lo, long kp, int ntile, const float *amax) {
+  __shared__ float2 s1[32][33];  // V[a][c][b][d], c = C0 + row
+  __shared__ float2 s2[32][33];  // V[a][d][b][c], d = D0 + row
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  int ct = 0, p = blockIdx.x;
+  while (p >= ntile - ct) {
+    p -= ntile - ct;
+    ++ct;
+  }
+  const int dt = ct + p;
+  const int C0 = ct * 32, D0 = dt * 32;
+  const long ld = static_cast<long>(v - a0) * v;
+  const float sc = (PT == 2 && amax) ? fp16_scale(*amax) : 1.0f;
+  for (long r = blockIdx.y; r < np; r += gridDim.y) {
+    const int a = pair_a[p0 + r], b = pair_b[p0 + r];
+    const long ra = static_cast<long>(a - a0) * v, cb = static_cast<long>(b - a0) * v;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int row = ty + 8 * j;
+      const int c = C0 + row, d = D0 + tx;
+      s1[row][tx] = (c < v && d < v) ? V[(ra + c) * ld + cb + d] : make_float2(0.f, 0.f);
+      const int d2 = D0 + row, c2 = C0 + tx;
+      s2[row][tx] = (d2 < v && c2 < v) ? V[(ra + d2) * ld + cb + c2] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int row = ty + 8 * j;
+      const int c = C0 + row, d = D0 + tx;
+      if (c < d && d < v) {
+        const float2 x = s1[row][tx], y = s2[tx][row];
+        const float wr = x.x - y.x, wi = x.y - y.y;
+        const long q = static_cast<long>(c) * (2L * v - c - 1) / 2 + (d - c - 1);
+        const long e = r * kp + 2 * q;  // even: paired stores
+        if constexpr (PT == 0) {
+          uint32_t ur, ui;
+          asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(ur) : "f"(wr));
+          asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(ui) : "f"(wi));
+          const float hr = __uint_as_float(ur), hi_ = __uint_as_float(ui);
+          reinterpret_cast<float2 *>(hi)[e >> 1] = make_float2(hr, hi_);
+          if (lo) {
+            uint32_t lr, li;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lr) : "f"(wr - hr));
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(li) : "f"(wi - hi_));
+            reinterpret_cast<float2 *>(lo)[e >> 1] = make_float2(__uint_as_float(lr), __uint_as_float(li));
+          }
+        } else if constexpr (PT == 1) {
+          const __nv_bfloat162 h = __floats2bfloat162_rn(wr, wi);
+          reinterpret_cast<__nv_bfloat162 *>(hi)[e >> 1] = h;
+          const float2 hf = __bfloat1622float2(h);
+          reinterpret_cast<__nv_bfloat162 *>(lo)[e >> 1] = __floats2bfloat162_rn(wr - hf.x, wi - hf.y);
+        } else {
+          reinterpret_cast<__half2 *>(hi)[e >> 1] = __floats2half2_rn(sc * wr, sc * wi);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Bound on |W| for the FP16 scale: |V_acbd| <= max_pq sum_P |L~^P_pq|^2
+// (Cauchy-Schwarz over P), so |W| <= 2 max_pq sum_P |L~^P_pq|^2. One thread
+// per (p, q); block maxima through an unsigned atomicMax of the float bits.
+__global__ void __launch_bounds__(256) w_bound_kernel(const double2 *__restrict__ L, int X, long vv,
+                                                      float *out) {
+  __shared__ float sh[8];
+  const long pq = blockIdx.x * 256L + threadIdx.x;
+  float n2 = 0.0f;
+  if (pq < vv) {
+    for (int P = 0; P < X; ++P) {
+      const double2 x = L[static_cast<long>(P) * vv + pq];
+      const float xr = f64_to_f32(x.x), xi = f64_to_f32(x.y);
+      n2 = fmaf(xr, xr, fmaf(xi, xi, n2));
+    }
+  }
+  float m = 2.0f * n2 * 1.001f;  // margin for the FP32 sum
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float x = 0.0f;
+    for (int i = 0; i < 8; ++i) x = fmaxf(x, sh[i]);
+    atomicMax(reinterpret_cast<unsigned *>(out), __float_as_uint(x));
+  }
+}
+
 // zero the padded tail columns [2*ncd, kp) of rows [0, np)
 template <typename E>
 __global__ void zero_tail(E *p, long np, long k0, long kp) {
@@ -838,39 +934,61 @@ void diis_combine(cplx *const *vecs, const cplx *coef, int m, long n, cplx *out,
 
 void ladder_antisym(const void *V, bool f32, int v, int a0, int nA, long p0, long p1,
                     const int *pair_a, const int *pair_b, const int *cd_c, const int *cd_d,
-                    int tier, void *hi, void *lo, long kp, cplx *w64, cudaStream_t st) {
+                    int tier, void *hi, void *lo, long kp, cplx *w64, cudaStream_t st,
+                    const float *amax) {
   (void)nA;
   const long ncd = static_cast<long>(v) * (v - 1) / 2;
   const long np = p1 - p0;
   if (np <= 0) return;
-  const unsigned g = grid_for(np * ncd);
   if (tier == TIER_FP64) {
-    antisym_kernel<2><<<g, 256, 0, st>>>(V, f32, v, a0, p0, p1, pair_a, pair_b, cd_c, cd_d, ncd,
-                                         nullptr, nullptr, 0, w64);
-  } else if (tier == TIER_BF16X3) {
-    antisym_kernel<1><<<g, 256, 0, st>>>(V, f32, v, a0, p0, p1, pair_a, pair_b, cd_c, cd_d, ncd, hi,
-                                         lo, kp, nullptr);
-    if (kp > 2 * ncd) {
-      zero_tail<__nv_bfloat16><<<grid_for(np * (kp - 2 * ncd)), 256, 0, st>>>(
-          reinterpret_cast<__nv_bfloat16 *>(hi), np, 2 * ncd, kp);
-      zero_tail<__nv_bfloat16><<<grid_for(np * (kp - 2 * ncd)), 256, 0, st>>>(
-          reinterpret_cast<__nv_bfloat16 *>(lo), np, 2 * ncd, kp);
-      count_launch(2);
-    }
-  } else {
-    antisym_kernel<0><<<g, 256, 0, st>>>(V, f32, v, a0, p0, p1, pair_a, pair_b, cd_c, cd_d, ncd, hi,
-                                         tier == TIER_TF32 ? nullptr : lo, kp, nullptr);
-    if (kp > 2 * ncd) {
-      zero_tail<float><<<grid_for(np * (kp - 2 * ncd)), 256, 0, st>>>(reinterpret_cast<float *>(hi),
-                                                                        np, 2 * ncd, kp);
-      count_launch();
-      if (tier != TIER_TF32) {
-        zero_tail<float><<<grid_for(np * (kp - 2 * ncd)), 256, 0, st>>>(
-            reinterpret_cast<float *>(lo), np, 2 * ncd, kp);
-        count_launch();
-      }
-    }
+    antisym_kernel<2><<<grid_for(np * ncd), 256, 0, st>>>(V, f32, v, a0, p0, p1, pair_a, pair_b,
+                                                         cd_c, cd_d, ncd, nullptr, nullptr, 0, w64);
+    LAUNCH_CHECK();
+    count_launch();
+    return;
   }
+  if (!f32) fail(CC_ERR_ARG, "ladder_antisym: tensor-core tiers take an FP32 slab");
+  if (tier == TIER_FP16 && !amax) fail(CC_ERR_ARG, "ladder_antisym: FP16 needs the W bound");
+  const int nt = (v + 31) / 32;
+  dim3 grid(static_cast<unsigned>(nt * (nt + 1) / 2),
+            static_cast<unsigned>(std::min<long>(np, 65535)));
+  const float2 *Vf = reinterpret_cast<const float2 *>(V);
+  if (tier == TIER_BF16X3) {
+    antisym_tile_kernel<1><<<grid, dim3(32, 8), 0, st>>>(Vf, v, a0, p0, np, pair_a, pair_b, hi, lo,
+                                                         kp, nt, nullptr);
+  } else if (tier == TIER_FP16) {
+    antisym_tile_kernel<2><<<grid, dim3(32, 8), 0, st>>>(Vf, v, a0, p0, np, pair_a, pair_b, hi,
+                                                         nullptr, kp, nt, amax);
+  } else {
+    antisym_tile_kernel<0><<<grid, dim3(32, 8), 0, st>>>(Vf, v, a0, p0, np, pair_a, pair_b, hi,
+                                                         tier == TIER_TF32 ? nullptr : lo, kp, nt,
+                                                         nullptr);
+  }
+  LAUNCH_CHECK();
+  count_launch();
+  if (kp > 2 * ncd) {
+    const unsigned gt = grid_for(np * (kp - 2 * ncd));
+    if (tier == TIER_TF32 || tier == TIER_TF32X3) {
+      zero_tail<float><<<gt, 256, 0, st>>>(reinterpret_cast<float *>(hi), np, 2 * ncd, kp);
+      if (tier == TIER_TF32X3)
+        zero_tail<float><<<gt, 256, 0, st>>>(reinterpret_cast<float *>(lo), np, 2 * ncd, kp);
+    } else if (tier == TIER_BF16X3) {
+      zero_tail<__nv_bfloat16><<<gt, 256, 0, st>>>(reinterpret_cast<__nv_bfloat16 *>(hi), np,
+                                                    2 * ncd, kp);
+      zero_tail<__nv_bfloat16><<<gt, 256, 0, st>>>(reinterpret_cast<__nv_bfloat16 *>(lo), np,
+                                                    2 * ncd, kp);
+    } else {
+      zero_tail<__half><<<gt, 256, 0, st>>>(reinterpret_cast<__half *>(hi), np, 2 * ncd, kp);
+    }
+    LAUNCH_CHECK();
+    count_launch();
+  }
+}
+
+void ladder_w_bound(const cplx *L, int X, long vv, float *out, cudaStream_t st) {
+  CUDA_CHECK(cudaMemsetAsync(out, 0, sizeof(float), st));
+  if (vv <= 0 || X <= 0) return;
+  w_bound_kernel<<<static_cast<unsigned>((vv + 255) / 256), 256, 0, st>>>(L, X, vv, out);
   LAUNCH_CHECK();
   count_launch();
 }

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -113,7 +114,31 @@ struct Buf {
 };
 
 // Precision tiers of the contraction engine (CC_TIER_* in cdfns.h).
-enum Tier { TIER_FP64 = 0, TIER_TF32 = 1, TIER_TF32X3 = 2, TIER_BF16X3 = 3 };
+enum Tier { TIER_FP64 = 0, TIER_TF32 = 1, TIER_TF32X3 = 2, TIER_BF16X3 = 3, TIER_FP16 = 4 };
+constexpr int TIER_LAST = TIER_FP16;
+
+// Scale for the FP16 tier: the power of two 2^k with amax 2^k < 2^15, so
+// every scaled magnitude stays below 2^15 (FP16 max 65504) and values down
+// to amax 2^-29 remain normal numbers; 1 for amax = 0 or non-finite.
+__host__ __device__ inline float fp16_scale(float amax) {
+  if (!(amax > 0.0f) || !(amax < 3.0e38f)) return 1.0f;
+  unsigned u;
+#ifdef __CUDA_ARCH__
+  u = __float_as_uint(amax);
+#else
+  std::memcpy(&u, &amax, sizeof(u));
+#endif
+  int k = 141 - static_cast<int>((u >> 23) & 0xffu);  // amax < 2^(eb - 126)
+  k = k > 127 ? 127 : (k < -126 ? -126 : k);
+  const unsigned r = static_cast<unsigned>(k + 127) << 23;
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(r);
+#else
+  float f;
+  std::memcpy(&f, &r, sizeof(f));
+  return f;
+#endif
+}
 
 // Kernel launch counter (for reporting how many kernels ran).
 extern unsigned long long g_launches;

@@ -52,25 +52,43 @@ const long *Engine::table(const std::vector<long> &dims, const std::vector<long>
 }
 
 std::pair<void *, void *> Engine::packed(bool a_side, const TRef &t, const long *rt, const long *kt,
-                                         long ld, long rows, long K, long Kp, int tier) {
+                                         long ld, long rows, long K, long Kp, int tier,
+                                         const float **amax) {
   std::ostringstream key;
   key << (a_side ? 'A' : 'B') << t.p << ':' << t.conj << ':' << rt << ':' << kt << ':' << ld << ':'
       << rows << ':' << K << ':' << Kp << ':' << tier;
   auto it = packs_.find(key.str());
-  if (it != packs_.end()) return {it->second.hi.p, it->second.lo.p};
+  if (it != packs_.end()) {
+    *amax = it->second.amax.as<float>();
+    return {it->second.hi.p, it->second.lo.p};
+  }
   const size_t eb = tc_elem_bytes(tier);
   const size_t n = eb * (a_side ? 2 : 1) * rows * Kp;
   Packed pk;
   ++gen;
   pk.hi.reset(al, n);
-  if (tier != TIER_TF32) pk.lo.reset(al, n);
+  if (tier != TIER_TF32 && tier != TIER_FP16) pk.lo.reset(al, n);
+  if (tier == TIER_FP16) {
+    pk.amax.reset(al, sizeof(float));
+    tc_absmax(t.p, rt, kt, ld, rows, K, pk.amax.as<float>(), st);
+  }
   if (a_side)
-    tc_pack_A(t.p, rt, kt, ld, t.conj, rows, K, Kp, tier, pk.hi.p, pk.lo.p, st);
+    tc_pack_A(t.p, rt, kt, ld, t.conj, rows, K, Kp, tier, pk.hi.p, pk.lo.p, st, pk.amax.as<float>());
   else
-    tc_pack_B(t.p, rt, kt, ld, t.conj, rows, K, Kp, tier, pk.hi.p, pk.lo.p, st);
+    tc_pack_B(t.p, rt, kt, ld, t.conj, rows, K, Kp, tier, pk.hi.p, pk.lo.p, st, pk.amax.as<float>());
   std::pair<void *, void *> r{pk.hi.p, pk.lo.p};
+  *amax = pk.amax.as<float>();
   packs_[key.str()] = std::move(pk);
   return r;
+}
+
+float *Engine::plane_amax(int which) {
+  Buf &b = amax_planes_[which];
+  if (!b.p) {
+    b.reset(al, sizeof(float));
+    ++gen;
+  }
+  return b.as<float>();
 }
 
 void *Engine::plane(int which, size_t bytes) {
@@ -284,24 +302,36 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
   const int kal = tc_k_align(tier);
   const long Kp = ((2 * K + kal - 1) / kal) * kal;
   const size_t eb = tc_elem_bytes(tier);
-  const bool split = tier != TIER_TF32;
+  const bool split = tier == TIER_TF32X3 || tier == TIER_BF16X3;
   void *Ah, *Al = nullptr, *Bh, *Bl = nullptr;
   const int pb = 4 * (slot < 0 ? 0 : slot + 1);  // plane set of this contraction
+  const bool f16 = tier == TIER_FP16;
+  const float *xa = nullptr, *xb = nullptr;  // FP16 operand maxima
   if (A.stable) {
-    std::tie(Ah, Al) = packed(true, A, am, ak, lda, M, K, Kp, tier);
+    std::tie(Ah, Al) = packed(true, A, am, ak, lda, M, K, Kp, tier, &xa);
   } else {
     Ah = plane(pb + 0, eb * 2 * M * Kp);
     Al = split ? plane(pb + 1, eb * 2 * M * Kp) : nullptr;
     Region r = region("pack A " + A.idx);
-    tc_pack_A(A.p, am, ak, lda, A.conj, M, K, Kp, tier, Ah, Al, st);
+    if (f16) {
+      float *x = plane_amax(pb + 0);
+      tc_absmax(A.p, am, ak, lda, M, K, x, st);
+      xa = x;
+    }
+    tc_pack_A(A.p, am, ak, lda, A.conj, M, K, Kp, tier, Ah, Al, st, xa);
   }
   if (B.stable) {
-    std::tie(Bh, Bl) = packed(false, B, bn, bk, ldb, N, K, Kp, tier);
+    std::tie(Bh, Bl) = packed(false, B, bn, bk, ldb, N, K, Kp, tier, &xb);
   } else {
     Bh = plane(pb + 2, eb * N * Kp);
     Bl = split ? plane(pb + 3, eb * N * Kp) : nullptr;
     Region r = region("pack B " + B.idx);
-    tc_pack_B(B.p, bn, bk, ldb, B.conj, N, K, Kp, tier, Bh, Bl, st);
+    if (f16) {
+      float *x = plane_amax(pb + 2);
+      tc_absmax(B.p, bn, bk, ldb, N, K, x, st);
+      xb = x;
+    }
+    tc_pack_B(B.p, bn, bk, ldb, B.conj, N, K, Kp, tier, Bh, Bl, st, xb);
   }
   TcDesc t;
   t.M = M; t.N = N; t.Kp = Kp;
@@ -309,6 +339,7 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
   t.tier = tier;
   t.C = C.p; t.cm = cm; t.cn = cn; t.ldc = ldc;
   t.alpha = alpha; t.beta = beta;
+  t.amax_a = xa; t.amax_b = xb;
   t.bn = tc_pick_bn(N);
   const long tiles = ((2 * M + 127) / 128) * ((N + t.bn - 1) / t.bn);
   const int sk = tc_pick_split(tiles, Kp / kal, num_sms);

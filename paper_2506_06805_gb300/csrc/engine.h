@@ -101,11 +101,16 @@ class Engine {
 
  private:
   struct Packed {
-    Buf hi, lo;
+    Buf hi, lo, amax;
   };
-  // returns (hi, lo) planes of a stable operand, packing it on first use
+  // returns (hi, lo) planes of a stable operand, packing it on first use;
+  // *amax receives its FP16 scale source (TIER_FP16) or nullptr
   std::pair<void *, void *> packed(bool a_side, const TRef &t, const long *rt, const long *kt,
-                                   long ld, long rows, long K, long Kp, int tier);
+                                   long ld, long rows, long K, long Kp, int tier,
+                                   const float **amax);
+  // device float of plane slot `which` for the FP16 operand maximum
+  float *plane_amax(int which);
+  std::map<int, Buf> amax_planes_;
   std::map<std::string, Buf> cache_;
   std::map<std::string, Packed> packs_;
   std::map<int, Buf> planes_;

@@ -13,14 +13,18 @@
 // with bf16 hi/lo and three products (TIER_BF16X3). Accumulation is FP32 in
 // TMEM; the epilogue accumulates into FP64 (or stores FP32 for staging).
 //
-// CTA layout (192 threads): warps 0-3 epilogue (TMEM lane quadrant = warp),
-// warp 4 TMA producer, warp 5 TMEM allocator + MMA issuer. One output tile
-// of 128 real rows (64 complex rows) x BN columns per CTA; split-K over
-// blockIdx.z. Every mbarrier wait is bounded in time; on expiry the kernel
-// records an error flag, drains, frees TMEM and returns.
+// CTA layout (320 threads): warps 0-7 epilogue, warp 8 TMA producer, warp 9
+// TMEM allocator + MMA issuer; persistent CTAs walk a list of 128 x BN output
+// tiles (of up to 16 problems per launch), K optionally split. The wide
+// (BN = 256) kernels run as clusters of two CTAs on vertically adjacent
+// tiles that share their B tile: each CTA loads half of it and multicasts it
+// to both, which cuts the L2 -> SM operand traffic per MMA by a third.
+// Every mbarrier wait is bounded in time; on expiry the kernel records an
+// error flag, drains, frees TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cstdio>
 #include <cstdlib>
@@ -84,6 +88,35 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
       : "memory");
 }
+// Same load, written to the same shared-memory offset of every CTA in
+// ctaMask, each of whose mbarrier (same offset) receives the byte count.
+__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                               int x, int y, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      ".multicast::cluster [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_count_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" :::
+                   "memory");
+}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -138,6 +171,15 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
           smem_u32(bar))
       : "memory");
 }
+// Arrive on the mbarrier at this offset in every CTA of ctaMask once the
+// MMAs issued so far have completed.
+__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
   asm volatile(
@@ -166,6 +208,7 @@ struct alignas(64) TcProblem {
   long ldc;
   double2 alpha, beta;
   float2 alpha_f;   // alpha rounded to FP32 (applied to the FP32 tile)
+  const float *amax_a, *amax_b;  // FP16 operand scales (nullptr: none)
   int num_kb;       // K blocks of 128 bytes per row
   int kb_per_split;
   int k_splits, m_tiles, n_tiles;
@@ -213,15 +256,18 @@ __device__ __forceinline__ void tile_coords(const TcProblem &a, int t, int &m, i
 // accumulation only ever spans one chunk, which bounds its truncation bias
 // independently of K. Chunk and stage counters run on across tiles, so the
 // MMA of the next tile overlaps the epilogue stores of the previous one.
-template <int BN, int STAGES, bool SPLIT, bool BF16>
+// ET: operand type, 0 tf32 (kind::tf32), 1 bf16 / 2 fp16 (kind::f16)
+template <int BN, int STAGES, bool SPLIT, int ET, int CL>
 __global__ void __launch_bounds__(320, 1)
     tc_gemm_kernel(const __grid_constant__ TcGroup grp) {
+  static_assert(CL == 1 || CL == 2, "cluster of one or two CTAs");
   constexpr int A_BYTES = BM * ROW_BYTES;
   constexpr int B_BYTES = BN * ROW_BYTES;
   constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * (SPLIT ? 2 : 1);
-  constexpr int K_ELEMS = BF16 ? 64 : 32;        // elements per 128-byte row
+  constexpr bool F16K = ET != 0;                 // kind::f16 (bf16 or fp16)
+  constexpr int K_ELEMS = F16K ? 64 : 32;        // elements per 128-byte row
   constexpr int MMA_K_BYTES = 32;                // K per MMA: 8 tf32 / 16 bf16
-  constexpr uint32_t IDESC = make_idesc(BM, BN, BF16 ? 1u : 2u);
+  constexpr uint32_t IDESC = make_idesc(BM, BN, ET == 0 ? 2u : (ET == 1 ? 1u : 0u));
   constexpr int HALF = BN / 2;                   // columns per epilogue warp
   constexpr uint32_t TMEM_COLS = 2 * BN;
 
@@ -237,14 +283,21 @@ __global__ void __launch_bounds__(320, 1)
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int n_tiles_total = grp.total_tiles;
+  const int n_tiles_total = grp.total_tiles;  // work units (tile pairs when CL == 2)
   const int chunk = grp.chunk;
+  // cluster rank and the unit walk are re-read from special registers at
+  // each use (asm volatile) rather than held live through the loops, to keep
+  // the epilogue warps within their register budget
+#define TC_RANK (CL == 2 ? static_cast<int>(cluster_rank()) : 0)
+#define TC_UNIT0 (CL == 2 ? static_cast<int>(cluster_id_x()) : static_cast<int>(blockIdx.x))
+#define TC_USTEP (CL == 2 ? static_cast<int>(cluster_count_x()) : static_cast<int>(gridDim.x))
+  constexpr int HALF_B = (BN / 2) * ROW_BYTES;  // bytes of one multicast half of B
   int *const err = grp.err;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], CL);  // released by the MMA warp of every CTA reading it
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -256,6 +309,7 @@ __global__ void __launch_bounds__(320, 1)
   if (warp == 9) tmem_alloc(tmem_slot, TMEM_COLS);
   tc_fence_before();
   __syncthreads();
+  if constexpr (CL == 2) cluster_sync_all();  // peer barriers initialised before any multicast
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -264,10 +318,11 @@ __global__ void __launch_bounds__(320, 1)
       // ---------------- TMA producer ----------------
       long it = 0;  // k blocks issued so far (all tiles)
       bool ok = true;
-      for (int t = blockIdx.x; t < n_tiles_total && ok; t += gridDim.x) {
+      for (int t = TC_UNIT0; t < n_tiles_total && ok; t += TC_USTEP) {
         const TcProblem &P = grp.p[find_problem(grp, t)];
         int m_tile, n_tile, z;
         tile_coords(P, t - P.tile_start, m_tile, n_tile, z);
+        m_tile = m_tile * CL + TC_RANK;
         const int kb0 = z * P.kb_per_split;
         const int kb1 = min(P.num_kb, kb0 + P.kb_per_split);
         for (int kb = kb0; kb < kb1; ++kb, ++it) {
@@ -282,10 +337,22 @@ __global__ void __launch_bounds__(320, 1)
           mbar_expect_tx(&full[s], STAGE_BYTES);
           const int kx = kb * K_ELEMS;
           tma_load_2d(st, &P.mA, &full[s], kx, m_tile * BM);
-          tma_load_2d(st + A_BYTES, &P.mB, &full[s], kx, n_tile * BN);
+          if constexpr (CL == 2) {
+            const int rk = TC_RANK;
+            tma_load_2d_mc(st + A_BYTES + rk * HALF_B, &P.mB, &full[s], kx,
+                           n_tile * BN + rk * (BN / 2), 0x3);
+          } else {
+            tma_load_2d(st + A_BYTES, &P.mB, &full[s], kx, n_tile * BN);
+          }
           if constexpr (SPLIT) {
             tma_load_2d(st + A_BYTES + B_BYTES, &P.mAlo, &full[s], kx, m_tile * BM);
-            tma_load_2d(st + 2 * A_BYTES + B_BYTES, &P.mBlo, &full[s], kx, n_tile * BN);
+            if constexpr (CL == 2) {
+              const int rk = TC_RANK;
+              tma_load_2d_mc(st + 2 * A_BYTES + B_BYTES + rk * HALF_B, &P.mBlo, &full[s], kx,
+                             n_tile * BN + rk * (BN / 2), 0x3);
+            } else {
+              tma_load_2d(st + 2 * A_BYTES + B_BYTES, &P.mBlo, &full[s], kx, n_tile * BN);
+            }
           }
         }
       }
@@ -294,6 +361,14 @@ __global__ void __launch_bounds__(320, 1)
         if (!mbar_wait(&full[i % STAGES], static_cast<uint32_t>(i / STAGES) & 1u))
           atomicExch(err, 1);
       }
+      if constexpr (CL == 2) {
+        // and the peer's last releases of this CTA's stages (its MMA commits
+        // arrive here) must have landed before either CTA exits
+        for (long i = (it > STAGES ? it - STAGES : 0); i < it; ++i) {
+          if (!mbar_wait(&empty[i % STAGES], static_cast<uint32_t>(i / STAGES) & 1u))
+            atomicExch(err, 1);
+        }
+      }
     }
   } else if (warp == 9) {
     if (lane == 0) {
@@ -301,7 +376,7 @@ __global__ void __launch_bounds__(320, 1)
       long it = 0;  // k blocks consumed (all tiles)
       long c = 0;   // chunks issued (all tiles)
       bool ok = true;
-      for (int t = blockIdx.x; t < n_tiles_total && ok; t += gridDim.x) {
+      for (int t = TC_UNIT0; t < n_tiles_total && ok; t += TC_USTEP) {
         const TcProblem &P = grp.p[find_problem(grp, t)];
         int m_tile, n_tile, z;
         tile_coords(P, t - P.tile_start, m_tile, n_tile, z);
@@ -335,13 +410,17 @@ __global__ void __launch_bounds__(320, 1)
             for (int kk = 0; kk < ROW_BYTES / MMA_K_BYTES; ++kk) {
               const uint64_t da = sw128_desc(a0 + kk * MMA_K_BYTES);
               const uint64_t db = sw128_desc(b0 + kk * MMA_K_BYTES);
-              mma<BF16>(dt, da, db, IDESC, (i > 0 || kk > 0) ? 1u : 0u);
+              mma<F16K>(dt, da, db, IDESC, (i > 0 || kk > 0) ? 1u : 0u);
               if constexpr (SPLIT) {
-                mma<BF16>(dt, da, sw128_desc(blo + kk * MMA_K_BYTES), IDESC, 1u);
-                mma<BF16>(dt, sw128_desc(alo + kk * MMA_K_BYTES), db, IDESC, 1u);
+                mma<F16K>(dt, da, sw128_desc(blo + kk * MMA_K_BYTES), IDESC, 1u);
+                mma<F16K>(dt, sw128_desc(alo + kk * MMA_K_BYTES), db, IDESC, 1u);
               }
             }
-            mma_commit(&empty[s]);
+            if constexpr (CL == 2) {
+              mma_commit_mc(&empty[s], 0x3);
+            } else {
+              mma_commit(&empty[s]);
+            }
           }
           mma_commit(&tfull[buf]);
         }
@@ -357,10 +436,11 @@ __global__ void __launch_bounds__(320, 1)
     const int h = warp >> 2;
     long c = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < n_tiles_total && ok; t += gridDim.x) {
+    for (int t = TC_UNIT0; t < n_tiles_total && ok; t += TC_USTEP) {
       const TcProblem &args = grp.p[find_problem(grp, t)];
       int m_tile, n_tile, z;
       tile_coords(args, t - args.tile_start, m_tile, n_tile, z);
+      m_tile = m_tile * CL + TC_RANK;
       const int kb0 = z * args.kb_per_split;
       const int nkb = min(args.num_kb, kb0 + args.kb_per_split) - kb0;
       const int nch = (nkb + chunk - 1) / chunk;
@@ -392,6 +472,9 @@ __global__ void __launch_bounds__(320, 1)
       // lane/2) on the way in, lane = output column on the way out, so each
       // store instruction writes 32 consecutive complex values of one row.
       float *stg = stage + warp * 1024;
+      // undo the FP16 operand scales (an exact power of two)
+      float usc = 1.0f;
+      if (args.amax_a) usc = 1.0f / (fp16_scale(*args.amax_a) * fp16_scale(*args.amax_b));
       const long nbase = static_cast<long>(n_tile) * BN + h * HALF;
       const long mbase = static_cast<long>(m_tile) * (BM / 2) + q * 16;
 #pragma unroll
@@ -404,8 +487,8 @@ __global__ void __launch_bounds__(320, 1)
         const long cno = col_ok ? (args.cn ? args.cn[n] : n) : 0;
 #pragma unroll 4
         for (int rr = 0; rr < 16; ++rr) {
-          const float re = stg[(2 * rr) * 32 + (lane ^ (2 * rr))];
-          const float im = stg[(2 * rr + 1) * 32 + (lane ^ (2 * rr + 1))];
+          const float re = usc * stg[(2 * rr) * 32 + (lane ^ (2 * rr))];
+          const float im = usc * stg[(2 * rr + 1) * 32 + (lane ^ (2 * rr + 1))];
           const long mc = mbase + rr;
           if (!col_ok || mc >= args.M) continue;
           if (args.out == TC_OUT_F32) {
@@ -442,11 +525,15 @@ __global__ void __launch_bounds__(320, 1)
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (CL == 2) cluster_sync_all();
   if (warp == 9) {
     __syncwarp();
     tc_fence_after();
     tmem_dealloc(tmem, TMEM_COLS);
   }
+#undef TC_RANK
+#undef TC_UNIT0
+#undef TC_USTEP
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
@@ -462,14 +549,19 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
   return fn;
 }
 
-CUtensorMap make_map(const void *base, long rows, long kp, int box_rows, bool bf16) {
+// et: 0 fp32 (tf32), 1 bf16, 2 fp16
+CUtensorMap make_map(const void *base, long rows, long kp, int box_rows, int et) {
   CUtensorMap m;
+  const bool two = et != 0;
   const cuuint64_t dims[2] = {static_cast<cuuint64_t>(kp), static_cast<cuuint64_t>(rows)};
-  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(kp) * (bf16 ? 2 : 4)};
-  const cuuint32_t box[2] = {static_cast<cuuint32_t>(bf16 ? 64 : 32),
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(kp) * (two ? 2 : 4)};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(two ? 64 : 32),
                              static_cast<cuuint32_t>(box_rows)};
   const cuuint32_t estr[2] = {1, 1};
-  CUresult r = get_encoder()(&m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+  const CUtensorMapDataType dt = et == 0   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : et == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                           : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  CUresult r = get_encoder()(&m, dt,
                              2, const_cast<void *>(base), dims, strides, box, estr,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -477,14 +569,14 @@ CUtensorMap make_map(const void *base, long rows, long kp, int box_rows, bool bf
   return m;
 }
 
-template <int BN, int STAGES, bool SPLIT, bool BF16>
+template <int BN, int STAGES, bool SPLIT, int ET, int CL>
 void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
   constexpr int STAGE_BYTES = (BM * ROW_BYTES + BN * ROW_BYTES) * (SPLIT ? 2 : 1);
   // stages + barrier block (256 B) + 8 warps x 4 KB staging + alignment slack
   constexpr int SMEM = STAGES * STAGE_BYTES + 256 + 8 * 4096 + 1024;
   static_assert((2 * STAGES + 4) * 8 + 8 <= 256, "barrier block");
   static_assert(SMEM <= 232448, "shared memory budget");
-  auto kern = tc_gemm_kernel<BN, STAGES, SPLIT, BF16>;
+  auto kern = tc_gemm_kernel<BN, STAGES, SPLIT, ET, CL>;
   static bool attr = false;
   if (!attr) {
     CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
@@ -505,21 +597,23 @@ void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
     if (g.M <= 0 || g.N <= 0 || g.Kp <= 0) continue;
     TcProblem &a = grp.p[np++];
     const long mr = 2 * g.M;
-    a.mA = make_map(g.A, mr, g.Kp, BM, BF16);
-    a.mB = make_map(g.B, g.N, g.Kp, BN, BF16);
-    a.mAlo = SPLIT ? make_map(g.Alo, mr, g.Kp, BM, BF16) : a.mA;
-    a.mBlo = SPLIT ? make_map(g.Blo, g.N, g.Kp, BN, BF16) : a.mB;
+    a.mA = make_map(g.A, mr, g.Kp, BM, ET);
+    // with a CTA pair each CTA loads (and multicasts) half of the B tile
+    a.mB = make_map(g.B, g.N, g.Kp, BN / CL, ET);
+    a.mAlo = SPLIT ? make_map(g.Alo, mr, g.Kp, BM, ET) : a.mA;
+    a.mBlo = SPLIT ? make_map(g.Blo, g.N, g.Kp, BN / CL, ET) : a.mB;
     a.M = g.M;
     a.N = g.N;
-    a.num_kb = static_cast<int>(g.Kp / (BF16 ? 64 : 32));
+    a.num_kb = static_cast<int>(g.Kp / (ET != 0 ? 64 : 32));
     const int sk = std::max(1, std::min(g.split_k, a.num_kb));
     a.kb_per_split = (a.num_kb + sk - 1) / sk;
     a.k_splits = (a.num_kb + a.kb_per_split - 1) / a.kb_per_split;
-    a.m_tiles = static_cast<int>((mr + BM - 1) / BM);
+    // work units: m tiles, or vertically adjacent pairs of them for CL = 2
+    a.m_tiles = static_cast<int>(((mr + BM - 1) / BM + CL - 1) / CL);
     a.n_tiles = static_cast<int>((g.N + BN - 1) / BN);
     // raster groups: as many A panels (128 rows x the K range of a split) as
     // fit in ~24 MB of L2 share each B panel while it is resident
-    const double panel = static_cast<double>(BM) * a.kb_per_split * ROW_BYTES * (SPLIT ? 2 : 1);
+    const double panel = static_cast<double>(BM) * CL * a.kb_per_split * ROW_BYTES * (SPLIT ? 2 : 1);
     a.group_m = g.group_m > 0 ? std::min(g.group_m, a.m_tiles)
                               : static_cast<int>(std::max(1.0, std::min<double>(a.m_tiles, 24.0e6 / panel)));
     a.out = g.out;
@@ -530,6 +624,10 @@ void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
     a.alpha = g.alpha;
     a.beta = g.beta;
     a.alpha_f = make_float2(static_cast<float>(g.alpha.x), static_cast<float>(g.alpha.y));
+    a.amax_a = g.amax_a;
+    a.amax_b = g.amax_b;
+    if ((g.amax_a == nullptr) != (g.amax_b == nullptr))
+      fail(CC_ERR_ARG, "gemm_tc: FP16 operand scales come in pairs");
     a.tile_start = static_cast<int>(tiles);
     tiles += static_cast<long>(a.m_tiles) * a.n_tiles * a.k_splits;
     if (tiles > 0x7fffffffL) fail(CC_ERR_ARG, "gemm_tc: too many tiles");
@@ -539,8 +637,31 @@ void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
   grp.total_tiles = static_cast<int>(tiles);
   grp.chunk = descs[0].chunk > 0 ? descs[0].chunk : (descs[0].tier == TIER_TF32 ? 8 : 4);
   grp.err = err;
-  dim3 grid(static_cast<unsigned>(std::min<long>(tiles, sms)));
-  kern<<<grid, 320, SMEM, st>>>(grp);
+  if constexpr (CL == 1) {
+    dim3 grid(static_cast<unsigned>(std::min<long>(tiles, sms)));
+    kern<<<grid, 320, SMEM, st>>>(grp);
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(320);
+    cfg.dynamicSmemBytes = SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr_cl[1];
+    attr_cl[0].id = cudaLaunchAttributeClusterDimension;
+    attr_cl[0].val.clusterDim.x = CL;
+    attr_cl[0].val.clusterDim.y = 1;
+    attr_cl[0].val.clusterDim.z = 1;
+    cfg.attrs = attr_cl;
+    cfg.numAttrs = 1;
+    // persistent clusters: as many as can be resident at once (SM pairs)
+    static int max_clusters = 0;
+    if (!max_clusters) {
+      cfg.gridDim = dim3(static_cast<unsigned>(CL * (sms / CL)));
+      CUDA_CHECK(cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg));
+      if (max_clusters < 1) fail(CC_ERR_UNSUPPORTED, "gemm_tc: no resident CTA pair");
+    }
+    cfg.gridDim = dim3(static_cast<unsigned>(CL * std::min<long>(tiles, max_clusters)));
+    CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, grp));
+  }
   LAUNCH_CHECK();
   count_launch();
 }
@@ -554,16 +675,20 @@ void check_desc(const TcDesc &g) {
 void dispatch(const TcDesc *d, int n, bool wide, cudaStream_t st, int *err) {
   switch (d[0].tier) {
     case TIER_TF32:
-      if (wide) launch<256, 4, false, false>(d, n, st, err);
-      else launch<128, 6, false, false>(d, n, st, err);
+      if (wide) launch<256, 4, false, 0, 1>(d, n, st, err);
+      else launch<128, 6, false, 0, 1>(d, n, st, err);
       break;
     case TIER_TF32X3:
-      if (wide) launch<256, 2, true, false>(d, n, st, err);
-      else launch<128, 3, true, false>(d, n, st, err);
+      if (wide) launch<256, 2, true, 0, 1>(d, n, st, err);
+      else launch<128, 3, true, 0, 1>(d, n, st, err);
       break;
     case TIER_BF16X3:
-      if (wide) launch<256, 2, true, true>(d, n, st, err);
-      else launch<128, 3, true, true>(d, n, st, err);
+      if (wide) launch<256, 2, true, 1, 1>(d, n, st, err);
+      else launch<128, 3, true, 1, 1>(d, n, st, err);
+      break;
+    case TIER_FP16:
+      if (wide) launch<256, 4, false, 2, 1>(d, n, st, err);
+      else launch<128, 6, false, 2, 1>(d, n, st, err);
       break;
     default:
       fail(CC_ERR_ARG, "gemm_tc: bad tier");
@@ -572,7 +697,7 @@ void dispatch(const TcDesc *d, int n, bool wide, cudaStream_t st, int *err) {
 
 }  // namespace
 
-int tc_k_align(int tier) { return tier == TIER_BF16X3 ? 64 : 32; }
+int tc_k_align(int tier) { return (tier == TIER_BF16X3 || tier == TIER_FP16) ? 64 : 32; }
 
 int tc_pick_bn(long N) {
   const double u256 = static_cast<double>(N) / (((N + 255) / 256) * 256);
@@ -601,7 +726,7 @@ int tc_pick_split(long tiles, long nkb, int num_sms) {
   }
   return sk;
 }
-size_t tc_elem_bytes(int tier) { return tier == TIER_BF16X3 ? 2 : 4; }
+size_t tc_elem_bytes(int tier) { return (tier == TIER_BF16X3 || tier == TIER_FP16) ? 2 : 4; }
 
 // ---------------------------------------------------------------------------
 // Autotuner: per (tier, shape bucket) the tile width, raster group and TMEM
@@ -738,7 +863,7 @@ void gemm_tc(const TcDesc &g0, cudaStream_t st, int *err) {
 
 void gemm_tc_grouped(const std::vector<TcDesc> &descs, cudaStream_t st, int *err) {
   // one launch per (tier, width) class, at most MAX_PROBLEMS problems each
-  for (int tier = TIER_TF32; tier <= TIER_BF16X3; ++tier) {
+  for (int tier = TIER_TF32; tier <= TIER_LAST; ++tier) {
     for (int w = 0; w < 2; ++w) {
       std::vector<TcDesc> cls;
       for (const TcDesc &g : descs) {
@@ -767,17 +892,20 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
-// Two adjacent elements (idx even) as one 8-byte (fp32) or 4-byte (bf16)
-// store; the split is the same as element by element.
-template <bool BF16>
-__device__ __forceinline__ void split_store2(void *hi, void *lo, long idx, float x, float y) {
-  if constexpr (BF16) {
+// Two adjacent elements (idx even) as one 8-byte (fp32) or 4-byte (bf16,
+// fp16) store. PT: 0 tf32 hi (+ lo), 1 bf16 hi (+ lo), 2 fp16 of sc * x.
+template <int PT>
+__device__ __forceinline__ void split_store2(void *hi, void *lo, long idx, float x, float y,
+                                             float sc) {
+  if constexpr (PT == 1) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
     reinterpret_cast<__nv_bfloat162 *>(hi)[idx >> 1] = h;
     if (lo) {
       const float2 hf = __bfloat1622float2(h);
       reinterpret_cast<__nv_bfloat162 *>(lo)[idx >> 1] = __floats2bfloat162_rn(x - hf.x, y - hf.y);
     }
+  } else if constexpr (PT == 2) {
+    reinterpret_cast<__half2 *>(hi)[idx >> 1] = __floats2half2_rn(sc * x, sc * y);
   } else {
     const float hx = to_tf32(x), hy = to_tf32(y);
     reinterpret_cast<float2 *>(hi)[idx >> 1] = make_float2(hx, hy);
@@ -785,46 +913,50 @@ __device__ __forceinline__ void split_store2(void *hi, void *lo, long idx, float
   }
 }
 
-template <bool BF16, bool EXPAND>
+template <int PT, bool EXPAND>
 __device__ __forceinline__ void pack_store(void *hi, void *lo, long r, long kc, long Kp, double2 a,
-                                           bool conj) {
+                                           bool conj, float sc) {
   const float re = f64_to_f32(a.x), im = conj ? -f64_to_f32(a.y) : f64_to_f32(a.y);
   if (EXPAND) {
-    split_store2<BF16>(hi, lo, (2 * r) * Kp + 2 * kc, re, -im);
-    split_store2<BF16>(hi, lo, (2 * r + 1) * Kp + 2 * kc, im, re);
+    split_store2<PT>(hi, lo, (2 * r) * Kp + 2 * kc, re, -im, sc);
+    split_store2<PT>(hi, lo, (2 * r + 1) * Kp + 2 * kc, im, re, sc);
   } else {
-    split_store2<BF16>(hi, lo, r * Kp + 2 * kc, re, im);
+    split_store2<PT>(hi, lo, r * Kp + 2 * kc, re, im, sc);
   }
 }
 
 // Block (BX, BY): x over complex k (padded to Kp/2), y over rows
 // (grid-stride); BX shrinks to the row length so short rows keep every
 // thread busy.
-template <bool BF16, bool EXPAND>
+template <int PT, bool EXPAND>
 __global__ void __launch_bounds__(256) pack_kernel(const double2 *__restrict__ src,
                                                    const long *__restrict__ rt,
                                                    const long *__restrict__ kt, long ld, bool conj,
-                                                   long rows, long K, long Kp, void *hi, void *lo) {
+                                                   long rows, long K, long Kp, void *hi, void *lo,
+                                                   const float *amax) {
   const long kc = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;  // complex k
   if (kc >= Kp / 2) return;
+  const float sc = (PT == 2 && amax) ? fp16_scale(*amax) : 1.0f;
   const long kof = kc < K ? (kt ? kt[kc] : kc) : 0;
   const long step = static_cast<long>(gridDim.y) * blockDim.y;
   for (long r = blockIdx.y * static_cast<long>(blockDim.y) + threadIdx.y; r < rows; r += step) {
     double2 a = make_double2(0.0, 0.0);
     if (kc < K) a = src[(rt ? rt[r] : r * ld) + kof];
-    pack_store<BF16, EXPAND>(hi, lo, r, kc, Kp, a, conj);
+    pack_store<PT, EXPAND>(hi, lo, r, kc, Kp, a, conj, sc);
   }
 }
 
 // Rows contiguous in the source (unit row stride, k through a table or a
 // large stride): 32 x 32 tiles transposed through shared memory so that the
 // loads run along rows and the stores along k. Block (32, 8).
-template <bool BF16, bool EXPAND>
+template <int PT, bool EXPAND>
 __global__ void __launch_bounds__(256) pack_t_kernel(const double2 *__restrict__ src,
-                                                     const long *__restrict__ kt, bool conj, long rows, long K, long Kp,
-                                                     void *hi, void *lo) {
+                                                     const long *__restrict__ kt, bool conj,
+                                                     long rows, long K, long Kp, void *hi,
+                                                     void *lo, const float *amax) {
   __shared__ double2 tile[32][33];
   const int tx = threadIdx.x, ty = threadIdx.y;
+  const float sc = (PT == 2 && amax) ? fp16_scale(*amax) : 1.0f;
   const long k0 = blockIdx.x * 32L;
   for (long r0 = blockIdx.y * 32L; r0 < rows; r0 += gridDim.y * 32L) {
 #pragma unroll
@@ -839,26 +971,68 @@ __global__ void __launch_bounds__(256) pack_t_kernel(const double2 *__restrict__
     for (int j = 0; j < 4; ++j) {
       const long r = r0 + ty + 8 * j, kc = k0 + tx;
       if (r < rows && kc < Kp / 2)
-        pack_store<BF16, EXPAND>(hi, lo, r, kc, Kp, tile[tx][ty + 8 * j], conj);
+        pack_store<PT, EXPAND>(hi, lo, r, kc, Kp, tile[tx][ty + 8 * j], conj, sc);
     }
     __syncthreads();
   }
 }
 
+// max(|Re|, |Im|) over a table-addressed operand; block maxima combined
+// with an unsigned atomicMax on the float bits (non-negative floats order
+// like their bit patterns).
+__device__ __forceinline__ void block_max_store(float m, float *amax) {
+  __shared__ float sh[8];
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const int w = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+  const int l = threadIdx.x & 31;
+  if (l == 0) sh[w] = m;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    float x = 0.0f;
+    const int nw = static_cast<int>(blockDim.x * blockDim.y) >> 5;
+    for (int i = 0; i < nw; ++i) x = fmaxf(x, sh[i]);
+    atomicMax(reinterpret_cast<unsigned *>(amax), __float_as_uint(x));
+  }
+}
+
+// Block (BX, BY): x along the operand's contiguous direction (rows when
+// rows_inner, else k), y along the other (grid-stride).
+__global__ void __launch_bounds__(256) absmax_kernel(const double2 *__restrict__ src,
+                                                     const long *__restrict__ rt,
+                                                     const long *__restrict__ kt, long ld,
+                                                     long rows, long K, bool rows_inner,
+                                                     float *amax) {
+  float m = 0.0f;
+  const long X = rows_inner ? rows : K, Y = rows_inner ? K : rows;
+  const long xi = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
+  if (xi < X) {
+    const long step = static_cast<long>(gridDim.y) * blockDim.y;
+    for (long yi = blockIdx.y * static_cast<long>(blockDim.y) + threadIdx.y; yi < Y; yi += step) {
+      const long r = rows_inner ? xi : yi, k = rows_inner ? yi : xi;
+      const double2 a = src[(rt ? rt[r] : r * ld) + (kt ? kt[k] : k)];
+      m = fmaxf(m, fmaxf(fabsf(f64_to_f32(a.x)), fabsf(f64_to_f32(a.y))));
+    }
+  }
+  block_max_store(m, amax);
+}
+
 template <bool EXPAND>
 void pack_launch(const cplx *src, const long *rt, const long *kt, long ld, bool conj, long rows,
-                 long K, long Kp, int tier, void *hi, void *lo, cudaStream_t st) {
+                 long K, long Kp, int tier, void *hi, void *lo, cudaStream_t st,
+                 const float *amax) {
   if (rows <= 0) return;
-  void *l = (tier == TIER_TF32) ? nullptr : lo;
+  void *l = (tier == TIER_TF32 || tier == TIER_FP16) ? nullptr : lo;
   const long kh = Kp / 2;
   if (!rt && ld == 1 && kt && rows > 1 && K > 1) {
     dim3 block(32, 8);
     dim3 grid(static_cast<unsigned>((kh + 31) / 32),
               static_cast<unsigned>(std::min<long>((rows + 31) / 32, 65535)));
     if (tier == TIER_BF16X3)
-      pack_t_kernel<true, EXPAND><<<grid, block, 0, st>>>(src, kt, conj, rows, K, Kp, hi, l);
+      pack_t_kernel<1, EXPAND><<<grid, block, 0, st>>>(src, kt, conj, rows, K, Kp, hi, l, amax);
+    else if (tier == TIER_FP16)
+      pack_t_kernel<2, EXPAND><<<grid, block, 0, st>>>(src, kt, conj, rows, K, Kp, hi, l, amax);
     else
-      pack_t_kernel<false, EXPAND><<<grid, block, 0, st>>>(src, kt, conj, rows, K, Kp, hi, l);
+      pack_t_kernel<0, EXPAND><<<grid, block, 0, st>>>(src, kt, conj, rows, K, Kp, hi, l, amax);
   } else {
     const int bx = static_cast<int>(std::min<long>(256, std::max<long>(32, (kh + 31) / 32 * 32)));
     const int by = 256 / bx;
@@ -866,9 +1040,11 @@ void pack_launch(const cplx *src, const long *rt, const long *kt, long ld, bool 
     dim3 grid(static_cast<unsigned>((kh + bx - 1) / bx),
               static_cast<unsigned>(std::min<long>((rows + by - 1) / by, 65535)));
     if (tier == TIER_BF16X3)
-      pack_kernel<true, EXPAND><<<grid, block, 0, st>>>(src, rt, kt, ld, conj, rows, K, Kp, hi, l);
+      pack_kernel<1, EXPAND><<<grid, block, 0, st>>>(src, rt, kt, ld, conj, rows, K, Kp, hi, l, amax);
+    else if (tier == TIER_FP16)
+      pack_kernel<2, EXPAND><<<grid, block, 0, st>>>(src, rt, kt, ld, conj, rows, K, Kp, hi, l, amax);
     else
-      pack_kernel<false, EXPAND><<<grid, block, 0, st>>>(src, rt, kt, ld, conj, rows, K, Kp, hi, l);
+      pack_kernel<0, EXPAND><<<grid, block, 0, st>>>(src, rt, kt, ld, conj, rows, K, Kp, hi, l, amax);
   }
   LAUNCH_CHECK();
   count_launch();
@@ -877,12 +1053,32 @@ void pack_launch(const cplx *src, const long *rt, const long *kt, long ld, bool 
 }  // namespace
 
 void tc_pack_A(const cplx *src, const long *am, const long *ak, long lda, bool conj, long M,
-               long K, long Kp, int tier, void *hi, void *lo, cudaStream_t st) {
-  pack_launch<true>(src, am, ak, lda, conj, M, K, Kp, tier, hi, lo, st);
+               long K, long Kp, int tier, void *hi, void *lo, cudaStream_t st, const float *amax) {
+  if (tier == TIER_FP16 && !amax) fail(CC_ERR_ARG, "tc_pack_A: FP16 planes need amax");
+  pack_launch<true>(src, am, ak, lda, conj, M, K, Kp, tier, hi, lo, st, amax);
 }
 void tc_pack_B(const cplx *src, const long *bn, const long *bk, long ldb, bool conj, long N,
-               long K, long Kp, int tier, void *hi, void *lo, cudaStream_t st) {
-  pack_launch<false>(src, bn, bk, ldb, conj, N, K, Kp, tier, hi, lo, st);
+               long K, long Kp, int tier, void *hi, void *lo, cudaStream_t st, const float *amax) {
+  if (tier == TIER_FP16 && !amax) fail(CC_ERR_ARG, "tc_pack_B: FP16 planes need amax");
+  pack_launch<false>(src, bn, bk, ldb, conj, N, K, Kp, tier, hi, lo, st, amax);
+}
+
+void tc_absmax(const cplx *src, const long *rt, const long *kt, long ld, long rows, long K,
+               float *amax, cudaStream_t st) {
+  CUDA_CHECK(cudaMemsetAsync(amax, 0, sizeof(float), st));
+  if (rows <= 0 || K <= 0) return;
+  const bool rows_inner = !rt && ld == 1;  // unit row stride: sweep rows fastest
+  const long X = rows_inner ? rows : K, Y = rows_inner ? K : rows;
+  const int bx = static_cast<int>(std::min<long>(256, std::max<long>(32, (X + 31) / 32 * 32)));
+  const int by = 256 / bx;
+  const long gx = (X + bx - 1) / bx;
+  if (gx > 0x7fffffffL) fail(CC_ERR_ARG, "tc_absmax: operand too wide");
+  const long gy = std::max<long>(
+      1, std::min<long>(std::min<long>((Y + by - 1) / by, 65535L), std::max<long>(1, 152L * 16 / gx)));
+  absmax_kernel<<<dim3(static_cast<unsigned>(gx), static_cast<unsigned>(gy)), dim3(bx, by), 0, st>>>(
+      src, rt, kt, ld, rows, K, rows_inner, amax);
+  LAUNCH_CHECK();
+  count_launch();
 }
 
 }  // namespace cdfns

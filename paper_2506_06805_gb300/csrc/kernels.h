@@ -74,6 +74,10 @@ struct TcDesc {
   // tile choices (0 = automatic): output tile width 128 or 256, m-tiles per
   // raster group, K blocks per TMEM promotion chunk
   int bn = 0, group_m = 0, chunk = 0;
+  // TIER_FP16: device floats holding max |element| of A and of B; the planes
+  // were packed with fp16_scale() of these and the product is unscaled in
+  // the epilogue (nullptr: unscaled)
+  const float *amax_a = nullptr, *amax_b = nullptr;
 };
 void gemm_tc(const TcDesc &g, cudaStream_t st, int *err_flag);
 // Several independent GEMMs (any shapes, same or mixed tiers) in as few
@@ -94,12 +98,17 @@ size_t tc_elem_bytes(int tier);
 
 // Expand/convert operands for gemm_tc from FP64 tensors addressed by tables.
 // A side: rows 2m, 2m+1 (M complex rows) x Kp real columns (2 per complex k).
+// TIER_FP16: amax (device float, from tc_absmax) sets the operand's scale.
 void tc_pack_A(const cplx *src, const long *am, const long *ak, long lda,
                bool conj, long M, long K, long Kp, int tier, void *hi,
-               void *lo, cudaStream_t st);
+               void *lo, cudaStream_t st, const float *amax = nullptr);
 void tc_pack_B(const cplx *src, const long *bn, const long *bk, long ldb,
                bool conj, long N, long K, long Kp, int tier, void *hi,
-               void *lo, cudaStream_t st);
+               void *lo, cudaStream_t st, const float *amax = nullptr);
+// *amax = max over the operand's elements of max(|Re|, |Im|), addressed like
+// tc_pack_A / tc_pack_B (rows x K through tables or strides).
+void tc_absmax(const cplx *src, const long *rt, const long *kt, long ld, long rows, long K,
+               float *amax, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Tensor helpers

@@ -414,7 +414,8 @@ void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr) {
     const int kal = tc_k_align(tr);
     const long Kp1 = ((2L * X + kal - 1) / kal) * kal;
     const long Kp2 = ((2L * n_cd + kal - 1) / kal) * kal;
-    const bool split = tr != TIER_TF32;
+    const bool split = tr == TIER_TF32X3 || tr == TIER_BF16X3;
+    const bool f16 = tr == TIER_FP16;
     Buf A1h(&al, eb * 2 * vv * Kp1), B1h(&al, eb * vv * Kp1), A2h(&al, eb * 2 * n_ij * Kp2);
     Buf A1l, B1l, A2l;
     if (split) {
@@ -422,12 +423,22 @@ void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr) {
       B1l.reset(&al, eb * vv * Kp1);
       A2l.reset(&al, eb * 2 * n_ij * Kp2);
     }
+    // FP16: operand maxima of L~ and tau, and a bound on |W|
+    Buf amx(&al, 4 * sizeof(float));
+    float *amx_L = f16 ? amx.as<float>() : nullptr;
+    float *amx_t = f16 ? amx.as<float>() + 1 : nullptr;
+    float *amx_W = f16 ? amx.as<float>() + 2 : nullptr;
     {
       Engine::Region r = eng.region("ladder pack");
-      tc_pack_A(Lv, nullptr, ptab, 1, false, vv, X, Kp1, tr, A1h.p, A1l.p, st);
-      tc_pack_B(Lv, nullptr, ptab, 1, false, vv, X, Kp1, tr, B1h.p, B1l.p, st);
+      if (f16) {
+        tc_absmax(Lv, nullptr, ptab, 1, vv, X, amx_L, st);
+        tc_absmax(tau, rt.as<long>(), kt.as<long>(), 0, n_ij, n_cd, amx_t, st);
+        ladder_w_bound(Lv, static_cast<int>(X), vv, amx_W, st);
+      }
+      tc_pack_A(Lv, nullptr, ptab, 1, false, vv, X, Kp1, tr, A1h.p, A1l.p, st, amx_L);
+      tc_pack_B(Lv, nullptr, ptab, 1, false, vv, X, Kp1, tr, B1h.p, B1l.p, st, amx_L);
       tc_pack_A(tau, rt.as<long>(), kt.as<long>(), 0, false, n_ij, n_cd, Kp2, tr, A2h.p, A2l.p,
-                st);
+                st, amx_t);
     }
     long a0 = 0;
     Buf Vs, Wh, Wl;
@@ -453,6 +464,7 @@ void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr) {
       g1.B = off(B1h, a0 * v * Kp1); g1.Blo = off(B1l, a0 * v * Kp1);
       g1.tier = tr; g1.out = TC_OUT_F32;
       g1.C = Vs.p; g1.ldc = (v - a0) * v;
+      g1.amax_a = amx_L; g1.amax_b = amx_L;
       {
         Engine::Region r = eng.region("ladder gemm1");
         gemm_tc(g1, st, err_d.as<int>());
@@ -461,13 +473,14 @@ void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr) {
         Engine::Region r = eng.region("ladder antisym");
         ladder_antisym(Vs.p, true, v, static_cast<int>(a0), static_cast<int>(nA), p0, p1,
                        ab_a.as<int>(), ab_b.as<int>(), ab_a.as<int>(), ab_b.as<int>(), tr, Wh.p,
-                       Wl.p, Kp2, nullptr, st);
+                       Wl.p, Kp2, nullptr, st, amx_W);
       }
       TcDesc g2;
       g2.M = n_ij; g2.N = np; g2.Kp = Kp2;
       g2.A = A2h.p; g2.Alo = A2l.p; g2.B = Wh.p; g2.Blo = Wl.p;
       g2.tier = tr; g2.out = TC_OUT_F64;
       g2.C = Rp.c() + p0; g2.ldc = n_ab;
+      g2.amax_a = amx_t; g2.amax_b = amx_W;
       g2.bn = tc_pick_bn(np);
       g2.split_k = tc_pick_split(((2 * n_ij + 127) / 128) * ((np + g2.bn - 1) / g2.bn), Kp2 / kal,
                                  num_sms);

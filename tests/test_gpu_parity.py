@@ -18,7 +18,7 @@ from paper_2506_06805_gb300 import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-REL = {"fp64": 1e-11, "tf32": 4e-3, "tf32x3": 2e-6, "bf16x3": 1e-4}
+REL = {"fp64": 1e-11, "tf32": 4e-3, "tf32x3": 2e-6, "bf16x3": 1e-4, "fp16": 4e-3}
 
 
 def _gpu():
@@ -54,7 +54,7 @@ def _relerr(a, b):
 
 # --- the tensor-core GEMM ----------------------------------------------------
 
-@pytest.mark.parametrize("tier", ["tf32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("tier", ["tf32", "tf32x3", "bf16x3", "fp16"])
 def test_gemm_accumulation_bias_flat_in_k(tier):
     """Same-sign products expose any systematic rounding of the tensor-core
     accumulation: without promotion from TMEM every few K blocks the
@@ -71,7 +71,7 @@ def test_gemm_accumulation_bias_flat_in_k(tier):
     got = C.cpu().numpy().real
     bias = float(np.mean((got - ref) / ref))
     assert abs(bias) < 3e-6, bias
-    assert float(np.abs(got - ref).max() / ref.max()) < {"tf32": 5e-5}.get(tier, 5e-6)
+    assert float(np.abs(got - ref).max() / ref.max()) < {"tf32": 5e-5, "fp16": 5e-5}.get(tier, 5e-6)
 
 
 # --- integrals: bit-exact ----------------------------------------------------
@@ -91,9 +91,25 @@ def test_integral_dump_bit_exact():
             assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), block
 
 
+@pytest.mark.parametrize("sa,sb", [(1e-7, 1e3), (1e4, 1e-9), (1.0, 1.0)])
+def test_fp16_operand_scaling(sa, sb):
+    """FP16 planes carry a power-of-two scale per operand chosen from its
+    largest magnitude, so operands far outside FP16's range (or spanning
+    many decades) keep TF32-class relative accuracy."""
+    P = _gpu()
+    rng = np.random.default_rng(5)
+    M, N, K = 300, 500, 700
+    A = sa * (rng.standard_normal((M, K)) + 1j * rng.standard_normal((M, K)))
+    A[:, :50] *= 1e-4  # a block of much smaller elements
+    B = sb * (rng.standard_normal((N, K)) + 1j * rng.standard_normal((N, K)))
+    C = torch.zeros((M, N), dtype=torch.complex128, device="cuda")
+    P.zgemm_dev(_dev(A), _dev(B), C, "fp16")
+    assert _relerr(C.cpu().numpy(), A @ B.T) <= REL["fp16"]
+
+
 # --- the particle-particle ladder (dominant CCSD term) ---------------------------------------------
 
-@pytest.mark.parametrize("tier", ["fp64", "tf32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("tier", ["fp64", "tf32", "tf32x3", "bf16x3", "fp16"])
 @pytest.mark.parametrize("o,v,X,budget", [(10, 30, 120, None), (6, 71, 97, 3 << 20)])
 def test_ladder_matches_oracle(tier, o, v, X, budget):
     """1/2 sum_cd <ab||cd> tau_ij^cd with <ab||cd> built from L (Eq. 23);
@@ -116,7 +132,7 @@ def test_ladder_matches_oracle(tier, o, v, X, budget):
 
 
 @pytest.mark.parametrize("M,N,K", [(20000, 37, 40), (33, 5000, 17), (3000, 1024, 48)])
-@pytest.mark.parametrize("tier", ["tf32", "tf32x3"])
+@pytest.mark.parametrize("tier", ["tf32", "tf32x3", "fp16"])
 def test_skinny_products_fp32(M, N, K, tier):
     """Short contracted index with one short side: FP32 on the CUDA cores,
     so the error is FP32's in both tensor-core tiers."""
@@ -149,7 +165,7 @@ def _residual_ref(o, v, X):
 
 # (16, 36, 150): o >= 16 sends the contractions over one occupied index
 # with a t1- or Fock-sized partner to the FP32 skinny kernel
-@pytest.mark.parametrize("tier", ["fp64", "tf32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("tier", ["fp64", "tf32", "tf32x3", "bf16x3", "fp16"])
 @pytest.mark.parametrize("o,v,X", [(10, 30, 120), (7, 45, 66), (16, 36, 150)])
 def test_ccsd_residual_matches_oracle(tier, o, v, X):
     P = _gpu()
@@ -205,7 +221,7 @@ def _oracle_roots(eps, L, o, n_roots, tol=1e-10):
     return res["e_corr"], np.sort_complex(w)
 
 
-@pytest.mark.parametrize("tier,tol_e", [("fp64", 1e-9), ("tf32", 1e-5),
+@pytest.mark.parametrize("tier,tol_e", [("fp64", 1e-9), ("tf32", 1e-5), ("fp16", 1e-5),
                                         ("tf32x3", 1e-7), ("bf16x3", 1e-6)])
 @pytest.mark.parametrize("scale", [1.0, 4.0])
 def test_end_to_end_tiny(tier, tol_e, scale):
@@ -217,8 +233,9 @@ def test_end_to_end_tiny(tier, tol_e, scale):
     L = L * scale
     o = c.n_occ
     e_ref, w_ref = _oracle_roots(eps, L, o, 4)
-    eom = "tf32x3" if tier == "tf32" else None
-    # TF32 (10-bit operands) cannot resolve steps below ~1e-8 at 4x coupling
+    eom = "tf32x3" if tier in ("tf32", "fp16") else None
+    # TF32 / FP16 (11-bit significands) cannot resolve steps below ~1e-8 at
+    # 4x coupling
     ctol = {"fp64": 1e-10, "tf32x3": 1e-9, "bf16x3": 1e-8}.get(tier, 1e-7)
     with P.System(eps, L, n_occ=o, tier=tier, eom_tier=eom) as s:
         e = s.ccsd(tol=ctol, max_iter=100)
