@@ -672,7 +672,27 @@ void check_desc(const TcDesc &g) {
     fail(CC_ERR_ARG, "gemm_tc: operands must be 16-byte aligned");
 }
 
+// Wide tiles as CTA pairs sharing B through cluster multicast: on when the
+// environment variable CDFNS_CTA_PAIR is "1" (read once).
+bool cta_pair() {
+  static int v = -1;
+  if (v < 0) {
+    const char *e = std::getenv("CDFNS_CTA_PAIR");
+    v = (e && e[0] == '1') ? 1 : 0;
+  }
+  return v == 1;
+}
+
 void dispatch(const TcDesc *d, int n, bool wide, cudaStream_t st, int *err) {
+  if (wide && cta_pair()) {
+    switch (d[0].tier) {
+      case TIER_TF32: launch<256, 4, false, 0, 2>(d, n, st, err); return;
+      case TIER_TF32X3: launch<256, 2, true, 0, 2>(d, n, st, err); return;
+      case TIER_BF16X3: launch<256, 2, true, 1, 2>(d, n, st, err); return;
+      case TIER_FP16: launch<256, 4, false, 2, 2>(d, n, st, err); return;
+      default: break;
+    }
+  }
   switch (d[0].tier) {
     case TIER_TF32:
       if (wide) launch<256, 4, false, 0, 1>(d, n, st, err);
@@ -715,11 +735,15 @@ int tc_pick_split(long tiles, long nkb, int num_sms) {
     const long tt = tiles * sp;
     return static_cast<double>(tt) / (static_cast<double>((tt + P - 1) / P) * P);
   };
+  // a split turns every output write into atomic additions in L2 (and the
+  // output into a read-modify-write in DRAM): only worth it for a clear
+  // gain in wave occupancy
   double best = eff(1);
+  const double need = tiles < 2L * P ? 0.02 : 0.15;
   const long smax = std::min<long>(32, nkb / 4);
   for (long sp = 2; sp <= smax; ++sp) {
     const double e = eff(sp) * (1.0 - 0.005 * static_cast<double>(sp - 1));
-    if (e > best + 0.02) {
+    if (e > best + need) {
       best = e;
       sk = static_cast<int>(sp);
     }
