@@ -44,7 +44,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--config", default=WORKLOAD)
     p.add_argument("--tier", default="fp16")
-    p.add_argument("--eom-tier", default="tf32x3")
+    p.add_argument("--eom-tier", default="fp16x3")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()

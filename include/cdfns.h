@@ -57,6 +57,8 @@ extern "C" {
                           * its largest magnitude, so the product rounding is
                           * that of TF32 (11-bit significands) at twice the
                           * tensor-core rate */
+#define CC_TIER_FP16X3 5 /* kind::f16 fp16 hi/lo split of the scaled operands,
+                          * 3 products: TF32X3-class accuracy at the f16 rate */
 
 typedef struct cc_ctx cc_ctx; /* one molecular (synthetic) system */
 

@@ -25,7 +25,7 @@ __all__ = ["lib", "System", "Mlp", "CCError", "TIERS", "LIB_PATH"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcdfns.so")
 
-TIERS = {"fp64": 0, "tf32": 1, "tf32x3": 2, "bf16x3": 3, "fp16": 4}
+TIERS = {"fp64": 0, "tf32": 1, "tf32x3": 2, "bf16x3": 3, "fp16": 4, "fp16x3": 5}
 _ERRORS = {
     -1: "CC_ERR_ARG", -2: "CC_ERR_INPUT", -3: "CC_ERR_OOM", -4: "CC_ERR_CUDA",
     -5: "CC_ERR_NOT_CONVERGED", -6: "CC_ERR_NUMERIC", -7: "CC_ERR_TIMEOUT",

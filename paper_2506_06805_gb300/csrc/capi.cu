@@ -168,7 +168,7 @@ int cc_init(int n_occ, int n_virt, int n_aux, const double *eps, const double *L
 
 int cc_set_precision(cc_ctx *ctx, int tier) {
   if (!ctx) return CC_ERR_ARG;
-  if (tier < CC_TIER_FP64 || tier > CC_TIER_FP16) return CC_ERR_ARG;
+  if (tier < CC_TIER_FP64 || tier > CC_TIER_FP16X3) return CC_ERR_ARG;
   ctx->c.tier = tier;
   ctx->c.hbar_done = false;
   return CC_OK;
@@ -176,7 +176,7 @@ int cc_set_precision(cc_ctx *ctx, int tier) {
 
 int cc_set_precision_eom(cc_ctx *ctx, int tier) {
   if (!ctx) return CC_ERR_ARG;
-  if (tier < -1 || tier > CC_TIER_FP16) return CC_ERR_ARG;
+  if (tier < -1 || tier > CC_TIER_FP16X3) return CC_ERR_ARG;
   ctx->c.eom_tier = tier;
   return CC_OK;
 }
@@ -333,7 +333,7 @@ int ipeom_sigma_dev(cc_ctx *ctx, int n_vec, const double *r_dev, double *s_dev) 
 }
 
 int cc_zgemm_dev(int tier, long M, long N, long K, const double *A, const double *B, double *C) {
-  if (tier < CC_TIER_FP64 || tier > CC_TIER_FP16 || M < 1 || N < 1 || K < 1 || !A || !B || !C)
+  if (tier < CC_TIER_FP64 || tier > CC_TIER_FP16X3 || M < 1 || N < 1 || K < 1 || !A || !B || !C)
     return CC_ERR_ARG;
   return guarded(nullptr, [&] {
     static cdfns::Allocator al;

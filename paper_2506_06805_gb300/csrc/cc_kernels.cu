@@ -500,7 +500,8 @@ __global__ void antisym_kernel(const void *Vp, bool f32, int v, int a0, long p0,
 // tiles of c and d: the tiles V[a][C][b][D] and V[a][D][b][C] are read along
 // their inner index into shared memory, and W is written along d (packed
 // (c<d) columns are contiguous in d for fixed c). Differences in FP32; PT:
-// 0 tf32 hi (+ lo), 1 bf16 hi (+ lo), 2 fp16 scaled by fp16_scale(*amax).
+// 0 tf32 hi (+ lo), 1 bf16 hi (+ lo), 2 fp16 scaled by fp16_scale(*amax),
+// 3 fp16 hi + lo of the scaled value.
 template <int PT>
 __global__ void __launch_bounds__(256) antisym_tile_kernel(
     const float2 *__restrict__ V, int v, int a0, long p0, long np, const int *__restrict__ pair_a,
@@ -516,7 +517,7 @@ __global__ void __launch_bounds__(256) antisym_tile_kernel(
   const int dt = ct + p;
   const int C0 = ct * 32, D0 = dt * 32;
   const long ld = static_cast<long>(v - a0) * v;
-  const float sc = (PT == 2 && amax) ? fp16_scale(*amax) : 1.0f;
+  const float sc = (PT >= 2 && amax) ? fp16_scale(*amax) : 1.0f;
   for (long r = blockIdx.y; r < np; r += gridDim.y) {
     const int a = pair_a[p0 + r], b = pair_b[p0 + r];
     const long ra = static_cast<long>(a - a0) * v, cb = static_cast<long>(b - a0) * v;
@@ -556,7 +557,13 @@ __global__ void __launch_bounds__(256) antisym_tile_kernel(
           const float2 hf = __bfloat1622float2(h);
           reinterpret_cast<__nv_bfloat162 *>(lo)[e >> 1] = __floats2bfloat162_rn(wr - hf.x, wi - hf.y);
         } else {
-          reinterpret_cast<__half2 *>(hi)[e >> 1] = __floats2half2_rn(sc * wr, sc * wi);
+          const float sr = sc * wr, si = sc * wi;
+          const __half2 h = __floats2half2_rn(sr, si);
+          reinterpret_cast<__half2 *>(hi)[e >> 1] = h;
+          if (PT == 3) {
+            const float2 hf = __half22float2(h);
+            reinterpret_cast<__half2 *>(lo)[e >> 1] = __floats2half2_rn(sr - hf.x, si - hf.y);
+          }
         }
       }
     }
@@ -948,7 +955,7 @@ void ladder_antisym(const void *V, bool f32, int v, int a0, int nA, long p0, lon
     return;
   }
   if (!f32) fail(CC_ERR_ARG, "ladder_antisym: tensor-core tiers take an FP32 slab");
-  if (tier == TIER_FP16 && !amax) fail(CC_ERR_ARG, "ladder_antisym: FP16 needs the W bound");
+  if (tier_scaled(tier) && !amax) fail(CC_ERR_ARG, "ladder_antisym: FP16 needs the W bound");
   const int nt = (v + 31) / 32;
   dim3 grid(static_cast<unsigned>(nt * (nt + 1) / 2),
             static_cast<unsigned>(std::min<long>(np, 65535)));
@@ -959,6 +966,9 @@ void ladder_antisym(const void *V, bool f32, int v, int a0, int nA, long p0, lon
   } else if (tier == TIER_FP16) {
     antisym_tile_kernel<2><<<grid, dim3(32, 8), 0, st>>>(Vf, v, a0, p0, np, pair_a, pair_b, hi,
                                                          nullptr, kp, nt, amax);
+  } else if (tier == TIER_FP16X3) {
+    antisym_tile_kernel<3><<<grid, dim3(32, 8), 0, st>>>(Vf, v, a0, p0, np, pair_a, pair_b, hi, lo,
+                                                         kp, nt, amax);
   } else {
     antisym_tile_kernel<0><<<grid, dim3(32, 8), 0, st>>>(Vf, v, a0, p0, np, pair_a, pair_b, hi,
                                                          tier == TIER_TF32 ? nullptr : lo, kp, nt,
@@ -979,6 +989,8 @@ void ladder_antisym(const void *V, bool f32, int v, int a0, int nA, long p0, lon
                                                     2 * ncd, kp);
     } else {
       zero_tail<__half><<<gt, 256, 0, st>>>(reinterpret_cast<__half *>(hi), np, 2 * ncd, kp);
+      if (tier == TIER_FP16X3)
+        zero_tail<__half><<<gt, 256, 0, st>>>(reinterpret_cast<__half *>(lo), np, 2 * ncd, kp);
     }
     LAUNCH_CHECK();
     count_launch();

@@ -114,8 +114,30 @@ struct Buf {
 };
 
 // Precision tiers of the contraction engine (CC_TIER_* in cdfns.h).
-enum Tier { TIER_FP64 = 0, TIER_TF32 = 1, TIER_TF32X3 = 2, TIER_BF16X3 = 3, TIER_FP16 = 4 };
-constexpr int TIER_LAST = TIER_FP16;
+enum Tier {
+  TIER_FP64 = 0,
+  TIER_TF32 = 1,
+  TIER_TF32X3 = 2,
+  TIER_BF16X3 = 3,
+  TIER_FP16 = 4,
+  TIER_FP16X3 = 5
+};
+constexpr int TIER_LAST = TIER_FP16X3;
+// hi/lo operand planes, three products
+__host__ __device__ inline bool tier_split(int t) {
+  return t == TIER_TF32X3 || t == TIER_BF16X3 || t == TIER_FP16X3;
+}
+// FP16 planes scaled by fp16_scale() of the operand maximum
+__host__ __device__ inline bool tier_scaled(int t) { return t == TIER_FP16 || t == TIER_FP16X3; }
+// 2-byte plane elements (kind::f16), else 4-byte (kind::tf32)
+__host__ __device__ inline bool tier_half(int t) { return t == TIER_BF16X3 || tier_scaled(t); }
+// the accurate split tier of the same operand family
+__host__ __device__ inline int tier_accurate(int t) {
+  return t == TIER_FP64 ? TIER_FP64
+         : tier_scaled(t) ? TIER_FP16X3
+         : t == TIER_BF16X3 ? TIER_BF16X3
+                            : TIER_TF32X3;
+}
 
 // Scale for the FP16 tier: the power of two 2^k with amax 2^k < 2^15, so
 // every scaled magnitude stays below 2^15 (FP16 max 65504) and values down

@@ -67,8 +67,8 @@ std::pair<void *, void *> Engine::packed(bool a_side, const TRef &t, const long 
   Packed pk;
   ++gen;
   pk.hi.reset(al, n);
-  if (tier != TIER_TF32 && tier != TIER_FP16) pk.lo.reset(al, n);
-  if (tier == TIER_FP16) {
+  if (tier_split(tier)) pk.lo.reset(al, n);
+  if (tier_scaled(tier)) {
     pk.amax.reset(al, sizeof(float));
     tc_absmax(t.p, rt, kt, ld, rows, K, pk.amax.as<float>(), st);
   }
@@ -302,10 +302,10 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
   const int kal = tc_k_align(tier);
   const long Kp = ((2 * K + kal - 1) / kal) * kal;
   const size_t eb = tc_elem_bytes(tier);
-  const bool split = tier == TIER_TF32X3 || tier == TIER_BF16X3;
+  const bool split = tier_split(tier);
   void *Ah, *Al = nullptr, *Bh, *Bl = nullptr;
   const int pb = 4 * (slot < 0 ? 0 : slot + 1);  // plane set of this contraction
-  const bool f16 = tier == TIER_FP16;
+  const bool f16 = tier_scaled(tier);
   const float *xa = nullptr, *xb = nullptr;  // FP16 operand maxima
   if (A.stable) {
     std::tie(Ah, Al) = packed(true, A, am, ak, lda, M, K, Kp, tier, &xa);

@@ -690,6 +690,7 @@ void dispatch(const TcDesc *d, int n, bool wide, cudaStream_t st, int *err) {
       case TIER_TF32X3: launch<256, 2, true, 0, 2>(d, n, st, err); return;
       case TIER_BF16X3: launch<256, 2, true, 1, 2>(d, n, st, err); return;
       case TIER_FP16: launch<256, 4, false, 2, 2>(d, n, st, err); return;
+      case TIER_FP16X3: launch<256, 2, true, 2, 2>(d, n, st, err); return;
       default: break;
     }
   }
@@ -710,6 +711,10 @@ void dispatch(const TcDesc *d, int n, bool wide, cudaStream_t st, int *err) {
       if (wide) launch<256, 4, false, 2, 1>(d, n, st, err);
       else launch<128, 6, false, 2, 1>(d, n, st, err);
       break;
+    case TIER_FP16X3:
+      if (wide) launch<256, 2, true, 2, 1>(d, n, st, err);
+      else launch<128, 3, true, 2, 1>(d, n, st, err);
+      break;
     default:
       fail(CC_ERR_ARG, "gemm_tc: bad tier");
   }
@@ -717,7 +722,7 @@ void dispatch(const TcDesc *d, int n, bool wide, cudaStream_t st, int *err) {
 
 }  // namespace
 
-int tc_k_align(int tier) { return (tier == TIER_BF16X3 || tier == TIER_FP16) ? 64 : 32; }
+int tc_k_align(int tier) { return tier_half(tier) ? 64 : 32; }
 
 int tc_pick_bn(long N) {
   const double u256 = static_cast<double>(N) / (((N + 255) / 256) * 256);
@@ -750,7 +755,7 @@ int tc_pick_split(long tiles, long nkb, int num_sms) {
   }
   return sk;
 }
-size_t tc_elem_bytes(int tier) { return (tier == TIER_BF16X3 || tier == TIER_FP16) ? 2 : 4; }
+size_t tc_elem_bytes(int tier) { return tier_half(tier) ? 2 : 4; }
 
 // ---------------------------------------------------------------------------
 // Autotuner: per (tier, shape bucket) the tile width, raster group and TMEM
@@ -917,7 +922,8 @@ __device__ __forceinline__ float to_tf32(float x) {
 }
 
 // Two adjacent elements (idx even) as one 8-byte (fp32) or 4-byte (bf16,
-// fp16) store. PT: 0 tf32 hi (+ lo), 1 bf16 hi (+ lo), 2 fp16 of sc * x.
+// fp16) store. PT: 0 tf32 hi (+ lo), 1 bf16 hi (+ lo), 2 fp16 of sc * x,
+// 3 fp16 hi + lo of sc * x.
 template <int PT>
 __device__ __forceinline__ void split_store2(void *hi, void *lo, long idx, float x, float y,
                                              float sc) {
@@ -928,8 +934,14 @@ __device__ __forceinline__ void split_store2(void *hi, void *lo, long idx, float
       const float2 hf = __bfloat1622float2(h);
       reinterpret_cast<__nv_bfloat162 *>(lo)[idx >> 1] = __floats2bfloat162_rn(x - hf.x, y - hf.y);
     }
-  } else if constexpr (PT == 2) {
-    reinterpret_cast<__half2 *>(hi)[idx >> 1] = __floats2half2_rn(sc * x, sc * y);
+  } else if constexpr (PT == 2 || PT == 3) {
+    const float sx = sc * x, sy = sc * y;
+    const __half2 h = __floats2half2_rn(sx, sy);
+    reinterpret_cast<__half2 *>(hi)[idx >> 1] = h;
+    if (PT == 3 && lo) {
+      const float2 hf = __half22float2(h);
+      reinterpret_cast<__half2 *>(lo)[idx >> 1] = __floats2half2_rn(sx - hf.x, sy - hf.y);
+    }
   } else {
     const float hx = to_tf32(x), hy = to_tf32(y);
     reinterpret_cast<float2 *>(hi)[idx >> 1] = make_float2(hx, hy);
@@ -960,7 +972,7 @@ __global__ void __launch_bounds__(256) pack_kernel(const double2 *__restrict__ s
                                                    const float *amax) {
   const long kc = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;  // complex k
   if (kc >= Kp / 2) return;
-  const float sc = (PT == 2 && amax) ? fp16_scale(*amax) : 1.0f;
+  const float sc = (PT >= 2 && amax) ? fp16_scale(*amax) : 1.0f;
   const long kof = kc < K ? (kt ? kt[kc] : kc) : 0;
   const long step = static_cast<long>(gridDim.y) * blockDim.y;
   for (long r = blockIdx.y * static_cast<long>(blockDim.y) + threadIdx.y; r < rows; r += step) {
@@ -980,7 +992,7 @@ __global__ void __launch_bounds__(256) pack_t_kernel(const double2 *__restrict__
                                                      void *lo, const float *amax) {
   __shared__ double2 tile[32][33];
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const float sc = (PT == 2 && amax) ? fp16_scale(*amax) : 1.0f;
+  const float sc = (PT >= 2 && amax) ? fp16_scale(*amax) : 1.0f;
   const long k0 = blockIdx.x * 32L;
   for (long r0 = blockIdx.y * 32L; r0 < rows; r0 += gridDim.y * 32L) {
 #pragma unroll
@@ -1045,30 +1057,31 @@ void pack_launch(const cplx *src, const long *rt, const long *kt, long ld, bool 
                  long K, long Kp, int tier, void *hi, void *lo, cudaStream_t st,
                  const float *amax) {
   if (rows <= 0) return;
-  void *l = (tier == TIER_TF32 || tier == TIER_FP16) ? nullptr : lo;
+  void *l = tier_split(tier) ? lo : nullptr;
+  const int pt = tier == TIER_BF16X3 ? 1 : (tier == TIER_FP16 ? 2 : (tier == TIER_FP16X3 ? 3 : 0));
   const long kh = Kp / 2;
   if (!rt && ld == 1 && kt && rows > 1 && K > 1) {
     dim3 block(32, 8);
     dim3 grid(static_cast<unsigned>((kh + 31) / 32),
               static_cast<unsigned>(std::min<long>((rows + 31) / 32, 65535)));
-    if (tier == TIER_BF16X3)
-      pack_t_kernel<1, EXPAND><<<grid, block, 0, st>>>(src, kt, conj, rows, K, Kp, hi, l, amax);
-    else if (tier == TIER_FP16)
-      pack_t_kernel<2, EXPAND><<<grid, block, 0, st>>>(src, kt, conj, rows, K, Kp, hi, l, amax);
-    else
-      pack_t_kernel<0, EXPAND><<<grid, block, 0, st>>>(src, kt, conj, rows, K, Kp, hi, l, amax);
+    switch (pt) {
+      case 1: pack_t_kernel<1, EXPAND><<<grid, block, 0, st>>>(src, kt, conj, rows, K, Kp, hi, l, amax); break;
+      case 2: pack_t_kernel<2, EXPAND><<<grid, block, 0, st>>>(src, kt, conj, rows, K, Kp, hi, l, amax); break;
+      case 3: pack_t_kernel<3, EXPAND><<<grid, block, 0, st>>>(src, kt, conj, rows, K, Kp, hi, l, amax); break;
+      default: pack_t_kernel<0, EXPAND><<<grid, block, 0, st>>>(src, kt, conj, rows, K, Kp, hi, l, amax);
+    }
   } else {
     const int bx = static_cast<int>(std::min<long>(256, std::max<long>(32, (kh + 31) / 32 * 32)));
     const int by = 256 / bx;
     dim3 block(bx, by);
     dim3 grid(static_cast<unsigned>((kh + bx - 1) / bx),
               static_cast<unsigned>(std::min<long>((rows + by - 1) / by, 65535)));
-    if (tier == TIER_BF16X3)
-      pack_kernel<1, EXPAND><<<grid, block, 0, st>>>(src, rt, kt, ld, conj, rows, K, Kp, hi, l, amax);
-    else if (tier == TIER_FP16)
-      pack_kernel<2, EXPAND><<<grid, block, 0, st>>>(src, rt, kt, ld, conj, rows, K, Kp, hi, l, amax);
-    else
-      pack_kernel<0, EXPAND><<<grid, block, 0, st>>>(src, rt, kt, ld, conj, rows, K, Kp, hi, l, amax);
+    switch (pt) {
+      case 1: pack_kernel<1, EXPAND><<<grid, block, 0, st>>>(src, rt, kt, ld, conj, rows, K, Kp, hi, l, amax); break;
+      case 2: pack_kernel<2, EXPAND><<<grid, block, 0, st>>>(src, rt, kt, ld, conj, rows, K, Kp, hi, l, amax); break;
+      case 3: pack_kernel<3, EXPAND><<<grid, block, 0, st>>>(src, rt, kt, ld, conj, rows, K, Kp, hi, l, amax); break;
+      default: pack_kernel<0, EXPAND><<<grid, block, 0, st>>>(src, rt, kt, ld, conj, rows, K, Kp, hi, l, amax);
+    }
   }
   LAUNCH_CHECK();
   count_launch();
@@ -1078,12 +1091,12 @@ void pack_launch(const cplx *src, const long *rt, const long *kt, long ld, bool 
 
 void tc_pack_A(const cplx *src, const long *am, const long *ak, long lda, bool conj, long M,
                long K, long Kp, int tier, void *hi, void *lo, cudaStream_t st, const float *amax) {
-  if (tier == TIER_FP16 && !amax) fail(CC_ERR_ARG, "tc_pack_A: FP16 planes need amax");
+  if (tier_scaled(tier) && !amax) fail(CC_ERR_ARG, "tc_pack_A: FP16 planes need amax");
   pack_launch<true>(src, am, ak, lda, conj, M, K, Kp, tier, hi, lo, st, amax);
 }
 void tc_pack_B(const cplx *src, const long *bn, const long *bk, long ldb, bool conj, long N,
                long K, long Kp, int tier, void *hi, void *lo, cudaStream_t st, const float *amax) {
-  if (tier == TIER_FP16 && !amax) fail(CC_ERR_ARG, "tc_pack_B: FP16 planes need amax");
+  if (tier_scaled(tier) && !amax) fail(CC_ERR_ARG, "tc_pack_B: FP16 planes need amax");
   pack_launch<false>(src, bn, bk, ldb, conj, N, K, Kp, tier, hi, lo, st, amax);
 }
 

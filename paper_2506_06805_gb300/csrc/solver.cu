@@ -414,8 +414,8 @@ void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr) {
     const int kal = tc_k_align(tr);
     const long Kp1 = ((2L * X + kal - 1) / kal) * kal;
     const long Kp2 = ((2L * n_cd + kal - 1) / kal) * kal;
-    const bool split = tr == TIER_TF32X3 || tr == TIER_BF16X3;
-    const bool f16 = tr == TIER_FP16;
+    const bool split = tier_split(tr);
+    const bool f16 = tier_scaled(tr);
     Buf A1h(&al, eb * 2 * vv * Kp1), B1h(&al, eb * vv * Kp1), A2h(&al, eb * 2 * n_ij * Kp2);
     Buf A1l, B1l, A2l;
     if (split) {
@@ -792,7 +792,7 @@ void Ctx::build_hbar() {
   Engine::Region rg = eng.region("hbar total");
   eng.clear_pack_cache();
   ++sig_gen;
-  const int tr = int_tier() == TIER_FP64 ? TIER_FP64 : TIER_TF32X3;
+  const int tr = hbar_tier();
   const long oo = static_cast<long>(o) * o, vv = static_cast<long>(v) * v, ov = static_cast<long>(o) * v;
   const long n2 = oo * vv;
   auto a1 = [&](const char *ix) { return T(t1.c(), ix, {o, v}); };

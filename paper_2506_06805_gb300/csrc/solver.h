@@ -79,7 +79,9 @@ struct Ctx {
   void check_err_flag();
   void ensure_pairs();
   int eom() const { return eom_tier < 0 ? tier : eom_tier; }
-  int int_tier() const { return tier == TIER_FP64 ? TIER_FP64 : TIER_TF32X3; }
+  // integrals, FNS and H-bar: the accurate split tier of the chosen family
+  int int_tier() const { return tier_accurate(tier); }
+  int hbar_tier() const { return tier_accurate(eom()); }
   long nij() const { return static_cast<long>(o) * (o - 1) / 2; }
   long nab() const { return static_cast<long>(v) * (v - 1) / 2; }
   long dim_ip() const { return o + nij() * v; }
