@@ -45,6 +45,7 @@ def main():
     p.add_argument("--N", type=int, default=4096)
     p.add_argument("--K", type=int, default=4096)
     p.add_argument("--tier", default="tf32")
+    p.add_argument("--eom-tier", default="tf32x3")
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=1)
     a = p.parse_args()
@@ -160,12 +161,13 @@ def batch_run(a):
         rng = np.random.default_rng(sp.seed)
         eps = synth.make_eps(rng, sp.n_occ, sp.n_virt)
         L = synth.make_cholesky(rng, sp.n_occ + sp.n_virt, sp.n_aux)
-        s = System(eps, L, n_occ=sp.n_occ, tier="tf32", eom_tier="tf32x3")
+        s = System(eps, L, n_occ=sp.n_occ, tier=a.tier, eom_tier=a.eom_tier)
         del L
         s.ccsd(tol=1e-8, max_iter=60)
         systems.append(s)
     torch.cuda.synchronize()
     out = {"systems": [[sp.n_occ, sp.n_virt, sp.n_aux] for sp in specs],
+           "tier": a.tier, "eom_tier": a.eom_tier,
            "ccsd_all_s": time.perf_counter() - t0, "roots": a.roots}
     # one at a time (a first untimed pass builds every system's H-bar)
     for s in systems:
