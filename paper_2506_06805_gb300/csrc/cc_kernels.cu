@@ -571,32 +571,6 @@ __global__ void __launch_bounds__(256) antisym_tile_kernel(
   }
 }
 
-// Bound on |W| for the FP16 scale: |V_acbd| <= max_pq sum_P |L~^P_pq|^2
-// (Cauchy-Schwarz over P), so |W| <= 2 max_pq sum_P |L~^P_pq|^2. One thread
-// per (p, q); block maxima through an unsigned atomicMax of the float bits.
-__global__ void __launch_bounds__(256) w_bound_kernel(const double2 *__restrict__ L, int X, long vv,
-                                                      float *out) {
-  __shared__ float sh[8];
-  const long pq = blockIdx.x * 256L + threadIdx.x;
-  float n2 = 0.0f;
-  if (pq < vv) {
-    for (int P = 0; P < X; ++P) {
-      const double2 x = L[static_cast<long>(P) * vv + pq];
-      const float xr = f64_to_f32(x.x), xi = f64_to_f32(x.y);
-      n2 = fmaf(xr, xr, fmaf(xi, xi, n2));
-    }
-  }
-  float m = 2.0f * n2 * 1.001f;  // margin for the FP32 sum
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float x = 0.0f;
-    for (int i = 0; i < 8; ++i) x = fmaxf(x, sh[i]);
-    atomicMax(reinterpret_cast<unsigned *>(out), __float_as_uint(x));
-  }
-}
-
 // zero the padded tail columns [2*ncd, kp) of rows [0, np)
 template <typename E>
 __global__ void zero_tail(E *p, long np, long k0, long kp) {
@@ -997,13 +971,6 @@ void ladder_antisym(const void *V, bool f32, int v, int a0, int nA, long p0, lon
   }
 }
 
-void ladder_w_bound(const cplx *L, int X, long vv, float *out, cudaStream_t st) {
-  CUDA_CHECK(cudaMemsetAsync(out, 0, sizeof(float), st));
-  if (vv <= 0 || X <= 0) return;
-  w_bound_kernel<<<static_cast<unsigned>((vv + 255) / 256), 256, 0, st>>>(L, X, vv, out);
-  LAUNCH_CHECK();
-  count_launch();
-}
 
 void unpack_pairs_add(const cplx *R, int o, int v, const int *ij_i, const int *ij_j,
                       const int *ab_a, const int *ab_b, cplx *R2, cudaStream_t st) {

@@ -64,15 +64,13 @@ void diis_combine(cplx *const *vecs, const cplx *coef, int m, long n, cplx *out,
 // complex (float2 if f32 else double2), rows (a - a0, c), cols (b - a0, d).
 // Output: fp32 planes (re, im interleaved over k, row stride kp, hi + lo),
 // bf16 planes, or a double2 matrix [p1-p0][ncd].
-// TIER_FP16: bf16/tf32 planes replaced by one fp16 plane scaled by
-// fp16_scale(*amax), amax a bound on |W| (ladder_w_bound).
+// FP16 tiers: fp16 plane(s) scaled by fp16_scale(*amax), amax a bound on
+// |W| (twice the slab maximum recorded by the GEMM that wrote V).
 void ladder_antisym(const void *V, bool f32, int v, int a0, int nA, long p0, long p1,
                     const int *pair_a, const int *pair_b, const int *cd_c, const int *cd_d,
                     int tier, void *hi, void *lo, long kp, cplx *w64, cudaStream_t st,
                     const float *amax = nullptr);
-// *out = 2 max_pq sum_P |L^P_pq|^2 (L [X][vv]), a bound on the antisymmetrised
-// ladder integrals built from L.
-void ladder_w_bound(const cplx *L, int X, long vv, float *out, cudaStream_t st);
+
 // R2[i][j][a][b] += R[(i<j)][(a<b)] with the four antisymmetric images.
 void unpack_pairs_add(const cplx *R, int o, int v, const int *ij_i, const int *ij_j,
                       const int *ab_a, const int *ab_b, cplx *R2, cudaStream_t st);

@@ -273,6 +273,7 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
     g.C = C.p; g.cm = cm; g.cn = cn; g.ldc = ldc;
     g.alpha = alpha; g.beta = beta;
     g.k_contig = kdim.empty() || (M == 1 ? bkstr.back() == 1 : akstr.back() == 1);
+    g.f32 = tier != TIER_FP64;
     gemm_f64(g, st, num_sms);
     return false;
   }
@@ -313,7 +314,9 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
     Ah = plane(pb + 0, eb * 2 * M * Kp);
     Al = split ? plane(pb + 1, eb * 2 * M * Kp) : nullptr;
     Region r = region("pack A " + A.idx);
-    if (f16) {
+    if (f16 && A.amax) {
+      xa = A.amax;
+    } else if (f16) {
       float *x = plane_amax(pb + 0);
       tc_absmax(A.p, am, ak, lda, M, K, x, st);
       xa = x;
@@ -326,7 +329,9 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
     Bh = plane(pb + 2, eb * N * Kp);
     Bl = split ? plane(pb + 3, eb * N * Kp) : nullptr;
     Region r = region("pack B " + B.idx);
-    if (f16) {
+    if (f16 && B.amax) {
+      xb = B.amax;
+    } else if (f16) {
       float *x = plane_amax(pb + 2);
       tc_absmax(B.p, bn, bk, ldb, N, K, x, st);
       xb = x;

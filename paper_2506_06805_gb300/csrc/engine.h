@@ -24,6 +24,9 @@ struct TRef {
   std::vector<long> str;  // element strides
   bool conj = false;
   bool stable = false;  // contents fixed until Engine::clear_pack_cache()
+  // FP16 tiers: device float >= max(|Re|, |Im|) over the whole tensor, when
+  // the caller already has it (saves the operand's own maximum pass)
+  const float *amax = nullptr;
   long size() const {
     long s = 1;
     for (long d : dims) s *= d;
@@ -39,6 +42,10 @@ TRef Tv(const cplx *p, const char *idx, std::initializer_list<long> dims,
         std::initializer_list<long> strides, bool conj = false);
 inline TRef conj(TRef t) {
   t.conj = !t.conj;
+  return t;
+}
+inline TRef with_amax(TRef t, const float *m) {
+  t.amax = m;
   return t;
 }
 // Mark an operand whose contents stay fixed across calls (integrals, H-bar):

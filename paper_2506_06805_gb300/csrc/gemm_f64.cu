@@ -139,6 +139,17 @@ __global__ void gemv_kernel(long N, long K, const double2 *__restrict__ A, const
 // Thread-per-output with the K range split over 8 thread rows of the block
 // (blockDim 32 x 8) and summed through shared memory: 8x the loads in
 // flight of gemv_kernel for long K with a strided operand.
+// F32 (tensor-core tiers): products and runs of 16 sums in FP32 on operands
+// narrowed on the integer pipes, each run then added in FP64.
+__device__ __forceinline__ void cfma32(double2 a, double2 b, bool ca, bool cb, float &xr, float &xi) {
+  const float ar = f64_to_f32(a.x), br = f64_to_f32(b.x);
+  const float ai = ca ? -f64_to_f32(a.y) : f64_to_f32(a.y);
+  const float bi = cb ? -f64_to_f32(b.y) : f64_to_f32(b.y);
+  xr = fmaf(ar, br, fmaf(-ai, bi, xr));
+  xi = fmaf(ar, bi, fmaf(ai, br, xi));
+}
+
+template <bool F32>
 __global__ void gemv_kt_kernel(long N, long K, const double2 *__restrict__ A,
                                const long *__restrict__ ak, bool conjA,
                                const double2 *__restrict__ B, const long *__restrict__ bn,
@@ -150,12 +161,23 @@ __global__ void gemv_kt_kernel(long N, long K, const double2 *__restrict__ A,
   double2 acc = make_double2(0.0, 0.0);
   if (n < N) {
     const long bo = bn ? bn[n] : n * ldb;
-    for (long k = ty; k < K; k += 8) {
-      double2 a = A[ak ? ak[k] : k];
-      double2 b = B[bo + (bk ? bk[k] : k)];
-      if (conjA) a.y = -a.y;
-      if (conjB) b.y = -b.y;
-      acc = cfma(a, b, acc);
+    if (F32) {
+      for (long k0 = ty; k0 < K; k0 += 8 * 16) {
+        float xr = 0.f, xi = 0.f;
+        const long k1 = min(K, k0 + 8 * 16);
+        for (long k = k0; k < k1; k += 8)
+          cfma32(A[ak ? ak[k] : k], B[bo + (bk ? bk[k] : k)], conjA, conjB, xr, xi);
+        acc.x += f32_to_f64(xr);
+        acc.y += f32_to_f64(xi);
+      }
+    } else {
+      for (long k = ty; k < K; k += 8) {
+        double2 a = A[ak ? ak[k] : k];
+        double2 b = B[bo + (bk ? bk[k] : k)];
+        if (conjA) a.y = -a.y;
+        if (conjB) b.y = -b.y;
+        acc = cfma(a, b, acc);
+      }
     }
   }
   red[ty][tx] = acc;
@@ -172,6 +194,7 @@ __global__ void gemv_kt_kernel(long N, long K, const double2 *__restrict__ A,
 
 // Same contraction with one warp per output element and the lanes striding
 // k: coalesced when the operand's innermost K index has unit stride.
+template <bool F32>
 __global__ void gemv_warp_kernel(long N, long K, const double2 *__restrict__ A,
                                  const long *__restrict__ ak, bool conjA,
                                  const double2 *__restrict__ B, const long *__restrict__ bn,
@@ -186,6 +209,19 @@ __global__ void gemv_warp_kernel(long N, long K, const double2 *__restrict__ A,
     double2 ac[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
                      make_double2(0.0, 0.0)};
     long k = lane;
+    if (F32) {
+      // runs of 4 x 4 products per lane in FP32, each run added in FP64
+      for (; k + 96 < K; k += 128) {
+        float xr = 0.f, xi = 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const long kk = k + 32 * u;
+          cfma32(A[ak ? ak[kk] : kk], B[bo + (bk ? bk[kk] : kk)], conjA, conjB, xr, xi);
+        }
+        ac[0].x += f32_to_f64(xr);
+        ac[0].y += f32_to_f64(xi);
+      }
+    }
     for (; k + 96 < K; k += 128) {
       long ia[4], ib[4];
 #pragma unroll
@@ -304,24 +340,26 @@ void gemm_f64(const GemmDesc &g, cudaStream_t st, int num_sms) {
     const long n_out = rowvec ? g.N : g.M;
     if (g.k_contig) {
       const unsigned wb = static_cast<unsigned>(std::min<long>((n_out + 7) / 8, 65535));
+      auto kern = g.f32 ? gemv_warp_kernel<true> : gemv_warp_kernel<false>;
       if (rowvec)
-        gemv_warp_kernel<<<wb, 256, 0, st>>>(n_out, g.K, g.A, g.ak, g.conjA, g.B, g.bn, g.bk, g.ldb,
-                                             g.conjB, g.C, g.cn, 1, g.alpha, g.beta);
+        kern<<<wb, 256, 0, st>>>(n_out, g.K, g.A, g.ak, g.conjA, g.B, g.bn, g.bk, g.ldb, g.conjB,
+                                 g.C, g.cn, 1, g.alpha, g.beta);
       else
-        gemv_warp_kernel<<<wb, 256, 0, st>>>(n_out, g.K, g.B, g.bk, g.conjB, g.A, g.am, g.ak, g.lda,
-                                             g.conjA, g.C, g.cm, g.ldc, g.alpha, g.beta);
+        kern<<<wb, 256, 0, st>>>(n_out, g.K, g.B, g.bk, g.conjB, g.A, g.am, g.ak, g.lda, g.conjA,
+                                 g.C, g.cm, g.ldc, g.alpha, g.beta);
       LAUNCH_CHECK();
       count_launch();
       return;
     }
     if (g.K >= 64 && n_out <= 65535L * 32) {
       const unsigned kb = static_cast<unsigned>((n_out + 31) / 32);
+      auto kern = g.f32 ? gemv_kt_kernel<true> : gemv_kt_kernel<false>;
       if (rowvec)
-        gemv_kt_kernel<<<kb, dim3(32, 8), 0, st>>>(n_out, g.K, g.A, g.ak, g.conjA, g.B, g.bn, g.bk,
-                                                   g.ldb, g.conjB, g.C, g.cn, 1, g.alpha, g.beta);
+        kern<<<kb, dim3(32, 8), 0, st>>>(n_out, g.K, g.A, g.ak, g.conjA, g.B, g.bn, g.bk, g.ldb,
+                                         g.conjB, g.C, g.cn, 1, g.alpha, g.beta);
       else
-        gemv_kt_kernel<<<kb, dim3(32, 8), 0, st>>>(n_out, g.K, g.B, g.bk, g.conjB, g.A, g.am, g.ak,
-                                                   g.lda, g.conjA, g.C, g.cm, g.ldc, g.alpha, g.beta);
+        kern<<<kb, dim3(32, 8), 0, st>>>(n_out, g.K, g.B, g.bk, g.conjB, g.A, g.am, g.ak, g.lda,
+                                         g.conjA, g.C, g.cm, g.ldc, g.alpha, g.beta);
       LAUNCH_CHECK();
       count_launch();
       return;

@@ -209,6 +209,8 @@ struct alignas(64) TcProblem {
   double2 alpha, beta;
   float2 alpha_f;   // alpha rounded to FP32 (applied to the FP32 tile)
   const float *amax_a, *amax_b;  // FP16 operand scales (nullptr: none)
+  float *amax_out;  // TC_OUT_F32: max |written value| x amax_mul (nullptr: none)
+  float amax_mul;
   int num_kb;       // K blocks of 128 bytes per row
   int kb_per_split;
   int k_splits, m_tiles, n_tiles;
@@ -472,6 +474,7 @@ __global__ void __launch_bounds__(320, 1)
       // lane/2) on the way in, lane = output column on the way out, so each
       // store instruction writes 32 consecutive complex values of one row.
       float *stg = stage + warp * 1024;
+      float omax = 0.0f;
       // undo the FP16 operand scales (an exact power of two)
       float usc = 1.0f;
       if (args.amax_a) usc = 1.0f / (fp16_scale(*args.amax_a) * fp16_scale(*args.amax_b));
@@ -494,6 +497,7 @@ __global__ void __launch_bounds__(320, 1)
           if (args.out == TC_OUT_F32) {
             float2 *Cf = reinterpret_cast<float2 *>(args.C);
             Cf[mc * args.ldc + n] = make_float2(re, im);
+            omax = fmaxf(omax, fmaxf(fabsf(re), fabsf(im)));
           } else {
             double2 *C = reinterpret_cast<double2 *>(args.C);
             const long off = (args.cm ? args.cm[mc] : mc * args.ldc) + cno;
@@ -519,6 +523,12 @@ __global__ void __launch_bounds__(320, 1)
           }
         }
         __syncwarp();
+      }
+      if (args.amax_out) {
+        // largest magnitude written (times amax_mul), for the consumer's FP16 scale
+        for (int o = 16; o > 0; o >>= 1) omax = fmaxf(omax, __shfl_xor_sync(0xffffffffu, omax, o));
+        if (lane == 0)
+          atomicMax(reinterpret_cast<unsigned *>(args.amax_out), __float_as_uint(omax * args.amax_mul));
       }
     }
     if (!ok && lane == 0) atomicExch(err, 1);
@@ -626,6 +636,8 @@ void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
     a.alpha_f = make_float2(static_cast<float>(g.alpha.x), static_cast<float>(g.alpha.y));
     a.amax_a = g.amax_a;
     a.amax_b = g.amax_b;
+    a.amax_out = g.out == TC_OUT_F32 ? g.amax_out : nullptr;
+    a.amax_mul = g.amax_mul;
     if ((g.amax_a == nullptr) != (g.amax_b == nullptr))
       fail(CC_ERR_ARG, "gemm_tc: FP16 operand scales come in pairs");
     a.tile_start = static_cast<int>(tiles);

@@ -23,6 +23,7 @@ struct GemmDesc {
   cplx *C = nullptr; const long *cm = nullptr, *cn = nullptr; long ldc = 0;
   cplx alpha = {1.0, 0.0}, beta = {0.0, 0.0};
   bool k_contig = false;  // the GEMV operand's innermost K index has unit stride
+  bool f32 = false;       // GEMV shapes: FP32 products, runs summed in FP64 (tensor-core tiers)
 };
 
 // FP64 SIMT path (CC_TIER_FP64).
@@ -78,6 +79,10 @@ struct TcDesc {
   // were packed with fp16_scale() of these and the product is unscaled in
   // the epilogue (nullptr: unscaled)
   const float *amax_a = nullptr, *amax_b = nullptr;
+  // TC_OUT_F32 only: atomically raised to amax_mul x max |Re|, |Im| over
+  // the values written (the caller zeroes it); nullptr: not tracked
+  float *amax_out = nullptr;
+  float amax_mul = 1.0f;
 };
 void gemm_tc(const TcDesc &g, cudaStream_t st, int *err_flag);
 // Several independent GEMMs (any shapes, same or mixed tiers) in as few

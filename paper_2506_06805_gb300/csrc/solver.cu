@@ -433,7 +433,9 @@ void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr) {
       if (f16) {
         tc_absmax(Lv, nullptr, ptab, 1, vv, X, amx_L, st);
         tc_absmax(tau, rt.as<long>(), kt.as<long>(), 0, n_ij, n_cd, amx_t, st);
-        ladder_w_bound(Lv, static_cast<int>(X), vv, amx_W, st);
+        // |W| <= 2 max |V|: each GEMM1 raises amx_W to twice the largest
+        // slab value it writes, before the antisymmetriser of its block
+        zero(amx_W, sizeof(float), st);
       }
       tc_pack_A(Lv, nullptr, ptab, 1, false, vv, X, Kp1, tr, A1h.p, A1l.p, st, amx_L);
       tc_pack_B(Lv, nullptr, ptab, 1, false, vv, X, Kp1, tr, B1h.p, B1l.p, st, amx_L);
@@ -465,6 +467,7 @@ void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr) {
       g1.tier = tr; g1.out = TC_OUT_F32;
       g1.C = Vs.p; g1.ldc = (v - a0) * v;
       g1.amax_a = amx_L; g1.amax_b = amx_L;
+      g1.amax_out = amx_W; g1.amax_mul = 2.0f;
       {
         Engine::Region r = eng.region("ladder gemm1");
         gemm_tc(g1, st, err_d.as<int>());
@@ -522,12 +525,29 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
     Engine::Region r = eng.region("make_tau x2");
     make_tau_pair(t1p, t2p, tau.c(), taut.c(), o, v, st, tr != TIER_FP64);
   }
+  // FP16 tiers: one maximum pass per doubles-sized operand, shared by all
+  // of its uses ([0] t2, [1] tau, [2] tau~, [3] Z)
+  const bool scaled = tier_scaled(tr);
+  Buf amx(&al, 4 * sizeof(float));
+  float *amx_t2 = nullptr, *amx_tau = nullptr, *amx_taut = nullptr, *amx_z = nullptr;
+  if (scaled) {
+    amx_t2 = amx.as<float>();
+    amx_tau = amx_t2 + 1;
+    amx_taut = amx_t2 + 2;
+    amx_z = amx_t2 + 3;
+    Engine::Region r = eng.region("absmax t2 tau tau~");
+    tc_absmax(t2p, nullptr, nullptr, 0, 1, n2, amx_t2, st);
+    tc_absmax(tau.c(), nullptr, nullptr, 0, 1, n2, amx_tau, st);
+    tc_absmax(taut.c(), nullptr, nullptr, 0, 1, n2, amx_taut, st);
+  }
+  auto t2 = [&](const char *ix) { return with_amax(T(t2p, ix, {o, o, v, v}), amx_t2); };
+  auto tauT = [&](const char *ix) { return with_amax(T(tau.c(), ix, {o, o, v, v}), amx_tau); };
+  auto tautT = [&](const char *ix) { return with_amax(T(taut.c(), ix, {o, o, v, v}), amx_taut); };
   Buf Fae(&al, sizeof(cplx) * vv), Fmi(&al, sizeof(cplx) * oo), Fme(&al, sizeof(cplx) * o * v);
   Buf cP(&al, sizeof(cplx) * X), Y(&al, sizeof(cplx) * X * v * o), Zm(&al, sizeof(cplx) * X * oo);
   Buf Q(&al, sizeof(cplx) * X * o * v);
   const std::vector<long> d_oo = {o, o}, d_ov = {o, v}, d_vv = {v, v};
   auto t1 = [&](const char *ix) { return T(t1p, ix, {o, v}); };
-  auto t2 = [&](const char *ix) { return T(t2p, ix, {o, o, v, v}); };
   auto g_oovv = [&](const char *ix) { return stable(T(oovv.c(), ix, {o, o, v, v})); };
   auto g_ooov = [&](const char *ix) { return stable(T(ooov.c(), ix, {o, o, o, v})); };
   auto g_ovvo = [&](const char *ix) { return stable(T(ovvo.c(), ix, {o, v, v, o})); };
@@ -543,11 +563,11 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
   eng.contract(C1(), Lvv_("Paf"), t1("mf"), C0(), T(Y.c(), "Pam", {X, v, o}), tr);
   eng.contract(C1(), T(cP.c(), "P", {X}), Lvv_("Pae"), C0(), T(Fae.c(), "ae", {v, v}), TIER_FP64);
   eng.contract(Cr(-1), Lov_("Pme"), T(Y.c(), "Pam", {X, v, o}), C1(), T(Fae.c(), "ae", {v, v}), tr);
-  eng.contract(Cr(-0.5), T(taut.c(), "mnaf", {o, o, v, v}), g_oovv("mnef"), C1(),
+  eng.contract(Cr(-0.5), tautT("mnaf"), g_oovv("mnef"), C1(),
                T(Fae.c(), "ae", {v, v}), tr);
   // F_mi = sum_ne t_n^e <mn||ie> + 1/2 tau~_in^ef <mn||ef>
   eng.contract(C1(), g_ooov("mnie"), t1("ne"), C0(), T(Fmi.c(), "mi", {o, o}), TIER_FP64);
-  eng.contract(Cr(0.5), g_oovv("mnef"), T(taut.c(), "inef", {o, o, v, v}), C1(),
+  eng.contract(Cr(0.5), g_oovv("mnef"), tautT("inef"), C1(),
                T(Fmi.c(), "mi", {o, o}), tr);
   taut.release();
 
@@ -602,10 +622,10 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
     eng.contract(C1(), g_ooov("mnie"), t1("je"), C0(), T(tmp.c(), "mnij", d4), tr);
     eng.permute_into(C1(), T(tmp.c(), "mnij", d4), C1(), T(Wp.c(), "mnij", d4));
     eng.permute_into(Cr(-1), T(tmp.c(), "mnji", d4), C1(), T(Wp.c(), "mnij", d4));
-    eng.contract(C1(), g_oovv("mnef"), T(tau.c(), "ijef", {o, o, v, v}), C0(), T(Zb.c(), "mnij", d4),
+    eng.contract(C1(), g_oovv("mnef"), tauT("ijef"), C0(), T(Zb.c(), "mnij", d4),
                  tr);
     // (i,j) as the GEMM rows so the output rows (a,b) are contiguous
-    eng.contract(Cr(0.5), T(Wp.c(), "mnij", d4), T(tau.c(), "mnab", {o, o, v, v}), C1(), R2t("ijab"),
+    eng.contract(Cr(0.5), T(Wp.c(), "mnij", d4), tauT("mnab"), C1(), R2t("ijab"),
                  tr);
     eng.contract(Cr(0.25), T(Zb.c(), "mnij", d4), t2("mnab"), C1(), R2t("ijab"), tr);
   }
@@ -637,8 +657,10 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
     {
       Engine::Region r = eng.region("make_z");
       make_z(t1p, t2p, z.c(), o, v, 0.5, st, tr != TIER_FP64);
+      if (scaled) tc_absmax(z.c(), nullptr, nullptr, 0, 1, n2, amx_z, st);
     }
-    eng.contract(Cr(-1), T(z.c(), "jnfb", {o, o, v, v}), g_oovv("mnef"), C1(), Wt("jbme"), tr);
+    eng.contract(Cr(-1), with_amax(T(z.c(), "jnfb", {o, o, v, v}), amx_z), g_oovv("mnef"), C1(),
+                 Wt("jbme"), tr);
   }
   // P(ij)P(ab) [t_im^ae W_mbej - t_i^e t_m^a <mb||ej>]
   eng.contract(C1(), t2("imae"), Wt("jbme"), C0(), Xt("ijab"), tr);
