@@ -4,9 +4,8 @@
 // short free side (a t1 or Fock-like block) and one long side (a doubles-
 // sized tensor) move far more bytes than they compute: on the tensor-core
 // path they would pay for expanded operand planes and for 128-row tiles
-// that are mostly padding. Here a lane pair owns one row of the long
-// operand (FP64 variant: one thread), keeps its K elements in registers, and
-// sweeps the short operand,
+// that are mostly padding. Here each thread owns one row of the long
+// operand, keeps its K elements in registers, and sweeps the short operand,
 // which sits in shared memory; consecutive threads take consecutive long
 // rows, whose outputs are adjacent in memory for every use in this library.
 // Products and sums are FP32 (24-bit mantissa, finer than TF32); the
@@ -30,30 +29,22 @@ __device__ __forceinline__ double2 epilogue(float pr, float pi, double2 old, flo
   return make_double2(beta.x * old.x - beta.y * old.y + xr, beta.x * old.y + beta.y * old.x + xi);
 }
 
-// Two threads per long row: lane pair (2i, 2i+1) splits the row's K
-// elements in halves (half the registers, so two to three blocks fit per
-// SM), the partial sums of two outputs are exchanged with one shuffle each,
-// and each lane of the pair writes one of the two outputs.
 template <int KM>
 __global__ void __launch_bounds__(SK_THREADS) skinny_kernel(const SkinnyDesc d, int chunk,
                                                             int beta_mode, float2 alpha_f) {
   extern __shared__ float4 s_sm[];  // [chunk][KM / 2]: two complex k per float4
-  constexpr int KH = KM / 2;        // float4 per short row
-  constexpr int KQ = KH / 2;        // float4 per half row
-  static_assert(KM % 4 == 0, "K tile must split into two even halves");
-  const int h = threadIdx.x & 1;
-  const long r = blockIdx.x * static_cast<long>(SK_THREADS / 2) + (threadIdx.x >> 1);
+  constexpr int KH = KM / 2;
+  const long r = blockIdx.x * static_cast<long>(SK_THREADS) + threadIdx.x;
   const bool live = r < d.Mb;
-  float2 g[KH];  // this lane's half: complex k = h * KH + j
+  float2 g[KM];
   {
     const long go = live ? (d.gr ? d.gr[r] : r * d.ldg) : 0;
 #pragma unroll
-    for (int j = 0; j < KH; ++j) {
-      const int k = h * KH + j;
+    for (int k = 0; k < KM; ++k) {
       double2 x = make_double2(0.0, 0.0);
       if (live && k < d.K) x = d.G[go + (d.gk ? d.gk[k] : k * d.gks)];
       const float im = f64_to_f32(x.y);
-      g[j] = make_float2(f64_to_f32(x.x), d.conjG ? -im : im);
+      g[k] = make_float2(f64_to_f32(x.x), d.conjG ? -im : im);
     }
   }
   const long cb = live ? (d.cb ? d.cb[r] : r * d.ldcb) : 0;
@@ -72,44 +63,46 @@ __global__ void __launch_bounds__(SK_THREADS) skinny_kernel(const SkinnyDesc d, 
                             sg * f64_to_f32(x1.y));
     }
     __syncthreads();
+    if (!live) continue;
+    // two outputs per pass; the old values of both are requested before the
+    // products so their latency overlaps the arithmetic
     for (int s = 0; s < ns; s += 2) {
       const bool two = s + 1 < ns;
-      const int my = s + h;  // the output this lane writes
-      const bool mine = live && my < ns;
-      const long co = mine ? cb + (d.cs ? d.cs[s0 + my] : static_cast<long>(s0 + my) * d.ldcs) : 0;
-      double2 old = make_double2(0.0, 0.0);
-      if (beta_mode && mine) old = d.C[co];
-      const float4 *q0 = s_sm + s * KH + h * KQ;
-      const float4 *q1 = (two ? s_sm + (s + 1) * KH : s_sm + s * KH) + h * KQ;
-      float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+      const long co0 = cb + (d.cs ? d.cs[s0 + s] : static_cast<long>(s0 + s) * d.ldcs);
+      const long co1 = two ? cb + (d.cs ? d.cs[s0 + s + 1] : static_cast<long>(s0 + s + 1) * d.ldcs)
+                           : co0;
+      double2 old0 = make_double2(0.0, 0.0), old1 = make_double2(0.0, 0.0);
+      if (beta_mode) {
+        old0 = d.C[co0];
+        if (two) old1 = d.C[co1];
+      }
+      const float4 *q0 = s_sm + s * KH;
+      const float4 *q1 = two ? q0 + KH : q0;
+      float ar0 = 0.f, ai0 = 0.f, ar1 = 0.f, ai1 = 0.f;  // output s
+      float br0 = 0.f, bi0 = 0.f, br1 = 0.f, bi1 = 0.f;  // output s + 1
 #pragma unroll
-      for (int kp = 0; kp < KQ; ++kp) {
+      for (int kp = 0; kp < KH; ++kp) {
         const float4 w = q0[kp], u = q1[kp];
         const float2 a = g[2 * kp], b = g[2 * kp + 1];
-        ar = fmaf(a.x, w.x, ar);
-        ar = fmaf(-a.y, w.y, ar);
-        ai = fmaf(a.x, w.y, ai);
-        ai = fmaf(a.y, w.x, ai);
-        ar = fmaf(b.x, w.z, ar);
-        ar = fmaf(-b.y, w.w, ar);
-        ai = fmaf(b.x, w.w, ai);
-        ai = fmaf(b.y, w.z, ai);
-        br = fmaf(a.x, u.x, br);
-        br = fmaf(-a.y, u.y, br);
-        bi = fmaf(a.x, u.y, bi);
-        bi = fmaf(a.y, u.x, bi);
-        br = fmaf(b.x, u.z, br);
-        br = fmaf(-b.y, u.w, br);
-        bi = fmaf(b.x, u.w, bi);
-        bi = fmaf(b.y, u.z, bi);
+        ar0 = fmaf(a.x, w.x, ar0);
+        ar0 = fmaf(-a.y, w.y, ar0);
+        ai0 = fmaf(a.x, w.y, ai0);
+        ai0 = fmaf(a.y, w.x, ai0);
+        ar1 = fmaf(b.x, w.z, ar1);
+        ar1 = fmaf(-b.y, w.w, ar1);
+        ai1 = fmaf(b.x, w.w, ai1);
+        ai1 = fmaf(b.y, w.z, ai1);
+        br0 = fmaf(a.x, u.x, br0);
+        br0 = fmaf(-a.y, u.y, br0);
+        bi0 = fmaf(a.x, u.y, bi0);
+        bi0 = fmaf(a.y, u.x, bi0);
+        br1 = fmaf(b.x, u.z, br1);
+        br1 = fmaf(-b.y, u.w, br1);
+        bi1 = fmaf(b.x, u.w, bi1);
+        bi1 = fmaf(b.y, u.z, bi1);
       }
-      // full sums: own half + the partner lane's half
-      ar += __shfl_xor_sync(0xffffffffu, ar, 1);
-      ai += __shfl_xor_sync(0xffffffffu, ai, 1);
-      br += __shfl_xor_sync(0xffffffffu, br, 1);
-      bi += __shfl_xor_sync(0xffffffffu, bi, 1);
-      if (mine) d.C[co] = h == 0 ? epilogue(ar, ai, old, alpha_f, beta_mode, d.beta)
-                                 : epilogue(br, bi, old, alpha_f, beta_mode, d.beta);
+      d.C[co0] = epilogue(ar0 + ar1, ai0 + ai1, old0, alpha_f, beta_mode, d.beta);
+      if (two) d.C[co1] = epilogue(br0 + br1, bi0 + bi1, old1, alpha_f, beta_mode, d.beta);
     }
   }
 }
@@ -174,8 +167,7 @@ void skinny_launch(const SkinnyDesc &d, cudaStream_t st) {
                         : (d.beta.x == 1.0 && d.beta.y == 0.0) ? 1
                                                                : 2;
   const float2 af = make_float2(static_cast<float>(d.alpha.x), static_cast<float>(d.alpha.y));
-  const long rows_per_block = SK_THREADS / 2;
-  const long blocks = (d.Mb + rows_per_block - 1) / rows_per_block;
+  const long blocks = (d.Mb + SK_THREADS - 1) / SK_THREADS;
   skinny_kernel<KM><<<static_cast<unsigned>(blocks), SK_THREADS, chunk * per_s, st>>>(d, chunk,
                                                                                      beta_mode, af);
   LAUNCH_CHECK();

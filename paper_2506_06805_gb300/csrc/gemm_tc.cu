@@ -1044,7 +1044,7 @@ __device__ __forceinline__ void block_max_store(float m, float *amax) {
 }
 
 // Block (BX, BY): x along the operand's contiguous direction (rows when
-// rows_inner, else k), y along the other (grid-stride).
+// rows_inner, else k), y along the other; both grid-stride.
 __global__ void __launch_bounds__(256) absmax_kernel(const double2 *__restrict__ src,
                                                      const long *__restrict__ rt,
                                                      const long *__restrict__ kt, long ld,
@@ -1052,10 +1052,10 @@ __global__ void __launch_bounds__(256) absmax_kernel(const double2 *__restrict__
                                                      float *amax) {
   float m = 0.0f;
   const long X = rows_inner ? rows : K, Y = rows_inner ? K : rows;
-  const long xi = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
-  if (xi < X) {
-    const long step = static_cast<long>(gridDim.y) * blockDim.y;
-    for (long yi = blockIdx.y * static_cast<long>(blockDim.y) + threadIdx.y; yi < Y; yi += step) {
+  const long xstep = static_cast<long>(gridDim.x) * blockDim.x;
+  const long ystep = static_cast<long>(gridDim.y) * blockDim.y;
+  for (long xi = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; xi < X; xi += xstep) {
+    for (long yi = blockIdx.y * static_cast<long>(blockDim.y) + threadIdx.y; yi < Y; yi += ystep) {
       const long r = rows_inner ? xi : yi, k = rows_inner ? yi : xi;
       const double2 a = src[(rt ? rt[r] : r * ld) + (kt ? kt[k] : k)];
       m = fmaxf(m, fmaxf(fabsf(f64_to_f32(a.x)), fabsf(f64_to_f32(a.y))));
@@ -1120,8 +1120,8 @@ void tc_absmax(const cplx *src, const long *rt, const long *kt, long ld, long ro
   const long X = rows_inner ? rows : K, Y = rows_inner ? K : rows;
   const int bx = static_cast<int>(std::min<long>(256, std::max<long>(32, (X + 31) / 32 * 32)));
   const int by = 256 / bx;
-  const long gx = (X + bx - 1) / bx;
-  if (gx > 0x7fffffffL) fail(CC_ERR_ARG, "tc_absmax: operand too wide");
+  // at most ~16 blocks per SM in all: threads stride over the operand
+  const long gx = std::min<long>((X + bx - 1) / bx, 152L * 16);
   const long gy = std::max<long>(
       1, std::min<long>(std::min<long>((Y + by - 1) / by, 65535L), std::max<long>(1, 152L * 16 / gx)));
   absmax_kernel<<<dim3(static_cast<unsigned>(gx), static_cast<unsigned>(gy)), dim3(bx, by), 0, st>>>(
