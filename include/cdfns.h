@@ -129,7 +129,7 @@ int fns_get_occupations(const cc_ctx *ctx, double *occ_host, int n);
  * ccsd_solve: CCSD amplitudes (Eqs. 13-14) and energy (Eq. 15).
  * Start t1 = 0, t2 = MP2 (or amplitudes given by cc_set_amplitudes).
  * Jacobi updates with FP64 denominators and Pulay DIIS (8 vectors, from
- * iteration 3). Converged when ||dt||_2 over unique amplitudes < tol and
+ * iteration 2). Converged when ||dt||_2 over unique amplitudes < tol and
  * |dE| < tol.
  * e_corr  host double[2]: complex correlation energy (re, im).
  * n_iter  host int (may be NULL): iterations taken.

@@ -711,7 +711,7 @@ int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
     d2h(&h, escr.c() + esl, sizeof(cplx), st);
     return h;
   };
-  const int m_max = 8, diis_start = 3;
+  const int m_max = 8, diis_start = 2;
   std::vector<Buf> hv(m_max), he(m_max);
   Buf Bm(&al, sizeof(cplx) * 16 * 16), coef(&al, sizeof(cplx) * 16), dstat(&al, sizeof(int) * 4);
   int n_hist = 0, slot = 0;
