@@ -142,7 +142,8 @@ int ccsd_solve(cc_ctx *ctx, double tol, int max_iter, double *e_corr,
  * ipeom_solve: the n_roots IP-EOM-CCSD roots of smallest real part
  * (Eqs. 17-18) by block Davidson with all roots' sigma vectors built in
  * one batch. H-bar elements with at most two virtual indices are built
- * once from the converged amplitudes.
+ * once from the converged amplitudes, in the CCSD tier (cc_set_precision);
+ * the sigma contractions run in the EOM tier (cc_set_precision_eom).
  * omega      host double[n_roots][2]: complex IPs, sorted by real part.
  * r1_weight  host double[n_roots] (may be NULL): ||r1||^2 / ||r||^2.
  * n_iter     host int (may be NULL): Davidson iterations.

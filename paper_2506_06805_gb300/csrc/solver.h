@@ -79,9 +79,12 @@ struct Ctx {
   void check_err_flag();
   void ensure_pairs();
   int eom() const { return eom_tier < 0 ? tier : eom_tier; }
-  // integrals, FNS and H-bar: the accurate split tier of the chosen family
+  // integrals and FNS: the accurate split tier of the chosen family
   int int_tier() const { return tier_accurate(tier); }
-  int hbar_tier() const { return tier_accurate(eom()); }
+  // H-bar is built once from the CCSD amplitudes with the residual's kinds
+  // of contractions, in the CCSD tier (FP16 H-bar moves the IPs of the small
+  // workload by 3e-9 Eh from FP64); the Davidson sigma uses the EOM tier
+  int hbar_tier() const { return tier; }
   long nij() const { return static_cast<long>(o) * (o - 1) / 2; }
   long nab() const { return static_cast<long>(v) * (v - 1) / 2; }
   long dim_ip() const { return o + nij() * v; }
