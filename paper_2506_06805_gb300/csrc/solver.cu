@@ -608,9 +608,11 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
     d2d(Fmj.p, Fmi.p, sizeof(cplx) * oo, st);
     eng.contract(Cr(0.5), t1("je"), T(Fme.c(), "me", {o, v}), C1(), T(Fmj.c(), "mj", {o, o}),
                  TIER_FP64);
-    eng.contract(Cr(-1), t2("imab"), T(Fmj.c(), "mj", {o, o}), C0(), Xt("ijab"), tr);
-    eng.contract(C1(), T(Y.c(), "Pai", {X, v, o}), Lvo_("Pbj"), C1(), Xt("ijab"), tr);
+    // the tensor-core product first, with beta = 0: plain stores rather
+    // than atomic additions for the first writer of X
+    eng.contract(C1(), T(Y.c(), "Pai", {X, v, o}), Lvo_("Pbj"), C0(), Xt("ijab"), tr);
     eng.contract(Cr(-1), Lvo_("Paj"), T(Y.c(), "Pbi", {X, v, o}), C1(), Xt("ijab"), tr);
+    eng.contract(Cr(-1), t2("imab"), T(Fmj.c(), "mj", {o, o}), C1(), Xt("ijab"), tr);
     { Engine::Region r_ = eng.region("antisym_add"); antisym_add(R2, Xb.c(), o, v, 1.0, 1, st); }
   }
   // hole ladder: 1/2 tau_mn^ab W'_mnij + 1/4 t_mn^ab Z_mnij, with
