@@ -10,15 +10,18 @@
 //
 // Precision tiers: kind::tf32 with one product (TIER_TF32) or with a hi/lo
 // split and three products hi*hi + hi*lo + lo*hi (TIER_TF32X3); kind::f16
-// with bf16 hi/lo and three products (TIER_BF16X3). Accumulation is FP32 in
-// TMEM; the epilogue accumulates into FP64 (or stores FP32 for staging).
+// with bf16 hi/lo and three products (TIER_BF16X3); kind::f16 with fp16
+// operands scaled by a power of two per operand, one product (TIER_FP16) or
+// hi/lo and three (TIER_FP16X3). Accumulation is FP32 in TMEM, promoted to
+// FP32 registers every few K blocks; the epilogue accumulates into FP64 (or
+// stores FP32 for staging).
 //
 // CTA layout (320 threads): warps 0-7 epilogue, warp 8 TMA producer, warp 9
 // TMEM allocator + MMA issuer; persistent CTAs walk a list of 128 x BN output
-// tiles (of up to 16 problems per launch), K optionally split. The wide
-// (BN = 256) kernels run as clusters of two CTAs on vertically adjacent
-// tiles that share their B tile: each CTA loads half of it and multicasts it
-// to both, which cuts the L2 -> SM operand traffic per MMA by a third.
+// tiles (of up to 16 problems per launch), K optionally split. With
+// CDFNS_CTA_PAIR=1 the wide (BN = 256) kernels run as clusters of two CTAs
+// on vertically adjacent tiles that share their B tile, each CTA loading
+// half of it and multicasting it to both (off by default: no gain measured).
 // Every mbarrier wait is bounded in time; on expiry the kernel records an
 // error flag, drains, frees TMEM and returns.
 #include <cuda.h>
@@ -579,6 +582,12 @@ CUtensorMap make_map(const void *base, long rows, long kp, int box_rows, int et)
   return m;
 }
 
+// K blocks accumulated in TMEM before promotion to FP32 registers: 8 for
+// TF32 and the FP16 tiers (256-512 K elements per chunk, which keeps the
+// accumulation bias below 1e-6 relative; the autotuner preferred 8 over 4 on
+// nearly every FP16 shape of the CCSD workload), 4 for BF16x3.
+inline int default_chunk(int tier) { return (tier == TIER_TF32 || tier_scaled(tier)) ? 8 : 4; }
+
 template <int BN, int STAGES, bool SPLIT, int ET, int CL>
 void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
   constexpr int STAGE_BYTES = (BM * ROW_BYTES + BN * ROW_BYTES) * (SPLIT ? 2 : 1);
@@ -647,7 +656,7 @@ void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
   if (np == 0) return;
   grp.nprob = np;
   grp.total_tiles = static_cast<int>(tiles);
-  grp.chunk = descs[0].chunk > 0 ? descs[0].chunk : (descs[0].tier == TIER_TF32 ? 8 : 4);
+  grp.chunk = descs[0].chunk > 0 ? descs[0].chunk : default_chunk(descs[0].tier);
   grp.err = err;
   if constexpr (CL == 1) {
     dim3 grid(static_cast<unsigned>(std::min<long>(tiles, sms)));
@@ -837,7 +846,7 @@ void tune_save() {
 }
 
 Choice tune(const TcDesc &g, cudaStream_t st, int *err) {
-  const int dch = g.tier == TIER_TF32 ? 8 : 4;
+  const int dch = default_chunk(g.tier);
   const Choice cands[] = {{256, 0, dch}, {256, 1, dch}, {256, 16, dch},
                           {128, 0, dch}, {256, 0, 2 * dch}, {128, 1, dch}};
   void *scratch = nullptr;
