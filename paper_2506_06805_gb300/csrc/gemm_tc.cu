@@ -583,10 +583,11 @@ CUtensorMap make_map(const void *base, long rows, long kp, int box_rows, int et)
 }
 
 // K blocks accumulated in TMEM before promotion to FP32 registers: 8 for
-// TF32 and the FP16 tiers (256-512 K elements per chunk, which keeps the
-// accumulation bias below 1e-6 relative; the autotuner preferred 8 over 4 on
-// nearly every FP16 shape of the CCSD workload), 4 for BF16x3.
-inline int default_chunk(int tier) { return (tier == TIER_TF32 || tier_scaled(tier)) ? 8 : 4; }
+// the one-product tiers TF32 and FP16 (256 / 512 K elements per chunk; the
+// autotuner preferred 8 over 4 on nearly every FP16 shape of the CCSD
+// workload), 4 for the three-product tiers, whose accuracy target leaves
+// less room for the accumulation bias of a longer chunk.
+inline int default_chunk(int tier) { return (tier == TIER_TF32 || tier == TIER_FP16) ? 8 : 4; }
 
 template <int BN, int STAGES, bool SPLIT, int ET, int CL>
 void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
