@@ -68,6 +68,14 @@ def max_over_ranks(value, device):
 ORACLE_CCSD_ITERATIONS = 5
 
 
+def workload_config(name, c, world):
+    """The JSON `config` of both arms for one workload."""
+    return {"workload": f"{name}: o={c.n_occ} v={c.n_virt} X={c.n_aux} kramers={c.kramers} "
+                        f"roots={c.n_roots} ccsd_tol={c.ccsd_tol} eom_tol={c.eom_tol}",
+            "l2": "inputs > L2 (L 2.2 GB, t2 2.3 GB); no flush",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def dist_env():
     r = int(os.environ.get("RANK", "0"))
     w = int(os.environ.get("WORLD_SIZE", "1"))
@@ -201,8 +209,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.config}: o={c.n_occ} v={c.n_virt} X={c.n_aux} "
-                   f"kramers={c.kramers} roots={c.n_roots}"},
+        "config": workload_config(args.config, c, 1),
         "cpu_baseline": {"value": value, "unit": "s", "cores": os.cpu_count(),
                          "kind": "oracle",
                          "sample": "per step one row a of the oracle ladder, scaled to "
@@ -312,10 +319,7 @@ def run_ours(args):
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": f"{args.tier}/{args.eom_tier} tensor (c128 FP64 control)",
         "data": "synthetic",
-        "config": {"workload": f"{args.config}: o={o} v={v} X={X} kramers={c.kramers} "
-                               f"roots={nr} ccsd_tol={c.ccsd_tol} eom_tol={c.eom_tol}",
-                   "l2": "inputs > L2 (L 2.2 GB, t2 2.3 GB); no flush",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": workload_config(args.config, c, world),
         "roofline": roofline, "clocks": clocks.summary(), "gpu_launches": launches,
         "ladder_tflops": ladder_tf, "ccsd_iterations": ccsd_iters,
         "e_corr": [e.real, e.imag], "ips_eh": [float(x) for x in w.real],
