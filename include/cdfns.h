@@ -171,6 +171,19 @@ int cc_batch_ipeom(cc_ctx **systems, int n_sys, int n_roots, double tol,
 /* Replay the batched sigma from CUDA graphs (1, default) or not (0). */
 int cc_set_graphs(cc_ctx *ctx, int on);
 
+/* Cap on the device bytes the context holds through its allocator (its
+ * tensors, workspaces and caches; 0, the default, removes the cap). An
+ * allocation beyond the cap fails with CC_ERR_OOM, as does one the device
+ * cannot serve. Within the room left (under the cap, and on the device less
+ * 2 GiB), ccsd_solve keeps the residual's transient buffers allocatable first
+ * and only then holds its optional buffers: the DIIS history (up to 8 pairs,
+ * fewer when short of room, none at all when not even one fits), the cache of
+ * packed stable operands (otherwise packed again on each use) and a permuted
+ * copy of <mb||ej>. The results do not depend on these choices beyond the
+ * convergence tolerance. Must not lower the cap below the bytes already held
+ * (CC_ERR_ARG). */
+int cc_set_memory_limit(cc_ctx *ctx, size_t bytes);
+
 /* Amplitudes as unique elements, host complex128: t1 [o][v] then t2 for
  * i<j, a<b in row-major pair order ([o(o-1)/2][v(v-1)/2]). */
 int cc_get_amplitudes(const cc_ctx *ctx, double *t1_host, double *t2_host);
@@ -267,7 +280,11 @@ int cc_dump_integrals(cc_ctx *ctx, int block, double *out_host);
  * flops per call, [3] fns ms, [4] ccsd ms, [5] ipeom ms, [6] kernel launches
  * since the context was created, [7] ccsd iterations, [8] Davidson
  * iterations, [9] tensor-core GEMM ms inside the ladder, [10] tc GEMM
- * launches inside the ladder. */
+ * launches inside the ladder, [11] high-water mark of the device bytes the
+ * context has held (its own buffers and caches, through its allocator),
+ * [12] DIIS pairs held in the last ccsd_solve (8 unless device memory was
+ * short), [13] high-water mark of the device bytes held during the CCSD
+ * iterations of the last ccsd_solve, [14] device bytes held now. */
 int cc_get_stats(const cc_ctx *ctx, double *out_host, int n);
 
 /*

@@ -89,6 +89,7 @@ _SIGS = {
     "cc_mlp_warm_start": (ctypes.c_int, [_P, _P]),
     "cc_free": (None, [_P]),
     "cc_set_graphs": (ctypes.c_int, [_P, ctypes.c_int]),
+    "cc_set_memory_limit": (ctypes.c_int, [_P, ctypes.c_size_t]),
     "cc_batch_ipeom": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, ctypes.c_int, _D, _D, _I, _I]),
 }
@@ -326,6 +327,10 @@ class System:
     def set_graphs(self, on=True):
         _check(lib().cc_set_graphs(self._ctx, 1 if on else 0), self._ctx)
 
+    def set_memory_limit(self, nbytes):
+        """Cap the device bytes this system holds (0: no cap)."""
+        _check(lib().cc_set_memory_limit(self._ctx, int(nbytes)), self._ctx)
+
     def get_amplitudes(self):
         o, v, _ = self.sizes()
         t1 = np.empty(o * v, np.complex128)
@@ -368,7 +373,9 @@ class System:
         s = np.zeros(16)
         _check(lib().cc_get_stats(self._ctx, _dptr(s), 16), self._ctx)
         keys = ["ladder_ms", "ladder_calls", "ladder_flops", "fns_ms", "ccsd_ms",
-                "ipeom_ms", "launches", "ccsd_iter", "davidson_iter"]
+                "ipeom_ms", "launches", "ccsd_iter", "davidson_iter", "ladder_tc_ms",
+                "ladder_tc_launches", "device_peak_bytes", "diis_depth",
+                "ccsd_loop_peak_bytes", "device_bytes_held"]
         return {k: float(s[i]) for i, k in enumerate(keys)}
 
 

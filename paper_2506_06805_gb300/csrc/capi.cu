@@ -1,4 +1,5 @@
 // extern "C" boundary of libcdfns.so (declared in include/cdfns.h).
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -34,6 +35,9 @@ void check_cuda(cudaError_t e, const char *what, const char *file, int line) {
 
 void *Allocator::get(size_t bytes) {
   if (bytes == 0) bytes = 16;
+  if (limit && in_use + bytes > limit)
+    fail(CC_ERR_OOM, "device allocation of " + std::to_string(bytes) +
+                         " bytes exceeds the context's memory limit");
   void *p = nullptr;
   if (alloc) {
     p = alloc(bytes, user);
@@ -45,13 +49,30 @@ void *Allocator::get(size_t bytes) {
       fail(CC_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
     }
   }
+  in_use += bytes;
+  peak = std::max(peak, in_use);
+  window = std::max(window, in_use);
   return p;
 }
 
-void Allocator::put(void *p) {
+void Allocator::put(void *p, size_t bytes) {
   if (!p) return;
+  in_use -= std::min(in_use, bytes ? bytes : size_t(16));
   if (free) free(p, user);
   else cudaFree(p);
+}
+
+size_t device_avail(const Allocator *al) {
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    fr = 0;
+  }
+  const size_t reserve = size_t(2) << 30;
+  fr = fr > reserve ? fr - reserve : 0;
+  if (al && al->alloc) fr += al->peak - std::min(al->peak, al->in_use);
+  if (al && al->limit) fr = std::min(fr, al->limit - std::min(al->limit, al->in_use));
+  return fr;
 }
 
 void Buf::reset(Allocator *a, size_t n) {
@@ -62,7 +83,7 @@ void Buf::reset(Allocator *a, size_t n) {
 }
 
 void Buf::release() {
-  if (p && al) al->put(p);
+  if (p && al) al->put(p, bytes);
   p = nullptr;
   bytes = 0;
 }
@@ -124,6 +145,7 @@ int cc_init_chunked(int n_occ, int n_virt, int n_aux, const double *eps, cc_ctx 
   {
     std::lock_guard<std::mutex> lk(cdfns::g_mu);
     ctx->c.al = cdfns::g_default_alloc;
+    ctx->c.al.in_use = ctx->c.al.peak = ctx->c.al.window = ctx->c.al.limit = 0;
     ctx->c.st = cdfns::g_default_stream;
   }
   const int rc = guarded(ctx, [&] {
@@ -429,6 +451,9 @@ int cc_get_stats(const cc_ctx *ctx, double *out, int n) {
   double s[16];
   std::memcpy(s, ctx->c.stat, sizeof(s));
   s[6] = static_cast<double>(cdfns::g_launches);
+  s[11] = static_cast<double>(ctx->c.al.peak);
+  s[12] = ctx->c.diis_depth;
+  s[14] = static_cast<double>(ctx->c.al.in_use);
   std::memcpy(out, s, sizeof(double) * n);
   return CC_OK;
 }
@@ -448,6 +473,13 @@ void cc_free(cc_ctx *ctx) {
 int cc_set_graphs(cc_ctx *ctx, int on) {
   if (!ctx) return CC_ERR_ARG;
   ctx->c.use_graphs = on != 0;
+  return CC_OK;
+}
+
+int cc_set_memory_limit(cc_ctx *ctx, size_t bytes) {
+  if (!ctx) return CC_ERR_ARG;
+  if (bytes && bytes < ctx->c.al.in_use) return CC_ERR_ARG;
+  ctx->c.al.limit = bytes;
   return CC_OK;
 }
 

@@ -87,9 +87,19 @@ struct Allocator {
   void *(*alloc)(size_t, void *) = nullptr;
   void (*free)(void *, void *) = nullptr;
   void *user = nullptr;
+  size_t in_use = 0;  // bytes currently held through this allocator
+  size_t peak = 0;    // high-water mark of in_use
+  size_t window = 0;  // high-water mark of in_use since the caller last set it
+  size_t limit = 0;   // cap on in_use (0: none); a get() beyond it fails
   void *get(size_t bytes);
-  void put(void *p);
+  void put(void *p, size_t bytes);
 };
+// Device bytes an allocation through `al` can still obtain: the driver's free
+// memory less 2 GiB for work outside the allocator (library workspaces,
+// fragmentation), plus, for a caller's caching allocator, the bytes this
+// allocator has returned since its high-water mark (held in that cache);
+// never more than the room left under al->limit.
+size_t device_avail(const Allocator *al);
 
 struct Buf {
   Allocator *al = nullptr;

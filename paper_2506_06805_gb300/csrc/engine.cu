@@ -51,13 +51,26 @@ const long *Engine::table(const std::vector<long> &dims, const std::vector<long>
   return p;
 }
 
-std::pair<void *, void *> Engine::packed(bool a_side, const TRef &t, const long *rt, const long *kt,
-                                         long ld, long rows, long K, long Kp, int tier,
-                                         const float **amax) {
+std::string Engine::pack_key(bool a_side, const TRef &t, const long *rt, const long *kt, long ld,
+                             long rows, long K, long Kp, int tier) {
   std::ostringstream key;
   key << (a_side ? 'A' : 'B') << t.p << ':' << t.conj << ':' << rt << ':' << kt << ':' << ld << ':'
       << rows << ':' << K << ':' << Kp << ':' << tier;
-  auto it = packs_.find(key.str());
+  return key.str();
+}
+
+bool Engine::may_cache(const std::string &key, size_t n) {
+  if (cache_reserve == 0 || packs_.count(key)) return true;
+  if (uncached_.count(key)) return false;
+  if (device_avail(al) >= n + cache_reserve) return true;
+  uncached_.insert(key);
+  return false;
+}
+
+std::pair<void *, void *> Engine::packed(const std::string &key, bool a_side, const TRef &t,
+                                         const long *rt, const long *kt, long ld, long rows, long K,
+                                         long Kp, int tier, const float **amax) {
+  auto it = packs_.find(key);
   if (it != packs_.end()) {
     *amax = it->second.amax.as<float>();
     return {it->second.hi.p, it->second.lo.p};
@@ -78,7 +91,7 @@ std::pair<void *, void *> Engine::packed(bool a_side, const TRef &t, const long 
     tc_pack_B(t.p, rt, kt, ld, t.conj, rows, K, Kp, tier, pk.hi.p, pk.lo.p, st, pk.amax.as<float>());
   std::pair<void *, void *> r{pk.hi.p, pk.lo.p};
   *amax = pk.amax.as<float>();
-  packs_[key.str()] = std::move(pk);
+  packs_[key] = std::move(pk);
   return r;
 }
 
@@ -308,8 +321,12 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
   const int pb = 4 * (slot < 0 ? 0 : slot + 1);  // plane set of this contraction
   const bool f16 = tier_scaled(tier);
   const float *xa = nullptr, *xb = nullptr;  // FP16 operand maxima
-  if (A.stable) {
-    std::tie(Ah, Al) = packed(true, A, am, ak, lda, M, K, Kp, tier, &xa);
+  const size_t nA_bytes = eb * 2 * M * Kp * (split ? 2 : 1), nB_bytes = eb * N * Kp * (split ? 2 : 1);
+  std::string keyA, keyB;
+  if (A.stable) keyA = pack_key(true, A, am, ak, lda, M, K, Kp, tier);
+  if (B.stable) keyB = pack_key(false, B, bn, bk, ldb, N, K, Kp, tier);
+  if (A.stable && may_cache(keyA, nA_bytes)) {
+    std::tie(Ah, Al) = packed(keyA, true, A, am, ak, lda, M, K, Kp, tier, &xa);
   } else {
     Ah = plane(pb + 0, eb * 2 * M * Kp);
     Al = split ? plane(pb + 1, eb * 2 * M * Kp) : nullptr;
@@ -323,8 +340,8 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
     }
     tc_pack_A(A.p, am, ak, lda, A.conj, M, K, Kp, tier, Ah, Al, st, xa);
   }
-  if (B.stable) {
-    std::tie(Bh, Bl) = packed(false, B, bn, bk, ldb, N, K, Kp, tier, &xb);
+  if (B.stable && may_cache(keyB, nB_bytes)) {
+    std::tie(Bh, Bl) = packed(keyB, false, B, bn, bk, ldb, N, K, Kp, tier, &xb);
   } else {
     Bh = plane(pb + 2, eb * N * Kp);
     Bl = split ? plane(pb + 3, eb * N * Kp) : nullptr;

@@ -10,6 +10,7 @@
 #pragma once
 
 #include <map>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -61,6 +62,11 @@ class Engine {
   cudaStream_t st = nullptr;
   int num_sms = 148;
   int *err_flag = nullptr;  // device int, set by bounded waits
+  // Device bytes to keep free when caching a stable operand's packed planes:
+  // 0 caches every stable operand; otherwise an operand whose planes would
+  // leave less free memory than this is packed into the scratch planes on
+  // each use instead (the decision holds until the pack cache is cleared).
+  size_t cache_reserve = 0;
   // statistics
   double flops = 0;
   long gen = 0;  // bumped whenever a plane or packed buffer is (re)allocated or freed
@@ -82,10 +88,12 @@ class Engine {
   void clear_cache() {
     cache_.clear();
     packs_.clear();
+    uncached_.clear();
     ++gen;
   }
   void clear_pack_cache() {
     packs_.clear();
+    uncached_.clear();
     ++gen;
   }
 
@@ -110,16 +118,21 @@ class Engine {
   struct Packed {
     Buf hi, lo, amax;
   };
+  static std::string pack_key(bool a_side, const TRef &t, const long *rt, const long *kt, long ld,
+                              long rows, long K, long Kp, int tier);
+  // whether the packed planes of `key` (n bytes) are, or may be, cached
+  bool may_cache(const std::string &key, size_t n);
   // returns (hi, lo) planes of a stable operand, packing it on first use;
   // *amax receives its FP16 scale source (TIER_FP16) or nullptr
-  std::pair<void *, void *> packed(bool a_side, const TRef &t, const long *rt, const long *kt,
-                                   long ld, long rows, long K, long Kp, int tier,
-                                   const float **amax);
+  std::pair<void *, void *> packed(const std::string &key, bool a_side, const TRef &t,
+                                   const long *rt, const long *kt, long ld, long rows, long K,
+                                   long Kp, int tier, const float **amax);
   // device float of plane slot `which` for the FP16 operand maximum
   float *plane_amax(int which);
   std::map<int, Buf> amax_planes_;
   std::map<std::string, Buf> cache_;
   std::map<std::string, Packed> packs_;
+  std::set<std::string> uncached_;
   std::map<int, Buf> planes_;
   struct TraceRec {
     std::string label;

@@ -677,6 +677,21 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
 // ===========================================================================
 // CCSD iterations with Jacobi updates and DIIS
 // ===========================================================================
+size_t Ctx::planes_bytes_estimate(int tr) const {
+  if (tr == TIER_FP64) return 0;
+  // the largest doubles-sized contraction (M K = o^2 v^2, N <= M) packs its
+  // A side into 2M x 2K and its B side into N x 2K elements of the tier's
+  // type, twice for the hi/lo tiers
+  const double mk = static_cast<double>(o) * o * v * v;
+  return static_cast<size_t>(6.0 * mk * tc_elem_bytes(tr) * (tier_split(tr) ? 2 : 1));
+}
+
+size_t Ctx::residual_bytes_estimate() const {
+  const double nb2 = static_cast<double>(sizeof(cplx)) * o * o * v * v;
+  const double lvv = static_cast<double>(sizeof(cplx)) * X * v * v;
+  return static_cast<size_t>(4 * nb2 + lvv) + planes_bytes_estimate(tier) + slab_budget;
+}
+
 int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
   if (!(tol > 0) || max_iter < 1) fail(CC_ERR_ARG, "tol must be > 0 and max_iter >= 1");
   ensure_ready();
@@ -693,14 +708,31 @@ int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
   }
   Buf R1(&al, sizeof(cplx) * n1), R2(&al, sizeof(cplx) * n2);
   Buf vcur(&al, sizeof(cplx) * na), vnew(&al, sizeof(cplx) * na), step(&al, sizeof(cplx) * na);
-  ovvo_jbme.reset(&al, sizeof(cplx) * n2);
-  eng.permute_into(C1(), T(ovvo.c(), "mbej", {o, v, v, o}), C0(),
-                   T(ovvo_jbme.c(), "jbme", {o, v, o, v}));
+  Buf invd(&al, sizeof(double) * na);
+  // Device memory beyond the buffers above: the residual's transient buffers
+  // must stay allocatable; what is left holds, in this order of preference,
+  // the DIIS history (m_max pairs of packed vectors), the cache of packed
+  // stable operands, and the <mb||ej> copy in the ring term's layout. On a
+  // device with room for everything (all but the largest systems) all three
+  // are kept; otherwise the copy is skipped, operands are packed on each use
+  // and the DIIS history grows only as far as memory allows.
+  const int m_max = 8, diis_start = 2;
+  const size_t pair_bytes = 2 * sizeof(cplx) * na;
+  size_t res_need = residual_bytes_estimate();
+  eng.cache_reserve = res_need + m_max * pair_bytes;
+  if (device_avail(&al) >= sizeof(cplx) * n2 + res_need + m_max * pair_bytes) {
+    ovvo_jbme.reset(&al, sizeof(cplx) * n2);
+    eng.permute_into(C1(), T(ovvo.c(), "mbej", {o, v, v, o}), C0(),
+                     T(ovvo_jbme.c(), "jbme", {o, v, o, v}));
+  }
   struct Release {
     Buf &b;
-    ~Release() { b.release(); }
-  } release_jbme{ovvo_jbme};
-  Buf invd(&al, sizeof(double) * na);
+    Engine &e;
+    ~Release() {
+      b.release();
+      e.cache_reserve = 0;
+    }
+  } release_jbme{ovvo_jbme, eng};
   amp_denoms(eps_d.as<double>(), o, v, ij_i.as<int>(), ij_j.as<int>(), ab_a.as<int>(),
              ab_b.as<int>(), invd.as<double>(), st);
   const long esl = energy_scratch_len(o, v);
@@ -713,10 +745,10 @@ int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
     d2h(&h, escr.c() + esl, sizeof(cplx), st);
     return h;
   };
-  const int m_max = 8, diis_start = 2;
   std::vector<Buf> hv(m_max), he(m_max);
   Buf Bm(&al, sizeof(cplx) * 16 * 16), coef(&al, sizeof(cplx) * 16), dstat(&al, sizeof(int) * 4);
-  int n_hist = 0, slot = 0;
+  int n_hist = 0, slot = 0, diis_cap = 0;
+  size_t loop_peak = 0;  // device bytes held at most during the iterations
   std::vector<int> order;  // slots in age order
   pack_amps(t1.c(), t2.c(), o, v, ij_i.as<int>(), ij_j.as<int>(), ab_a.as<int>(), ab_b.as<int>(), vcur.c(), st);
   cplx e_old = energy_of(vcur);
@@ -724,8 +756,13 @@ int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
   int it = 0;
   for (it = 1; it <= max_iter; ++it) {
     {
+      // the bytes this residual allocates beyond what it started with
+      const size_t base = al.in_use;
+      al.window = base;
       Engine::Region r = eng.region("residual total");
       residual(t1.c(), t2.c(), R1.c(), R2.c());
+      res_need = al.window - base;
+      loop_peak = std::max(loop_peak, al.window);
     }
     Engine::Region r_upd = eng.region("update+diis");
     jacobi_packed(R1.c(), R2.c(), invd.as<double>(), o, v, ij_i.as<int>(), ij_j.as<int>(),
@@ -745,9 +782,13 @@ int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
       converged = true;
       break;
     }
-    if (it >= diis_start) {
-      // push (vnew, step) into the ring of m_max slots
-      if (n_hist < m_max) {
+    // a new history slot only while the next residual keeps room
+    if (it >= diis_start && n_hist < m_max && n_hist == diis_cap &&
+        device_avail(&al) >= pair_bytes + res_need)
+      ++diis_cap;
+    if (it >= diis_start && diis_cap > 0) {
+      // push (vnew, step) into the ring of diis_cap slots
+      if (n_hist < diis_cap) {
         slot = n_hist++;
         hv[slot].reset(&al, sizeof(cplx) * na);
         he[slot].reset(&al, sizeof(cplx) * na);
@@ -804,6 +845,8 @@ int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
   eng.trace_flush();
   stat[4] += now_ms() - t0;
   stat[7] = it;
+  stat[13] = static_cast<double>(loop_peak);
+  diis_depth = n_hist;
   ccsd_done = true;
   hbar_done = false;
   return converged ? CC_OK : CC_ERR_NOT_CONVERGED;
@@ -815,6 +858,14 @@ int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
 void Ctx::build_hbar() {
   Engine::Region rg = eng.region("hbar total");
   eng.clear_pack_cache();
+  // packed operands are cached while tau, Q, the <mb||ej> - Q copy, the
+  // (me|bf) block and the operand planes stay allocatable
+  eng.cache_reserve = static_cast<size_t>(3.0 * sizeof(cplx) * o * o * v * v) +
+                      planes_bytes_estimate(hbar_tier()) + slab_budget;
+  struct ResetReserve {
+    Engine &e;
+    ~ResetReserve() { e.cache_reserve = 0; }
+  } reset_reserve{eng};
   ++sig_gen;
   const int tr = hbar_tier();
   const long oo = static_cast<long>(o) * o, vv = static_cast<long>(v) * v, ov = static_cast<long>(o) * v;
@@ -923,6 +974,9 @@ void Ctx::build_hbar() {
   split_diag(Hvv.c(), v, Hvv_off.c(), dvv.c(), st);
   CUDA_CHECK(cudaStreamSynchronize(st));
   check_err_flag();
+  // the sigma packs its operands in the EOM tier: the H-bar build's packed
+  // planes are not used again
+  eng.clear_pack_cache();
   hbar_done = true;
 }
 

@@ -21,6 +21,7 @@ struct Ctx {
   bool use_graphs = true;  // replay the batched sigma from CUDA graphs
   int num_sms = 148;
   size_t slab_budget = size_t(4) << 30;  // bytes for ladder V slabs
+  int diis_depth = 0;                    // DIIS pairs held in the last ccsd_solve
 
   // inputs
   Buf eps_d;
@@ -78,6 +79,11 @@ struct Ctx {
   cplx energy(const cplx *t1, const cplx *t2);
   void check_err_flag();
   void ensure_pairs();
+  // upper estimate of the scratch planes of the tensor-core operands
+  size_t planes_bytes_estimate(int tier) const;
+  // upper estimate of the device bytes one CCSD residual allocates and frees
+  // again (tau, tau~, X, W, z, the dressed L, ladder slabs, operand planes)
+  size_t residual_bytes_estimate() const;
   int eom() const { return eom_tier < 0 ? tier : eom_tier; }
   // integrals and FNS: the accurate split tier of the chosen family
   int int_tier() const { return tier_accurate(tier); }

@@ -4,6 +4,7 @@
     python -m paper_2506_06805_gb300.kernel_bench gemm --M 4096 --N 4096 --K 4096
     python -m paper_2506_06805_gb300.kernel_bench fns --config fns --keep-frac 0.4
     python -m paper_2506_06805_gb300.kernel_bench batch --n-sys 8 --roots 8
+    python -m paper_2506_06805_gb300.kernel_bench solve --config batched_big --roots 16
 
 ``ladder`` times cc_ladder_dev (1/2 sum_cd <ab||cd> tau_ij^cd with <ab||cd>
 formed from Cholesky vectors) and reports algorithmic TFLOP/s with the
@@ -18,6 +19,11 @@ n_aux = 4 n_virt, shapes and inputs from ``synth.batch_specs``), solves
 CCSD for each, then times IP-EOM for all of them one after another and as
 one batch (batched sigma in grouped launches, with and without CUDA graphs)
 and compares the roots.
+``solve`` runs one configured system end to end (Cholesky vectors fed in
+chunks of 200, CCSD, IP-EOM with all roots in one block) on the library's
+own cudaMalloc allocations, and reports the phase times, iteration counts,
+the ladder rate, the DIIS depth the device memory allowed and the high-water
+mark of the library's device memory.
 One JSON line per run.
 """
 from __future__ import annotations
@@ -33,7 +39,7 @@ def main():
 
     from . import System, synth, use_torch_memory, zgemm_dev
     p = argparse.ArgumentParser()
-    p.add_argument("what", choices=["ladder", "gemm", "fns", "batch"])
+    p.add_argument("what", choices=["ladder", "gemm", "fns", "batch", "solve"])
     p.add_argument("--n-sys", type=int, default=8)
     p.add_argument("--roots", type=int, default=8)
     p.add_argument("--config", default="fns")
@@ -49,6 +55,8 @@ def main():
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=1)
     a = p.parse_args()
+    if a.what == "solve":
+        return solve_run(a)
     use_torch_memory()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -145,6 +153,44 @@ def fns_run(a):
     out["runs"] = res
     out["max_dIP_tf32_vs_tf32x3"] = float(np.abs(np.array(res["tf32"]["ips"])
                                                  - np.array(res["tf32x3"]["ips"])).max())
+    print(json.dumps(out))
+
+
+def solve_run(a):
+    import time
+
+    from . import System, synth
+    c = synth.CONFIGS[a.config]
+    o, v, X = c.n_occ, c.n_virt, c.n_aux
+    nr = a.roots if a.roots > 0 else c.n_roots
+    rng = np.random.default_rng(c.seed)
+    eps = synth.make_eps(rng, o, v, c.kramers)
+    out = {"config": a.config, "o": o, "v": v, "X": X, "roots": nr, "tier": a.tier,
+           "eom_tier": a.eom_tier}
+    t0 = time.perf_counter()
+    with System(eps, None, n_occ=o, n_aux=X, tier=a.tier, eom_tier=a.eom_tier,
+                torch_memory=False) as s:
+        for p0 in range(0, X, 200):
+            p1 = min(X, p0 + 200)
+            s.add_cholesky(p0, p1, synth.cholesky_chunks(rng, o + v, X, p0, p1, c.kramers))
+        t1 = time.perf_counter()
+        e = s.ccsd(tol=c.ccsd_tol, max_iter=60)
+        t2 = time.perf_counter()
+        w, r1 = s.ipeom(nr, tol=c.eom_tol, max_iter=100)
+        t3 = time.perf_counter()
+        st = s.stats()
+    order = np.argsort(w.real)
+    out.update({
+        "input_s": t1 - t0, "ccsd_s": t2 - t1, "ipeom_s": t3 - t2,
+        "ccsd_iter": s.ccsd_iterations, "davidson_iter": s.davidson_iterations,
+        "e_corr": [e.real, e.imag],
+        "ips": [float(x) for x in w.real[order]],
+        "r1_weight": [float(x) for x in r1[order]],
+        "ladder_tflops": st["ladder_flops"] * st["ladder_calls"] / st["ladder_ms"] / 1e9
+        if st["ladder_ms"] > 0 else None,
+        "ladder_ms_per_call": st["ladder_ms"] / max(1.0, st["ladder_calls"]),
+        "diis_depth": int(st["diis_depth"]), "device_peak_gb": st["device_peak_bytes"] / 1e9,
+    })
     print(json.dumps(out))
 
 

@@ -32,6 +32,7 @@ def test_null_arguments_rejected_without_device():
     assert L.ccsd_solve(None, 1e-8, 10, None, None) == -1
     assert L.cc_set_precision(None, 0) == -1
     assert L.cc_dump_integrals(None, 9, None) == -1
+    assert L.cc_set_memory_limit(None, ctypes.c_size_t(1 << 30)) == -1
 
 
 def test_allocator_pair_must_be_complete():
