@@ -13,7 +13,8 @@ symmetry-reduced count 8 [X v^3 (v-1)/2 + (v(v-1)/2)^2 o(o-1)/2].
 ``fns`` feeds a configured system's Cholesky vectors in chunks of 200
 (cc_add_cholesky), reports the natural-spinor occupations and the count
 kept at the literal threshold, then runs FNS with the kept fraction,
-CCSD and IP-EOM in two tier pairs and compares their IPs.
+CCSD and IP-EOM with CCSD in --tier and in --eom-tier (the EOM sigma in
+--eom-tier both times) and compares their IPs.
 ``batch`` builds the uneven batch of systems (n_occ 20-50, n_virt 150-400,
 n_aux = 4 n_virt, shapes and inputs from ``synth.batch_specs``), solves
 CCSD for each, then times IP-EOM for all of them one after another and as
@@ -50,8 +51,8 @@ def main():
     p.add_argument("--M", type=int, default=4096)
     p.add_argument("--N", type=int, default=4096)
     p.add_argument("--K", type=int, default=4096)
-    p.add_argument("--tier", default="tf32")
-    p.add_argument("--eom-tier", default="tf32x3")
+    p.add_argument("--tier", default="fp16")
+    p.add_argument("--eom-tier", default="fp16x3")
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=1)
     a = p.parse_args()
@@ -125,7 +126,7 @@ def fns_run(a):
         return s
 
     thr = c.get("fns_threshold", 1e-5)
-    with make("tf32", "tf32x3") as s:
+    with make(a.tier, a.eom_tier) as s:
         t0 = time.perf_counter()
         out["kept_at_threshold"] = s.fns_truncate(threshold=thr)
         torch.cuda.synchronize()
@@ -136,7 +137,9 @@ def fns_run(a):
         out["n_ge"] = {f"{t:.3g}": int((occ >= t).sum()) for t in (1e-4, 10 ** -4.5, 1e-5, 1e-6)}
     n_keep = max(1, int(round(a.keep_frac * v)))
     res = {}
-    for tier, eom in (("tf32", "tf32x3"), ("tf32x3", "tf32x3")):
+    # the CCSD tier against the accurate EOM tier used throughout
+    pairs = ((a.tier, a.eom_tier), (a.eom_tier, a.eom_tier))
+    for tier, eom in pairs:
         with make(tier, eom) as s:
             t0 = time.perf_counter()
             s.fns_truncate(n_keep=n_keep)
@@ -151,8 +154,9 @@ def fns_run(a):
                          "ips": [float(x) for x in np.sort(w.real)]}
     out["n_keep"] = n_keep
     out["runs"] = res
-    out["max_dIP_tf32_vs_tf32x3"] = float(np.abs(np.array(res["tf32"]["ips"])
-                                                 - np.array(res["tf32x3"]["ips"])).max())
+    t0, t1 = pairs[0][0], pairs[1][0]
+    out[f"max_dIP_{t0}_vs_{t1}"] = float(np.abs(np.array(res[t0]["ips"])
+                                               - np.array(res[t1]["ips"])).max())
     print(json.dumps(out))
 
 
