@@ -130,7 +130,11 @@ int fns_get_occupations(const cc_ctx *ctx, double *occ_host, int n);
  * Start t1 = 0, t2 = MP2 (or amplitudes given by cc_set_amplitudes).
  * Jacobi updates with FP64 denominators and Pulay DIIS (8 vectors, from
  * iteration 2). Converged when ||dt||_2 over unique amplitudes < tol and
- * |dE| < tol.
+ * |dE| < tol. In the one-product tiers (TF32, FP16) the residual's rounding
+ * leaves a floor under ||dt|| that rises with the amplitudes' size: when the
+ * best ||dt|| has not halved for three iterations, the remaining iterations
+ * run in the tier's split form (TF32X3, FP16X3), the DIIS history restarts,
+ * and cc_get_stats [15] records the iteration.
  * e_corr  host double[2]: complex correlation energy (re, im).
  * n_iter  host int (may be NULL): iterations taken.
  * Errors: CC_ERR_NOT_CONVERGED (results still written), CC_ERR_NUMERIC.
@@ -142,7 +146,8 @@ int ccsd_solve(cc_ctx *ctx, double tol, int max_iter, double *e_corr,
  * ipeom_solve: the n_roots IP-EOM-CCSD roots of smallest real part
  * (Eqs. 17-18) by block Davidson with all roots' sigma vectors built in
  * one batch. H-bar elements with at most two virtual indices are built
- * once from the converged amplitudes, in the CCSD tier (cc_set_precision);
+ * once from the converged amplitudes, in the tier the CCSD iterations
+ * finished in (cc_set_precision, or its split form after the move above);
  * the sigma contractions run in the EOM tier (cc_set_precision_eom).
  * omega      host double[n_roots][2]: complex IPs, sorted by real part.
  * r1_weight  host double[n_roots] (may be NULL): ||r1||^2 / ||r||^2.
@@ -284,7 +289,9 @@ int cc_dump_integrals(cc_ctx *ctx, int block, double *out_host);
  * context has held (its own buffers and caches, through its allocator),
  * [12] DIIS pairs held in the last ccsd_solve (8 unless device memory was
  * short), [13] high-water mark of the device bytes held during the CCSD
- * iterations of the last ccsd_solve, [14] device bytes held now. */
+ * iterations of the last ccsd_solve, [14] device bytes held now, [15] the
+ * CCSD iteration after which the residual moved from a one-product tier to
+ * its split form (0: it did not). */
 int cc_get_stats(const cc_ctx *ctx, double *out_host, int n);
 
 /*

@@ -375,7 +375,7 @@ class System:
         keys = ["ladder_ms", "ladder_calls", "ladder_flops", "fns_ms", "ccsd_ms",
                 "ipeom_ms", "launches", "ccsd_iter", "davidson_iter", "ladder_tc_ms",
                 "ladder_tc_launches", "device_peak_bytes", "diis_depth",
-                "ccsd_loop_peak_bytes", "device_bytes_held"]
+                "ccsd_loop_peak_bytes", "device_bytes_held", "ccsd_escalated_at"]
         return {k: float(s[i]) for i, k in enumerate(keys)}
 
 

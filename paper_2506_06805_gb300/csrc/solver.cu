@@ -518,7 +518,7 @@ void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr) {
 // CCSD residual (Eqs. 13-14, spin-orbital intermediate form)
 // ===========================================================================
 void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
-  const int tr = tier;
+  const int tr = res_tier();
   const long oo = static_cast<long>(o) * o, vv = static_cast<long>(v) * v, n2 = oo * vv;
   Buf tau(&al, sizeof(cplx) * n2), taut(&al, sizeof(cplx) * n2);
   {
@@ -689,7 +689,7 @@ size_t Ctx::planes_bytes_estimate(int tr) const {
 size_t Ctx::residual_bytes_estimate() const {
   const double nb2 = static_cast<double>(sizeof(cplx)) * o * o * v * v;
   const double lvv = static_cast<double>(sizeof(cplx)) * X * v * v;
-  return static_cast<size_t>(4 * nb2 + lvv) + planes_bytes_estimate(tier) + slab_budget;
+  return static_cast<size_t>(4 * nb2 + lvv) + planes_bytes_estimate(res_tier()) + slab_budget;
 }
 
 int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
@@ -725,14 +725,18 @@ int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
     eng.permute_into(C1(), T(ovvo.c(), "mbej", {o, v, v, o}), C0(),
                      T(ovvo_jbme.c(), "jbme", {o, v, o, v}));
   }
+  cc_tier = -1;
+  cc_done_tier = -1;
   struct Release {
     Buf &b;
     Engine &e;
+    int &t;
     ~Release() {
       b.release();
       e.cache_reserve = 0;
+      t = -1;
     }
-  } release_jbme{ovvo_jbme, eng};
+  } release_jbme{ovvo_jbme, eng, cc_tier};
   amp_denoms(eps_d.as<double>(), o, v, ij_i.as<int>(), ij_j.as<int>(), ab_a.as<int>(),
              ab_b.as<int>(), invd.as<double>(), st);
   const long esl = energy_scratch_len(o, v);
@@ -749,6 +753,14 @@ int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
   Buf Bm(&al, sizeof(cplx) * 16 * 16), coef(&al, sizeof(cplx) * 16), dstat(&al, sizeof(int) * 4);
   int n_hist = 0, slot = 0, diis_cap = 0;
   size_t loop_peak = 0;  // device bytes held at most during the iterations
+  // The one-product tiers (TF32, FP16) leave a floor under ||dt|| that
+  // rises with the size of the amplitudes. When the best step norm has not
+  // halved for three iterations, the remaining iterations run in the
+  // tier's split form (TF32x3, FP16x3) and the DIIS history starts again
+  // from errors of that residual.
+  const int acc_tier = tier_accurate(tier);
+  double best_step = HUGE_VAL;
+  int since_best = 0, escalated_at = 0;
   std::vector<int> order;  // slots in age order
   pack_amps(t1.c(), t2.c(), o, v, ij_i.as<int>(), ij_j.as<int>(), ab_a.as<int>(), ab_b.as<int>(), vcur.c(), st);
   cplx e_old = energy_of(vcur);
@@ -782,11 +794,31 @@ int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
       converged = true;
       break;
     }
-    // a new history slot only while the next residual keeps room
-    if (it >= diis_start && n_hist < m_max && n_hist == diis_cap &&
+    if (dnorm < 0.5 * best_step) {
+      best_step = dnorm;
+      since_best = 0;
+    } else if (++since_best >= 3 && !escalated_at && acc_tier != tier) {
+      escalated_at = it;
+      cc_tier = acc_tier;
+      eng.clear_pack_cache();  // packed in the one-product tier
+      for (int k = 0; k < m_max; ++k) {
+        hv[k].release();
+        he[k].release();
+      }
+      n_hist = 0;
+      diis_cap = 0;
+      order.clear();
+      best_step = HUGE_VAL;
+      since_best = 0;
+    }
+    // a new history slot only while the next residual keeps room (the
+    // step just taken in the one-product tier does not enter a history
+    // restarted for the split tier)
+    const bool use_diis = it >= diis_start && escalated_at != it;
+    if (use_diis && n_hist < m_max && n_hist == diis_cap &&
         device_avail(&al) >= pair_bytes + res_need)
       ++diis_cap;
-    if (it >= diis_start && diis_cap > 0) {
+    if (use_diis && diis_cap > 0) {
       // push (vnew, step) into the ring of diis_cap slots
       if (n_hist < diis_cap) {
         slot = n_hist++;
@@ -846,7 +878,9 @@ int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
   stat[4] += now_ms() - t0;
   stat[7] = it;
   stat[13] = static_cast<double>(loop_peak);
+  stat[15] = escalated_at;
   diis_depth = n_hist;
+  cc_done_tier = res_tier();
   ccsd_done = true;
   hbar_done = false;
   return converged ? CC_OK : CC_ERR_NOT_CONVERGED;

@@ -22,6 +22,8 @@ struct Ctx {
   int num_sms = 148;
   size_t slab_budget = size_t(4) << 30;  // bytes for ladder V slabs
   int diis_depth = 0;                    // DIIS pairs held in the last ccsd_solve
+  int cc_tier = -1;       // tier of the CCSD residual while ccsd_solve runs (-1: tier)
+  int cc_done_tier = -1;  // tier the last ccsd_solve finished in (-1: none)
 
   // inputs
   Buf eps_d;
@@ -88,9 +90,11 @@ struct Ctx {
   // integrals and FNS: the accurate split tier of the chosen family
   int int_tier() const { return tier_accurate(tier); }
   // H-bar is built once from the CCSD amplitudes with the residual's kinds
-  // of contractions, in the CCSD tier (FP16 H-bar moves the IPs of the small
-  // workload by 3e-9 Eh from FP64); the Davidson sigma uses the EOM tier
-  int hbar_tier() const { return tier; }
+  // of contractions, in the tier the CCSD iterations finished in (FP16 H-bar
+  // moves the IPs of the small workload by 3e-9 Eh from FP64); the Davidson
+  // sigma uses the EOM tier
+  int hbar_tier() const { return cc_done_tier >= 0 ? cc_done_tier : tier; }
+  int res_tier() const { return cc_tier >= 0 ? cc_tier : tier; }
   long nij() const { return static_cast<long>(o) * (o - 1) / 2; }
   long nab() const { return static_cast<long>(v) * (v - 1) / 2; }
   long dim_ip() const { return o + nij() * v; }
