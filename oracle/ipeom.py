@@ -1,4 +1,5 @@
-"""IP-EOM-CCSD (Eqs. 16-18): H-bar intermediates, sigma, dense eigenproblem.
+"""IP-EOM-CCSD (Eqs. 16-20): H-bar intermediates, sigma, dense eigenproblem,
+left vectors.
 
 Test infrastructure (see ``oracle/__init__``).
 
@@ -16,7 +17,9 @@ enters through <mn||ef> and t2 directly. The brute-force module
 ``oracle.fci`` pins every element.
 
 Vector layout: [r_i for i in range(o)] + [r_ij^b for (i<j) in
-numpy.triu_indices order, b fastest].
+numpy.triu_indices order, b fastest]. Left vectors (Eq. 20) use the same
+layout for l^i and l^ij_b; Eq. 19 pairs them with right vectors bilinearly
+over these unique elements.
 """
 from __future__ import annotations
 
@@ -95,6 +98,68 @@ def sigma(H, vec, o, v):
     xe = 0.5 * np.einsum("mnef,mnf->e", H["oovv"], r2)
     s2 -= np.einsum("e,ijeb->ijb", xe, H["t2"])
     return pack_r(s1, s2)
+
+
+def left_sigma(H, lvec, o, v):
+    """l^T H-bar_IP for a left vector in the same packed layout.
+
+    Eqs. 19-20 pair a left vector with a right one bilinearly over the unique
+    elements, <L|R> = sum_i l^i r_i + sum_{i<j,b} l^ij_b r_ij^b, so the left
+    eigenproblem is l^T M = omega l^T for the matrix M of ``sigma``. Each
+    term of ``sigma`` is read here with input and output exchanged: with
+    l_ij^b antisymmetric, a term s_ijb <- f(r) contributes
+    (1/2) sum l_ijb f(r) to <L|sigma(R)>, written as sum G_pqb r_pqb, and the
+    packed derivative with respect to r_{p<q}^b is G_pqb - G_qpb.
+    """
+    l1, l2 = unpack_r(lvec, o, v)
+    s1 = (-np.einsum("mi,i->m", H["oo"], l1)
+          - 0.5 * np.einsum("mbij,ijb->m", H["ovoo"], l2))
+    # G[p, q, b], from the terms of sigma in the order written there
+    g = np.einsum("i,me->ime", l1, H["ov"])
+    g -= 0.5 * np.einsum("i,mnie->mne", l1, H["ooov"])
+    g += 0.5 * np.einsum("ijb,be->ije", l2, H["vv"])
+    g -= np.einsum("ijb,mi->mjb", l2, H["oo"])
+    g += 0.25 * np.einsum("ijb,mnij->mnb", l2, H["oooo"])
+    g += np.einsum("ijb,mbej->ime", l2, H["ovvo"])
+    ye = 0.5 * np.einsum("ijb,ijeb->e", l2, H["t2"])
+    g -= 0.5 * np.einsum("e,mnef->mnf", ye, H["oovv"])
+    return pack_r(s1, g - g.transpose(1, 0, 2))
+
+
+def dense_left_right(H, o, v, n_roots):
+    """The n_roots eigenvalues of smallest real part with right vectors R
+    (unit 2-norm) and left vectors L scaled so that L^T R = 1 (Eq. 19).
+
+    Left vectors are the right eigenvectors of M^T, M from ``dense_matrix``;
+    they are matched to the right ones by the largest |l^T r| and the whole
+    selected set is made biorthonormal by L <- L (L^T R)^-T, which also
+    separates degenerate roots.
+    """
+    M = dense_matrix(H, o, v)
+    w, R = np.linalg.eig(M)
+    order = np.argsort(w.real, kind="stable")[:n_roots]
+    w, R = w[order], R[:, order]
+    wl, Lall = np.linalg.eig(M.T)
+    L = np.empty_like(R)
+    used = np.zeros(len(wl), bool)
+    for k in range(n_roots):
+        d = np.abs(wl - w[k])
+        d[used] = np.inf
+        # candidates at this eigenvalue; keep the one overlapping r_k most
+        cand = np.flatnonzero(d <= 1e-8 * max(1.0, abs(w[k])) + d.min())
+        j = cand[np.argmax(np.abs(Lall[:, cand].T @ R[:, k]))]
+        used[j] = True
+        L[:, k] = Lall[:, j]
+    S = L.T @ R
+    L = L @ np.linalg.inv(S).T
+    return w, R, L
+
+
+def pole_strength(lvec, rvec, o):
+    """The 1h part of the biorthonormal pair's overlap, sum_i l^i r_i
+    (equal to 1 for a Koopmans root at zero coupling, 0 for a 2h1p one;
+    summed over all roots it is o)."""
+    return complex(np.dot(lvec[:o], rvec[:o]))
 
 
 def diagonal(H, o, v):

@@ -169,6 +169,53 @@ def test_ip_matrix_equals_bruteforce(o, v, X, seed):
     assert np.abs(M - M_bf).max() <= 1e-10 * max(1.0, np.abs(M_bf).max())
 
 
+@pytest.mark.parametrize("o,v,X,seed", [(3, 5, 12, 1), (4, 3, 10, 6)])
+def test_left_vectors_against_bruteforce(o, v, X, seed):
+    """Eqs. 19-20: left_sigma is the transpose of the brute-force H-bar_IP
+    (every sign and factor of the exchanged terms), and the oracle's left and
+    right vectors are eigenvectors of that matrix, biorthonormal over all
+    roots, with 1h overlaps summing to o (completeness)."""
+    eps, L = _system(o, v, X, seed=seed, scale=10.0)
+    G = integrals.antisym_full(L)
+    g = integrals.Blocks(G, o)
+    res = ccsd.solve(g, eps, tol=1e-13, max_iter=400)
+    assert res["converged"]
+    M_bf = fci.BruteForce(eps, G, o).ip_matrix(res["t1"], res["t2"])
+    H = ipeom.hbar(g, eps, res["t1"], res["t2"])
+    n = ipeom.dim(o, v)
+    scale = max(1.0, np.abs(M_bf).max())
+    rng = np.random.default_rng(seed)
+    for _ in range(3):
+        x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        assert np.abs(ipeom.left_sigma(H, x, o, v) - M_bf.T @ x).max() <= 1e-12 * scale * n
+    w, R, Lv = ipeom.dense_left_right(H, o, v, n)
+    for k in range(n):
+        assert np.abs(Lv[:, k] @ M_bf - w[k] * Lv[:, k]).max() <= 1e-10 * scale * np.abs(Lv[:, k]).max()
+        assert np.abs(M_bf @ R[:, k] - w[k] * R[:, k]).max() <= 1e-10 * scale
+    assert np.abs(Lv.T @ R - np.eye(n)).max() <= 1e-10
+    total = sum(ipeom.pole_strength(Lv[:, k], R[:, k], o) for k in range(n))
+    assert abs(total - o) <= 1e-9
+
+
+def test_pole_strengths_at_zero_coupling():
+    """L = 0: H-bar_IP is the diagonal Koopmans matrix; each 1h root has
+    1h overlap 1 and each 2h1p root 0."""
+    o, v = 4, 5
+    eps, L = _system(o, v, 8)
+    L = 0 * L
+    g = integrals.blocks_from_cholesky(L, o)
+    z1 = np.zeros((o, v), complex)
+    z2 = np.zeros((o, o, v, v), complex)
+    H = ipeom.hbar(g, eps, z1, z2)
+    n = ipeom.dim(o, v)
+    w, R, Lv = ipeom.dense_left_right(H, o, v, n)
+    p = np.array([ipeom.pole_strength(Lv[:, k], R[:, k], o) for k in range(n)])
+    is_1h = np.abs(R[:o, :]).max(axis=0) > 0.5
+    assert is_1h.sum() == o
+    assert np.abs(p[is_1h] - 1).max() <= 1e-12
+    assert np.abs(p[~is_1h]).max() <= 1e-12
+
+
 # --- closed forms and invariances ---------------------------------------------
 
 def test_koopmans_at_zero_coupling():
