@@ -159,6 +159,28 @@ int ipeom_solve(cc_ctx *ctx, int n_roots, double tol, int max_iter,
                 double *omega, double *r1_weight, int *n_iter);
 
 /*
+ * ipeom_solve_lr: ipeom_solve's right vectors together with the left ones
+ * of Eqs. 19-20. The left vectors solve l^T H-bar = omega l^T with the same
+ * block Davidson on the transposed sigma (ipeom_left_sigma_dev), and are
+ * then scaled and combined so that the pairs are biorthonormal over the
+ * n_roots roots, sum_i l_k^i r_l,i + sum_{i<j,b} l_k^ij_b r_l,ij^b = delta_kl
+ * (Eq. 19; bilinear, no complex conjugation). Right vectors have unit
+ * 2-norm.
+ * omega   host double[n_roots][2]: IPs, sorted by real part.
+ * r_host, l_host  host complex128 [n_roots][dim] (may be NULL), the layout
+ *   of ipeom_sigma_dev.
+ * pole    host double[n_roots][2] (may be NULL): sum_i l^i r_i, the 1h part
+ *   of each pair's unit overlap.
+ * n_iter  host int[2] (may be NULL): right and left Davidson iterations.
+ * Errors: CC_ERR_STATE (no converged CCSD), CC_ERR_NOT_CONVERGED (either
+ * Davidson; results written), CC_ERR_NUMERIC (left and right sets do not
+ * pair up).
+ */
+int ipeom_solve_lr(cc_ctx *ctx, int n_roots, double tol, int max_iter,
+                   double *omega, double *r_host, double *l_host, double *pole,
+                   int *n_iter);
+
+/*
  * cc_batch_ipeom: ipeom_solve for several independent systems (uneven sizes
  * allowed), each with converged CCSD. Their block Davidson iterations run in
  * lockstep; each round builds the sigma vectors of every still-active
@@ -211,12 +233,17 @@ int cc_set_amplitudes(cc_ctx *ctx, const double *t1_host,
  * ipeom_sigma_dev: sigma vectors for n_vec packed IP vectors
  *   r[n_vec][dim] -> s[n_vec][dim], dim = o + o(o-1)/2 v, layout r_i then
  *   r_ij^b for i<j (row-major pairs), b fastest. Needs H-bar (ccsd_solve).
+ * ipeom_left_sigma_dev: l^T H-bar_IP for n_vec packed left vectors (Eq. 20,
+ *   same layout): the transpose of ipeom_sigma_dev's map under the bilinear
+ *   pairing of Eq. 19.
  */
 int cc_ladder_dev(cc_ctx *ctx, const double *tau_dev, double *out_dev);
 int cc_residual_dev(cc_ctx *ctx, const double *t1_dev, const double *t2_dev,
                     double *r1_dev, double *r2_dev);
 int ipeom_sigma_dev(cc_ctx *ctx, int n_vec, const double *r_dev,
                     double *s_dev);
+int ipeom_left_sigma_dev(cc_ctx *ctx, int n_vec, const double *l_dev,
+                         double *s_dev);
 
 /*
  * cc_zgemm_dev: the library's complex GEMM on device buffers,

@@ -63,6 +63,9 @@ _SIGS = {
     "cc_ladder_dev": (ctypes.c_int, [_P, _P, _P]),
     "cc_residual_dev": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "ipeom_sigma_dev": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "ipeom_left_sigma_dev": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "ipeom_solve_lr": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                      _D, _D, _D, _D, _I]),
     "cc_dump_integrals": (ctypes.c_int, [_P, ctypes.c_int, _D]),
     "cc_selftest_conversions": (ctypes.c_int, [_P, ctypes.c_long,
                                                ctypes.POINTER(ctypes.c_longlong)]),
@@ -324,6 +327,25 @@ class System:
         self.davidson_iterations = it.value
         return w[0::2] + 1j * w[1::2], r1
 
+    def ipeom_lr(self, n_roots, tol=1e-7, max_iter=100, allow_unconverged=False):
+        """IPs with right and left vectors (Eqs. 18-20), biorthonormal:
+        L @ R.T = 1 over the roots. Returns (omega, R, L, pole) with R, L
+        [n_roots][dim] in the packed layout and pole[k] = sum_i L[k,i] R[k,i]."""
+        o, v, _ = self.sizes()
+        dim = o + o * (o - 1) // 2 * v
+        w = np.zeros(2 * n_roots)
+        pole = np.zeros(2 * n_roots)
+        R = np.empty((n_roots, dim), np.complex128)
+        Lv = np.empty((n_roots, dim), np.complex128)
+        it = (ctypes.c_int * 2)()
+        ok = (0, -5) if allow_unconverged else (0,)
+        _check(lib().ipeom_solve_lr(self._ctx, n_roots, tol, max_iter, _dptr(w),
+                                    R.view(np.float64).ctypes.data_as(_D),
+                                    Lv.view(np.float64).ctypes.data_as(_D), _dptr(pole),
+                                    ctypes.cast(it, _I)), self._ctx, ok)
+        self.davidson_iterations = (it[0], it[1])
+        return w[0::2] + 1j * w[1::2], R, Lv, pole[0::2] + 1j * pole[1::2]
+
     def set_graphs(self, on=True):
         _check(lib().cc_set_graphs(self._ctx, 1 if on else 0), self._ctx)
 
@@ -360,6 +382,10 @@ class System:
     def sigma_dev(self, r, s):
         _check(lib().ipeom_sigma_dev(self._ctx, int(r.shape[0]), _P(r.data_ptr()),
                                      _P(s.data_ptr())), self._ctx)
+
+    def left_sigma_dev(self, l, s):
+        _check(lib().ipeom_left_sigma_dev(self._ctx, int(l.shape[0]), _P(l.data_ptr()),
+                                          _P(s.data_ptr())), self._ctx)
 
     def dump_integrals(self, block):
         o, v, _ = self.sizes()

@@ -261,6 +261,46 @@ int ipeom_solve(cc_ctx *ctx, int n_roots, double tol, int max_iter, double *omeg
   });
 }
 
+int ipeom_solve_lr(cc_ctx *ctx, int n_roots, double tol, int max_iter, double *omega,
+                   double *r_host, double *l_host, double *pole, int *n_iter) {
+  if (!ctx || !omega || n_roots < 1) return CC_ERR_ARG;
+  return guarded(ctx, [&] {
+    Ctx &c = ctx->c;
+    if (!c.ccsd_done) cdfns::fail(CC_ERR_STATE, "ipeom needs a converged ccsd_solve");
+    if (n_roots > c.dim_ip() || n_roots > 64) cdfns::fail(CC_ERR_ARG, "n_roots out of range");
+    const long dim = c.dim_ip();
+    const size_t bytes = sizeof(cdfns::cplx) * n_roots * dim;
+    cdfns::Buf R(&c.al, bytes), L(&c.al, bytes);
+    const int rc = c.ipeom_lr(n_roots, tol, max_iter, omega, R.c(), L.c(), n_iter);
+    if (r_host) CUDA_CHECK(cudaMemcpyAsync(r_host, R.p, bytes, cudaMemcpyDeviceToHost, c.st));
+    if (l_host) CUDA_CHECK(cudaMemcpyAsync(l_host, L.p, bytes, cudaMemcpyDeviceToHost, c.st));
+    if (pole) {
+      // sum_i l^i r_i over the 1h block, per root
+      std::vector<cdfns::cplx> r1(static_cast<size_t>(n_roots) * c.o), l1(r1.size());
+      CUDA_CHECK(cudaMemcpy2DAsync(r1.data(), sizeof(cdfns::cplx) * c.o, R.p,
+                                   sizeof(cdfns::cplx) * dim, sizeof(cdfns::cplx) * c.o, n_roots,
+                                   cudaMemcpyDeviceToHost, c.st));
+      CUDA_CHECK(cudaMemcpy2DAsync(l1.data(), sizeof(cdfns::cplx) * c.o, L.p,
+                                   sizeof(cdfns::cplx) * dim, sizeof(cdfns::cplx) * c.o, n_roots,
+                                   cudaMemcpyDeviceToHost, c.st));
+      CUDA_CHECK(cudaStreamSynchronize(c.st));
+      for (int k = 0; k < n_roots; ++k) {
+        double re = 0, im = 0;
+        for (int i = 0; i < c.o; ++i) {
+          const cdfns::cplx a = l1[static_cast<size_t>(k) * c.o + i];
+          const cdfns::cplx b = r1[static_cast<size_t>(k) * c.o + i];
+          re += a.x * b.x - a.y * b.y;
+          im += a.x * b.y + a.y * b.x;
+        }
+        pole[2 * k] = re;
+        pole[2 * k + 1] = im;
+      }
+    }
+    CUDA_CHECK(cudaStreamSynchronize(c.st));
+    return rc;
+  });
+}
+
 int cc_get_amplitudes(const cc_ctx *cctx, double *t1_host, double *t2_host) {
   cc_ctx *ctx = const_cast<cc_ctx *>(cctx);
   if (!ctx || !t1_host || !t2_host) return CC_ERR_ARG;
@@ -348,6 +388,20 @@ int ipeom_sigma_dev(cc_ctx *ctx, int n_vec, const double *r_dev, double *s_dev) 
     if (!c.ccsd_done && !c.amps) cdfns::fail(CC_ERR_STATE, "sigma needs amplitudes");
     if (!c.hbar_done) c.build_hbar();
     c.sigma(n_vec, reinterpret_cast<const cdfns::cplx *>(r_dev), reinterpret_cast<cdfns::cplx *>(s_dev));
+    CUDA_CHECK(cudaStreamSynchronize(c.st));
+    c.check_err_flag();
+    return CC_OK;
+  });
+}
+
+int ipeom_left_sigma_dev(cc_ctx *ctx, int n_vec, const double *l_dev, double *s_dev) {
+  if (!ctx || !l_dev || !s_dev || n_vec < 1) return CC_ERR_ARG;
+  return guarded(ctx, [&] {
+    Ctx &c = ctx->c;
+    if (!c.ccsd_done && !c.amps) cdfns::fail(CC_ERR_STATE, "sigma needs amplitudes");
+    if (!c.hbar_done) c.build_hbar();
+    c.left_sigma(n_vec, reinterpret_cast<const cdfns::cplx *>(l_dev),
+                 reinterpret_cast<cdfns::cplx *>(s_dev));
     CUDA_CHECK(cudaStreamSynchronize(c.st));
     c.check_err_flag();
     return CC_OK;

@@ -236,6 +236,65 @@ void batch_sigma(std::vector<Ctx *> &sys, const std::vector<int> &k,
 }
 
 // ---------------------------------------------------------------------------
+// left sigma (Eqs. 19-20)
+// ---------------------------------------------------------------------------
+namespace {
+
+// s = l^T H-bar_IP for kk packed left vectors, in the same layout as sigma's
+// vectors. Eq. 19 pairs left and right vectors bilinearly over the unique
+// elements, so this is the transpose of sigma_body's map: each of its terms
+// is read with input and output exchanged, into G[K][p][q][b] (which is not
+// antisymmetric in p, q); the packed result is G - G(p<->q), plus the
+// one-body diagonal, which the transposition leaves unchanged.
+void left_sigma_body(Ctx &c, int kk, const cplx *lin, cplx *sout) {
+  const int o = c.o, v = c.v, tr = c.eom();
+  const cudaStream_t st = c.st;
+  auto &w = c.sws;
+  auto L1 = [&](const char *ix) { return T(w.r1.c(), ix, {kk, o}); };
+  auto L2 = [&](const char *ix) { return T(w.r2.c(), ix, {kk, o, o, v}); };
+  auto G = [&](const char *ix) { return T(w.tA.c(), ix, {kk, o, o, v}); };
+  auto S1 = [&](const char *ix) { return T(w.s1.c(), ix, {kk, o}); };
+  auto S2 = [&](const char *ix) { return T(w.s2.c(), ix, {kk, o, o, v}); };
+  ip_unpack(lin, kk, o, v, w.r1.c(), w.r2.c(), st);
+  // 1h: -sum_i H_mi l_i - 1/2 sum_bij H_mbij l_ij^b
+  c.eng.contract(Cr(-1), L1("Ki"), T(c.Hoo_off.c(), "mi", {o, o}), C0(), S1("Km"), TIER_FP64);
+  c.eng.contract(Cr(-0.5), L2("Kijb"), stable(T(c.Hovoo.c(), "mbij", {o, v, o, o})), C1(), S1("Km"),
+                 tr);
+  // 2h1p, one line per term of the right sigma (H_me, H_mnie, H_be, H_mi,
+  // H_mnij, H_mbej, three-body), each with input and output exchanged
+  c.eng.contract(C1(), L1("Ki"), T(c.Hov.c(), "me", {o, v}), C0(), G("Kime"), TIER_FP64);
+  c.eng.contract(Cr(-0.5), L1("Ki"), stable(T(c.Hooov.c(), "mnie", {o, o, o, v})), C1(), G("Kmne"),
+                 tr);
+  c.eng.contract(Cr(0.5), L2("Kijb"), stable(T(c.Hvv_off.c(), "be", {v, v})), C1(), G("Kije"), tr);
+  c.eng.contract(Cr(-1), stable(T(c.Hoo_off.c(), "mi", {o, o})), L2("Kijb"), C1(), G("Kmjb"), tr);
+  c.eng.contract(Cr(0.25), L2("Kijb"), stable(T(c.Hoooo.c(), "mnij", {o, o, o, o})), C1(),
+                 G("Kmnb"), tr);
+  c.eng.contract(C1(), L2("Kijb"), stable(T(c.Hovvo.c(), "mbej", {o, v, v, o})), C1(), G("Kime"),
+                 tr);
+  c.eng.contract(Cr(0.5), L2("Kijb"), stable(T(c.t2.c(), "ijeb", {o, o, v, v})), C0(),
+                 T(w.xe.c(), "Ke", {kk, v}), tr);
+  c.eng.contract(Cr(-0.5), T(w.xe.c(), "Ke", {kk, v}), stable(T(c.oovv.c(), "mnef", {o, o, v, v})),
+                 C1(), G("Kmnf"), tr);
+  c.eng.permute_into(C1(), G("Kijb"), C0(), S2("Kijb"));
+  c.eng.permute_into(Cr(-1), G("Kjib"), C1(), S2("Kijb"));
+  ip_diag_apply(w.r1.c(), w.r2.c(), c.doo.c(), c.dvv.c(), kk, o, v, w.s1.c(), w.s2.c(), st);
+  ip_pack(w.s1.c(), w.s2.c(), kk, o, v, sout, st);
+}
+
+}  // namespace
+
+void batch_left_sigma(std::vector<Ctx *> &sys, const std::vector<int> &k,
+                      const std::vector<const cplx *> &r, const std::vector<cplx *> &s) {
+  for (size_t q = 0; q < sys.size(); ++q) {
+    Ctx &c = *sys[q];
+    if (!c.hbar_done) c.build_hbar();
+    if (k[q] == 0) continue;
+    ensure_ws(c, k[q]);
+    left_sigma_body(c, k[q], r[q], s[q]);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // block Davidson as a per-system state machine
 // ---------------------------------------------------------------------------
 namespace {
@@ -431,7 +490,8 @@ struct Dav {
 // Lockstep block Davidson over several systems (one batched sigma per round).
 // status[q] = CC_OK or CC_ERR_NOT_CONVERGED per system.
 void run_ipeom(std::vector<Ctx *> &sys, int nr, double tol, int max_iter, double *omega,
-               double *r1w, int *n_iter, int *status, bool use_graph) {
+               double *r1w, int *n_iter, int *status, bool use_graph, bool left,
+               const std::vector<cplx *> *vecs) {
   const double t0 = now_ms();
   for (Ctx *c : sys) {
     if (!c->ccsd_done) fail(CC_ERR_STATE, "ipeom needs a converged ccsd_solve");
@@ -453,7 +513,10 @@ void run_ipeom(std::vector<Ctx *> &sys, int nr, double tol, int max_iter, double
       ss.push_back(d.S.c() + d.req_off * d.dim);
     }
     if (act.empty()) break;
-    batch_sigma(act, ks, rs, ss, use_graph);
+    if (left)
+      batch_left_sigma(act, ks, rs, ss);
+    else
+      batch_sigma(act, ks, rs, ss, use_graph);
     for (auto &d : dv)
       if (!d.done) d.step();
   }
@@ -461,6 +524,7 @@ void run_ipeom(std::vector<Ctx *> &sys, int nr, double tol, int max_iter, double
     dv[q].results(omega + 2L * nr * q, r1w ? r1w + static_cast<long>(nr) * q : nullptr);
     if (n_iter) n_iter[q] = dv[q].it;
     if (status) status[q] = dv[q].converged ? CC_OK : CC_ERR_NOT_CONVERGED;
+    if (vecs) d2d((*vecs)[q], dv[q].Xr.p, sizeof(cplx) * nr * dv[q].dim, dv[q].st());
     sys[q]->stat[8] = dv[q].it;
     sys[q]->check_err_flag();
   }

@@ -1022,6 +1022,93 @@ void Ctx::sigma(int k, const cplx *r, cplx *s) {
   batch_sigma(one, {k}, {r}, {s}, false);
 }
 
+void Ctx::left_sigma(int k, const cplx *l, cplx *s) {
+  std::vector<Ctx *> one{this};
+  batch_left_sigma(one, {k}, {l}, {s});
+}
+
+namespace {
+
+// In-place inverse of a small complex matrix (Gauss-Jordan, partial
+// pivoting); false when a pivot vanishes.
+bool invert_small(std::vector<cplx> &a, int n) {
+  std::vector<cplx> inv(static_cast<size_t>(n) * n, mk(0, 0));
+  for (int i = 0; i < n; ++i) inv[i * n + i] = mk(1, 0);
+  double scale = 0;
+  for (const cplx &x : a) scale = std::max(scale, std::hypot(x.x, x.y));
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    double best = 0;
+    for (int r = col; r < n; ++r) {
+      const double m = std::hypot(a[r * n + col].x, a[r * n + col].y);
+      if (m > best) {
+        best = m;
+        piv = r;
+      }
+    }
+    if (!(best > 1e-12 * scale)) return false;
+    if (piv != col)
+      for (int j = 0; j < n; ++j) {
+        std::swap(a[piv * n + j], a[col * n + j]);
+        std::swap(inv[piv * n + j], inv[col * n + j]);
+      }
+    const cplx p = a[col * n + col];
+    const double d = p.x * p.x + p.y * p.y;
+    const cplx pinv = mk(p.x / d, -p.y / d);
+    for (int j = 0; j < n; ++j) {
+      a[col * n + j] = cmul(pinv, a[col * n + j]);
+      inv[col * n + j] = cmul(pinv, inv[col * n + j]);
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      const cplx f = a[r * n + col];
+      for (int j = 0; j < n; ++j) {
+        a[r * n + j] = csub(a[r * n + j], cmul(f, a[col * n + j]));
+        inv[r * n + j] = csub(inv[r * n + j], cmul(f, inv[col * n + j]));
+      }
+    }
+  }
+  a = inv;
+  return true;
+}
+
+}  // namespace
+
+// Right vectors by the block Davidson of Eq. 18, left vectors (Eq. 20) by
+// the same Davidson on the transposed sigma, then L <- (L^T R)^-1 L so that
+// the pairs are biorthonormal over the nr roots (Eq. 19); this also
+// separates degenerate roots and any difference in the order of ties.
+int Ctx::ipeom_lr(int nr, double tol, int max_iter, double *omega, cplx *R_dev, cplx *L_dev,
+                  int *n_iter) {
+  if (!(tol > 0) || max_iter < 1) fail(CC_ERR_ARG, "tol must be > 0 and max_iter >= 1");
+  std::vector<Ctx *> one{this};
+  const long dim = dim_ip();
+  int st_r = CC_OK, st_l = CC_OK, it_r = 0, it_l = 0;
+  std::vector<double> wl(2 * static_cast<size_t>(nr));
+  Buf Lraw(&al, sizeof(cplx) * nr * dim);
+  const std::vector<cplx *> pr{R_dev}, pl{Lraw.c()};
+  run_ipeom(one, nr, tol, max_iter, omega, nullptr, &it_r, &st_r, use_graphs, false, &pr);
+  run_ipeom(one, nr, tol, max_iter, wl.data(), nullptr, &it_l, &st_l, false, true, &pl);
+  if (n_iter) {
+    n_iter[0] = it_r;
+    n_iter[1] = it_l;
+  }
+  // S[k][l] = l_k . r_l (bilinear), A = S^-1, L = A Lraw
+  Buf S(&al, sizeof(cplx) * nr * nr);
+  eng.contract(C1(), T(Lraw.c(), "kd", {nr, dim}), T(R_dev, "ld", {nr, dim}), C0(),
+               T(S.c(), "kl", {nr, nr}), TIER_FP64);
+  std::vector<cplx> a(static_cast<size_t>(nr) * nr);
+  d2h(a.data(), S.p, sizeof(cplx) * nr * nr, st);
+  if (!invert_small(a, nr))
+    fail(CC_ERR_NUMERIC, "left and right IP vectors cannot be made biorthonormal");
+  h2d(S.p, a.data(), sizeof(cplx) * nr * nr, st);
+  eng.contract(C1(), T(S.c(), "kj", {nr, nr}), T(Lraw.c(), "jd", {nr, dim}), C0(),
+               T(L_dev, "kd", {nr, dim}), TIER_FP64);
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  check_err_flag();
+  return (st_r == CC_OK && st_l == CC_OK) ? CC_OK : CC_ERR_NOT_CONVERGED;
+}
+
 int Ctx::ipeom(int nr, double tol, int max_iter, double *omega, double *r1w, int *n_iter) {
   if (!(tol > 0) || max_iter < 1) fail(CC_ERR_ARG, "tol must be > 0 and max_iter >= 1");
   std::vector<Ctx *> one{this};

@@ -73,11 +73,15 @@ struct Ctx {
   int fns(double threshold, int n_keep);
   int ccsd(double tol, int max_iter, double *e_out, int *n_iter);
   int ipeom(int n_roots, double tol, int max_iter, double *omega, double *r1w, int *n_iter);
+  // right and left vectors (Eqs. 18-20), biorthonormal: L^T R = 1
+  int ipeom_lr(int n_roots, double tol, int max_iter, double *omega, cplx *R_dev, cplx *L_dev,
+               int *n_iter);
   // --- components ---
   void residual(const cplx *t1, const cplx *t2, cplx *R1, cplx *R2);
   void ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tier);
   void build_hbar();
   void sigma(int k, const cplx *r, cplx *s);
+  void left_sigma(int k, const cplx *l, cplx *s);
   cplx energy(const cplx *t1, const cplx *t2);
   void check_err_flag();
   void ensure_pairs();
@@ -108,8 +112,14 @@ struct Ctx {
 // eom.cu: batched sigma, lockstep block Davidson, graph cache
 void batch_sigma(std::vector<Ctx *> &sys, const std::vector<int> &k,
                  const std::vector<const cplx *> &r, const std::vector<cplx *> &s, bool use_graph);
+// Lockstep block Davidson; `left` solves l^T H-bar = omega l^T instead
+// (transposed sigma, no graphs); `vecs` (device, per system) receives the
+// nr Ritz vectors [nr][dim] when given.
 void run_ipeom(std::vector<Ctx *> &sys, int nr, double tol, int max_iter, double *omega,
-               double *r1w, int *n_iter, int *status, bool use_graph);
+               double *r1w, int *n_iter, int *status, bool use_graph, bool left = false,
+               const std::vector<cplx *> *vecs = nullptr);
+void batch_left_sigma(std::vector<Ctx *> &sys, const std::vector<int> &k,
+                      const std::vector<const cplx *> &r, const std::vector<cplx *> &s);
 void drop_graphs(const void *ctx);
 void geev_dev(Allocator *al, cudaStream_t st, cplx *A, int m, cplx *w, cplx *vr);
 
