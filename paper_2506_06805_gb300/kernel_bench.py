@@ -24,7 +24,9 @@ and compares the roots.
 chunks of 200, CCSD, IP-EOM with all roots in one block) on the library's
 own cudaMalloc allocations, and reports the phase times, iteration counts,
 the ladder rate, the DIIS depth the device memory allowed and the high-water
-mark of the library's device memory.
+mark of the library's device memory; with --left it then solves for the
+right and left vectors together (ipeom_solve_lr) and reports their
+biorthonormality and 1h overlaps.
 One JSON line per run.
 """
 from __future__ import annotations
@@ -55,6 +57,8 @@ def main():
     p.add_argument("--eom-tier", default="fp16x3")
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=1)
+    p.add_argument("--left", action="store_true",
+                   help="solve: left vectors too (ipeom_solve_lr)")
     a = p.parse_args()
     if a.what == "solve":
         return solve_run(a)
@@ -183,6 +187,15 @@ def solve_run(a):
         w, r1 = s.ipeom(nr, tol=c.eom_tol, max_iter=100)
         t3 = time.perf_counter()
         st = s.stats()
+        if a.left:
+            # right and left vectors again from the same H-bar (built above)
+            t4 = time.perf_counter()
+            wl, R, Lv, pole = s.ipeom_lr(nr, tol=c.eom_tol, max_iter=100)
+            out["ipeom_lr_s"] = time.perf_counter() - t4
+            out["davidson_iter_right_left"] = list(s.davidson_iterations)
+            out["biorth_err"] = float(np.abs(Lv @ R.T - np.eye(nr)).max())
+            out["max_dIP_lr_vs_right"] = float(np.abs(np.sort_complex(wl) - np.sort_complex(w)).max())
+            out["pole"] = [[p.real, p.imag] for p in pole]
     order = np.argsort(w.real)
     out.update({
         "input_s": t1 - t0, "ccsd_s": t2 - t1, "ipeom_s": t3 - t2,
