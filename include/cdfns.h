@@ -256,6 +256,25 @@ int cc_zgemm_dev(int tier, long M, long N, long K, const double *A_dev,
                  const double *B_dev, double *C_dev);
 
 /*
+ * cc_cholesky_dev: single-step pivoted Cholesky decomposition (Eq. 21) of
+ * the Hermitian positive semidefinite matrix M = B B^H (N x N), which stands
+ * for the two-electron integral matrix over orbital pairs; its generator B
+ * (device complex128 [N][r], row-major) supplies columns on demand,
+ * column p = B conj(B[p]). Step k takes the largest remaining diagonal
+ * element d_p and stops when d_p < tau (or after max_vec vectors); otherwise
+ * l_k = (M[:,p] - sum_{j<k} l_j conj(l_j[p])) / sqrt(d_p) and d -= |l_k|^2.
+ * Every element of M - sum_k l_k l_k^H is then below tau in magnitude.
+ * L_dev        device complex128 [max_vec][N]: rows 0..n_vec-1 receive l_k.
+ * pivots_host  host long[max_vec] (may be NULL): the pivots p in order.
+ * n_vec        host int: vectors formed.
+ * FP64 throughout, on the default stream, O(N max_vec) device scratch from
+ * the default allocator. Errors: CC_ERR_ARG, CC_ERR_NUMERIC (non-finite
+ * diagonal).
+ */
+int cc_cholesky_dev(long N, int r, const double *B_dev, double tau,
+                    int max_vec, double *L_dev, long *pivots_host, int *n_vec);
+
+/*
  * cc_zgemm_noalloc: the same complex GEMM as cc_zgemm_dev, for callers that
  * must not allocate device memory: code running while a stream is being
  * captured into a CUDA graph, frameworks that own all device memory through

@@ -13,9 +13,10 @@ Modules (each function cites the passage of the paper it follows):
 * ``mp2``       -- first-order doubles and the MP2 energy.
 * ``fns``       -- frozen natural spinors (Eqs. 24-28).
 * ``ccsd``      -- spin-orbital CCSD with DIIS (Eqs. 12-15).
-* ``ipeom``     -- IP-EOM-CCSD sigma, dense H-bar and its eigenvalues
-                   (Eqs. 16-18).
+* ``ipeom``     -- IP-EOM-CCSD sigma, dense H-bar, its eigenvalues and
+                   left vectors (Eqs. 16-20).
 * ``davidson``  -- a plain non-Hermitian Davidson for larger sizes.
+* ``cholesky``  -- single-step pivoted Cholesky decomposition (Eq. 21).
 * ``fci``       -- brute-force second quantisation on determinant
                    bitstrings, used to pin the working equations.
 

@@ -64,6 +64,8 @@ _SIGS = {
     "cc_residual_dev": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "ipeom_sigma_dev": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "ipeom_left_sigma_dev": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "cc_cholesky_dev": (ctypes.c_int, [ctypes.c_long, ctypes.c_int, _P, ctypes.c_double,
+                                       ctypes.c_int, _P, ctypes.POINTER(ctypes.c_long), _I]),
     "ipeom_solve_lr": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                       _D, _D, _D, _D, _I]),
     "cc_dump_integrals": (ctypes.c_int, [_P, ctypes.c_int, _D]),
@@ -203,6 +205,22 @@ def selftest_conversions(x):
     out = (ctypes.c_longlong * 2)()
     _check(lib().cc_selftest_conversions(_P(x.data_ptr()), x.numel(), out))
     return int(out[0]), int(out[1])
+
+
+def cholesky_dev(B, tau, max_vec):
+    """Single-step pivoted Cholesky vectors (Eq. 21) of M = B B^H for a
+    device complex128 tensor B [N][r]. Returns (L [n][N] on the device,
+    pivots [n])."""
+    import torch
+    N, r = B.shape
+    L = torch.empty((max_vec, N), dtype=torch.complex128, device=B.device)
+    piv = np.zeros(max_vec, dtype=np.int64)
+    n = ctypes.c_int()
+    _check(lib().cc_cholesky_dev(N, r, _P(B.data_ptr()), float(tau), int(max_vec),
+                                 _P(L.data_ptr()),
+                                 piv.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                                 ctypes.byref(n)))
+    return L[:n.value], piv[:n.value]
 
 
 def zgemm_noalloc(A, B, C, tier="fp64"):

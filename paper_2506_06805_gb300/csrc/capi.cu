@@ -435,6 +435,21 @@ int cc_zgemm_dev(int tier, long M, long N, long K, const double *A, const double
   });
 }
 
+int cc_cholesky_dev(long N, int r, const double *B_dev, double tau, int max_vec, double *L_dev,
+                    long *pivots_host, int *n_vec) {
+  if (N < 1 || r < 1 || max_vec < 1 || !B_dev || !L_dev || !n_vec || !(tau >= 0.0))
+    return CC_ERR_ARG;
+  return guarded(nullptr, [&] {
+    int dev = 0, sms = 0;
+    CUDA_CHECK(cudaGetDevice(&dev));
+    CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    *n_vec = cdfns::pivoted_cholesky(reinterpret_cast<const cdfns::cplx *>(B_dev), N, r, tau,
+                                     max_vec, reinterpret_cast<cdfns::cplx *>(L_dev), pivots_host,
+                                     &cdfns::g_default_alloc, cdfns::g_default_stream, sms);
+    return CC_OK;
+  });
+}
+
 int cc_selftest_conversions(const double *x_dev, long n, long long *mismatches) {
   if (!x_dev || n < 0 || !mismatches) return CC_ERR_ARG;
   return guarded(nullptr, [&] {

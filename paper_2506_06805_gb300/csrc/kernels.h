@@ -154,4 +154,10 @@ void dot_multi(const cplx *const *xs, int m, const cplx *y, long n, bool f32, cp
 void dot_dev(const cplx *x, const cplx *y, long n, bool conj_x, cplx *res,
              cudaStream_t st, cplx *dev_scratch);
 
+// Single-step pivoted Cholesky decomposition (Eq. 21) of M = B B^H, B
+// [N][r] on the device: vectors L [n][N] (n <= max_vec, row-major), pivots
+// piv[n] on the host (may be NULL); returns n.
+int pivoted_cholesky(const cplx *B, long N, int r, double tau, int max_vec, cplx *L, long *piv,
+                     Allocator *al, cudaStream_t st, int num_sms);
+
 }  // namespace cdfns

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from paper_2506_06805_gb300 import synth
-from oracle import ccsd, davidson, fci, fns, integrals, ipeom, mp2
+from oracle import ccsd, cholesky, davidson, fci, fns, integrals, ipeom, mp2
 
 
 def _system(o, v, X, seed=1, scale=1.0, kramers=False):
@@ -360,6 +360,60 @@ def test_fns_truncation_keeps_largest_occupations():
     e_fns = ccsd.solve(integrals.blocks_from_cholesky(Lr, o), out["eps"],
                        tol=1e-10)["e_corr"].real
     assert 0.5 * e_full > e_fns > 1.05 * e_full or e_full < e_fns < 0
+
+
+# --- pivoted Cholesky (Eq. 21) -----------------------------------------------------
+
+def _generator(N, r, seed):
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal((N, r)) + 1j * rng.standard_normal((N, r))) / np.sqrt(2 * r)
+
+
+def test_cholesky_error_bound_and_rank():
+    """The remainder is PSD with diagonal below tau, so no element of
+    M - L^T conj(L) exceeds tau; at a tau far below the spectrum the count
+    equals the rank of M and M is recovered to rounding."""
+    N, r = 60, 25
+    B = _generator(N, r, 2)
+    M = B @ B.conj().T
+    prev = 0
+    for tau in (1e-1, 1e-2, 1e-5):
+        L, piv = cholesky.pivoted_cholesky(B, tau)
+        E = M - L.T @ L.conj()
+        assert np.abs(E).max() < tau
+        assert len(piv) == len(set(piv.tolist())) and len(piv) >= prev
+        prev = len(piv)
+    L, _ = cholesky.pivoted_cholesky(B, 1e-12)
+    assert L.shape[0] == r
+    assert np.abs(M - L.T @ L.conj()).max() < 1e-12
+
+
+def test_cholesky_full_rank_equals_lapack():
+    """Full rank with tau = 0: in pivot order the vectors are the lower
+    triangular Cholesky factor of the permuted matrix (LAPACK's, unique with
+    a positive diagonal)."""
+    N = 30
+    B = _generator(N, 50, 3)
+    M = B @ B.conj().T
+    L, piv = cholesky.pivoted_cholesky(B, 0.0, max_vec=N)
+    assert sorted(piv.tolist()) == list(range(N))
+    C = np.linalg.cholesky(M[np.ix_(piv, piv)])
+    assert np.abs(L[:, piv].T - C).max() < 1e-12
+
+
+def test_cholesky_recovers_coulomb_integrals():
+    """Generator B[(pq), P] = L^P_pq from Hermitian Cholesky vectors: the
+    new vectors reproduce (pr|qs) = sum_P L^P_pr L^P_qs (Eq. 21 in the
+    pair-matrix form M[(pr), (sq)] = (pr|qs)) and their count is X."""
+    n, X = 7, 12
+    L_in = synth.make_cholesky(np.random.default_rng(4), n, X)
+    B = L_in.reshape(X, n * n).T.copy()
+    Lc, _ = cholesky.pivoted_cholesky(B, 1e-13)
+    assert Lc.shape[0] == X
+    eri = np.einsum("Ppr,Pqs->prqs", L_in, L_in)
+    Mc = Lc.T @ Lc.conj()  # [(pr), (sq)]
+    eri_c = Mc.reshape(n, n, n, n).transpose(0, 1, 3, 2)  # (pr|qs) at [p][r][q][s]
+    assert np.abs(eri_c - eri).max() < 1e-12
 
 
 # --- Davidson -------------------------------------------------------------------
