@@ -27,6 +27,9 @@ the ladder rate, the DIIS depth the device memory allowed and the high-water
 mark of the library's device memory; with --left it then solves for the
 right and left vectors together (ipeom_solve_lr) and reports their
 biorthonormality and 1h overlaps.
+``cholesky`` times the single-step pivoted Cholesky decomposition (Eq. 21)
+of M = B B^H for a seeded generator B [N][r] and reports the HBM rate on its
+algorithmic bytes.
 One JSON line per run.
 """
 from __future__ import annotations
@@ -42,7 +45,11 @@ def main():
 
     from . import System, synth, use_torch_memory, zgemm_dev
     p = argparse.ArgumentParser()
-    p.add_argument("what", choices=["ladder", "gemm", "fns", "batch", "solve"])
+    p.add_argument("what", choices=["ladder", "gemm", "fns", "batch", "solve", "cholesky"])
+    p.add_argument("--pairs", type=int, default=435600, help="cholesky: N (orbital pairs)")
+    p.add_argument("--rank", type=int, default=600, help="cholesky: columns of the generator")
+    p.add_argument("--tau", type=float, default=0.0, help="cholesky: threshold")
+    p.add_argument("--max-vec", type=int, default=600, help="cholesky: vector limit")
     p.add_argument("--n-sys", type=int, default=8)
     p.add_argument("--roots", type=int, default=8)
     p.add_argument("--config", default="fns")
@@ -69,6 +76,8 @@ def main():
         return fns_run(a)
     if a.what == "batch":
         return batch_run(a)
+    if a.what == "cholesky":
+        return cholesky_run(a)
     if a.what == "ladder":
         eps, L = synth.make_system(a.o, a.v, a.X, seed=0, kramers=False)
         rng = np.random.default_rng(1)
@@ -162,6 +171,36 @@ def fns_run(a):
     out[f"max_dIP_{t0}_vs_{t1}"] = float(np.abs(np.array(res[t0]["ips"])
                                                - np.array(res[t1]["ips"])).max())
     print(json.dumps(out))
+
+
+def cholesky_run(a):
+    """Times cc_cholesky_dev on a seeded generator B [N][r] (the oracle's
+    test recipe) and reports HBM throughput on the algorithmic bytes: each
+    step k reads B and the k vectors so far, 16 N (r + k) bytes."""
+    import torch
+
+    from . import cholesky_dev
+    N, r = a.pairs, a.rank
+    rng = np.random.default_rng(0)
+    B = torch.empty((N, r), dtype=torch.complex128, device="cuda")
+    for q0 in range(0, N, 65536):  # generate in slices to bound host memory
+        q1 = min(N, q0 + 65536)
+        x = (rng.standard_normal((q1 - q0, r)) + 1j * rng.standard_normal((q1 - q0, r)))
+        B[q0:q1] = torch.from_numpy(x / np.sqrt(2 * r))
+    cholesky_dev(B[:4096].contiguous(), a.tau, 4)  # warm-up (module load)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    L, piv = cholesky_dev(B, a.tau, a.max_vec)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    n = L.shape[0]
+    byts = 16.0 * N * (n * r + n * (n - 1) / 2)
+    print(json.dumps({"kernel": "pivoted_cholesky", "N": N, "r": r, "tau": a.tau, "n_vec": n,
+                      "ms": ms, "ms_per_vector": ms / max(1, n),
+                      "algorithmic_GB": byts / 1e9, "GBps": byts / ms / 1e6}))
 
 
 def solve_run(a):

@@ -33,6 +33,9 @@ def test_null_arguments_rejected_without_device():
     assert L.cc_set_precision(None, 0) == -1
     assert L.cc_dump_integrals(None, 9, None) == -1
     assert L.cc_set_memory_limit(None, ctypes.c_size_t(1 << 30)) == -1
+    assert L.cc_cholesky_dev(0, 1, None, 1e-6, 1, None, None, None) == -1
+    assert L.ipeom_solve_lr(None, 1, 1e-7, 10, None, None, None, None, None) == -1
+    assert L.ipeom_left_sigma_dev(None, 1, None, None) == -1
 
 
 def test_allocator_pair_must_be_complete():
