@@ -96,7 +96,10 @@ int cc_init_chunked(int n_occ, int n_virt, int n_aux, const double *eps,
                     cc_ctx **out);
 int cc_add_cholesky(cc_ctx *ctx, int p0, int p1, const double *L_chunk);
 
-int cc_set_precision(cc_ctx *ctx, int tier); /* CC_TIER_*; default FP64 */
+/* Tier of the CCSD contractions and of the H-bar build (CC_TIER_*; default
+ * FP64). Set after ccsd_solve, it also replaces the tier that ccsd_solve
+ * finished in for the next H-bar build. */
+int cc_set_precision(cc_ctx *ctx, int tier);
 /* Tier of the IP-EOM sigma contractions (-1: same as cc_set_precision).
  * The one-body parts of sigma always run in FP64. */
 int cc_set_precision_eom(cc_ctx *ctx, int tier);

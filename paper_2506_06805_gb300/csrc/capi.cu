@@ -193,6 +193,7 @@ int cc_set_precision(cc_ctx *ctx, int tier) {
   if (tier < CC_TIER_FP64 || tier > CC_TIER_FP16X3) return CC_ERR_ARG;
   ctx->c.tier = tier;
   ctx->c.hbar_done = false;
+  ctx->c.cc_done_tier = -1;  // an explicit choice also sets H-bar's tier
   return CC_OK;
 }
 
