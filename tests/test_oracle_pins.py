@@ -430,6 +430,16 @@ def test_davidson_matches_dense():
         tol=1e-9)
     assert conv
     assert np.abs(w - w_dense).max() <= 1e-9
+    # the same Davidson on the transposed sigma: the left problem has the
+    # same eigenvalues, and its vectors are left eigenvectors of the matrix
+    wl, Xl, _, conv = davidson.davidson(
+        lambda x: ipeom.left_sigma(H, x, o, v), ipeom.diagonal(H, o, v), 6,
+        tol=1e-9)
+    assert conv
+    assert np.abs(wl - w_dense).max() <= 1e-9
+    M = ipeom.dense_matrix(H, o, v)
+    for k in range(6):
+        assert np.linalg.norm(Xl[:, k] @ M - wl[k] * Xl[:, k]) <= 1e-8
 
 
 # --- warm-start network (oracle side) ------------------------------------------
