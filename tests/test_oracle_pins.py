@@ -129,6 +129,21 @@ def test_ladder_term_alone_equals_bruteforce():
     assert np.abs(lad).max() > 1e-3
 
 
+def test_diis_does_not_move_the_fixed_point():
+    """DIIS (from iteration 2 or 3, any depth) only accelerates: the
+    converged amplitudes solve the same equations as plain Jacobi."""
+    o, v, X = 4, 9, 20
+    eps, L = _system(o, v, X, seed=8, scale=4.0)
+    g = integrals.blocks_from_cholesky(L, o)
+    plain = ccsd.solve(g, eps, tol=1e-12, max_iter=500, diis_start=10 ** 9)
+    assert plain["converged"]
+    for size, start in ((8, 2), (8, 3), (3, 2)):
+        res = ccsd.solve(g, eps, tol=1e-12, max_iter=200, diis_size=size, diis_start=start)
+        assert res["converged"] and res["n_iter"] <= plain["n_iter"]
+        assert abs(res["e_corr"] - plain["e_corr"]) < 1e-11
+        assert np.abs(res["t2"] - plain["t2"]).max() < 1e-10
+
+
 def test_ccsd_two_electrons_is_fci():
     """n_occ = 2: CCSD is exact; 1h + 2h1p spans the whole one-electron
     sector, so the IP-EOM roots are FCI(N-1) - FCI(N)."""
