@@ -908,7 +908,6 @@ void Ctx::build_hbar() {
   auto t2t = [&](const char *ix) { return T(t2.c(), ix, {o, o, v, v}); };
   auto g_oovv = [&](const char *ix) { return T(oovv.c(), ix, {o, o, v, v}); };
   auto g_ooov = [&](const char *ix) { return T(ooov.c(), ix, {o, o, o, v}); };
-  auto g_ovvo = [&](const char *ix) { return T(ovvo.c(), ix, {o, v, v, o}); };
   auto Lov_ = [&](const char *ix) { return T(Lov.c(), ix, {X, o, v}); };
   auto Lvv_ = [&](const char *ix) { return T(Lvv.c(), ix, {X, v, v}); };
   const std::initializer_list<long> d4 = {o, o, o, o};
