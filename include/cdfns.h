@@ -279,22 +279,28 @@ int cc_cholesky_dev(long N, int r, const double *B_dev, double tau,
 
 /*
  * cc_zgemm_noalloc: the same complex GEMM as cc_zgemm_dev, for callers that
- * must not allocate device memory: code running while a stream is being
- * captured into a CUDA graph, frameworks that own all device memory through
- * their own pool, and loops where a cudaMalloc would stall the device. (The
- * paper has no counterpart; this is a property of the library interface.)
+ * cannot let the library allocate device memory: host frameworks that
+ * reserve nearly all device memory for their own pool (an outside cudaMalloc
+ * fails there, or takes memory the framework has promised elsewhere),
+ * applications whose device-memory budget is fixed and audited at start-up,
+ * and latency-critical loops where cudaMalloc / cudaFree would synchronise
+ * the device. (The paper has no counterpart; this is a property of the
+ * library interface.)
  *   C[m][n] = sum_k A[m][k] * B[n][k]   (complex128, row-major, C overwritten)
+ * A_dev, B_dev, C_dev are device buffers owned by the caller.
  * Temporaries live in one fixed 64 MiB array in device global memory that
- * every GPU loading the library holds until exit; nothing is allocated and
- * no allocating library routine is called. The tensor-core tiers need
+ * every GPU loading the library holds until exit; nothing is allocated, no
+ * allocating library routine is called, and the tile autotuner
+ * (CDFNS_AUTOTUNE) is never run for these calls (cached choices only). The
+ * tensor-core tiers need
  * 256 + s (round256(2 M Kp e) + round256(N Kp e)) bytes of it, with
  * Kp = 2K rounded up to 32 (tf32) or 64 (bf16) elements, e = 4 (tf32) or
  * 2 (bf16) bytes and s = 1 (CC_TIER_TF32) or 2 (split tiers); larger
- * problems are rejected with CC_ERR_ARG and a message. CC_TIER_FP16 (whose
- * operand scales need device scratch of their own) is rejected with
- * CC_ERR_ARG. CC_TIER_FP64 uses
- * no temporaries. Work runs on the default stream (cc_set_default_stream)
- * and the call returns after it completes.
+ * problems, and sizes whose byte counts overflow, are rejected with
+ * CC_ERR_ARG and a message. CC_TIER_FP16 and CC_TIER_FP16X3 (whose operand
+ * scales need device scratch of their own) are rejected with CC_ERR_ARG.
+ * CC_TIER_FP64 uses no temporaries. Work runs on the default stream
+ * (cc_set_default_stream) and the call returns after it completes.
  * The first call on each device looks up the array's device address with
  * that device current; make that first call before any stream capture.
  * All calls share the array and it keeps the last call's contents: calls

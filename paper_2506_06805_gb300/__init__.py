@@ -225,8 +225,9 @@ def cholesky_dev(B, tau, max_vec):
 
 def zgemm_noalloc(A, B, C, tier="fp64"):
     """Same product as zgemm_dev with every temporary in the library's fixed
-    device scratch array: no device allocation (for callers that cannot
-    allocate, e.g. during stream capture). Calls must not overlap."""
+    device scratch array: no device allocation, for callers whose device
+    memory is owned by a framework pool or fixed at start-up. Calls share
+    the array and must not overlap on the GPU."""
     t = TIERS[tier] if isinstance(tier, str) else int(tier)
     M, K = A.shape
     N = B.shape[0]

@@ -18,10 +18,7 @@
 //
 // CTA layout (320 threads): warps 0-7 epilogue, warp 8 TMA producer, warp 9
 // TMEM allocator + MMA issuer; persistent CTAs walk a list of 128 x BN output
-// tiles (of up to 16 problems per launch), K optionally split. With
-// CDFNS_CTA_PAIR=1 the wide (BN = 256) kernels run as clusters of two CTAs
-// on vertically adjacent tiles that share their B tile, each CTA loading
-// half of it and multicasting it to both (off by default: no gain measured).
+// tiles (of up to 16 problems per launch), K optionally split.
 // Every mbarrier wait is bounded in time; on expiry the kernel records an
 // error flag, drains, frees TMEM and returns.
 #include <cuda.h>
@@ -91,35 +88,6 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
       : "memory");
 }
-// Same load, written to the same shared-memory offset of every CTA in
-// ctaMask, each of whose mbarrier (same offset) receives the byte count.
-__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map, uint64_t *bar,
-                                               int x, int y, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      ".multicast::cluster [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_id_x() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_count_x() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" :::
-                   "memory");
-}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -172,15 +140,6 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(bar))
-      : "memory");
-}
-// Arrive on the mbarrier at this offset in every CTA of ctaMask once the
-// MMAs issued so far have completed.
-__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-      " [%0], %1;" ::"r"(smem_u32(bar)),
-      "h"(mask)
       : "memory");
 }
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
@@ -262,10 +221,9 @@ __device__ __forceinline__ void tile_coords(const TcProblem &a, int t, int &m, i
 // independently of K. Chunk and stage counters run on across tiles, so the
 // MMA of the next tile overlaps the epilogue stores of the previous one.
 // ET: operand type, 0 tf32 (kind::tf32), 1 bf16 / 2 fp16 (kind::f16)
-template <int BN, int STAGES, bool SPLIT, int ET, int CL>
+template <int BN, int STAGES, bool SPLIT, int ET>
 __global__ void __launch_bounds__(320, 1)
     tc_gemm_kernel(const __grid_constant__ TcGroup grp) {
-  static_assert(CL == 1 || CL == 2, "cluster of one or two CTAs");
   constexpr int A_BYTES = BM * ROW_BYTES;
   constexpr int B_BYTES = BN * ROW_BYTES;
   constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * (SPLIT ? 2 : 1);
@@ -288,21 +246,14 @@ __global__ void __launch_bounds__(320, 1)
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int n_tiles_total = grp.total_tiles;  // work units (tile pairs when CL == 2)
+  const int n_tiles_total = grp.total_tiles;
   const int chunk = grp.chunk;
-  // cluster rank and the unit walk are re-read from special registers at
-  // each use (asm volatile) rather than held live through the loops, to keep
-  // the epilogue warps within their register budget
-#define TC_RANK (CL == 2 ? static_cast<int>(cluster_rank()) : 0)
-#define TC_UNIT0 (CL == 2 ? static_cast<int>(cluster_id_x()) : static_cast<int>(blockIdx.x))
-#define TC_USTEP (CL == 2 ? static_cast<int>(cluster_count_x()) : static_cast<int>(gridDim.x))
-  constexpr int HALF_B = (BN / 2) * ROW_BYTES;  // bytes of one multicast half of B
   int *const err = grp.err;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], CL);  // released by the MMA warp of every CTA reading it
+      mbar_init(&empty[s], 1);  // released by the MMA warp's commit
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -314,7 +265,6 @@ __global__ void __launch_bounds__(320, 1)
   if (warp == 9) tmem_alloc(tmem_slot, TMEM_COLS);
   tc_fence_before();
   __syncthreads();
-  if constexpr (CL == 2) cluster_sync_all();  // peer barriers initialised before any multicast
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -323,11 +273,10 @@ __global__ void __launch_bounds__(320, 1)
       // ---------------- TMA producer ----------------
       long it = 0;  // k blocks issued so far (all tiles)
       bool ok = true;
-      for (int t = TC_UNIT0; t < n_tiles_total && ok; t += TC_USTEP) {
+      for (int t = blockIdx.x; t < n_tiles_total && ok; t += gridDim.x) {
         const TcProblem &P = grp.p[find_problem(grp, t)];
         int m_tile, n_tile, z;
         tile_coords(P, t - P.tile_start, m_tile, n_tile, z);
-        m_tile = m_tile * CL + TC_RANK;
         const int kb0 = z * P.kb_per_split;
         const int kb1 = min(P.num_kb, kb0 + P.kb_per_split);
         for (int kb = kb0; kb < kb1; ++kb, ++it) {
@@ -342,22 +291,10 @@ __global__ void __launch_bounds__(320, 1)
           mbar_expect_tx(&full[s], STAGE_BYTES);
           const int kx = kb * K_ELEMS;
           tma_load_2d(st, &P.mA, &full[s], kx, m_tile * BM);
-          if constexpr (CL == 2) {
-            const int rk = TC_RANK;
-            tma_load_2d_mc(st + A_BYTES + rk * HALF_B, &P.mB, &full[s], kx,
-                           n_tile * BN + rk * (BN / 2), 0x3);
-          } else {
-            tma_load_2d(st + A_BYTES, &P.mB, &full[s], kx, n_tile * BN);
-          }
+          tma_load_2d(st + A_BYTES, &P.mB, &full[s], kx, n_tile * BN);
           if constexpr (SPLIT) {
             tma_load_2d(st + A_BYTES + B_BYTES, &P.mAlo, &full[s], kx, m_tile * BM);
-            if constexpr (CL == 2) {
-              const int rk = TC_RANK;
-              tma_load_2d_mc(st + 2 * A_BYTES + B_BYTES + rk * HALF_B, &P.mBlo, &full[s], kx,
-                             n_tile * BN + rk * (BN / 2), 0x3);
-            } else {
-              tma_load_2d(st + 2 * A_BYTES + B_BYTES, &P.mBlo, &full[s], kx, n_tile * BN);
-            }
+            tma_load_2d(st + 2 * A_BYTES + B_BYTES, &P.mBlo, &full[s], kx, n_tile * BN);
           }
         }
       }
@@ -366,14 +303,6 @@ __global__ void __launch_bounds__(320, 1)
         if (!mbar_wait(&full[i % STAGES], static_cast<uint32_t>(i / STAGES) & 1u))
           atomicExch(err, 1);
       }
-      if constexpr (CL == 2) {
-        // and the peer's last releases of this CTA's stages (its MMA commits
-        // arrive here) must have landed before either CTA exits
-        for (long i = (it > STAGES ? it - STAGES : 0); i < it; ++i) {
-          if (!mbar_wait(&empty[i % STAGES], static_cast<uint32_t>(i / STAGES) & 1u))
-            atomicExch(err, 1);
-        }
-      }
     }
   } else if (warp == 9) {
     if (lane == 0) {
@@ -381,7 +310,7 @@ __global__ void __launch_bounds__(320, 1)
       long it = 0;  // k blocks consumed (all tiles)
       long c = 0;   // chunks issued (all tiles)
       bool ok = true;
-      for (int t = TC_UNIT0; t < n_tiles_total && ok; t += TC_USTEP) {
+      for (int t = blockIdx.x; t < n_tiles_total && ok; t += gridDim.x) {
         const TcProblem &P = grp.p[find_problem(grp, t)];
         int m_tile, n_tile, z;
         tile_coords(P, t - P.tile_start, m_tile, n_tile, z);
@@ -421,11 +350,7 @@ __global__ void __launch_bounds__(320, 1)
                 mma<F16K>(dt, sw128_desc(alo + kk * MMA_K_BYTES), db, IDESC, 1u);
               }
             }
-            if constexpr (CL == 2) {
-              mma_commit_mc(&empty[s], 0x3);
-            } else {
-              mma_commit(&empty[s]);
-            }
+            mma_commit(&empty[s]);
           }
           mma_commit(&tfull[buf]);
         }
@@ -441,11 +366,10 @@ __global__ void __launch_bounds__(320, 1)
     const int h = warp >> 2;
     long c = 0;
     bool ok = true;
-    for (int t = TC_UNIT0; t < n_tiles_total && ok; t += TC_USTEP) {
+    for (int t = blockIdx.x; t < n_tiles_total && ok; t += gridDim.x) {
       const TcProblem &args = grp.p[find_problem(grp, t)];
       int m_tile, n_tile, z;
       tile_coords(args, t - args.tile_start, m_tile, n_tile, z);
-      m_tile = m_tile * CL + TC_RANK;
       const int kb0 = z * args.kb_per_split;
       const int nkb = min(args.num_kb, kb0 + args.kb_per_split) - kb0;
       const int nch = (nkb + chunk - 1) / chunk;
@@ -538,15 +462,11 @@ __global__ void __launch_bounds__(320, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if constexpr (CL == 2) cluster_sync_all();
   if (warp == 9) {
     __syncwarp();
     tc_fence_after();
     tmem_dealloc(tmem, TMEM_COLS);
   }
-#undef TC_RANK
-#undef TC_UNIT0
-#undef TC_USTEP
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
@@ -589,14 +509,14 @@ CUtensorMap make_map(const void *base, long rows, long kp, int box_rows, int et)
 // less room for the accumulation bias of a longer chunk.
 inline int default_chunk(int tier) { return (tier == TIER_TF32 || tier == TIER_FP16) ? 8 : 4; }
 
-template <int BN, int STAGES, bool SPLIT, int ET, int CL>
+template <int BN, int STAGES, bool SPLIT, int ET>
 void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
   constexpr int STAGE_BYTES = (BM * ROW_BYTES + BN * ROW_BYTES) * (SPLIT ? 2 : 1);
   // stages + barrier block (256 B) + 8 warps x 4 KB staging + alignment slack
   constexpr int SMEM = STAGES * STAGE_BYTES + 256 + 8 * 4096 + 1024;
   static_assert((2 * STAGES + 4) * 8 + 8 <= 256, "barrier block");
   static_assert(SMEM <= 232448, "shared memory budget");
-  auto kern = tc_gemm_kernel<BN, STAGES, SPLIT, ET, CL>;
+  auto kern = tc_gemm_kernel<BN, STAGES, SPLIT, ET>;
   static bool attr = false;
   if (!attr) {
     CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
@@ -618,22 +538,20 @@ void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
     TcProblem &a = grp.p[np++];
     const long mr = 2 * g.M;
     a.mA = make_map(g.A, mr, g.Kp, BM, ET);
-    // with a CTA pair each CTA loads (and multicasts) half of the B tile
-    a.mB = make_map(g.B, g.N, g.Kp, BN / CL, ET);
+    a.mB = make_map(g.B, g.N, g.Kp, BN, ET);
     a.mAlo = SPLIT ? make_map(g.Alo, mr, g.Kp, BM, ET) : a.mA;
-    a.mBlo = SPLIT ? make_map(g.Blo, g.N, g.Kp, BN / CL, ET) : a.mB;
+    a.mBlo = SPLIT ? make_map(g.Blo, g.N, g.Kp, BN, ET) : a.mB;
     a.M = g.M;
     a.N = g.N;
     a.num_kb = static_cast<int>(g.Kp / (ET != 0 ? 64 : 32));
     const int sk = std::max(1, std::min(g.split_k, a.num_kb));
     a.kb_per_split = (a.num_kb + sk - 1) / sk;
     a.k_splits = (a.num_kb + a.kb_per_split - 1) / a.kb_per_split;
-    // work units: m tiles, or vertically adjacent pairs of them for CL = 2
-    a.m_tiles = static_cast<int>(((mr + BM - 1) / BM + CL - 1) / CL);
+    a.m_tiles = static_cast<int>((mr + BM - 1) / BM);
     a.n_tiles = static_cast<int>((g.N + BN - 1) / BN);
     // raster groups: as many A panels (128 rows x the K range of a split) as
     // fit in ~24 MB of L2 share each B panel while it is resident
-    const double panel = static_cast<double>(BM) * CL * a.kb_per_split * ROW_BYTES * (SPLIT ? 2 : 1);
+    const double panel = static_cast<double>(BM) * a.kb_per_split * ROW_BYTES * (SPLIT ? 2 : 1);
     a.group_m = g.group_m > 0 ? std::min(g.group_m, a.m_tiles)
                               : static_cast<int>(std::max(1.0, std::min<double>(a.m_tiles, 24.0e6 / panel)));
     a.out = g.out;
@@ -659,31 +577,8 @@ void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
   grp.total_tiles = static_cast<int>(tiles);
   grp.chunk = descs[0].chunk > 0 ? descs[0].chunk : default_chunk(descs[0].tier);
   grp.err = err;
-  if constexpr (CL == 1) {
-    dim3 grid(static_cast<unsigned>(std::min<long>(tiles, sms)));
-    kern<<<grid, 320, SMEM, st>>>(grp);
-  } else {
-    cudaLaunchConfig_t cfg = {};
-    cfg.blockDim = dim3(320);
-    cfg.dynamicSmemBytes = SMEM;
-    cfg.stream = st;
-    cudaLaunchAttribute attr_cl[1];
-    attr_cl[0].id = cudaLaunchAttributeClusterDimension;
-    attr_cl[0].val.clusterDim.x = CL;
-    attr_cl[0].val.clusterDim.y = 1;
-    attr_cl[0].val.clusterDim.z = 1;
-    cfg.attrs = attr_cl;
-    cfg.numAttrs = 1;
-    // persistent clusters: as many as can be resident at once (SM pairs)
-    static int max_clusters = 0;
-    if (!max_clusters) {
-      cfg.gridDim = dim3(static_cast<unsigned>(CL * (sms / CL)));
-      CUDA_CHECK(cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg));
-      if (max_clusters < 1) fail(CC_ERR_UNSUPPORTED, "gemm_tc: no resident CTA pair");
-    }
-    cfg.gridDim = dim3(static_cast<unsigned>(CL * std::min<long>(tiles, max_clusters)));
-    CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, grp));
-  }
+  dim3 grid(static_cast<unsigned>(std::min<long>(tiles, sms)));
+  kern<<<grid, 320, SMEM, st>>>(grp);
   LAUNCH_CHECK();
   count_launch();
 }
@@ -694,48 +589,27 @@ void check_desc(const TcDesc &g) {
     fail(CC_ERR_ARG, "gemm_tc: operands must be 16-byte aligned");
 }
 
-// Wide tiles as CTA pairs sharing B through cluster multicast: on when the
-// environment variable CDFNS_CTA_PAIR is "1" (read once).
-bool cta_pair() {
-  static int v = -1;
-  if (v < 0) {
-    const char *e = std::getenv("CDFNS_CTA_PAIR");
-    v = (e && e[0] == '1') ? 1 : 0;
-  }
-  return v == 1;
-}
-
 void dispatch(const TcDesc *d, int n, bool wide, cudaStream_t st, int *err) {
-  if (wide && cta_pair()) {
-    switch (d[0].tier) {
-      case TIER_TF32: launch<256, 4, false, 0, 2>(d, n, st, err); return;
-      case TIER_TF32X3: launch<256, 2, true, 0, 2>(d, n, st, err); return;
-      case TIER_BF16X3: launch<256, 2, true, 1, 2>(d, n, st, err); return;
-      case TIER_FP16: launch<256, 4, false, 2, 2>(d, n, st, err); return;
-      case TIER_FP16X3: launch<256, 2, true, 2, 2>(d, n, st, err); return;
-      default: break;
-    }
-  }
   switch (d[0].tier) {
     case TIER_TF32:
-      if (wide) launch<256, 4, false, 0, 1>(d, n, st, err);
-      else launch<128, 6, false, 0, 1>(d, n, st, err);
+      if (wide) launch<256, 4, false, 0>(d, n, st, err);
+      else launch<128, 6, false, 0>(d, n, st, err);
       break;
     case TIER_TF32X3:
-      if (wide) launch<256, 2, true, 0, 1>(d, n, st, err);
-      else launch<128, 3, true, 0, 1>(d, n, st, err);
+      if (wide) launch<256, 2, true, 0>(d, n, st, err);
+      else launch<128, 3, true, 0>(d, n, st, err);
       break;
     case TIER_BF16X3:
-      if (wide) launch<256, 2, true, 1, 1>(d, n, st, err);
-      else launch<128, 3, true, 1, 1>(d, n, st, err);
+      if (wide) launch<256, 2, true, 1>(d, n, st, err);
+      else launch<128, 3, true, 1>(d, n, st, err);
       break;
     case TIER_FP16:
-      if (wide) launch<256, 4, false, 2, 1>(d, n, st, err);
-      else launch<128, 6, false, 2, 1>(d, n, st, err);
+      if (wide) launch<256, 4, false, 2>(d, n, st, err);
+      else launch<128, 6, false, 2>(d, n, st, err);
       break;
     case TIER_FP16X3:
-      if (wide) launch<256, 2, true, 2, 1>(d, n, st, err);
-      else launch<128, 3, true, 2, 1>(d, n, st, err);
+      if (wide) launch<256, 2, true, 2>(d, n, st, err);
+      else launch<128, 3, true, 2>(d, n, st, err);
       break;
     default:
       fail(CC_ERR_ARG, "gemm_tc: bad tier");
@@ -897,7 +771,7 @@ void gemm_tc(const TcDesc &g0, cudaStream_t st, int *err) {
     auto it = g_tune.find(key);
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(st, &cap);
-    if (it == g_tune.end() && tune_enabled() && cap == cudaStreamCaptureStatusNone) {
+    if (it == g_tune.end() && tune_enabled() && !g.no_tune && cap == cudaStreamCaptureStatusNone) {
       g_tune[key] = tune(g, st, err);
       tune_save();
       it = g_tune.find(key);

@@ -83,6 +83,9 @@ struct TcDesc {
   // the values written (the caller zeroes it); nullptr: not tracked
   float *amax_out = nullptr;
   float amax_mul = 1.0f;
+  // never time tile candidates for this call (the autotuner allocates a
+  // scratch output and events): use a cached choice or the defaults
+  bool no_tune = false;
 };
 void gemm_tc(const TcDesc &g, cudaStream_t st, int *err_flag);
 // Several independent GEMMs (any shapes, same or mixed tiers) in as few

@@ -1,14 +1,15 @@
 // cc_zgemm_noalloc: the complex GEMM of cc_zgemm_dev for callers that must
 // not allocate device memory.
 //
-// Some callers cannot let a library call cudaMalloc: code running while a
-// CUDA stream is being captured into a graph (allocation is not a capturable
-// operation), host frameworks that hand out all device memory from their own
-// pre-sized pool and treat any outside allocation as a leak or an
-// out-of-memory risk, and latency-critical loops where a cudaMalloc would
-// synchronise the device. For them this entry point keeps every temporary
-// (the tensor-core operand planes and the error flag) in one fixed array in
-// device global memory, declared below, so a call allocates nothing.
+// Some callers cannot let a library call cudaMalloc: host frameworks that
+// reserve nearly all device memory up front for their own pool, where an
+// outside allocation either fails or eats into memory the framework has
+// promised elsewhere; applications whose device-memory budget is fixed at
+// start-up and audited; and latency-critical loops, where cudaMalloc and
+// cudaFree can synchronise the device and stall the pipeline. For them this
+// entry point keeps every temporary (the tensor-core operand planes and the
+// error flag) in one fixed array in device global memory, declared below, so
+// a call allocates nothing and calls no allocating library routine.
 //
 // The array has a fixed size (kScratchBytes); every GPU that loads this
 // library holds it until the process exits. All calls share it: it keeps the
@@ -62,9 +63,22 @@ void noalloc_record_error(const std::string &m);  // message for cc_last_error(N
 extern "C" int cc_zgemm_noalloc(int tier, long M, long N, long K, const double *A, const double *B,
                                 double *C) {
   using namespace cdfns;
-  if (tier < CC_TIER_FP64 || tier > CC_TIER_BF16X3 || M < 1 || N < 1 || K < 1 || !A || !B || !C)
-    return CC_ERR_ARG;
   try {
+    if (tier < CC_TIER_FP64 || tier > CC_TIER_FP16X3)
+      fail(CC_ERR_ARG, "cc_zgemm_noalloc: unknown tier " + std::to_string(tier));
+    if (tier == CC_TIER_FP16 || tier == CC_TIER_FP16X3)
+      fail(CC_ERR_ARG,
+           "cc_zgemm_noalloc: the FP16 tiers need device scratch for their operand scales; "
+           "use CC_TIER_FP64, CC_TIER_TF32, CC_TIER_TF32X3 or CC_TIER_BF16X3");
+    if (M < 1 || N < 1 || K < 1 || !A || !B || !C)
+      fail(CC_ERR_ARG, "cc_zgemm_noalloc: sizes must be >= 1 and pointers non-NULL");
+    // byte extents of A, B and C (16 bytes per complex element) must be
+    // representable, so no size computed below can wrap around
+    long bytes = 0;
+    if (__builtin_mul_overflow(M, K, &bytes) || __builtin_mul_overflow(bytes, 16L, &bytes) ||
+        __builtin_mul_overflow(N, K, &bytes) || __builtin_mul_overflow(bytes, 16L, &bytes) ||
+        __builtin_mul_overflow(M, N, &bytes) || __builtin_mul_overflow(bytes, 16L, &bytes))
+      fail(CC_ERR_ARG, "cc_zgemm_noalloc: M, N, K too large (byte sizes overflow)");
     cudaStream_t st = noalloc_stream();
     const cplx *a = reinterpret_cast<const cplx *>(A);
     const cplx *b = reinterpret_cast<const cplx *>(B);
@@ -83,6 +97,12 @@ extern "C" int cc_zgemm_noalloc(int tier, long M, long N, long K, const double *
       CUDA_CHECK(cudaStreamSynchronize(st));
       return CC_OK;
     }
+    // every operand plane needs at least one byte per row and K element:
+    // anything larger than the array is refused before sizing the planes
+    if (M > static_cast<long>(kScratchBytes) || N > static_cast<long>(kScratchBytes) ||
+        K > static_cast<long>(kScratchBytes))
+      fail(CC_ERR_ARG, "cc_zgemm_noalloc: operands exceed the fixed " +
+                           std::to_string(kScratchBytes) + "-byte scratch array");
     const int kal = tc_k_align(tier);
     const long Kp = ((2 * K + kal - 1) / kal) * kal;
     const size_t eb = tc_elem_bytes(tier);
@@ -115,6 +135,7 @@ extern "C" int cc_zgemm_noalloc(int tier, long M, long N, long K, const double *
     t.out = TC_OUT_F64;
     t.C = c; t.ldc = N;
     t.split_k = 1;
+    t.no_tune = true;  // the tile autotuner would allocate; cached choices only
     gemm_tc(t, st, err);
     int h = 0;
     CUDA_CHECK(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
