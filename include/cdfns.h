@@ -69,6 +69,12 @@ typedef struct cc_ctx cc_ctx; /* one molecular (synthetic) system */
 int cc_set_default_allocator(void *(*alloc)(size_t, void *),
                              void (*free_fn)(void *, void *), void *user);
 int cc_set_default_stream(void *stream);
+/* Allocator of one context from now on (same contract as the default; NULLs
+ * restore cudaMalloc/cudaFree). Buffers the context already holds are
+ * released later through the functions that allocated them. Errors:
+ * CC_ERR_ARG (NULL ctx, or only one of alloc/free given). */
+int cc_set_allocator(cc_ctx *ctx, void *(*alloc)(size_t, void *),
+                     void (*free_fn)(void *, void *), void *user);
 
 /*
  * cc_init: create a context from orbital energies and Cholesky vectors.
@@ -185,19 +191,42 @@ int ipeom_solve_lr(cc_ctx *ctx, int n_roots, double tol, int max_iter,
 
 /*
  * cc_batch_ipeom: ipeom_solve for several independent systems (uneven sizes
- * allowed), each with converged CCSD. Their block Davidson iterations run in
- * lockstep; each round builds the sigma vectors of every still-active
+ * allowed; each context at most once). Their block Davidson iterations run
+ * in lockstep; each round builds the sigma vectors of every still-active
  * system in one batched pass whose two-body contractions share one grouped
  * persistent tensor-core launch, replayed from a CUDA graph after its first
  * use (cc_set_graphs). Work runs on systems[0]'s stream.
  * omega [n_sys][n_roots][2], r1_weight [n_sys][n_roots] (may be NULL),
- * n_iter [n_sys] (may be NULL), status [n_sys] (CC_OK or
- * CC_ERR_NOT_CONVERGED per system). Returns CC_ERR_NOT_CONVERGED if any
- * system did not converge; errors are reported on systems[0].
+ * n_iter [n_sys] (may be NULL), status [n_sys]: per system CC_OK,
+ * CC_ERR_NOT_CONVERGED (iteration limit), or the error that stopped that
+ * system alone -- CC_ERR_STATE (no converged CCSD), CC_ERR_ARG (n_roots
+ * larger than its IP space), CC_ERR_NUMERIC (its Davidson residual became
+ * non-finite); its message is then in cc_last_error(systems[q]) and its
+ * omega entries are 0 (or the last Ritz values). The other systems are
+ * unaffected: their results equal those of a batch without the failed one.
+ * Returns CC_OK, CC_ERR_NOT_CONVERGED if any status is not CC_OK, or an
+ * error of the whole call (CC_ERR_CUDA, CC_ERR_OOM, CC_ERR_TIMEOUT; message
+ * on systems[0]).
  */
 int cc_batch_ipeom(cc_ctx **systems, int n_sys, int n_roots, double tol,
                    int max_iter, double *omega, double *r1_weight, int *n_iter,
                    int *status);
+/*
+ * cc_batch_solve: CCSD (Eqs. 13-15) then IP-EOM-CCSD (Eqs. 17-18) for
+ * several independent systems of uneven size, each context at most once.
+ * CCSD runs system after system in each context's own tier (each residual's
+ * products already fill the GPU at the sizes batched here); the IP-EOM
+ * step is cc_batch_ipeom over the systems whose CCSD converged.
+ * e_corr [n_sys][2], omega [n_sys][n_roots][2], r1_weight [n_sys][n_roots]
+ * (may be NULL), status [n_sys]: CC_OK, or the first error of that system
+ * (its CCSD's CC_ERR_NOT_CONVERGED / CC_ERR_NUMERIC / ..., or its IP-EOM
+ * status as in cc_batch_ipeom); a failed system never changes the others'
+ * results. Returns CC_OK, CC_ERR_NOT_CONVERGED if any status is not CC_OK,
+ * or an error of the whole batched IP-EOM call.
+ */
+int cc_batch_solve(cc_ctx **systems, int n_sys, int n_roots, double ccsd_tol,
+                   double eom_tol, int max_iter, double *e_corr, double *omega,
+                   double *r1_weight, int *status);
 /* Replay the batched sigma from CUDA graphs (1, default) or not (0). */
 int cc_set_graphs(cc_ctx *ctx, int on);
 
@@ -387,6 +416,25 @@ int cc_mlp_features(cc_ctx *ctx, long n, float *X_host);
 /* Set the context's starting amplitudes t1 = 0, t2 = rho(MLP) * t_MP2; the
  * next ccsd_solve starts from them. Errors: CC_ERR_STATE after ccsd_solve. */
 int cc_mlp_warm_start(cc_mlp *mlp, cc_ctx *ctx);
+
+/*
+ * Test hooks for the error paths (no counterpart in the paper).
+ * cc_set_wait_limit: limit (ns) of every pipeline wait inside the
+ *   tensor-core kernels launched from now on, process-wide; 0 restores the
+ *   default of 2 s. A wait that runs out makes the kernel record an error
+ *   flag, wait (2 s at most) for its own copies and MMAs in flight, free its
+ *   tensor memory and return; the call then fails with CC_ERR_TIMEOUT and the
+ *   context stays usable. A limit of a few ns makes the first wait that does
+ *   not succeed at once run out.
+ * cc_set_fault_injection: kind 1 writes a NaN into the CCSD residual of
+ *   iteration at_iteration (ccsd_solve then fails with CC_ERR_NUMERIC); kind
+ *   2 writes one into the sigma vectors of Davidson iteration at_iteration
+ *   (ipeom_solve fails with CC_ERR_NUMERIC; in cc_batch_ipeom only this
+ *   system stops); 0 switches injection off. Host-side: the value is copied
+ *   into device memory between kernels. Fires once.
+ */
+int cc_set_wait_limit(unsigned long long ns);
+int cc_set_fault_injection(cc_ctx *ctx, int kind, int at_iteration);
 
 const char *cc_last_error(const cc_ctx *ctx); /* NULL ctx: last global */
 void cc_free(cc_ctx *ctx);

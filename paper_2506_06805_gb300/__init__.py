@@ -97,6 +97,12 @@ _SIGS = {
     "cc_set_memory_limit": (ctypes.c_int, [_P, ctypes.c_size_t]),
     "cc_batch_ipeom": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, ctypes.c_int, _D, _D, _I, _I]),
+    "cc_batch_solve": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                      _D, _D, _D, _I]),
+    "cc_set_allocator": (ctypes.c_int, [_P, _ALLOC, _FREE, _P]),
+    "cc_set_wait_limit": (ctypes.c_int, [ctypes.c_ulonglong]),
+    "cc_set_fault_injection": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
 }
 
 _lib = None
@@ -196,6 +202,30 @@ def batch_ipeom(systems, n_roots, tol=1e-7, max_iter=100, allow_unconverged=Fals
                               it.ctypes.data_as(_I), stt.ctypes.data_as(_I))
     _check(rc, systems[0]._ctx, (0, -5) if allow_unconverged else (0,))
     return w[..., 0] + 1j * w[..., 1], r1, it, stt
+
+
+def batch_solve(systems, n_roots, ccsd_tol=1e-8, eom_tol=1e-7, max_iter=100):
+    """CCSD then batched IP-EOM for several systems (cc_batch_solve).
+
+    Returns (e_corr [n_sys] complex, omega [n_sys][n_roots] complex,
+    r1_weight, status [n_sys]); a failed system has a nonzero status and
+    does not affect the others."""
+    n = len(systems)
+    arr = (_P * n)(*[s._ctx for s in systems])
+    e = np.zeros((n, 2))
+    w = np.zeros((n, n_roots, 2))
+    r1 = np.zeros((n, n_roots))
+    stt = np.zeros(n, np.int32)
+    rc = lib().cc_batch_solve(arr, n, n_roots, ccsd_tol, eom_tol, max_iter, _dptr(e),
+                              _dptr(w), _dptr(r1), stt.ctypes.data_as(_I))
+    _check(rc, systems[0]._ctx, (0, -5))
+    return e[:, 0] + 1j * e[:, 1], w[..., 0] + 1j * w[..., 1], r1, stt
+
+
+def set_wait_limit(ns):
+    """Limit (ns) of the tensor-core kernels' pipeline waits, process-wide
+    (0: the default 2 s). A test hook for the timeout path."""
+    _check(lib().cc_set_wait_limit(int(ns)))
 
 
 def selftest_conversions(x):
@@ -367,6 +397,23 @@ class System:
 
     def set_graphs(self, on=True):
         _check(lib().cc_set_graphs(self._ctx, 1 if on else 0), self._ctx)
+
+    def set_allocator(self, alloc, free, user=None):
+        """Route this system's later device allocations through ctypes
+        callbacks alloc(nbytes, user) -> ptr and free(ptr, user) (None, None:
+        cudaMalloc/cudaFree). The callbacks must outlive the system."""
+        if alloc is None:
+            _check(lib().cc_set_allocator(self._ctx, _ALLOC(), _FREE(), None), self._ctx)
+            self._alloc_hooks = None
+            return
+        hooks = (_ALLOC(alloc), _FREE(free))
+        _check(lib().cc_set_allocator(self._ctx, hooks[0], hooks[1], user), self._ctx)
+        self._alloc_hooks = hooks
+
+    def set_fault_injection(self, kind, at_iteration=1):
+        """Test hook: kind 1 = NaN into the CCSD residual of an iteration,
+        2 = NaN into the Davidson sigma vectors of an iteration, 0 = off."""
+        _check(lib().cc_set_fault_injection(self._ctx, int(kind), int(at_iteration)), self._ctx)
 
     def set_memory_limit(self, nbytes):
         """Cap the device bytes this system holds (0: no cap)."""

@@ -55,10 +55,10 @@ void *Allocator::get(size_t bytes) {
   return p;
 }
 
-void Allocator::put(void *p, size_t bytes) {
+void Allocator::put(void *p, size_t bytes, void (*fr)(void *, void *), void *fr_user) {
   if (!p) return;
   in_use -= std::min(in_use, bytes ? bytes : size_t(16));
-  if (free) free(p, user);
+  if (fr) fr(p, fr_user);
   else cudaFree(p);
 }
 
@@ -80,10 +80,12 @@ void Buf::reset(Allocator *a, size_t n) {
   al = a;
   p = a->get(n);
   bytes = n;
+  fr = a->free;
+  fr_user = a->user;
 }
 
 void Buf::release() {
-  if (p && al) al->put(p, bytes);
+  if (p && al) al->put(p, bytes, fr, fr_user);
   p = nullptr;
   bytes = 0;
 }
@@ -124,6 +126,16 @@ int cc_set_default_allocator(void *(*alloc)(size_t, void *), void (*free_fn)(voi
   cdfns::g_default_alloc.alloc = alloc;
   cdfns::g_default_alloc.free = free_fn;
   cdfns::g_default_alloc.user = user;
+  return CC_OK;
+}
+
+int cc_set_allocator(cc_ctx *ctx, void *(*alloc)(size_t, void *),
+                     void (*free_fn)(void *, void *), void *user) {
+  if (!ctx || (alloc == nullptr) != (free_fn == nullptr)) return CC_ERR_ARG;
+  cdfns::Allocator &al = ctx->c.al;
+  al.alloc = alloc;
+  al.free = free_fn;
+  al.user = user;
   return CC_OK;
 }
 
@@ -520,7 +532,7 @@ int cc_get_stats(const cc_ctx *ctx, double *out, int n) {
   if (!ctx || !out || n < 0 || n > 16) return CC_ERR_ARG;
   double s[16];
   std::memcpy(s, ctx->c.stat, sizeof(s));
-  s[6] = static_cast<double>(cdfns::g_launches);
+  s[6] = static_cast<double>(cdfns::g_launches.load());
   s[11] = static_cast<double>(ctx->c.al.peak);
   s[12] = ctx->c.diis_depth;
   s[14] = static_cast<double>(ctx->c.al.in_use);
@@ -558,16 +570,92 @@ int cc_batch_ipeom(cc_ctx **systems, int n_sys, int n_roots, double tol, int max
   if (!systems || n_sys < 1 || !omega || !status) return CC_ERR_ARG;
   for (int q = 0; q < n_sys; ++q)
     if (!systems[q]) return CC_ERR_ARG;
-  if (!(tol > 0) || max_iter < 1) return CC_ERR_ARG;
+  for (int q = 0; q < n_sys; ++q)
+    for (int r = q + 1; r < n_sys; ++r)
+      if (systems[q] == systems[r]) return CC_ERR_ARG;
+  if (!(tol > 0) || max_iter < 1 || n_roots < 1) return CC_ERR_ARG;
   return guarded(systems[0], [&] {
     std::vector<cdfns::Ctx *> sys;
     for (int q = 0; q < n_sys; ++q) sys.push_back(&systems[q]->c);
     cdfns::run_ipeom(sys, n_roots, tol, max_iter, omega, r1_weight, n_iter, status,
-                     systems[0]->c.use_graphs);
+                     systems[0]->c.use_graphs, false, nullptr, true);
     for (int q = 0; q < n_sys; ++q)
       if (status[q] != CC_OK) return CC_ERR_NOT_CONVERGED;
     return CC_OK;
   });
+}
+
+int cc_batch_solve(cc_ctx **systems, int n_sys, int n_roots, double ccsd_tol, double eom_tol,
+                   int max_iter, double *e_corr, double *omega, double *r1_weight,
+                   int *status) {
+  if (!systems || n_sys < 1 || !e_corr || !omega || !status) return CC_ERR_ARG;
+  for (int q = 0; q < n_sys; ++q)
+    if (!systems[q]) return CC_ERR_ARG;
+  for (int q = 0; q < n_sys; ++q)
+    for (int r = q + 1; r < n_sys; ++r)
+      if (systems[q] == systems[r]) return CC_ERR_ARG;
+  if (!(ccsd_tol > 0) || !(eom_tol > 0) || max_iter < 1 || n_roots < 1) return CC_ERR_ARG;
+  // CCSD system by system: a system that fails keeps its own status and
+  // leaves the others untouched
+  std::vector<int> cc_status(n_sys, CC_OK);
+  for (int q = 0; q < n_sys; ++q) {
+    e_corr[2 * q] = e_corr[2 * q + 1] = 0.0;
+    cc_status[q] = guarded(systems[q], [&] {
+      return systems[q]->c.ccsd(ccsd_tol, max_iter, e_corr + 2 * q, nullptr);
+    });
+  }
+  // the batched IP-EOM over the systems whose CCSD converged
+  std::vector<cc_ctx *> ok;
+  std::vector<int> idx;
+  for (int q = 0; q < n_sys; ++q) {
+    status[q] = cc_status[q];
+    for (int r = 0; r < n_roots; ++r) {
+      omega[2L * (static_cast<long>(q) * n_roots + r)] = 0.0;
+      omega[2L * (static_cast<long>(q) * n_roots + r) + 1] = 0.0;
+      if (r1_weight) r1_weight[static_cast<long>(q) * n_roots + r] = 0.0;
+    }
+    if (cc_status[q] == CC_OK) {
+      ok.push_back(systems[q]);
+      idx.push_back(q);
+    }
+  }
+  if (!ok.empty()) {
+    const int m = static_cast<int>(ok.size());
+    std::vector<double> w(2L * m * n_roots), r1(static_cast<size_t>(m) * n_roots);
+    std::vector<int> st(m);
+    const int rc = cc_batch_ipeom(ok.data(), m, n_roots, eom_tol, max_iter, w.data(), r1.data(),
+                                  nullptr, st.data());
+    if (rc != CC_OK && rc != CC_ERR_NOT_CONVERGED) {
+      for (int j = 0; j < m; ++j) status[idx[j]] = rc;
+      if (ok[0] != systems[0]) systems[0]->c.last_error = ok[0]->c.last_error;
+      return rc;
+    }
+    for (int j = 0; j < m; ++j) {
+      const int q = idx[j];
+      status[q] = st[j];
+      for (int r = 0; r < n_roots; ++r) {
+        omega[2L * (static_cast<long>(q) * n_roots + r)] = w[2L * (static_cast<long>(j) * n_roots + r)];
+        omega[2L * (static_cast<long>(q) * n_roots + r) + 1] =
+            w[2L * (static_cast<long>(j) * n_roots + r) + 1];
+        if (r1_weight) r1_weight[static_cast<long>(q) * n_roots + r] = r1[static_cast<long>(j) * n_roots + r];
+      }
+    }
+  }
+  for (int q = 0; q < n_sys; ++q)
+    if (status[q] != CC_OK) return CC_ERR_NOT_CONVERGED;
+  return CC_OK;
+}
+
+int cc_set_wait_limit(unsigned long long ns) {
+  cdfns::tc_set_wait_limit(ns);
+  return CC_OK;
+}
+
+int cc_set_fault_injection(cc_ctx *ctx, int kind, int at_iteration) {
+  if (!ctx || kind < 0 || kind > 2 || (kind && at_iteration < 1)) return CC_ERR_ARG;
+  ctx->c.inject_kind = kind;
+  ctx->c.inject_at = at_iteration;
+  return CC_OK;
 }
 
 }  // extern "C"

@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -92,7 +93,9 @@ struct Allocator {
   size_t window = 0;  // high-water mark of in_use since the caller last set it
   size_t limit = 0;   // cap on in_use (0: none); a get() beyond it fails
   void *get(size_t bytes);
-  void put(void *p, size_t bytes);
+  // release p (bytes long) through the functions that allocated it (the
+  // allocator may have been replaced since)
+  void put(void *p, size_t bytes, void (*fr)(void *, void *), void *fr_user);
 };
 // Device bytes an allocation through `al` can still obtain: the driver's free
 // memory less 2 GiB for work outside the allocator (library workspaces,
@@ -105,6 +108,8 @@ struct Buf {
   Allocator *al = nullptr;
   void *p = nullptr;
   size_t bytes = 0;
+  void (*fr)(void *, void *) = nullptr;  // free function in force at allocation
+  void *fr_user = nullptr;
   Buf() = default;
   Buf(Allocator *a, size_t n) { reset(a, n); }
   Buf(const Buf &) = delete;
@@ -112,7 +117,7 @@ struct Buf {
   Buf(Buf &&o) noexcept { *this = std::move(o); }
   Buf &operator=(Buf &&o) noexcept {
     release();
-    al = o.al; p = o.p; bytes = o.bytes;
+    al = o.al; p = o.p; bytes = o.bytes; fr = o.fr; fr_user = o.fr_user;
     o.p = nullptr; o.bytes = 0;
     return *this;
   }
@@ -172,8 +177,13 @@ __host__ __device__ inline float fp16_scale(float amax) {
 #endif
 }
 
-// Kernel launch counter (for reporting how many kernels ran).
-extern unsigned long long g_launches;
-inline void count_launch(unsigned long long n = 1) { g_launches += n; }
+// Kernel launch counters (for reporting how many kernels ran): the process
+// total and the calling thread's own count.
+extern std::atomic<unsigned long long> g_launches;
+extern thread_local unsigned long long t_launches;
+inline void count_launch(unsigned long long n = 1) {
+  g_launches += n;
+  t_launches += n;
+}
 
 }  // namespace cdfns

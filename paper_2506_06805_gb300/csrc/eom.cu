@@ -188,9 +188,9 @@ void batch_sigma(std::vector<Ctx *> &sys, const std::vector<int> &k,
       count_launch(ge->launches);
     } else {
       // run once directly (allocates and packs whatever is new), then capture
-      const unsigned long long l0 = g_launches;
+      const unsigned long long l0 = t_launches;
       sigma_body(sys, k, cs);
-      const unsigned long long nl = g_launches - l0;
+      const unsigned long long nl = t_launches - l0;
       if (use_graph) {
         // The direct pass may have (re)allocated buffers: key the graph on
         // the generations after it. A capture that fails leaves no graph and
@@ -217,7 +217,9 @@ void batch_sigma(std::vector<Ctx *> &sys, const std::vector<int> &k,
         }
         if (graph) cudaGraphDestroy(graph);
         cudaGetLastError();
-        g_launches = l0 + nl;  // the captured pass did not run
+        // the captured pass did not run
+        g_launches -= t_launches - (l0 + nl);
+        t_launches = l0 + nl;
       }
     }
   } catch (...) {
@@ -310,6 +312,8 @@ struct Dav {
   int m = 0, it = 0, added = 0;
   enum { FULL, ADDED } pending = FULL;
   bool done = false, converged = false;
+  bool isolate = false;  // stop this system alone on a non-finite residual
+  int failed = 0;        // CC_ERR_* that stopped this system (0: none)
   std::vector<cplx> w_out;
   std::vector<double> rn;
   int req_k = 0;
@@ -407,6 +411,19 @@ struct Dav {
     const size_t z = sizeof(cplx);
     const long ld = max_sp;
     c->eng.permute_into(C1(), Tv(Gm.c(), "ba", {m, m}, {ld, 1}), C0(), T(G.c(), "ba", {m, m}));
+    {
+      // a non-finite subspace matrix (a NaN or Inf sigma) stops this system
+      // before the eigensolver sees it
+      std::vector<cplx> gh(static_cast<size_t>(m) * m);
+      d2h(gh.data(), G.p, z * m * m, st());
+      for (const cplx &x : gh)
+        if (!std::isfinite(x.x) || !std::isfinite(x.y)) {
+          if (!isolate) fail(CC_ERR_NUMERIC, "Davidson subspace matrix is not finite");
+          failed = CC_ERR_NUMERIC;
+          done = true;
+          return;
+        }
+    }
     geev_dev(&c->al, st(), G.c(), m, wv.c(), VR.c());
     std::vector<cplx> wh(m), vh(static_cast<size_t>(m) * m);
     d2h(wh.data(), wv.p, z * m, st());
@@ -436,7 +453,12 @@ struct Dav {
       axpby(dim, mk(-w_out[r].x, -w_out[r].y), Xr.c() + r * dim, C1(), R.c() + r * dim, st());
       const cplx n2 = dot(R.c() + r * dim, R.c() + r * dim, dim, true, st(), c->red.c());
       rn[r] = std::sqrt(std::max(n2.x, 0.0));
-      if (!std::isfinite(rn[r])) fail(CC_ERR_NUMERIC, "Davidson residual NaN");
+      if (!std::isfinite(rn[r])) {
+        if (!isolate) fail(CC_ERR_NUMERIC, "Davidson residual NaN");
+        failed = CC_ERR_NUMERIC;
+        done = true;
+        return;
+      }
       if (rn[r] >= tol) all = false;
     }
     if (all) {
@@ -473,6 +495,13 @@ struct Dav {
   }
 
   void results(double *omega, double *r1w) {
+    if (!c) {  // never started: no roots
+      for (int r = 0; r < nr; ++r) {
+        omega[2 * r] = omega[2 * r + 1] = 0.0;
+        if (r1w) r1w[r] = 0.0;
+      }
+      return;
+    }
     for (int r = 0; r < nr; ++r) {
       omega[2 * r] = w_out[r].x;
       omega[2 * r + 1] = w_out[r].y;
@@ -488,42 +517,73 @@ struct Dav {
 }  // namespace
 
 // Lockstep block Davidson over several systems (one batched sigma per round).
-// status[q] = CC_OK or CC_ERR_NOT_CONVERGED per system.
+// status[q] = CC_OK or CC_ERR_NOT_CONVERGED per system (and, with isolate,
+// the error that stopped that system alone).
 void run_ipeom(std::vector<Ctx *> &sys, int nr, double tol, int max_iter, double *omega,
                double *r1w, int *n_iter, int *status, bool use_graph, bool left,
-               const std::vector<cplx *> *vecs) {
+               const std::vector<cplx *> *vecs, bool isolate) {
   const double t0 = now_ms();
-  for (Ctx *c : sys) {
-    if (!c->ccsd_done) fail(CC_ERR_STATE, "ipeom needs a converged ccsd_solve");
-    if (nr < 1 || nr > c->dim_ip() || nr > 64) fail(CC_ERR_ARG, "n_roots out of range");
-    if (!c->hbar_done) c->build_hbar();
-  }
   std::vector<Dav> dv(sys.size());
-  for (size_t q = 0; q < sys.size(); ++q) dv[q].start(sys[q], nr, tol, max_iter);
+  for (size_t q = 0; q < sys.size(); ++q) {
+    Ctx *c = sys[q];
+    dv[q].nr = nr;
+    dv[q].isolate = isolate;
+    try {
+      if (!c->ccsd_done) fail(CC_ERR_STATE, "ipeom needs a converged ccsd_solve");
+      if (nr < 1 || nr > c->dim_ip() || nr > 64) fail(CC_ERR_ARG, "n_roots out of range");
+      if (!c->hbar_done) c->build_hbar();
+      dv[q].start(c, nr, tol, max_iter);
+    } catch (const Error &e) {
+      if (!isolate) throw;
+      c->last_error = e.msg;
+      dv[q] = Dav();
+      dv[q].nr = nr;
+      dv[q].failed = e.code;
+      dv[q].done = true;
+    }
+  }
   while (true) {
     std::vector<Ctx *> act;
     std::vector<int> ks;
     std::vector<const cplx *> rs;
     std::vector<cplx *> ss;
+    std::vector<Dav *> ad;
     for (auto &d : dv) {
       if (d.done) continue;
       act.push_back(d.c);
       ks.push_back(d.req_k);
       rs.push_back(d.V.c() + d.req_off * d.dim);
       ss.push_back(d.S.c() + d.req_off * d.dim);
+      ad.push_back(&d);
     }
     if (act.empty()) break;
     if (left)
       batch_left_sigma(act, ks, rs, ss);
     else
       batch_sigma(act, ks, rs, ss, use_graph);
-    for (auto &d : dv)
-      if (!d.done) d.step();
+    for (Dav *d : ad) d->c->maybe_inject(2, d->it + 1, d->S.c() + d->req_off * d->dim);
+    for (auto &d : dv) {
+      if (d.done) continue;
+      if (!isolate) {
+        d.step();
+        continue;
+      }
+      try {
+        d.step();
+      } catch (const Error &e) {
+        if (e.code == CC_ERR_CUDA || e.code == CC_ERR_OOM || e.code == CC_ERR_TIMEOUT) throw;
+        d.c->last_error = e.msg;
+        d.failed = e.code;
+        d.done = true;
+      }
+    }
   }
   for (size_t q = 0; q < sys.size(); ++q) {
     dv[q].results(omega + 2L * nr * q, r1w ? r1w + static_cast<long>(nr) * q : nullptr);
     if (n_iter) n_iter[q] = dv[q].it;
-    if (status) status[q] = dv[q].converged ? CC_OK : CC_ERR_NOT_CONVERGED;
+    if (status)
+      status[q] = dv[q].failed ? dv[q].failed : (dv[q].converged ? CC_OK : CC_ERR_NOT_CONVERGED);
+    if (!dv[q].c) continue;
     if (vecs) d2d((*vecs)[q], dv[q].Xr.p, sizeof(cplx) * nr * dv[q].dim, dv[q].st());
     sys[q]->stat[8] = dv[q].it;
     sys[q]->check_err_flag();

@@ -168,12 +168,13 @@ __global__ void __launch_bounds__(SK_THREADS) skinny64_kernel(const SkinnyDesc d
 
 template <int KM>
 void skinny_launch(const SkinnyDesc &d, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
+  // set once per process (thread-safe static initialisation)
+  static const bool attr = [&] {
     CUDA_CHECK(cudaFuncSetAttribute(skinny_kernel<KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     SK_SMEM));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   const int per_s = (KM / 2) * static_cast<int>(sizeof(float4));
   const int chunk = std::max(1, std::min(d.Ns, SK_SMEM / per_s));
   const int beta_mode = (d.beta.x == 0.0 && d.beta.y == 0.0) ? 0
@@ -189,12 +190,13 @@ void skinny_launch(const SkinnyDesc &d, cudaStream_t st) {
 
 template <int KM>
 void skinny64_launch(const SkinnyDesc &d, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
+  // set once per process (thread-safe static initialisation)
+  static const bool attr = [&] {
     CUDA_CHECK(cudaFuncSetAttribute(skinny64_kernel<KM>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, SK_SMEM));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   const int per_s = KM * static_cast<int>(sizeof(double2));
   const int chunk = std::max(1, std::min(d.Ns, SK_SMEM / per_s));
   const long blocks = (d.Mb + SK_THREADS - 1) / SK_THREADS;

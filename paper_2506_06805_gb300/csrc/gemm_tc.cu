@@ -26,6 +26,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -42,7 +43,8 @@ namespace {
 
 constexpr int BM = 128;            // real rows per tile (TMEM lanes)
 constexpr int ROW_BYTES = 128;     // one swizzle row: 32 fp32 or 64 bf16
-constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per wait
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // default limit of a pipeline wait (2 s)
+constexpr unsigned long long DRAIN_NS = 2000000000ull;  // limit of the waits that drain copies and MMAs
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -71,13 +73,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase of the given parity to complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Bounded wait for the phase of the given parity to complete: false once
+// limit_ns have passed without it.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (global_ns() - t0 > WAIT_NS) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
 }
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
@@ -187,6 +190,7 @@ struct TcGroup {
   int total_tiles;
   int chunk;        // K blocks accumulated in TMEM before promotion
   int *err;
+  unsigned long long wait_ns;  // limit of each pipeline wait
 };
 
 __device__ __forceinline__ int find_problem(const TcGroup &g, int t) {
@@ -241,7 +245,8 @@ __global__ void __launch_bounds__(320, 1)
   uint64_t *empty = full + STAGES;
   uint64_t *tfull = empty + STAGES;   // [2]
   uint64_t *tempty = tfull + 2;       // [2]
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+  uint64_t *mdone = tempty + 2;       // every MMA issued has completed
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mdone + 1);
   float *stage = reinterpret_cast<float *>(smem + STAGES * STAGE_BYTES + 256);  // 8 x 4 KB
 
   const int warp = threadIdx.x >> 5;
@@ -249,6 +254,7 @@ __global__ void __launch_bounds__(320, 1)
   const int n_tiles_total = grp.total_tiles;
   const int chunk = grp.chunk;
   int *const err = grp.err;
+  const unsigned long long wait_ns = grp.wait_ns;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -259,6 +265,7 @@ __global__ void __launch_bounds__(320, 1)
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], 8);
     }
+    mbar_init(mdone, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -282,7 +289,7 @@ __global__ void __launch_bounds__(320, 1)
         for (int kb = kb0; kb < kb1; ++kb, ++it) {
           const int s = static_cast<int>(it % STAGES);
           const uint32_t ph = static_cast<uint32_t>(it / STAGES) & 1u;
-          if (!mbar_wait(&empty[s], ph ^ 1u)) {
+          if (!mbar_wait(&empty[s], ph ^ 1u, wait_ns)) {
             atomicExch(err, 1);
             ok = false;
             break;
@@ -299,8 +306,10 @@ __global__ void __launch_bounds__(320, 1)
         }
       }
       // the last load issued into each stage must land before the CTA exits
+      // (also after an expired wait: no copy may outlive the CTA's shared
+      // memory), each with the drain limit
       for (long i = (it > STAGES ? it - STAGES : 0); i < it; ++i) {
-        if (!mbar_wait(&full[i % STAGES], static_cast<uint32_t>(i / STAGES) & 1u))
+        if (!mbar_wait(&full[i % STAGES], static_cast<uint32_t>(i / STAGES) & 1u, DRAIN_NS))
           atomicExch(err, 1);
       }
     }
@@ -319,7 +328,7 @@ __global__ void __launch_bounds__(320, 1)
         const int nch = (nkb + chunk - 1) / chunk;
         for (int cc = 0; cc < nch && ok; ++cc, ++c) {
           const int buf = static_cast<int>(c & 1);
-          if (c >= 2 && !mbar_wait(&tempty[buf], static_cast<uint32_t>((c - 2) >> 1) & 1u)) {
+          if (c >= 2 && !mbar_wait(&tempty[buf], static_cast<uint32_t>((c - 2) >> 1) & 1u, wait_ns)) {
             atomicExch(err, 1);
             ok = false;
             break;
@@ -330,7 +339,7 @@ __global__ void __launch_bounds__(320, 1)
           for (int i = 0, kb = cc * chunk; kb < kend; ++i, ++kb, ++it) {
             const int s = static_cast<int>(it % STAGES);
             const uint32_t ph = static_cast<uint32_t>(it / STAGES) & 1u;
-            if (!mbar_wait(&full[s], ph)) {
+            if (!mbar_wait(&full[s], ph, wait_ns)) {
               atomicExch(err, 1);
               ok = false;
               break;
@@ -355,10 +364,10 @@ __global__ void __launch_bounds__(320, 1)
           mma_commit(&tfull[buf]);
         }
       }
-      if (!ok) {
-        // release the epilogue of every chunk it still waits for
-        for (int b = 0; b < 2; ++b) mma_commit(&tfull[b]);
-      }
+      // every MMA issued must complete before TMEM is freed (after an
+      // expired wait the epilogue no longer waits for them)
+      mma_commit(mdone);
+      if (!mbar_wait(mdone, 0u, DRAIN_NS)) atomicExch(err, 1);
     }
   } else {
     // ---------------- epilogue: 8 warps ----------------
@@ -378,7 +387,7 @@ __global__ void __launch_bounds__(320, 1)
       for (int j = 0; j < HALF; ++j) acc[j] = 0.f;
       for (int cc = 0; cc < nch; ++cc, ++c) {
         const int buf = static_cast<int>(c & 1);
-        if (!mbar_wait(&tfull[buf], static_cast<uint32_t>(c >> 1) & 1u)) {
+        if (!mbar_wait(&tfull[buf], static_cast<uint32_t>(c >> 1) & 1u, wait_ns)) {
           ok = false;
           break;
         }
@@ -514,14 +523,15 @@ void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
   constexpr int STAGE_BYTES = (BM * ROW_BYTES + BN * ROW_BYTES) * (SPLIT ? 2 : 1);
   // stages + barrier block (256 B) + 8 warps x 4 KB staging + alignment slack
   constexpr int SMEM = STAGES * STAGE_BYTES + 256 + 8 * 4096 + 1024;
-  static_assert((2 * STAGES + 4) * 8 + 8 <= 256, "barrier block");
+  static_assert((2 * STAGES + 5) * 8 + 8 <= 256, "barrier block");
   static_assert(SMEM <= 232448, "shared memory budget");
   auto kern = tc_gemm_kernel<BN, STAGES, SPLIT, ET>;
-  static bool attr = false;
-  if (!attr) {
+  // set once per process (thread-safe static initialisation)
+  static const bool attr = [&] {
     CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   static int sms = 0;
   if (!sms) {
     int dev = 0;
@@ -577,6 +587,7 @@ void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
   grp.total_tiles = static_cast<int>(tiles);
   grp.chunk = descs[0].chunk > 0 ? descs[0].chunk : default_chunk(descs[0].tier);
   grp.err = err;
+  grp.wait_ns = tc_wait_limit();
   dim3 grid(static_cast<unsigned>(std::min<long>(tiles, sms)));
   kern<<<grid, 320, SMEM, st>>>(grp);
   LAUNCH_CHECK();
@@ -617,6 +628,16 @@ void dispatch(const TcDesc *d, int n, bool wide, cudaStream_t st, int *err) {
 }
 
 }  // namespace
+
+namespace {
+std::atomic<unsigned long long> g_wait_ns{0};
+}  // namespace
+
+void tc_set_wait_limit(unsigned long long ns) { g_wait_ns.store(ns); }
+unsigned long long tc_wait_limit() {
+  const unsigned long long ns = g_wait_ns.load();
+  return ns ? ns : WAIT_NS;
+}
 
 int tc_k_align(int tier) { return tier_half(tier) ? 64 : 32; }
 

@@ -102,6 +102,11 @@ int tc_pick_bn(long N);
 // tiles already make 8 or more waves.
 int tc_pick_split(long tiles, long nkb, int num_sms);
 int tc_k_align(int tier);
+// Limit of every pipeline wait in the tensor-core kernels launched from now
+// on (ns; 0 restores the default of 2 s). Waits that drain copies and MMAs
+// before a kernel exits keep their own 2 s limit.
+void tc_set_wait_limit(unsigned long long ns);
+unsigned long long tc_wait_limit();
 size_t tc_elem_bytes(int tier);
 
 // Expand/convert operands for gemm_tc from FP64 tensors addressed by tables.

@@ -62,6 +62,12 @@ struct Ctx {
   std::vector<double> fns_occ;
   double stat[16] = {0};
   std::string last_error;
+  // host-side fault injection for tests of the error paths
+  // (cc_set_fault_injection): kind 1 writes NaN into the CCSD residual of
+  // iteration `inject_at`, kind 2 into the sigma vectors of Davidson
+  // iteration `inject_at`; cleared once it has fired
+  int inject_kind = 0, inject_at = 0;
+  void maybe_inject(int kind, int iteration, cplx *target);
 
   // --- lifecycle ---
   void create(int n_occ, int n_virt, int n_aux, const double *eps_host);
@@ -115,9 +121,13 @@ void batch_sigma(std::vector<Ctx *> &sys, const std::vector<int> &k,
 // Lockstep block Davidson; `left` solves l^T H-bar = omega l^T instead
 // (transposed sigma, no graphs); `vecs` (device, per system) receives the
 // nr Ritz vectors [nr][dim] when given.
+// With isolate, a system that cannot start (no converged CCSD, n_roots out
+// of range) or whose iteration turns non-finite stops with its own status
+// (CC_ERR_STATE, CC_ERR_ARG, CC_ERR_NUMERIC) while the others go on;
+// without it such a failure is raised for the whole call.
 void run_ipeom(std::vector<Ctx *> &sys, int nr, double tol, int max_iter, double *omega,
                double *r1w, int *n_iter, int *status, bool use_graph, bool left = false,
-               const std::vector<cplx *> *vecs = nullptr);
+               const std::vector<cplx *> *vecs = nullptr, bool isolate = false);
 void batch_left_sigma(std::vector<Ctx *> &sys, const std::vector<int> &k,
                       const std::vector<const cplx *> &r, const std::vector<cplx *> &s);
 void drop_graphs(const void *ctx);

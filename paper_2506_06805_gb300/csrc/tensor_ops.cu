@@ -7,7 +7,8 @@
 
 namespace cdfns {
 
-unsigned long long g_launches = 0;
+std::atomic<unsigned long long> g_launches{0};
+thread_local unsigned long long t_launches = 0;
 
 namespace {
 

@@ -65,6 +65,72 @@ def test_integrals_against_scalar_loop():
         assert abs(g[p, q, r, s] - ref) <= 1e-15
 
 
+def _fixed_order_scalar(L, p, q, r, s):
+    """One element of Eq. 23 in plain Python floats: P ascending, each
+    complex product as (ar*br - ai*bi, ar*bi + ai*br), term = direct -
+    exchange added to the running sum (Python rounds every operation to
+    nearest, with no fused multiply-add)."""
+    acc_r = 0.0
+    acc_i = 0.0
+    for P in range(L.shape[0]):
+        ar, ai = float(L[P, p, r].real), float(L[P, p, r].imag)
+        br, bi = float(L[P, q, s].real), float(L[P, q, s].imag)
+        cr, ci = float(L[P, p, s].real), float(L[P, p, s].imag)
+        dr, di = float(L[P, q, r].real), float(L[P, q, r].imag)
+        d1r = ar * br - ai * bi
+        d1i = ar * bi + ai * br
+        d2r = cr * dr - ci * di
+        d2i = cr * di + ci * dr
+        acc_r = acc_r + (d1r - d2r)
+        acc_i = acc_i + (d1i - d2i)
+    return acc_r, acc_i
+
+
+def test_fixed_order_integrals_equal_scalar_loop_bit_for_bit():
+    """antisym_fixed_order (the comparator of the bit-exact integral dump)
+    equals the element-by-element scalar loop bit for bit on random blocks,
+    and the unordered einsum form within 1e-15 relative."""
+    o, v = 3, 7
+    eps, L = _system(o, v, 11, seed=4, scale=5.0)
+    n = o + v
+    rng = np.random.default_rng(2)
+    for _ in range(4):
+        lo = rng.integers(0, n - 2, size=4)
+        hi = [int(x) + int(rng.integers(1, 3)) for x in lo]
+        sl = [slice(int(a), b) for a, b in zip(lo, hi)]
+        got = integrals.antisym_fixed_order(L, *sl)
+        ref = integrals.antisym_full(L)[tuple(sl)]
+        assert np.abs(got - ref).max() <= 1e-15 * np.abs(ref).max()
+        for idx in np.ndindex(got.shape):
+            pqrs = [s_.start + k for s_, k in zip(sl, idx)]
+            er, ei = _fixed_order_scalar(L, *pqrs)
+            assert got[idx].real == er and got[idx].imag == ei, (idx, got[idx], er, ei)
+
+
+def test_fixed_order_integrals_exact_on_integer_vectors():
+    """With small-integer Cholesky vectors every product and partial sum is
+    an integer below 2^53, so FP64 evaluation in any order is exact: the
+    result must equal Eq. 23 in exact integer arithmetic, and swapping p, q
+    (or r, s) must negate it bit for bit."""
+    rng = np.random.default_rng(8)
+    X, n = 6, 5
+    L = (rng.integers(-40, 41, size=(X, n, n))
+         + 1j * rng.integers(-40, 41, size=(X, n, n))).astype(np.complex128)
+    full = slice(0, n)
+    got = integrals.antisym_fixed_order(L, full, full, full, full)
+    Li = [[[complex(L[P, a, b]) for b in range(n)] for a in range(n)] for P in range(X)]
+    for p, q, r, s in np.ndindex(n, n, n, n):
+        re = im = 0
+        for P in range(X):
+            d1 = Li[P][p][r] * Li[P][q][s]
+            d2 = Li[P][p][s] * Li[P][q][r]
+            re += int(d1.real) - int(d2.real)
+            im += int(d1.imag) - int(d2.imag)
+        assert got[p, q, r, s] == complex(re, im)
+    assert np.array_equal(got, -got.transpose(1, 0, 2, 3))
+    assert np.array_equal(got, -got.transpose(0, 1, 3, 2))
+
+
 # --- MP2 ---------------------------------------------------------------------
 
 def test_mp2_equals_rayleigh_schroedinger_second_order():
@@ -229,6 +295,38 @@ def test_pole_strengths_at_zero_coupling():
     assert is_1h.sum() == o
     assert np.abs(p[is_1h] - 1).max() <= 1e-12
     assert np.abs(p[~is_1h]).max() <= 1e-12
+
+
+def test_r1_weight_limits():
+    """r1_weight = ||r1||^2 / ||r||^2: exactly 1 for the 1h roots and 0 for
+    the 2h1p roots at zero coupling; unchanged by a complex scale of the
+    vector; and at weak coupling the 2h1p admixture of a 1h root follows
+    first-order perturbation theory, 1 - w -> sum_nu |M_nu,i|^2 /
+    |omega_i - M_nu,nu|^2 (the relative deviation shrinks with lam)."""
+    o, v = 3, 4
+    eps, L0 = _system(o, v, 9, seed=5, scale=6.0)
+    g = integrals.blocks_from_cholesky(0 * L0, o)
+    z1, z2 = np.zeros((o, v), complex), np.zeros((o, o, v, v), complex)
+    H = ipeom.hbar(g, eps, z1, z2)
+    n = ipeom.dim(o, v)
+    w, V = ipeom.dense_roots(H, o, v, n)
+    wts = np.array([ipeom.r1_weight(V[:, k], o) for k in range(n)])
+    assert np.sum(wts == 1.0) == o and np.sum(wts == 0.0) == n - o
+    x = np.random.default_rng(0).standard_normal(n) + 1j
+    assert ipeom.r1_weight((2.5 - 1.5j) * x, o) == pytest.approx(ipeom.r1_weight(x, o), rel=1e-14)
+    devs = []
+    for lam in (0.2, 0.1):
+        L = lam * L0
+        gb = integrals.blocks_from_cholesky(L, o)
+        res = ccsd.solve(gb, eps, tol=1e-13, max_iter=300)
+        Hb = ipeom.hbar(gb, eps, res["t1"], res["t2"])
+        M = ipeom.dense_matrix(Hb, o, v)
+        w, V = ipeom.dense_roots(Hb, o, v, n)
+        k = int(np.argmax([ipeom.r1_weight(V[:, j], o) for j in range(n)]))
+        i = int(np.argmax(np.abs(V[:o, k])))
+        pt = sum(abs(M[nu, i]) ** 2 / abs(w[k] - M[nu, nu]) ** 2 for nu in range(o, n))
+        devs.append(abs((1.0 - ipeom.r1_weight(V[:, k], o)) / pt - 1.0))
+    assert devs[1] < 0.6 * devs[0] and devs[1] < 1e-3
 
 
 # --- closed forms and invariances ---------------------------------------------
