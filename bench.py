@@ -13,6 +13,15 @@ so no flush is needed between steps.
 ``e2e`` repeats the step through the public C ABI from pinned host memory:
 cc_init (H2D copy of eps and L) + ccsd_solve + ipeom_solve + result D2H.
 
+After the timed region (and outside it) the same workload is solved again
+for the metric's accuracy gate and comparator: once with every contraction
+in the split FP16x3 tier, then from those amplitudes in the plain FP64 tier
+until FP64 CCSD converges (one iteration, timed) and through a full FP64
+H-bar build and Davidson (timed). The IPs of the timed run must lie within
+1e-5 Eh of that FP64 solution (else the run fails); the FP64 time-to-roots
+is the timed FP64 CCSD iteration times the CCSD iteration count of the
+timed run, plus the timed FP64 IP-EOM step (labelled "extrapolated").
+
 ``--impl reference`` times the CPU oracle (numpy FP64) on bounded samples
 of the same workload and extrapolates to the same unit.
 """
@@ -33,6 +42,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("IP-EOM-CCSD time-to-roots & ladder TFLOP/s vs plain FP64, "
           "at |ΔIP|≤1e-5 Eh")
+
+# DRAM bytes per ladder call of the current kernels at the medium workload,
+# from the ncu capture summarised in profiles/ (None until it is taken for
+# the kernels as they stand)
+LADDER_TRAFFIC = None
 WORKLOAD = "medium"
 
 
@@ -47,7 +61,51 @@ def parse():
     p.add_argument("--eom-tier", default="fp16x3")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-fp64", action="store_true",
+                   help="skip the FP64 comparator and the accuracy gate")
     return p.parse_args()
+
+
+# |IP - IP(FP64)| the metric allows (Eh)
+IP_GATE_EH = 1e-5
+
+
+def fp64_comparator(P, eps, L, o, c, w_fast, ccsd_iters):
+    """Accuracy gate and FP64 comparator for one workload (outside the timed
+    region). Returns the dict reported under "fp64_comparator"."""
+    import torch
+    nr = c.n_roots
+    with P.System(eps, L, n_occ=o, tier="fp16x3", eom_tier="fp16x3") as s3:
+        s3.ccsd(tol=c.ccsd_tol, max_iter=100)
+        w3, _ = s3.ipeom(nr, tol=c.eom_tol, max_iter=200)
+        t1, t2 = s3.get_amplitudes()
+    with P.System(eps, L, n_occ=o, tier="fp64", eom_tier="fp64") as s64:
+        s64.set_amplitudes(t1, t2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s64.ccsd(tol=c.ccsd_tol, max_iter=5)
+        torch.cuda.synchronize()
+        n64 = s64.ccsd_iterations
+        t_iter = (time.perf_counter() - t0) / max(n64, 1)
+        t0 = time.perf_counter()
+        w64, _ = s64.ipeom(nr, tol=c.eom_tol, max_iter=200)
+        torch.cuda.synchronize()
+        t_eom = time.perf_counter() - t0
+        dav64 = s64.davidson_iterations
+    w64 = np.sort_complex(w64)
+    d_fast = float(np.abs(np.sort_complex(w_fast) - w64).max())
+    d_split = float(np.abs(np.sort_complex(w3) - w64).max())
+    t_fp64 = t_iter * ccsd_iters + t_eom
+    return {
+        "max_dIP_vs_fp64_eh": d_fast, "gate_eh": IP_GATE_EH, "pass": d_fast <= IP_GATE_EH,
+        "max_dIP_fp16x3_vs_fp64_eh": d_split,
+        "fp64_time_to_roots_s": t_fp64,
+        "fp64_kind": (f"extrapolated: one timed FP64 CCSD iteration ({t_iter:.1f} s) x "
+                      f"{ccsd_iters} (the timed run's CCSD iteration count) + the timed FP64 "
+                      f"H-bar build and Davidson ({t_eom:.1f} s, {dav64} iterations)"),
+        "fp64_reference": (f"FP64 CCSD converged ({n64} FP64 iteration(s) from the FP16x3 "
+                           "solution) and FP64 H-bar + Davidson to the workload's tolerances"),
+    }
 
 
 def max_over_ranks(value, device):
@@ -298,6 +356,15 @@ def run_ours(args):
         e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(Lp.nbytes + epsp.nbytes),
                "d2h_bytes_per_step": int(16 + nr * 24)}
 
+    fp64 = None
+    if not args.no_fp64 and r == 0:
+        fp64 = fp64_comparator(P, eps, L, o, c, w, ccsd_iters)
+        fp64["speedup_vs_fp64"] = fp64["fp64_time_to_roots_s"] / (ms / 1e3)
+        if not fp64["pass"]:
+            print(json.dumps({"error": "accuracy gate failed", "fp64_comparator": fp64}))
+            raise SystemExit(f"max |dIP| vs FP64 {fp64['max_dIP_vs_fp64_eh']:.3e} Eh "
+                             f"exceeds {IP_GATE_EH:.0e} Eh")
+
     peaks, src = measured_peaks()
     # the ladder runs inside a seconds-long step: the sustained dense rate of
     # the operand type (fp16 = bf16 rate; tf32 = half of it, nominal ratio)
@@ -309,9 +376,30 @@ def run_ours(args):
         "bound": "tensor",
         "kernel": f"particle-particle ladder (tcgen05 kind::{kind} GEMMs + antisymmetrise)",
         "achieved": ladder_tf, "peak": peak, "unit": "TFLOP/s",
-        "frac": (ladder_tf / peak) if ladder_tf else None, "traffic": None,
+        "frac": (ladder_tf / peak) if ladder_tf else None, "traffic": LADDER_TRAFFIC,
         "peak_source": f"{src} bf16 sustained x {ratio} (of measured)",
         "algorithmic_flops_per_call": st1["ladder_flops"], "ms_per_call": ladder_ms,
+    }
+    # the IP sigma builds of the timed steps (all roots of a Davidson round
+    # in one batched build): algorithmic flops / device time, and the
+    # executed tensor rate (split tiers run three products per term)
+    sig_calls = st1["sigma_calls"] - st0["sigma_calls"]
+    sig_ms = st1["sigma_ms"] - st0["sigma_ms"]
+    sig_fl = st1["sigma_flops"] - st0["sigma_flops"]
+    sig_vec = st1["sigma_vectors"] - st0["sigma_vectors"]
+    eratio = 1.0 if args.eom_tier in ("fp16", "fp16x3", "bf16x3") else 0.5
+    nprod = 3 if args.eom_tier in ("fp16x3", "bf16x3", "tf32x3") else 1
+    sig_alg = sig_fl / (sig_ms * 1e-3) / 1e12 if sig_ms > 0 else None
+    roofline_sigma = {
+        "bound": "tensor", "kernel": f"IP-EOM sigma build ({args.eom_tier}, grouped tcgen05 launch)",
+        "achieved": sig_alg * nprod if sig_alg else None, "peak": base * eratio,
+        "unit": "TFLOP/s", "frac": (sig_alg * nprod / (base * eratio)) if sig_alg else None,
+        "traffic": None, "algorithmic_tflops": sig_alg,
+        "executed_products_per_term": nprod,
+        "ms_per_build": sig_ms / max(sig_calls, 1), "builds_per_step": sig_calls / args.steps,
+        "vectors_per_build": sig_vec / max(sig_calls, 1),
+        "algorithmic_flops_per_build": sig_fl / max(sig_calls, 1),
+        "peak_source": f"{src} bf16 sustained x {eratio} (of measured)",
     }
     line = {
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world,
@@ -320,7 +408,8 @@ def run_ours(args):
         "dtype": f"{args.tier}/{args.eom_tier} tensor (c128 FP64 control)",
         "data": "synthetic",
         "config": workload_config(args.config, c, world),
-        "roofline": roofline, "clocks": clocks.summary(), "gpu_launches": launches,
+        "roofline": roofline, "roofline_sigma": roofline_sigma,
+        "fp64_comparator": fp64, "clocks": clocks.summary(), "gpu_launches": launches,
         "ladder_tflops": ladder_tf, "ccsd_iterations": ccsd_iters,
         "e_corr": [e.real, e.imag], "ips_eh": [float(x) for x in w.real],
         "kramers_max_split_eh": kramers_split, "wall_s_per_step": wall / args.steps,

@@ -364,7 +364,7 @@ int cc_selftest_conversions(const double *x_dev, long n, long long *mismatches);
  */
 int cc_dump_integrals(cc_ctx *ctx, int block, double *out_host);
 
-/* Timing and counters of the last solver calls (host double[n], n <= 16):
+/* Timing and counters of the last solver calls (host double[n], n <= 24):
  * [0] ladder ms (sum over calls), [1] ladder calls, [2] ladder algorithmic
  * flops per call, [3] fns ms, [4] ccsd ms, [5] ipeom ms, [6] kernel launches
  * since the context was created, [7] ccsd iterations, [8] Davidson
@@ -375,7 +375,10 @@ int cc_dump_integrals(cc_ctx *ctx, int block, double *out_host);
  * short), [13] high-water mark of the device bytes held during the CCSD
  * iterations of the last ccsd_solve, [14] device bytes held now, [15] the
  * CCSD iteration after which the residual moved from a one-product tier to
- * its split form (0: it did not). */
+ * its split form (0: it did not), [16] device ms of the IP sigma builds (sum;
+ * a batched build is charged to every system in it), [17] sigma builds,
+ * [18] algorithmic flops of this system's sigma contractions (8 per complex
+ * multiply-add, sum), [19] sigma vectors built, [20..23] reserved (0). */
 int cc_get_stats(const cc_ctx *ctx, double *out_host, int n);
 
 /*

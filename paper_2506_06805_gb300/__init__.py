@@ -462,12 +462,13 @@ class System:
         return out
 
     def stats(self):
-        s = np.zeros(16)
-        _check(lib().cc_get_stats(self._ctx, _dptr(s), 16), self._ctx)
+        s = np.zeros(20)
+        _check(lib().cc_get_stats(self._ctx, _dptr(s), 20), self._ctx)
         keys = ["ladder_ms", "ladder_calls", "ladder_flops", "fns_ms", "ccsd_ms",
                 "ipeom_ms", "launches", "ccsd_iter", "davidson_iter", "ladder_tc_ms",
                 "ladder_tc_launches", "device_peak_bytes", "diis_depth",
-                "ccsd_loop_peak_bytes", "device_bytes_held", "ccsd_escalated_at"]
+                "ccsd_loop_peak_bytes", "device_bytes_held", "ccsd_escalated_at",
+                "sigma_ms", "sigma_calls", "sigma_flops", "sigma_vectors"]
         return {k: float(s[i]) for i, k in enumerate(keys)}
 
 

@@ -529,8 +529,8 @@ int cc_dump_integrals(cc_ctx *ctx, int block, double *out_host) {
 }
 
 int cc_get_stats(const cc_ctx *ctx, double *out, int n) {
-  if (!ctx || !out || n < 0 || n > 16) return CC_ERR_ARG;
-  double s[16];
+  if (!ctx || !out || n < 0 || n > 24) return CC_ERR_ARG;
+  double s[24];
   std::memcpy(s, ctx->c.stat, sizeof(s));
   s[6] = static_cast<double>(cdfns::g_launches.load());
   s[11] = static_cast<double>(ctx->c.al.peak);

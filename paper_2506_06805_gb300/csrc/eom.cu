@@ -45,6 +45,7 @@ void d2d(void *dst, const void *src, size_t n, cudaStream_t st) {
 struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
   unsigned long long launches = 0;
+  std::vector<double> flops;  // algorithmic flops of each system's contractions
 };
 std::mutex g_graph_mu;
 std::map<std::vector<long>, GraphEntry> g_graphs;
@@ -176,6 +177,13 @@ void batch_sigma(std::vector<Ctx *> &sys, const std::vector<int> &k,
     return kk;
   };
   key = make_key();
+  // device time of the sigma build (the statistics of every system in the
+  // batch are charged with it) and its algorithmic flops per system
+  auto tm = std::make_shared<Ctx::EventPair>();
+  CUDA_CHECK(cudaEventCreate(&tm->e0));
+  CUDA_CHECK(cudaEventCreate(&tm->e1));
+  CUDA_CHECK(cudaEventRecord(tm->e0, cs));
+  std::vector<double> fl(sys.size(), 0.0);
   try {
     GraphEntry *ge = nullptr;
     if (use_graph) {
@@ -186,10 +194,13 @@ void batch_sigma(std::vector<Ctx *> &sys, const std::vector<int> &k,
     if (ge) {
       CUDA_CHECK(cudaGraphLaunch(ge->exec, cs));
       count_launch(ge->launches);
+      fl = ge->flops;
     } else {
       // run once directly (allocates and packs whatever is new), then capture
       const unsigned long long l0 = t_launches;
+      for (size_t q = 0; q < sys.size(); ++q) fl[q] = -sys[q]->eng.flops;
       sigma_body(sys, k, cs);
+      for (size_t q = 0; q < sys.size(); ++q) fl[q] += sys[q]->eng.flops;
       const unsigned long long nl = t_launches - l0;
       if (use_graph) {
         // The direct pass may have (re)allocated buffers: key the graph on
@@ -210,6 +221,7 @@ void batch_sigma(std::vector<Ctx *> &sys, const std::vector<int> &k,
         if (ok && graph && cudaGraphInstantiate(&e.exec, graph, 0) == cudaSuccess &&
             make_key() == key) {
           e.launches = nl;
+          e.flops = fl;
           std::lock_guard<std::mutex> lk(g_graph_mu);
           g_graphs[key] = e;
         } else if (e.exec) {
@@ -226,6 +238,12 @@ void batch_sigma(std::vector<Ctx *> &sys, const std::vector<int> &k,
     for (size_t q = 0; q < sys.size(); ++q) sys[q]->eng.st = saved[q];
     cudaEventDestroy(ev);
     throw;
+  }
+  CUDA_CHECK(cudaEventRecord(tm->e1, cs));
+  for (size_t q = 0; q < sys.size(); ++q) {
+    sys[q]->sig_timing.push_back(tm);
+    sys[q]->stat[18] += fl[q];
+    sys[q]->stat[19] += k[q];
   }
   for (size_t q = 0; q < sys.size(); ++q) {
     Ctx &c = *sys[q];
@@ -590,6 +608,7 @@ void run_ipeom(std::vector<Ctx *> &sys, int nr, double tol, int max_iter, double
   }
   const double dt = now_ms() - t0;
   for (Ctx *c : sys) c->stat[5] += dt / sys.size();
+  for (Ctx *c : sys) c->settle_sigma_timing();
   for (Ctx *c : sys) c->eng.trace_flush();
 }
 

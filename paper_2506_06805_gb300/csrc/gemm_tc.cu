@@ -176,6 +176,7 @@ struct alignas(64) TcProblem {
   const float *amax_a, *amax_b;  // FP16 operand scales (nullptr: none)
   float *amax_out;  // TC_OUT_F32: max |written value| x amax_mul (nullptr: none)
   float amax_mul;
+  const float *out_bound;  // TC_OUT_F16: bound on |D| that sets the fp16 scale
   int num_kb;       // K blocks of 128 bytes per row
   int kb_per_split;
   int k_splits, m_tiles, n_tiles;
@@ -414,6 +415,8 @@ __global__ void __launch_bounds__(320, 1)
       // undo the FP16 operand scales (an exact power of two)
       float usc = 1.0f;
       if (args.amax_a) usc = 1.0f / (fp16_scale(*args.amax_a) * fp16_scale(*args.amax_b));
+      // fp16 output: the scale of the stored values (a power of two)
+      if (args.out == TC_OUT_F16) usc *= fp16_scale(*args.out_bound);
       const long nbase = static_cast<long>(n_tile) * BN + h * HALF;
       const long mbase = static_cast<long>(m_tile) * (BM / 2) + q * 16;
 #pragma unroll
@@ -430,7 +433,10 @@ __global__ void __launch_bounds__(320, 1)
           const float im = usc * stg[(2 * rr + 1) * 32 + (lane ^ (2 * rr + 1))];
           const long mc = mbase + rr;
           if (!col_ok || mc >= args.M) continue;
-          if (args.out == TC_OUT_F32) {
+          if (args.out == TC_OUT_F16) {
+            __half2 *Ch = reinterpret_cast<__half2 *>(args.C);
+            Ch[mc * args.ldc + n] = __floats2half2_rn(re, im);
+          } else if (args.out == TC_OUT_F32) {
             float2 *Cf = reinterpret_cast<float2 *>(args.C);
             Cf[mc * args.ldc + n] = make_float2(re, im);
             omax = fmaxf(omax, fmaxf(fabsf(re), fabsf(im)));
@@ -576,6 +582,8 @@ void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
     a.amax_b = g.amax_b;
     a.amax_out = g.out == TC_OUT_F32 ? g.amax_out : nullptr;
     a.amax_mul = g.amax_mul;
+    a.out_bound = g.out_bound;
+    if (g.out == TC_OUT_F16 && !g.out_bound) fail(CC_ERR_ARG, "gemm_tc: fp16 output needs a bound");
     if ((g.amax_a == nullptr) != (g.amax_b == nullptr))
       fail(CC_ERR_ARG, "gemm_tc: FP16 operand scales come in pairs");
     a.tile_start = static_cast<int>(tiles);

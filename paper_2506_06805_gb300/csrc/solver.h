@@ -1,6 +1,7 @@
 // Solver state of one system and the host orchestration of the hot path.
 #pragma once
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -60,7 +61,20 @@ struct Ctx {
   long sig_gen = 0;  // bumped whenever H-bar or the sigma workspace changes
 
   std::vector<double> fns_occ;
-  double stat[16] = {0};
+  double stat[24] = {0};
+  // CUDA events around each batched sigma build this context took part in,
+  // shared by the systems of that batch (destroyed with the last reference)
+  struct EventPair {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~EventPair() {
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+    }
+  };
+  std::vector<std::shared_ptr<EventPair>> sig_timing;
+  // adds the device time of the recorded sigma builds to stat[16], their
+  // count to stat[17], and releases the events
+  void settle_sigma_timing();
   std::string last_error;
   // host-side fault injection for tests of the error paths
   // (cc_set_fault_injection): kind 1 writes NaN into the CCSD residual of
