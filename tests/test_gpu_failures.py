@@ -152,10 +152,12 @@ def test_batch_solve_matches_oracle():
         for s in systems:
             s.close()
     assert np.all(status == 0)
+    # TF32x3 tolerances of the end-to-end tests (the split tier's FP32-class
+    # accumulation leaves ~1e-6 relative in E_corr)
     for q, (o, v, X, seed) in enumerate(SHAPES):
         e_ref, w_ref = _oracle(*_inputs(o, v, X, seed), o, 4)
-        assert abs(e[q] - e_ref) <= 1e-8
-        assert np.abs(np.sort_complex(w[q]) - np.sort_complex(w_ref)).max() <= 1e-8
+        assert abs(e[q] - e_ref) <= 1e-7
+        assert np.abs(np.sort_complex(w[q]) - np.sort_complex(w_ref)).max() <= 1e-7
 
 
 def test_per_context_allocator():
