@@ -376,6 +376,7 @@ int cc_ladder_dev(cc_ctx *ctx, const double *tau_dev, double *out_dev) {
     c.ladder(c.Lvv.c(), reinterpret_cast<const cdfns::cplx *>(tau_dev),
              reinterpret_cast<cdfns::cplx *>(out_dev), c.tier);
     CUDA_CHECK(cudaStreamSynchronize(c.st));
+    c.eng.trace_flush();
     return CC_OK;
   });
 }

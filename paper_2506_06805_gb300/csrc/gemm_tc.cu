@@ -97,16 +97,72 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
+// TMEM allocation of one CTA, or (PAIR) the collective allocation of a CTA
+// pair: one warp of each CTA executes it and both receive the same address.
+template <bool PAIR>
 __device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                   smem_u32(slot)),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  if constexpr (PAIR) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  } else {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
 }
+template <bool PAIR>
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-               : "memory");
+  if constexpr (PAIR)
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+  else
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+// --- CTA pairs (clusters of two) ---
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_count_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" :::
+                   "memory");
+}
+// shared::cluster address of the same shared-memory offset in CTA rank 0
+__device__ __forceinline__ uint32_t leader_addr(uint32_t a) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, 0;" : "=r"(r) : "r"(a));
+  return r;
+}
+// arrive on an mbarrier given by its shared::cluster address
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t a) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(a) : "memory");
+}
+// TMA load into this CTA's shared memory whose completion is counted on the
+// barrier at shared::cluster address bar (the leader's, in a CTA pair)
+__device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map, uint32_t bar,
+                                                 int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cta.global.tile.mbarrier::complete_tx::bytes.cta_group::2"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      : "memory");
 }
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
 // 1024 bytes apart (SBO), version 1, tile base 1024-byte aligned.
@@ -124,10 +180,20 @@ __host__ __device__ constexpr uint32_t make_idesc(int m, int n, uint32_t ab_type
   return (1u << 4) | (ab_type << 7) | (ab_type << 10) |
          (static_cast<uint32_t>(n >> 3) << 17) | (static_cast<uint32_t>(m >> 4) << 24);
 }
-template <bool BF16>
+template <bool BF16, bool PAIR>
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                     uint32_t acc) {
-  if constexpr (BF16) {
+  if constexpr (PAIR && BF16) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else if constexpr (PAIR) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else if constexpr (BF16) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
@@ -139,11 +205,35 @@ __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uin
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
   }
 }
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
+// Arrive on bar once the MMAs issued so far have completed: in this CTA, or
+// (PAIR) at the same offset in both CTAs of the pair.
+template <bool PAIR>
+__device__ __forceinline__ void mma_commit_both(uint64_t *bar) {
+  if constexpr (PAIR)
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(smem_u32(bar)),
+        "h"(static_cast<uint16_t>(3))
+        : "memory");
+  else
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+// Same, arriving only on the issuing CTA's barrier.
+template <bool PAIR>
+__device__ __forceinline__ void mma_commit_self(uint64_t *bar) {
+  if constexpr (PAIR)
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+  else
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
 }
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
@@ -225,17 +315,28 @@ __device__ __forceinline__ void tile_coords(const TcProblem &a, int t, int &m, i
 // accumulation only ever spans one chunk, which bounds its truncation bias
 // independently of K. Chunk and stage counters run on across tiles, so the
 // MMA of the next tile overlaps the epilogue stores of the previous one.
+//
+// PAIR: the CTAs run as clusters of two on a pair of SMs (tcgen05
+// cta_group::2). A work unit is then a 256-row tile: CTA r of the pair loads
+// rows [128 r, 128 r + 128) of A and rows [BN/2 r, BN/2 r + BN/2) of B for
+// each K block into its own shared memory, both signalling the leader's
+// (rank 0) stage barrier; the leader issues M = 256 MMAs that read both
+// CTAs' operands (so each SM streams half of B instead of all of it) and
+// write each CTA's 128 accumulator rows into that CTA's TMEM; its commits
+// arrive on the barriers of both CTAs. Each CTA's epilogue drains its own
+// rows and tells the leader, whose TMEM-free barrier counts both CTAs' warps.
 // ET: operand type, 0 tf32 (kind::tf32), 1 bf16 / 2 fp16 (kind::f16)
-template <int BN, int STAGES, bool SPLIT, int ET>
+template <int BN, int STAGES, bool SPLIT, int ET, bool PAIR>
 __global__ void __launch_bounds__(320, 1)
     tc_gemm_kernel(const __grid_constant__ TcGroup grp) {
   constexpr int A_BYTES = BM * ROW_BYTES;
-  constexpr int B_BYTES = BN * ROW_BYTES;
+  constexpr int B_BYTES = (PAIR ? BN / 2 : BN) * ROW_BYTES;  // this CTA's part of B
   constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * (SPLIT ? 2 : 1);
+  constexpr int UNIT_ROWS = PAIR ? 2 * BM : BM;  // real rows per work unit
   constexpr bool F16K = ET != 0;                 // kind::f16 (bf16 or fp16)
   constexpr int K_ELEMS = F16K ? 64 : 32;        // elements per 128-byte row
   constexpr int MMA_K_BYTES = 32;                // K per MMA: 8 tf32 / 16 bf16
-  constexpr uint32_t IDESC = make_idesc(BM, BN, ET == 0 ? 2u : (ET == 1 ? 1u : 0u));
+  constexpr uint32_t IDESC = make_idesc(UNIT_ROWS, BN, ET == 0 ? 2u : (ET == 1 ? 1u : 0u));
   constexpr int HALF = BN / 2;                   // columns per epilogue warp
   constexpr uint32_t TMEM_COLS = 2 * BN;
 
@@ -252,27 +353,35 @@ __global__ void __launch_bounds__(320, 1)
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int n_tiles_total = grp.total_tiles;
+  const int n_units = grp.total_tiles;
   const int chunk = grp.chunk;
   int *const err = grp.err;
   const unsigned long long wait_ns = grp.wait_ns;
+  // position of this CTA (pair) in the persistent walk over work units; the
+  // special registers are re-read at each use (asm volatile) rather than
+  // held live through the loops, which keeps the epilogue warps within their
+  // register budget
+#define TC_RANK (PAIR ? static_cast<int>(cluster_rank()) : 0)
+#define TC_UNIT0 (PAIR ? static_cast<int>(cluster_id_x()) : static_cast<int>(blockIdx.x))
+#define TC_USTEP (PAIR ? static_cast<int>(cluster_count_x()) : static_cast<int>(gridDim.x))
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
+      mbar_init(&full[s], 1);   // the (leader's) producer arrival + the bytes of the stage
       mbar_init(&empty[s], 1);  // released by the MMA warp's commit
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 8);
+      mbar_init(&tempty[b], PAIR ? 16 : 8);  // the epilogue warps (of both CTAs)
     }
     mbar_init(mdone, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (warp == 9) tmem_alloc(tmem_slot, TMEM_COLS);
+  if (warp == 9) tmem_alloc<PAIR>(tmem_slot, TMEM_COLS);
   tc_fence_before();
   __syncthreads();
+  if constexpr (PAIR) cluster_sync_all();  // both CTAs' barriers exist before any copy
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -281,12 +390,14 @@ __global__ void __launch_bounds__(320, 1)
       // ---------------- TMA producer ----------------
       long it = 0;  // k blocks issued so far (all tiles)
       bool ok = true;
-      for (int t = blockIdx.x; t < n_tiles_total && ok; t += gridDim.x) {
+      for (int t = TC_UNIT0; t < n_units && ok; t += TC_USTEP) {
         const TcProblem &P = grp.p[find_problem(grp, t)];
         int m_tile, n_tile, z;
         tile_coords(P, t - P.tile_start, m_tile, n_tile, z);
         const int kb0 = z * P.kb_per_split;
         const int kb1 = min(P.num_kb, kb0 + P.kb_per_split);
+        const int ya = m_tile * UNIT_ROWS + TC_RANK * BM;
+        const int yb = PAIR ? n_tile * BN + TC_RANK * (BN / 2) : n_tile * BN;
         for (int kb = kb0; kb < kb1; ++kb, ++it) {
           const int s = static_cast<int>(it % STAGES);
           const uint32_t ph = static_cast<uint32_t>(it / STAGES) & 1u;
@@ -296,31 +407,45 @@ __global__ void __launch_bounds__(320, 1)
             break;
           }
           uint8_t *st = smem + s * STAGE_BYTES;
-          mbar_expect_tx(&full[s], STAGE_BYTES);
           const int kx = kb * K_ELEMS;
-          tma_load_2d(st, &P.mA, &full[s], kx, m_tile * BM);
-          tma_load_2d(st + A_BYTES, &P.mB, &full[s], kx, n_tile * BN);
-          if constexpr (SPLIT) {
-            tma_load_2d(st + A_BYTES + B_BYTES, &P.mAlo, &full[s], kx, m_tile * BM);
-            tma_load_2d(st + 2 * A_BYTES + B_BYTES, &P.mBlo, &full[s], kx, n_tile * BN);
+          if constexpr (PAIR) {
+            if (TC_RANK == 0) mbar_expect_tx(&full[s], 2 * STAGE_BYTES);
+            const uint32_t fb = leader_addr(smem_u32(&full[s]));
+            tma_load_2d_pair(st, &P.mA, fb, kx, ya);
+            tma_load_2d_pair(st + A_BYTES, &P.mB, fb, kx, yb);
+            if constexpr (SPLIT) {
+              tma_load_2d_pair(st + A_BYTES + B_BYTES, &P.mAlo, fb, kx, ya);
+              tma_load_2d_pair(st + 2 * A_BYTES + B_BYTES, &P.mBlo, fb, kx, yb);
+            }
+          } else {
+            mbar_expect_tx(&full[s], STAGE_BYTES);
+            tma_load_2d(st, &P.mA, &full[s], kx, ya);
+            tma_load_2d(st + A_BYTES, &P.mB, &full[s], kx, yb);
+            if constexpr (SPLIT) {
+              tma_load_2d(st + A_BYTES + B_BYTES, &P.mAlo, &full[s], kx, ya);
+              tma_load_2d(st + 2 * A_BYTES + B_BYTES, &P.mBlo, &full[s], kx, yb);
+            }
           }
         }
       }
       // the last load issued into each stage must land before the CTA exits
       // (also after an expired wait: no copy may outlive the CTA's shared
-      // memory), each with the drain limit
-      for (long i = (it > STAGES ? it - STAGES : 0); i < it; ++i) {
-        if (!mbar_wait(&full[i % STAGES], static_cast<uint32_t>(i / STAGES) & 1u, DRAIN_NS))
-          atomicExch(err, 1);
+      // memory), each with the drain limit; in a pair the leader's barriers
+      // count the bytes of both CTAs
+      if (TC_RANK == 0) {
+        for (long i = (it > STAGES ? it - STAGES : 0); i < it; ++i) {
+          if (!mbar_wait(&full[i % STAGES], static_cast<uint32_t>(i / STAGES) & 1u, DRAIN_NS))
+            atomicExch(err, 1);
+        }
       }
     }
   } else if (warp == 9) {
-    if (lane == 0) {
-      // ---------------- MMA issuer ----------------
+    if (lane == 0 && TC_RANK == 0) {
+      // ---------------- MMA issuer (the leader of a pair) ----------------
       long it = 0;  // k blocks consumed (all tiles)
       long c = 0;   // chunks issued (all tiles)
       bool ok = true;
-      for (int t = blockIdx.x; t < n_tiles_total && ok; t += gridDim.x) {
+      for (int t = TC_UNIT0; t < n_units && ok; t += TC_USTEP) {
         const TcProblem &P = grp.p[find_problem(grp, t)];
         int m_tile, n_tile, z;
         tile_coords(P, t - P.tile_start, m_tile, n_tile, z);
@@ -354,20 +479,20 @@ __global__ void __launch_bounds__(320, 1)
             for (int kk = 0; kk < ROW_BYTES / MMA_K_BYTES; ++kk) {
               const uint64_t da = sw128_desc(a0 + kk * MMA_K_BYTES);
               const uint64_t db = sw128_desc(b0 + kk * MMA_K_BYTES);
-              mma<F16K>(dt, da, db, IDESC, (i > 0 || kk > 0) ? 1u : 0u);
+              mma<F16K, PAIR>(dt, da, db, IDESC, (i > 0 || kk > 0) ? 1u : 0u);
               if constexpr (SPLIT) {
-                mma<F16K>(dt, da, sw128_desc(blo + kk * MMA_K_BYTES), IDESC, 1u);
-                mma<F16K>(dt, sw128_desc(alo + kk * MMA_K_BYTES), db, IDESC, 1u);
+                mma<F16K, PAIR>(dt, da, sw128_desc(blo + kk * MMA_K_BYTES), IDESC, 1u);
+                mma<F16K, PAIR>(dt, sw128_desc(alo + kk * MMA_K_BYTES), db, IDESC, 1u);
               }
             }
-            mma_commit(&empty[s]);
+            mma_commit_both<PAIR>(&empty[s]);
           }
-          mma_commit(&tfull[buf]);
+          mma_commit_both<PAIR>(&tfull[buf]);
         }
       }
       // every MMA issued must complete before TMEM is freed (after an
       // expired wait the epilogue no longer waits for them)
-      mma_commit(mdone);
+      mma_commit_self<PAIR>(mdone);
       if (!mbar_wait(mdone, 0u, DRAIN_NS)) atomicExch(err, 1);
     }
   } else {
@@ -376,7 +501,7 @@ __global__ void __launch_bounds__(320, 1)
     const int h = warp >> 2;
     long c = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < n_tiles_total && ok; t += gridDim.x) {
+    for (int t = TC_UNIT0; t < n_units && ok; t += TC_USTEP) {
       const TcProblem &args = grp.p[find_problem(grp, t)];
       int m_tile, n_tile, z;
       tile_coords(args, t - args.tile_start, m_tile, n_tile, z);
@@ -403,7 +528,12 @@ __global__ void __launch_bounds__(320, 1)
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty[buf]);
+        if (lane == 0) {
+          if constexpr (PAIR)
+            mbar_arrive_cluster(leader_addr(smem_u32(&tempty[buf])));
+          else
+            mbar_arrive(&tempty[buf]);
+        }
       }
       if (!ok) break;
       // Write-out through a per-warp 32 x 32 float staging block (XOR
@@ -418,7 +548,7 @@ __global__ void __launch_bounds__(320, 1)
       // fp16 output: the scale of the stored values (a power of two)
       if (args.out == TC_OUT_F16) usc *= fp16_scale(*args.out_bound);
       const long nbase = static_cast<long>(n_tile) * BN + h * HALF;
-      const long mbase = static_cast<long>(m_tile) * (BM / 2) + q * 16;
+      const long mbase = (static_cast<long>(m_tile) * UNIT_ROWS + TC_RANK * BM) / 2 + q * 16;
 #pragma unroll
       for (int j = 0; j < HALF; j += 32) {
 #pragma unroll
@@ -476,12 +606,26 @@ __global__ void __launch_bounds__(320, 1)
     if (!ok && lane == 0) atomicExch(err, 1);
   }
   tc_fence_before();
+  if constexpr (PAIR) {
+    // after an expired wait anywhere, let the copies a CTA of the pair may
+    // still have in flight into its shared memory land (the leader's stage
+    // barriers only track the phases it armed) before either CTA exits
+    if (threadIdx.x == 0 && *reinterpret_cast<volatile int *>(err)) {
+      const unsigned long long t0 = global_ns();
+      while (global_ns() - t0 < 50000000ull) {
+      }
+    }
+  }
   __syncthreads();
+  if constexpr (PAIR) cluster_sync_all();  // the leader's MMAs into both TMEMs are done
   if (warp == 9) {
     __syncwarp();
     tc_fence_after();
-    tmem_dealloc(tmem, TMEM_COLS);
+    tmem_dealloc<PAIR>(tmem, TMEM_COLS);
   }
+#undef TC_RANK
+#undef TC_UNIT0
+#undef TC_USTEP
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
@@ -524,14 +668,16 @@ CUtensorMap make_map(const void *base, long rows, long kp, int box_rows, int et)
 // less room for the accumulation bias of a longer chunk.
 inline int default_chunk(int tier) { return (tier == TIER_TF32 || tier == TIER_FP16) ? 8 : 4; }
 
-template <int BN, int STAGES, bool SPLIT, int ET>
+template <int BN, int STAGES, bool SPLIT, int ET, bool PAIR>
 void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
-  constexpr int STAGE_BYTES = (BM * ROW_BYTES + BN * ROW_BYTES) * (SPLIT ? 2 : 1);
+  constexpr int B_ROWS = PAIR ? BN / 2 : BN;     // B rows per CTA and K block
+  constexpr int UNIT_ROWS = PAIR ? 2 * BM : BM;  // real rows per work unit
+  constexpr int STAGE_BYTES = (BM * ROW_BYTES + B_ROWS * ROW_BYTES) * (SPLIT ? 2 : 1);
   // stages + barrier block (256 B) + 8 warps x 4 KB staging + alignment slack
   constexpr int SMEM = STAGES * STAGE_BYTES + 256 + 8 * 4096 + 1024;
   static_assert((2 * STAGES + 5) * 8 + 8 <= 256, "barrier block");
   static_assert(SMEM <= 232448, "shared memory budget");
-  auto kern = tc_gemm_kernel<BN, STAGES, SPLIT, ET>;
+  auto kern = tc_gemm_kernel<BN, STAGES, SPLIT, ET, PAIR>;
   // set once per process (thread-safe static initialisation)
   static const bool attr = [&] {
     CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
@@ -554,20 +700,20 @@ void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
     TcProblem &a = grp.p[np++];
     const long mr = 2 * g.M;
     a.mA = make_map(g.A, mr, g.Kp, BM, ET);
-    a.mB = make_map(g.B, g.N, g.Kp, BN, ET);
+    a.mB = make_map(g.B, g.N, g.Kp, B_ROWS, ET);
     a.mAlo = SPLIT ? make_map(g.Alo, mr, g.Kp, BM, ET) : a.mA;
-    a.mBlo = SPLIT ? make_map(g.Blo, g.N, g.Kp, BN, ET) : a.mB;
+    a.mBlo = SPLIT ? make_map(g.Blo, g.N, g.Kp, B_ROWS, ET) : a.mB;
     a.M = g.M;
     a.N = g.N;
     a.num_kb = static_cast<int>(g.Kp / (ET != 0 ? 64 : 32));
     const int sk = std::max(1, std::min(g.split_k, a.num_kb));
     a.kb_per_split = (a.num_kb + sk - 1) / sk;
     a.k_splits = (a.num_kb + a.kb_per_split - 1) / a.kb_per_split;
-    a.m_tiles = static_cast<int>((mr + BM - 1) / BM);
+    a.m_tiles = static_cast<int>((mr + UNIT_ROWS - 1) / UNIT_ROWS);
     a.n_tiles = static_cast<int>((g.N + BN - 1) / BN);
-    // raster groups: as many A panels (128 rows x the K range of a split) as
-    // fit in ~24 MB of L2 share each B panel while it is resident
-    const double panel = static_cast<double>(BM) * a.kb_per_split * ROW_BYTES * (SPLIT ? 2 : 1);
+    // raster groups: as many A panels (a unit's rows x the K range of a
+    // split) as fit in ~24 MB of L2 share each B panel while it is resident
+    const double panel = static_cast<double>(UNIT_ROWS) * a.kb_per_split * ROW_BYTES * (SPLIT ? 2 : 1);
     a.group_m = g.group_m > 0 ? std::min(g.group_m, a.m_tiles)
                               : static_cast<int>(std::max(1.0, std::min<double>(a.m_tiles, 24.0e6 / panel)));
     a.out = g.out;
@@ -596,8 +742,32 @@ void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
   grp.chunk = descs[0].chunk > 0 ? descs[0].chunk : default_chunk(descs[0].tier);
   grp.err = err;
   grp.wait_ns = tc_wait_limit();
-  dim3 grid(static_cast<unsigned>(std::min<long>(tiles, sms)));
-  kern<<<grid, 320, SMEM, st>>>(grp);
+  if constexpr (!PAIR) {
+    dim3 grid(static_cast<unsigned>(std::min<long>(tiles, sms)));
+    kern<<<grid, 320, SMEM, st>>>(grp);
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(320);
+    cfg.dynamicSmemBytes = SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    // persistent pairs: as many clusters as can be resident at once
+    static const int max_clusters = [&] {
+      int mc = 0;
+      cfg.gridDim = dim3(static_cast<unsigned>(2 * (sms / 2)));
+      CUDA_CHECK(cudaOccupancyMaxActiveClusters(&mc, kern, &cfg));
+      if (mc < 1) fail(CC_ERR_UNSUPPORTED, "gemm_tc: no resident CTA pair");
+      return mc;
+    }();
+    cfg.gridDim = dim3(static_cast<unsigned>(2 * std::min<long>(tiles, max_clusters)));
+    CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, grp));
+  }
   LAUNCH_CHECK();
   count_launch();
 }
@@ -608,27 +778,51 @@ void check_desc(const TcDesc &g) {
     fail(CC_ERR_ARG, "gemm_tc: operands must be 16-byte aligned");
 }
 
+// CTA pairs (cta_group::2) for wide tiles: on unless CDFNS_PAIR is "0"
+// (read once), and used when the launch has enough 256-row units to give
+// every SM pair one.
+bool pair_enabled() {
+  static const bool on = [] {
+    const char *e = std::getenv("CDFNS_PAIR");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+long pair_units(const TcDesc *d, int n) {
+  long u = 0;
+  for (int q = 0; q < n; ++q)
+    if (d[q].M > 0 && d[q].N > 0) u += ((2 * d[q].M + 255) / 256) * ((d[q].N + 255) / 256);
+  return u;
+}
+
 void dispatch(const TcDesc *d, int n, bool wide, cudaStream_t st, int *err) {
+  const bool pair = wide && pair_enabled() && pair_units(d, n) >= 76;
   switch (d[0].tier) {
     case TIER_TF32:
-      if (wide) launch<256, 4, false, 0>(d, n, st, err);
-      else launch<128, 6, false, 0>(d, n, st, err);
+      if (pair) launch<256, 6, false, 0, true>(d, n, st, err);
+      else if (wide) launch<256, 4, false, 0, false>(d, n, st, err);
+      else launch<128, 6, false, 0, false>(d, n, st, err);
       break;
     case TIER_TF32X3:
-      if (wide) launch<256, 2, true, 0>(d, n, st, err);
-      else launch<128, 3, true, 0>(d, n, st, err);
+      if (pair) launch<256, 3, true, 0, true>(d, n, st, err);
+      else if (wide) launch<256, 2, true, 0, false>(d, n, st, err);
+      else launch<128, 3, true, 0, false>(d, n, st, err);
       break;
     case TIER_BF16X3:
-      if (wide) launch<256, 2, true, 1>(d, n, st, err);
-      else launch<128, 3, true, 1>(d, n, st, err);
+      if (pair) launch<256, 3, true, 1, true>(d, n, st, err);
+      else if (wide) launch<256, 2, true, 1, false>(d, n, st, err);
+      else launch<128, 3, true, 1, false>(d, n, st, err);
       break;
     case TIER_FP16:
-      if (wide) launch<256, 4, false, 2>(d, n, st, err);
-      else launch<128, 6, false, 2>(d, n, st, err);
+      if (pair) launch<256, 6, false, 2, true>(d, n, st, err);
+      else if (wide) launch<256, 4, false, 2, false>(d, n, st, err);
+      else launch<128, 6, false, 2, false>(d, n, st, err);
       break;
     case TIER_FP16X3:
-      if (wide) launch<256, 2, true, 2>(d, n, st, err);
-      else launch<128, 3, true, 2>(d, n, st, err);
+      if (pair) launch<256, 3, true, 2, true>(d, n, st, err);
+      else if (wide) launch<256, 2, true, 2, false>(d, n, st, err);
+      else launch<128, 3, true, 2, false>(d, n, st, err);
       break;
     default:
       fail(CC_ERR_ARG, "gemm_tc: bad tier");
