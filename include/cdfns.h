@@ -439,6 +439,38 @@ int cc_mlp_warm_start(cc_mlp *mlp, cc_ctx *ctx);
 int cc_set_wait_limit(unsigned long long ns);
 int cc_set_fault_injection(cc_ctx *ctx, int kind, int at_iteration);
 
+/*
+ * Davidson starting vectors (an extension beyond the paper, which names the
+ * Davidson method without a start). The n_roots lowest diagonal elements of
+ * H-bar_IP seed the roots. Mode 0 (default): unit vectors there. Mode 1: a
+ * root seeded at a 1h element i starts from r_i = 1 plus the first-order
+ * (Rayleigh-Schroedinger) 2h1p components c_nu = M_nu,i / (d_i - d_nu)
+ * about the diagonal d (M_nu,i = -W_ibjk for nu = (j<k, b)); roots seeded at
+ * 2h1p elements keep unit vectors. Mode 2: the components are rho_nu c_nu
+ * with rho_nu from a trained network (cc_mlp, same architecture as the
+ * amplitude warm start, features listed at cc_mlp_guess_features). The
+ * roots do not depend on the start; it changes the iteration count only.
+ * The network must outlive its use by the context.
+ */
+int cc_set_davidson_guess(cc_ctx *ctx, int mode, const cc_mlp *mlp);
+/* The n_roots starting vectors of the current mode before orthonormalisation
+ * (device complex128 [n_roots][dim], the ipeom_sigma_dev layout). Needs a
+ * converged ccsd_solve; builds H-bar if needed. */
+int ipeom_guess_dev(cc_ctx *ctx, int n_roots, double *out_dev);
+/* Features of the first n 2h1p elements (j<k row-major, b fastest) for a
+ * root seeded at 1h element `seed` (host float [n][8]): log10|c_nu|,
+ * Re(d_i - d_nu) / d_scale, |W_ibjk| / g_scale, [seed is j or k],
+ * Re(d_i) / d_scale, <jk||jk> / g_scale, (<jb||jb> + <kb||kb>) / g_scale,
+ * |<jb||jb> - <kb||kb>| / g_scale, with the scales of the amplitude
+ * features. */
+int cc_mlp_guess_features(cc_ctx *ctx, int seed, long n, float *X_host);
+/* Training samples for the learned start from the right vectors of the
+ * context's last converged ipeom_solve: for every root whose 1h weight is at
+ * least one half, seeded at its largest 1h element i and scaled to r_i = 1,
+ * the targets rho_nu = r_nu / c_nu (up to max_samples evenly strided
+ * elements; weights |c_nu|^2 normalised to mean one). */
+int cc_mlp_add_guess_samples(cc_mlp *mlp, cc_ctx *ctx, long max_samples);
+
 const char *cc_last_error(const cc_ctx *ctx); /* NULL ctx: last global */
 void cc_free(cc_ctx *ctx);
 

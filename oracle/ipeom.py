@@ -171,6 +171,22 @@ def diagonal(H, o, v):
     return np.concatenate([-hoo, d2])
 
 
+def first_order_guess(H, o, v, i):
+    """Starting vector of a Davidson root seeded at the 1h element i: r_i = 1
+    and the 2h1p elements of first-order (Rayleigh-Schroedinger) perturbation
+    theory about the diagonal, r_nu = M_nu,i / (M_ii - M_nu,nu), with
+    M_nu,i the 2h1p <- 1h coupling (the sigma of the unit vector e_i) and the
+    diagonal of ``diagonal``. The Davidson iterations converge to the same
+    roots from any start; this one only shortens them."""
+    d = diagonal(H, o, v)
+    e = np.zeros(dim(o, v), dtype=np.complex128)
+    e[i] = 1.0
+    col = sigma(H, e, o, v)
+    g = e.copy()
+    g[o:] = col[o:] / (d[i] - d[o:])
+    return g
+
+
 def dense_matrix(H, o, v):
     """H-bar_IP by applying sigma to unit vectors (small sizes only)."""
     n = dim(o, v)

@@ -91,3 +91,38 @@ def features(L, eps, n_occ, n):
                       abs(oovv[i, j, a, b]) / gs]
             k += 1
     return out[:k]
+
+
+def guess_features(H, g, eps, n_occ, seed, n):
+    """Features of the learned Davidson start for the first n 2h1p elements
+    (j<k row-major, b fastest) of a root seeded at the 1h element `seed`:
+    log10|c|, Re(d_i - d_nu) / ds, |W_ibjk| / gs, [seed is j or k],
+    Re(d_i) / ds, <jk||jk> / gs, (<jb||jb> + <kb||kb>) / gs and
+    |<jb||jb> - <kb||kb>| / gs, with c the first-order component
+    -W_ibjk / (d_i - d_nu) and d the IP diagonal (``ipeom.diagonal``); the
+    scales are those of ``features``. ``H`` is ``ipeom.hbar``'s dict, ``g``
+    the integral blocks."""
+    from .ipeom import diagonal
+    o = n_occ
+    v = len(eps) - o
+    d = diagonal(H, o, v)
+    iu = [(i, j) for i in range(o) for j in range(i + 1, o)]
+    gs = np.sqrt(np.mean([g.oooo[i, j, i, j].real ** 2 for i, j in iu]))
+    ds = 2.0 * (np.sum(eps[o:]) - np.sum(eps[:o])) / (o + v)
+    dia = np.array([[g.ovov[i, a, i, a].real for a in range(v)] for i in range(o)])
+    i = seed
+    out = np.empty((n, F))
+    k = 0
+    for p, (j, kk) in enumerate(iu):
+        for b in range(v):
+            if k == n:
+                return out
+            nu = o + p * v + b
+            w = -H["ovoo"][i, b, j, kk]
+            c = w / (d[i] - d[nu])
+            out[k] = [np.log10(abs(c) + 1e-30), (d[i] - d[nu]).real / ds, abs(w) / gs,
+                      1.0 if i in (j, kk) else 0.0, d[i].real / ds,
+                      g.oooo[j, kk, j, kk].real / gs, (dia[j, b] + dia[kk, b]) / gs,
+                      abs(dia[j, b] - dia[kk, b]) / gs]
+            k += 1
+    return out[:k]

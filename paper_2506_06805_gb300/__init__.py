@@ -103,6 +103,11 @@ _SIGS = {
     "cc_set_allocator": (ctypes.c_int, [_P, _ALLOC, _FREE, _P]),
     "cc_set_wait_limit": (ctypes.c_int, [ctypes.c_ulonglong]),
     "cc_set_fault_injection": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+    "cc_set_davidson_guess": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "ipeom_guess_dev": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "cc_mlp_guess_features": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_long,
+                                             ctypes.POINTER(ctypes.c_float)]),
+    "cc_mlp_add_guess_samples": (ctypes.c_int, [_P, _P, ctypes.c_long]),
 }
 
 _lib = None
@@ -415,6 +420,24 @@ class System:
         2 = NaN into the Davidson sigma vectors of an iteration, 0 = off."""
         _check(lib().cc_set_fault_injection(self._ctx, int(kind), int(at_iteration)), self._ctx)
 
+    def set_davidson_guess(self, mode, mlp=None):
+        """Davidson start: "unit" (0), "first_order" (1) or "learned" (2,
+        needs a trained Mlp that outlives this system)."""
+        m = {"unit": 0, "first_order": 1, "learned": 2}.get(mode, mode)
+        _check(lib().cc_set_davidson_guess(self._ctx, int(m), mlp._h if mlp else None),
+               self._ctx)
+        self._guess_mlp = mlp
+
+    def guess_dev(self, n_roots):
+        """The n_roots Davidson starting vectors of the current mode (device
+        complex128 tensor [n_roots][dim])."""
+        import torch
+        o, v, _ = self.sizes()
+        dim = o + o * (o - 1) // 2 * v
+        out = torch.zeros((n_roots, dim), dtype=torch.complex128, device="cuda")
+        _check(lib().ipeom_guess_dev(self._ctx, int(n_roots), _P(out.data_ptr())), self._ctx)
+        return out
+
     def set_memory_limit(self, nbytes):
         """Cap the device bytes this system holds (0: no cap)."""
         _check(lib().cc_set_memory_limit(self._ctx, int(nbytes)), self._ctx)
@@ -556,6 +579,18 @@ class Mlp:
         self._err(lib().cc_mlp_loss_grad(self._h, X.shape[0], _fptr(X), _fptr(Y),
                                          ctypes.byref(loss), _fptr(g)))
         return loss.value, g
+
+    def add_guess_samples(self, system, max_samples):
+        """Davidson-start training samples from system's last converged
+        ipeom_solve."""
+        self._err(lib().cc_mlp_add_guess_samples(self._h, system._ctx, int(max_samples)))
+
+    @staticmethod
+    def guess_features(system, seed, n):
+        out = np.empty((n, 8), np.float32)
+        _check(lib().cc_mlp_guess_features(system._ctx, int(seed), int(n), _fptr(out)),
+               system._ctx)
+        return out
 
     def warm_start(self, system):
         self._err(lib().cc_mlp_warm_start(self._h, system._ctx))

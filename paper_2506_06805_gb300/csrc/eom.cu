@@ -407,12 +407,22 @@ struct Dav {
     std::vector<long> idx(dim);
     std::iota(idx.begin(), idx.end(), 0);
     std::stable_sort(idx.begin(), idx.end(), [&](long a, long b) { return dh[a].x < dh[b].x; });
-    CUDA_CHECK(cudaMemsetAsync(V.p, 0, z * nr * dim, st()));
-    const cplx one = mk(1.0, 0.0);
-    for (int r = 0; r < nr; ++r) h2d(V.c() + r * dim + idx[r], &one, z, st());
-    m = nr;
+    if (c->guess_mode > 0) {
+      // first-order (optionally learned) 2h1p parts for the roots seeded at
+      // a 1h element, orthonormalised into V
+      std::vector<int> seeds(nr);
+      for (int r = 0; r < nr; ++r) seeds[r] = idx[r] < c->o ? static_cast<int>(idx[r]) : static_cast<int>(-2 - idx[r]);
+      davidson_guess(*c, seeds, corr.c());
+      m = orth_new(corr.c(), nr, 0);
+      if (m < nr) fail(CC_ERR_NUMERIC, "Davidson starting vectors are linearly dependent");
+    } else {
+      CUDA_CHECK(cudaMemsetAsync(V.p, 0, z * nr * dim, st()));
+      const cplx one = mk(1.0, 0.0);
+      for (int r = 0; r < nr; ++r) h2d(V.c() + r * dim + idx[r], &one, z, st());
+      m = nr;
+    }
     pending = FULL;
-    req_k = nr;
+    req_k = m;
     req_off = 0;
   }
 

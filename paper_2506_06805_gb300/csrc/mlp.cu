@@ -10,8 +10,10 @@
 // caller-shuffled sample order.
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "solver.h"
 
@@ -261,6 +263,116 @@ __global__ void apply_rho_kernel(FeatArgs A, const float2 *rho, double2 *vec, lo
   }
 }
 
+// ---------------------------------------------------------------------------
+// Learned Davidson start. A root seeded at the 1h element i starts from
+// r_i = 1 and 2h1p elements rho_nu c_nu, with c_nu = M_nu,i / (d_i - d_nu)
+// the first-order (Rayleigh-Schroedinger) component about the diagonal d of
+// H-bar_IP, M_nu,i = -W_ibjk for nu = (j<k, b) the 2h1p <- 1h coupling, and
+// rho_nu the same network's complex ratio (1 without a network). Training
+// targets are the converged right vectors, scaled so that r_i = 1:
+// rho_nu = r_nu / c_nu.
+// ---------------------------------------------------------------------------
+struct GuessArgs {
+  const double2 *Hovoo, *oooo, *ovvo, *d, *R;
+  const int *ij_i, *ij_j, *seed;
+  int o, v, nroots;
+  long n2, dim, stride, n;
+  double g_scale, d_scale;
+};
+
+__device__ __forceinline__ double2 first_order_component(const GuessArgs &A, int i, long q,
+                                                         double2 *num) {
+  const int o = A.o, v = A.v;
+  const long p = q / v;
+  const int b = static_cast<int>(q - p * v);
+  const int j = A.ij_i[p], k = A.ij_j[p];
+  const double2 h = A.Hovoo[((static_cast<long>(i) * v + b) * o + j) * o + k];
+  *num = make_double2(-h.x, -h.y);
+  const double2 den = csub(A.d[i], A.d[o + q]);
+  const double dd = den.x * den.x + den.y * den.y;
+  if (!(dd > 0.0)) return make_double2(0.0, 0.0);
+  // num / den
+  return make_double2((num->x * den.x + num->y * den.y) / dd, (num->y * den.x - num->x * den.y) / dd);
+}
+
+// Features of sample s = (root r, 2h1p element q) at flat index stride * s
+// over [nroots][n2]: log10 |c|, (d_i - d_nu) / d_scale, |W_ibjk| / g_scale,
+// whether the seed hole is j or k, d_i / d_scale, <jk||jk> / g_scale, and the
+// sum and spread of <jb||jb>, <kb||kb> (/ g_scale); all invariant under
+// spinor phase changes. Y (needs R): Re, Im of rho - 1 and the weight |c|^2.
+__global__ void guess_features_kernel(GuessArgs A, float *X, float *Y, double *wsum) {
+  const int o = A.o, v = A.v;
+  for (long s = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; s < A.n;
+       s += static_cast<long>(gridDim.x) * blockDim.x) {
+    const long flat = s * A.stride;
+    const int r = static_cast<int>(flat / A.n2);
+    const long q = flat - static_cast<long>(r) * A.n2;
+    const int i = A.seed[r];
+    if (i < 0) {  // root not seeded at a 1h element: no features
+      for (int f = 0; f < F; ++f) X[s * F + f] = 0.f;
+      if (Y) Y[s * 3] = Y[s * 3 + 1] = Y[s * 3 + 2] = 0.f;
+      continue;
+    }
+    const long p = q / v;
+    const int b = static_cast<int>(q - p * v);
+    const int j = A.ij_i[p], k = A.ij_j[p];
+    double2 num;
+    const double2 c = first_order_component(A, i, q, &num);
+    const double ac = sqrt(c.x * c.x + c.y * c.y);
+    const double2 den = csub(A.d[i], A.d[o + q]);
+    auto dia = [&](int ii, int aa) {  // <ia||ia> = -<ia||ai>
+      return -A.ovvo[((static_cast<long>(ii) * v + aa) * v + aa) * o + ii].x;
+    };
+    const double djb = dia(j, b), dkb = dia(k, b);
+    float *x = X + s * F;
+    x[0] = static_cast<float>(log10(ac + 1e-30));
+    x[1] = static_cast<float>(den.x / A.d_scale);
+    x[2] = static_cast<float>(sqrt(num.x * num.x + num.y * num.y) / A.g_scale);
+    x[3] = (i == j || i == k) ? 1.f : 0.f;
+    x[4] = static_cast<float>(A.d[i].x / A.d_scale);
+    x[5] = static_cast<float>(A.oooo[((static_cast<long>(j) * o + k) * o + j) * o + k].x / A.g_scale);
+    x[6] = static_cast<float>((djb + dkb) / A.g_scale);
+    x[7] = static_cast<float>(fabs(djb - dkb) / A.g_scale);
+    if (Y) {
+      const double2 *Rr = A.R + static_cast<long>(r) * A.dim;
+      const double2 ri = Rr[i], rn = Rr[o + q];
+      const double den_i = ri.x * ri.x + ri.y * ri.y;
+      // t = r_nu / r_i, then rho = t / c
+      const double tx = (rn.x * ri.x + rn.y * ri.y) / den_i, ty = (rn.y * ri.x - rn.x * ri.y) / den_i;
+      const double cc = c.x * c.x + c.y * c.y;
+      float *y = Y + s * 3;
+      if (cc > 0.0) {
+        y[0] = static_cast<float>((tx * c.x + ty * c.y) / cc - 1.0);
+        y[1] = static_cast<float>((ty * c.x - tx * c.y) / cc);
+        y[2] = static_cast<float>(cc);
+        atomicAdd(wsum, cc);
+      } else {
+        y[0] = y[1] = y[2] = 0.f;
+      }
+    }
+  }
+}
+
+// Starting vectors: V[r] = e_i + sum_nu rho_nu c_nu e_nu for the seeded roots
+// (rho = 1 where no network is given), V zeroed beforehand by the caller.
+__global__ void build_guess_kernel(GuessArgs A, const float2 *rho, double2 *V) {
+  const int o = A.o;
+  const long tot = static_cast<long>(A.nroots) * A.n2;
+  for (long s = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; s < tot;
+       s += static_cast<long>(gridDim.x) * blockDim.x) {
+    const int r = static_cast<int>(s / A.n2);
+    const long q = s - static_cast<long>(r) * A.n2;
+    const int i = A.seed[r];
+    if (i < 0) continue;
+    double2 num;
+    double2 c = first_order_component(A, i, q, &num);
+    if (rho) c = cmul(make_double2(rho[s].x, rho[s].y), c);
+    double2 *Vr = V + static_cast<long>(r) * A.dim;
+    Vr[o + q] = c;
+    if (q == 0) Vr[i] = make_double2(1.0, 0.0);
+  }
+}
+
 }  // namespace
 
 struct Mlp {
@@ -315,6 +427,74 @@ static void feature_setup(Ctx &c, FeatArgs &A, Buf &dvv_buf) {
   A.nab = c.nab();
   A.g_scale = std::sqrt(g2 / std::max<long>(cnt, 1)) + 1e-300;
   A.d_scale = 2.0 * dm / (o + v);  // mean |eps|-weighted scale, of order one Eh
+}
+
+// Inputs of the Davidson-start kernels for a context with H-bar built: the
+// IP diagonal d (device, filled here) and the same scales as the amplitude
+// features.
+static void guess_setup(Ctx &c, GuessArgs &A, Buf &dbuf, const int *seed_dev, int nroots) {
+  if (!c.hbar_done) fail(CC_ERR_STATE, "the Davidson start needs H-bar (a converged ccsd_solve)");
+  c.ensure_pairs();
+  const int o = c.o, v = c.v;
+  dbuf.reset(&c.al, sizeof(cplx) * c.dim_ip());
+  ip_diag(c.Hoo.c(), c.Hvv.c(), o, v, dbuf.c(), c.st);
+  FeatArgs F0;
+  Buf dvv;
+  feature_setup(c, F0, dvv);
+  A.Hovoo = c.Hovoo.c();
+  A.oooo = c.oooo.c();
+  A.ovvo = c.ovvo.c();
+  A.d = dbuf.c();
+  A.R = nullptr;
+  A.ij_i = c.ij_i.as<int>();
+  A.ij_j = c.ij_j.as<int>();
+  A.seed = seed_dev;
+  A.o = o;
+  A.v = v;
+  A.nroots = nroots;
+  A.n2 = c.nij() * v;
+  A.dim = c.dim_ip();
+  A.stride = 1;
+  A.n = static_cast<long>(nroots) * A.n2;
+  A.g_scale = F0.g_scale;
+  A.d_scale = F0.d_scale;
+}
+
+void davidson_guess(Ctx &c, const std::vector<int> &seeds, cplx *V) {
+  const int nr = static_cast<int>(seeds.size());
+  Buf sd(&c.al, sizeof(int) * std::max(nr, 1));
+  CUDA_CHECK(cudaMemcpyAsync(sd.p, seeds.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, c.st));
+  GuessArgs A;
+  Buf dbuf;
+  guess_setup(c, A, dbuf, sd.as<int>(), nr);
+  CUDA_CHECK(cudaMemsetAsync(V, 0, sizeof(cplx) * nr * A.dim, c.st));
+  Buf X, rho;
+  const float2 *rp = nullptr;
+  if (c.guess_mode == 2) {
+    if (!c.guess_mlp) fail(CC_ERR_STATE, "learned Davidson start without a network");
+    const Mlp *m = static_cast<const Mlp *>(c.guess_mlp);
+    X.reset(&c.al, sizeof(float) * A.n * F);
+    rho.reset(&c.al, sizeof(float2) * A.n);
+    guess_features_kernel<<<grid_for(A.n), 256, 0, c.st>>>(A, X.as<float>(), nullptr, nullptr);
+    LAUNCH_CHECK();
+    mlp_infer_kernel<<<grid_for(A.n, 128), 128, 0, c.st>>>(m->w16.as<__half>(), X.as<float>(), A.n,
+                                                          rho.as<float2>());
+    LAUNCH_CHECK();
+    count_launch(2);
+    rp = rho.as<float2>();
+  }
+  build_guess_kernel<<<grid_for(A.n), 256, 0, c.st>>>(A, rp, V);
+  LAUNCH_CHECK();
+  count_launch();
+  // roots not seeded at a 1h element start as unit vectors at their seed
+  const cplx one = mk(1.0, 0.0);
+  for (int r = 0; r < nr; ++r)
+    if (seeds[r] < 0) {
+      const long pos = -2 - seeds[r];  // encoded position of the 2h1p element
+      CUDA_CHECK(cudaMemcpyAsync(V + static_cast<long>(r) * A.dim + pos, &one, sizeof(cplx),
+                                 cudaMemcpyHostToDevice, c.st));
+    }
+  CUDA_CHECK(cudaStreamSynchronize(c.st));
 }
 
 }  // namespace cdfns
@@ -534,6 +714,137 @@ int cc_mlp_features(cc_ctx *ctx, long n, float *X_host) {
     c.last_error = e.msg;
     return e.code;
   }
+}
+
+int cc_set_davidson_guess(cc_ctx *ctx, int mode, const cc_mlp *mlp) {
+  if (!ctx || mode < 0 || mode > 2 || (mode == 2 && !mlp)) return CC_ERR_ARG;
+  ctx->c.guess_mode = mode;
+  ctx->c.guess_mlp = mode == 2 ? static_cast<const void *>(&mlp->m) : nullptr;
+  return CC_OK;
+}
+
+int ipeom_guess_dev(cc_ctx *ctx, int n_roots, double *out_dev) {
+  if (!ctx || n_roots < 1 || !out_dev) return CC_ERR_ARG;
+  cdfns::Ctx &c = ctx->c;
+  try {
+    if (!c.ccsd_done) cdfns::fail(CC_ERR_STATE, "the Davidson start needs a converged ccsd_solve");
+    if (!c.hbar_done) c.build_hbar();
+    if (n_roots > c.dim_ip()) cdfns::fail(CC_ERR_ARG, "n_roots out of range");
+    const long dim = c.dim_ip();
+    Buf d(&c.al, sizeof(cdfns::cplx) * dim);
+    cdfns::ip_diag(c.Hoo.c(), c.Hvv.c(), c.o, c.v, d.c(), c.st);
+    std::vector<cdfns::cplx> dh(dim);
+    CUDA_CHECK(cudaMemcpyAsync(dh.data(), d.p, sizeof(cdfns::cplx) * dim, cudaMemcpyDeviceToHost, c.st));
+    CUDA_CHECK(cudaStreamSynchronize(c.st));
+    std::vector<long> idx(dim);
+    for (long k = 0; k < dim; ++k) idx[k] = k;
+    std::stable_sort(idx.begin(), idx.end(), [&](long a, long b) { return dh[a].x < dh[b].x; });
+    std::vector<int> seeds(n_roots);
+    for (int r = 0; r < n_roots; ++r)
+      seeds[r] = idx[r] < c.o ? static_cast<int>(idx[r]) : static_cast<int>(-2 - idx[r]);
+    cdfns::cplx *V = reinterpret_cast<cdfns::cplx *>(out_dev);
+    if (c.guess_mode == 0) {
+      CUDA_CHECK(cudaMemsetAsync(V, 0, sizeof(cdfns::cplx) * n_roots * dim, c.st));
+      const cdfns::cplx one = cdfns::mk(1.0, 0.0);
+      for (int r = 0; r < n_roots; ++r)
+        CUDA_CHECK(cudaMemcpyAsync(V + r * dim + idx[r], &one, sizeof(one), cudaMemcpyHostToDevice, c.st));
+      CUDA_CHECK(cudaStreamSynchronize(c.st));
+    } else {
+      cdfns::davidson_guess(c, seeds, V);
+    }
+    return CC_OK;
+  } catch (const cdfns::Error &e) {
+    c.last_error = e.msg;
+    return e.code;
+  }
+}
+
+int cc_mlp_guess_features(cc_ctx *ctx, int seed, long n, float *X_host) {
+  if (!ctx || seed < 0 || n < 1 || !X_host) return CC_ERR_ARG;
+  cdfns::Ctx &c = ctx->c;
+  try {
+    if (seed >= c.o) cdfns::fail(CC_ERR_ARG, "seed must be a 1h element");
+    Buf sd(&c.al, sizeof(int));
+    CUDA_CHECK(cudaMemcpyAsync(sd.p, &seed, sizeof(int), cudaMemcpyHostToDevice, c.st));
+    cdfns::GuessArgs A;
+    Buf dbuf;
+    cdfns::guess_setup(c, A, dbuf, sd.as<int>(), 1);
+    A.n = std::min<long>(n, A.n2);
+    Buf X(&c.al, sizeof(float) * A.n * cdfns::F);
+    cdfns::guess_features_kernel<<<cdfns::grid_for(A.n), 256, 0, c.st>>>(A, X.as<float>(), nullptr,
+                                                                        nullptr);
+    LAUNCH_CHECK();
+    CUDA_CHECK(cudaMemcpyAsync(X_host, X.p, sizeof(float) * A.n * cdfns::F, cudaMemcpyDeviceToHost, c.st));
+    CUDA_CHECK(cudaStreamSynchronize(c.st));
+    return CC_OK;
+  } catch (const cdfns::Error &e) {
+    c.last_error = e.msg;
+    return e.code;
+  }
+}
+
+int cc_mlp_add_guess_samples(cc_mlp *p, cc_ctx *ctx, long max_samples) {
+  if (!p || !ctx || max_samples < 1) return CC_ERR_ARG;
+  return guard(p, [&] {
+    cdfns::Ctx &c = ctx->c;
+    if (c.last_nr < 1) cdfns::fail(CC_ERR_STATE, "add_guess_samples needs a converged ipeom_solve");
+    Mlp &m = p->m;
+    const int nr = c.last_nr, o = c.o;
+    const long dim = c.dim_ip();
+    // seed of each converged root: its largest 1h element, for roots whose
+    // 1h weight is at least one half (the others give no samples)
+    std::vector<cdfns::cplx> R1(static_cast<size_t>(nr) * dim);
+    CUDA_CHECK(cudaMemcpyAsync(R1.data(), c.last_R.p, sizeof(cdfns::cplx) * nr * dim,
+                               cudaMemcpyDeviceToHost, c.st));
+    CUDA_CHECK(cudaStreamSynchronize(c.st));
+    std::vector<int> seeds(nr, -1);
+    for (int r = 0; r < nr; ++r) {
+      double w1 = 0, wt = 0, best = -1;
+      for (long k = 0; k < dim; ++k) {
+        const cdfns::cplx x = R1[static_cast<size_t>(r) * dim + k];
+        const double a2 = x.x * x.x + x.y * x.y;
+        wt += a2;
+        if (k < o) {
+          w1 += a2;
+          if (a2 > best) {
+            best = a2;
+            seeds[r] = static_cast<int>(k);
+          }
+        }
+      }
+      if (w1 < 0.5 * wt) seeds[r] = -1;
+    }
+    Buf sd(&c.al, sizeof(int) * nr);
+    CUDA_CHECK(cudaMemcpyAsync(sd.p, seeds.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, c.st));
+    cdfns::GuessArgs A;
+    Buf dbuf;
+    cdfns::guess_setup(c, A, dbuf, sd.as<int>(), nr);
+    A.R = c.last_R.c();
+    const long total = static_cast<long>(nr) * A.n2;
+    A.stride = std::max<long>(1, total / max_samples);
+    A.n = total / A.stride;
+    if (m.n + A.n > m.cap) {
+      const long cap = (m.n + A.n) * 2;
+      Buf X2(&m.al, sizeof(float) * cap * cdfns::F), Y2(&m.al, sizeof(float) * cap * 3);
+      if (m.n) {
+        CUDA_CHECK(cudaMemcpy(X2.p, m.X.p, sizeof(float) * m.n * cdfns::F, cudaMemcpyDeviceToDevice));
+        CUDA_CHECK(cudaMemcpy(Y2.p, m.Y.p, sizeof(float) * m.n * 3, cudaMemcpyDeviceToDevice));
+      }
+      m.X = std::move(X2);
+      m.Y = std::move(Y2);
+      m.cap = cap;
+    }
+    CUDA_CHECK(cudaMemsetAsync(m.ws.p, 0, sizeof(double), c.st));
+    float *Xp = m.X.as<float>() + m.n * cdfns::F, *Yp = m.Y.as<float>() + m.n * 3;
+    cdfns::guess_features_kernel<<<cdfns::grid_for(A.n), 256, 0, c.st>>>(A, Xp, Yp, m.ws.as<double>());
+    LAUNCH_CHECK();
+    cdfns::scale_weights_kernel<<<cdfns::grid_for(A.n), 256, 0, c.st>>>(Yp, A.n, m.ws.as<double>());
+    LAUNCH_CHECK();
+    cdfns::count_launch(2);
+    CUDA_CHECK(cudaStreamSynchronize(c.st));
+    m.n += A.n;
+    return CC_OK;
+  });
 }
 
 int cc_mlp_warm_start(cc_mlp *p, cc_ctx *ctx) {

@@ -1153,7 +1153,13 @@ int Ctx::ipeom(int nr, double tol, int max_iter, double *omega, double *r1w, int
   if (!(tol > 0) || max_iter < 1) fail(CC_ERR_ARG, "tol must be > 0 and max_iter >= 1");
   std::vector<Ctx *> one{this};
   int status = CC_OK;
-  run_ipeom(one, nr, tol, max_iter, omega, r1w, n_iter, &status, use_graphs);
+  // keep the right vectors (training samples for the learned start)
+  if (nr >= 1 && nr <= dim_ip() && last_R.bytes < sizeof(cplx) * nr * dim_ip())
+    last_R.reset(&al, sizeof(cplx) * nr * dim_ip());
+  last_nr = 0;
+  std::vector<cplx *> vecs{last_R.c()};
+  run_ipeom(one, nr, tol, max_iter, omega, r1w, n_iter, &status, use_graphs, false, &vecs);
+  if (status == CC_OK) last_nr = nr;
   return status;
 }
 

@@ -76,6 +76,14 @@ struct Ctx {
   // count to stat[17], and releases the events
   void settle_sigma_timing();
   std::string last_error;
+  // Davidson start (cc_set_davidson_guess): 0 unit vectors at the lowest
+  // diagonal elements, 1 first-order 2h1p components for 1h-seeded roots,
+  // 2 the same scaled by the network guess_mlp (a cc_mlp's state)
+  int guess_mode = 0;
+  const void *guess_mlp = nullptr;
+  // right vectors of the last ipeom_solve ([last_nr][dim], unit norm)
+  Buf last_R;
+  int last_nr = 0;
   // host-side fault injection for tests of the error paths
   // (cc_set_fault_injection): kind 1 writes NaN into the CCSD residual of
   // iteration `inject_at`, kind 2 into the sigma vectors of Davidson
@@ -145,6 +153,10 @@ void run_ipeom(std::vector<Ctx *> &sys, int nr, double tol, int max_iter, double
 void batch_left_sigma(std::vector<Ctx *> &sys, const std::vector<int> &k,
                       const std::vector<const cplx *> &r, const std::vector<cplx *> &s);
 void drop_graphs(const void *ctx);
+// mlp.cu: starting vectors V [seeds.size()][dim] of the Davidson iterations
+// for c.guess_mode 1 or 2; seeds[r] >= 0 is the 1h element root r is seeded
+// at, -2 - pos a root that starts as the unit vector at 2h1p position pos.
+void davidson_guess(Ctx &c, const std::vector<int> &seeds, cplx *V);
 void geev_dev(Allocator *al, cudaStream_t st, cplx *A, int m, cplx *w, cplx *vr);
 
 }  // namespace cdfns

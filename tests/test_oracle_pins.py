@@ -329,6 +329,41 @@ def test_r1_weight_limits():
     assert devs[1] < 0.6 * devs[0] and devs[1] < 1e-3
 
 
+def test_first_order_guess_is_perturbation_theory():
+    """The first-order Davidson start of a 1h-dominated root against the
+    exact eigenvector x (dense H-bar_IP), by the overlap deficit
+    1 - |<g|x>|^2 / (|g|^2 |x|^2). With L -> lam L the couplings scale as
+    lam^2, so the unit vector e_i misses a 2h1p part of order lam^2 (deficit
+    ~ lam^4, a factor 16 per halving) while the first-order vector leaves
+    only the second-order part (deficit ~ lam^8, a factor 256)."""
+    o, v = 3, 5
+    eps, L0 = _system(o, v, 10, seed=7, scale=5.0)
+    n = ipeom.dim(o, v)
+
+    def deficits(lam):
+        L = lam * L0
+        g = integrals.blocks_from_cholesky(L, o)
+        res = ccsd.solve(g, eps, tol=1e-13, max_iter=300)
+        H = ipeom.hbar(g, eps, res["t1"], res["t2"])
+        w, V = ipeom.dense_roots(H, o, v, n)
+        k = int(np.argmax([ipeom.r1_weight(V[:, j], o) for j in range(n)]))
+        x = V[:, k]
+        i = int(np.argmax(np.abs(x[:o])))
+        e = np.zeros(n, complex)
+        e[i] = 1.0
+        gfo = ipeom.first_order_guess(H, o, v, i)
+
+        def deficit(y):
+            return 1.0 - abs(np.vdot(y, x)) ** 2 / (np.vdot(y, y).real * np.vdot(x, x).real)
+        return deficit(gfo), deficit(e)
+
+    f1, u1 = deficits(0.4)
+    f2, u2 = deficits(0.2)
+    assert f1 < 1e-3 * u1 and f2 < 1e-3 * u2
+    assert 10.0 < u1 / u2 < 25.0         # deficit of e_i ~ lam^4
+    assert 150.0 < f1 / f2 < 400.0       # first-order deficit ~ lam^8
+
+
 # --- closed forms and invariances ---------------------------------------------
 
 def test_koopmans_at_zero_coupling():
