@@ -571,76 +571,6 @@ __global__ void __launch_bounds__(256) antisym_tile_kernel(
   }
 }
 
-// FP16 tier: W[(a,b)][(c<d)] = V[a][c][b][d] - V[a][d][b][c] from the fp16
-// slab (half2 per complex element, scaled by sv). Block (32, 8) per (a, b)
-// pair row and (C <= D) pair of 64-wide tiles of c and d: both tiles are read
-// along their inner index into shared memory (16 independent 4-byte loads per
-// thread), W = (x - y) is formed in FP32 (exact for fp16 inputs) and stored
-// as fp16 scaled by sw / sv, along d (packed (c<d) columns are contiguous in d
-// for fixed c).
-__global__ void __launch_bounds__(256) antisym_h_kernel(
-    const __half2 *__restrict__ V, int v, int a0, long p0, long np, const int *__restrict__ pair_a,
-    const int *__restrict__ pair_b, __half2 *__restrict__ W, long kp2, int ntile,
-    const float *__restrict__ vbound) {
-  __shared__ __half2 s1[64][65];  // V[a][c][b][d], c = C0 + row
-  __shared__ __half2 s2[64][65];  // V[a][d][b][c], d = D0 + row
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  int ct = 0, p = blockIdx.x;
-  while (p >= ntile - ct) {
-    p -= ntile - ct;
-    ++ct;
-  }
-  const int dt = ct + p;
-  const bool diag = ct == dt;
-  const int C0 = ct * 64, D0 = dt * 64;
-  const long ld = static_cast<long>(v - a0) * v;
-  const float ratio = fp16_scale(vbound[1]) / fp16_scale(vbound[0]);  // sw / sv, a power of two
-  const __half2 zero = __floats2half2_rn(0.f, 0.f);
-  for (long r = blockIdx.y; r < np; r += gridDim.y) {
-    const int a = pair_a[p0 + r], b = pair_b[p0 + r];
-    const long ra = static_cast<long>(a - a0) * v, cb = static_cast<long>(b - a0) * v;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int row = ty + 8 * j;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int col = tx + 32 * h;
-        const int c = C0 + row, d = D0 + col;
-        s1[row][col] = (c < v && d < v) ? V[(ra + c) * ld + cb + d] : zero;
-        if (!diag) {
-          const int d2 = D0 + row, c2 = C0 + col;
-          s2[row][col] = (d2 < v && c2 < v) ? V[(ra + d2) * ld + cb + c2] : zero;
-        }
-      }
-    }
-    __syncthreads();
-    const __half2(*t2)[65] = diag ? s1 : s2;
-    const long wrow = r * kp2;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int row = ty + 8 * j;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int col = tx + 32 * h;
-        const int c = C0 + row, d = D0 + col;
-        if (c < d && d < v) {
-          const float2 x = __half22float2(s1[row][col]), y = __half22float2(t2[col][row]);
-          const long q = static_cast<long>(c) * (2L * v - c - 1) / 2 + (d - c - 1);
-          W[wrow + q] = __floats2half2_rn(ratio * (x.x - y.x), ratio * (x.y - y.y));
-        }
-      }
-    }
-    __syncthreads();
-  }
-}
-
-__global__ void ladder_vbound_kernel(const float *amax_L, float X, float *vbound) {
-  const float m = *amax_L;
-  const float b = 2.0f * X * m * m;
-  vbound[0] = b;
-  vbound[1] = 2.0f * b;
-}
-
 // zero the padded tail columns [2*ncd, kp) of rows [0, np)
 template <typename E>
 __global__ void zero_tail(E *p, long np, long k0, long kp) {
@@ -1041,33 +971,6 @@ void ladder_antisym(const void *V, bool f32, int v, int a0, int nA, long p0, lon
   }
 }
 
-
-void ladder_antisym_h(const void *Vh, int v, int a0, long p0, long p1, const int *pair_a,
-                      const int *pair_b, void *hi, long kp, const float *vbound, cudaStream_t st) {
-  const long ncd = static_cast<long>(v) * (v - 1) / 2;
-  const long np = p1 - p0;
-  if (np <= 0) return;
-  const int nt = (v + 63) / 64;
-  dim3 grid(static_cast<unsigned>(nt * (nt + 1) / 2),
-            static_cast<unsigned>(std::min<long>(np, 65535)));
-  antisym_h_kernel<<<grid, dim3(32, 8), 0, st>>>(reinterpret_cast<const __half2 *>(Vh), v, a0, p0,
-                                                 np, pair_a, pair_b, reinterpret_cast<__half2 *>(hi),
-                                                 kp / 2, nt, vbound);
-  LAUNCH_CHECK();
-  count_launch();
-  if (kp > 2 * ncd) {
-    const unsigned gt = grid_for(np * (kp - 2 * ncd));
-    zero_tail<__half><<<gt, 256, 0, st>>>(reinterpret_cast<__half *>(hi), np, 2 * ncd, kp);
-    LAUNCH_CHECK();
-    count_launch();
-  }
-}
-
-void ladder_vbound(const float *amax_L, long X, float *vbound, cudaStream_t st) {
-  ladder_vbound_kernel<<<1, 1, 0, st>>>(amax_L, static_cast<float>(X), vbound);
-  LAUNCH_CHECK();
-  count_launch();
-}
 
 void unpack_pairs_add(const cplx *R, int o, int v, const int *ij_i, const int *ij_j,
                       const int *ab_a, const int *ab_b, cplx *R2, cudaStream_t st) {

@@ -71,15 +71,6 @@ void ladder_antisym(const void *V, bool f32, int v, int a0, int nA, long p0, lon
                     int tier, void *hi, void *lo, long kp, cplx *w64, cudaStream_t st,
                     const float *amax = nullptr);
 
-// FP16 tier, from an fp16 slab: Vh as V above but half2, holding
-// fp16_scale(*vbound) V; W written as fp16_scale(2 *vbound) W (|W| <= 2 max|V|).
-void ladder_antisym_h(const void *Vh, int v, int a0, long p0, long p1, const int *pair_a,
-                      const int *pair_b, void *hi, long kp, const float *vbound, cudaStream_t st);
-// vbound[0] = 2 X amax_L^2, a bound on |V| = |sum_P L_ac L_bd| (each complex
-// factor has modulus <= sqrt(2) amax_L, amax_L = max |Re|, |Im| of L), and
-// vbound[1] = 2 vbound[0], a bound on |W|.
-void ladder_vbound(const float *amax_L, long X, float *vbound, cudaStream_t st);
-
 // R2[i][j][a][b] += R[(i<j)][(a<b)] with the four antisymmetric images.
 void unpack_pairs_add(const cplx *R, int o, int v, const int *ij_i, const int *ij_j,
                       const int *ab_a, const int *ab_b, cplx *R2, cudaStream_t st);

@@ -63,7 +63,6 @@ enum TcOut {
   TC_OUT_F64 = 0,        // C(m, n) = alpha D + beta C through tables (double2)
   TC_OUT_F64_ATOMIC = 1, // C(m, n) += alpha D (split-K partials)
   TC_OUT_F32 = 2,        // Cf[m * ldc + n] = D (float2, plain row-major)
-  TC_OUT_F16 = 3,        // Ch[m * ldc + n] = fp16(fp16_scale(*out_bound) D) (half2)
 };
 struct TcDesc {
   long M = 0, N = 0, Kp = 0;  // complex rows, columns, padded real K
@@ -84,9 +83,6 @@ struct TcDesc {
   // the values written (the caller zeroes it); nullptr: not tracked
   float *amax_out = nullptr;
   float amax_mul = 1.0f;
-  // TC_OUT_F16 only: device float bounding max |Re|, |Im| of D; the values
-  // are stored as fp16 scaled by fp16_scale(*out_bound)
-  const float *out_bound = nullptr;
   // never time tile candidates for this call (the autotuner allocates a
   // scratch output and events): use a cached choice or the defaults
   bool no_tune = false;

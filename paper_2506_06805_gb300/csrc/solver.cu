@@ -4,7 +4,6 @@
 // at most two virtual indices are stored (<ij||kl>, <ij||ka>, <ij||ab>,
 // <ia||bj>); everything with three or four virtual indices is formed from
 // the Cholesky vectors (Eq. 23) inside the contraction that needs it.
-#include <cuda_fp16.h>
 #include <cusolverDn.h>
 
 #include <algorithm>
@@ -436,10 +435,6 @@ void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr) {
     const long Kp2 = ((2L * n_cd + kal - 1) / kal) * kal;
     const bool split = tier_split(tr);
     const bool f16 = tier_scaled(tr);
-    // the one-product FP16 tier stages V itself in fp16 (4 bytes per complex
-    // element instead of 8), scaled from an a-priori bound on |V|
-    const bool vh = tr == TIER_FP16;
-    const size_t veb_t = vh ? sizeof(__half2) : veb;
     Buf A1h(&al, eb * 2 * vv * Kp1), B1h(&al, eb * vv * Kp1), A2h(&al, eb * 2 * n_ij * Kp2);
     Buf A1l, B1l, A2l;
     if (split) {
@@ -451,22 +446,15 @@ void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr) {
     Buf amx(&al, 4 * sizeof(float));
     float *amx_L = f16 ? amx.as<float>() : nullptr;
     float *amx_t = f16 ? amx.as<float>() + 1 : nullptr;
-    // amx_W: a bound on |W|; with the fp16 slab amx_V precedes it: the
-    // bound on |V| that sets the slab's scale
-    float *amx_V = vh ? amx.as<float>() + 2 : nullptr;
-    float *amx_W = f16 ? amx.as<float>() + 3 : nullptr;
+    float *amx_W = f16 ? amx.as<float>() + 2 : nullptr;
     {
       Engine::Region r = eng.region("ladder pack");
       if (f16) {
         tc_absmax(Lv, nullptr, ptab, 1, vv, X, amx_L, st);
         tc_absmax(tau, rt.as<long>(), kt.as<long>(), 0, n_ij, n_cd, amx_t, st);
-        if (vh) {
-          ladder_vbound(amx_L, X, amx_V, st);  // amx_V, amx_W = 2 amx_V
-        } else {
-          // |W| <= 2 max |V|: each GEMM1 raises amx_W to twice the largest
-          // slab value it writes, before the antisymmetriser of its block
-          zero(amx_W, sizeof(float), st);
-        }
+        // |W| <= 2 max |V|: each GEMM1 raises amx_W to twice the largest
+        // slab value it writes, before the antisymmetriser of its block
+        zero(amx_W, sizeof(float), st);
       }
       tc_pack_A(Lv, nullptr, ptab, 1, false, vv, X, Kp1, tr, A1h.p, A1l.p, st, amx_L);
       tc_pack_B(Lv, nullptr, ptab, 1, false, vv, X, Kp1, tr, B1h.p, B1l.p, st, amx_L);
@@ -480,13 +468,13 @@ void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr) {
     };
     while (a0 < v - 1) {
       const long per_a = static_cast<long>(v) * (v - a0) * v;
-      long nA = std::max<long>(1, static_cast<long>(slab_budget / (per_a * veb_t)));
+      long nA = std::max<long>(1, static_cast<long>(slab_budget / (per_a * veb)));
       nA = std::min<long>(nA, v - 1 - a0);
       const long a1 = a0 + nA;
       const long p0 = a0 * v - a0 * (a0 + 1) / 2;
       const long p1 = a1 * v - a1 * (a1 + 1) / 2;
       const long np = p1 - p0;
-      if (Vs.bytes < veb_t * nA * per_a) Vs.reset(&al, veb_t * nA * per_a);
+      if (Vs.bytes < veb * nA * per_a) Vs.reset(&al, veb * nA * per_a);
       if (Wh.bytes < eb * np * Kp2) {
         Wh.reset(&al, eb * np * Kp2);
         if (split) Wl.reset(&al, eb * np * Kp2);
@@ -495,27 +483,19 @@ void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr) {
       g1.M = nA * v; g1.N = (v - a0) * v; g1.Kp = Kp1;
       g1.A = off(A1h, 2 * a0 * v * Kp1); g1.Alo = off(A1l, 2 * a0 * v * Kp1);
       g1.B = off(B1h, a0 * v * Kp1); g1.Blo = off(B1l, a0 * v * Kp1);
-      g1.tier = tr; g1.out = vh ? TC_OUT_F16 : TC_OUT_F32;
+      g1.tier = tr; g1.out = TC_OUT_F32;
       g1.C = Vs.p; g1.ldc = (v - a0) * v;
       g1.amax_a = amx_L; g1.amax_b = amx_L;
-      if (vh) {
-        g1.out_bound = amx_V;
-      } else {
-        g1.amax_out = amx_W; g1.amax_mul = 2.0f;
-      }
+      g1.amax_out = amx_W; g1.amax_mul = 2.0f;
       {
         Engine::Region r = eng.region("ladder gemm1");
         gemm_tc(g1, st, err_d.as<int>());
       }
       {
         Engine::Region r = eng.region("ladder antisym");
-        if (vh)
-          ladder_antisym_h(Vs.p, v, static_cast<int>(a0), p0, p1, ab_a.as<int>(), ab_b.as<int>(),
-                           Wh.p, Kp2, amx_V, st);
-        else
-          ladder_antisym(Vs.p, true, v, static_cast<int>(a0), static_cast<int>(nA), p0, p1,
-                         ab_a.as<int>(), ab_b.as<int>(), ab_a.as<int>(), ab_b.as<int>(), tr, Wh.p,
-                         Wl.p, Kp2, nullptr, st, amx_W);
+        ladder_antisym(Vs.p, true, v, static_cast<int>(a0), static_cast<int>(nA), p0, p1,
+                       ab_a.as<int>(), ab_b.as<int>(), ab_a.as<int>(), ab_b.as<int>(), tr, Wh.p,
+                       Wl.p, Kp2, nullptr, st, amx_W);
       }
       TcDesc g2;
       g2.M = n_ij; g2.N = np; g2.Kp = Kp2;
