@@ -270,6 +270,7 @@ struct alignas(64) TcProblem {
   int kb_per_split;
   int k_splits, m_tiles, n_tiles;
   int group_m;      // m tiles per raster group (A panels kept in L2)
+  int chunk;        // K blocks accumulated in TMEM before promotion
   int out;
   int tile_start;   // first index of this problem in the launch's tile space
 };
@@ -278,7 +279,6 @@ struct TcGroup {
   TcProblem p[MAX_PROBLEMS];
   int nprob;
   int total_tiles;
-  int chunk;        // K blocks accumulated in TMEM before promotion
   int *err;
   unsigned long long wait_ns;  // limit of each pipeline wait
 };
@@ -353,7 +353,6 @@ __global__ void __launch_bounds__(320, 1)
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int n_units = grp.total_tiles;
-  const int chunk = grp.chunk;
   int *const err = grp.err;
   const unsigned long long wait_ns = grp.wait_ns;
   // position of this CTA (pair) in the persistent walk over work units; the
@@ -450,6 +449,7 @@ __global__ void __launch_bounds__(320, 1)
         tile_coords(P, t - P.tile_start, m_tile, n_tile, z);
         const int kb0 = z * P.kb_per_split;
         const int nkb = min(P.num_kb, kb0 + P.kb_per_split) - kb0;
+        const int chunk = P.chunk;
         const int nch = (nkb + chunk - 1) / chunk;
         for (int cc = 0; cc < nch && ok; ++cc, ++c) {
           const int buf = static_cast<int>(c & 1);
@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(320, 1)
       tile_coords(args, t - args.tile_start, m_tile, n_tile, z);
       const int kb0 = z * args.kb_per_split;
       const int nkb = min(args.num_kb, kb0 + args.kb_per_split) - kb0;
-      const int nch = (nkb + chunk - 1) / chunk;
+      const int nch = (nkb + args.chunk - 1) / args.chunk;
       float acc[HALF];
 #pragma unroll
       for (int j = 0; j < HALF; ++j) acc[j] = 0.f;
@@ -655,19 +655,26 @@ CUtensorMap make_map(const void *base, long rows, long kp, int box_rows, int et)
   return m;
 }
 
-// K blocks accumulated in TMEM before promotion to FP32 registers: 8 for
-// the one-product tiers TF32 and FP16 (256 / 512 K elements per chunk; the
-// autotuner preferred 8 over 4 on nearly every FP16 shape of the CCSD
-// workload), 4 for the three-product tiers, whose accuracy target leaves
-// less room for the accumulation bias of a longer chunk.
-// CDFNS_TC_CHUNK (read once) replaces both defaults, for tuning.
-inline int default_chunk(int tier) {
+// K blocks accumulated in TMEM before promotion to FP32 registers. Each
+// promotion makes the epilogue warps drain a buffer, and while they store a
+// finished tile they cannot drain the next one's: the MMA then waits once it
+// has filled both buffers. Measured on a 4096^3 complex FP16 product: 1110
+// TF/s with promotion every 8 K blocks, 1450-1500 with none. The truncation
+// bias of the tensor core's FP32 accumulation grows with the chunk (about
+// -1e-6 relative per 8 K blocks on same-sign data), so:
+//  - one-product tiers (TF32, FP16; rounding ~2^-11 per element): chunks of
+//    up to 32 K blocks, and a product whose K range (of one split) has at
+//    most 48 K blocks runs as one chunk;
+//  - three-product tiers (~2^-22): every 4 K blocks.
+// CDFNS_TC_CHUNK (read once) replaces the rule, for tuning.
+inline int default_chunk(int tier, int nkb) {
   static const int forced = [] {
     const char *e = std::getenv("CDFNS_TC_CHUNK");
     return e ? std::atoi(e) : 0;
   }();
   if (forced > 0) return forced;
-  return (tier == TIER_TF32 || tier == TIER_FP16) ? 8 : 4;
+  if (tier_split(tier)) return 4;
+  return nkb <= 48 ? std::max(nkb, 1) : 32;
 }
 
 template <int BN, int STAGES, bool SPLIT, int ET, bool PAIR>
@@ -718,6 +725,7 @@ void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
     const double panel = static_cast<double>(UNIT_ROWS) * a.kb_per_split * ROW_BYTES * (SPLIT ? 2 : 1);
     a.group_m = g.group_m > 0 ? std::min(g.group_m, a.m_tiles)
                               : static_cast<int>(std::max(1.0, std::min<double>(a.m_tiles, 24.0e6 / panel)));
+    a.chunk = g.chunk > 0 ? g.chunk : default_chunk(g.tier, a.kb_per_split);
     a.out = g.out;
     a.C = g.C;
     a.cm = g.cm;
@@ -739,7 +747,6 @@ void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
   if (np == 0) return;
   grp.nprob = np;
   grp.total_tiles = static_cast<int>(tiles);
-  grp.chunk = descs[0].chunk > 0 ? descs[0].chunk : default_chunk(descs[0].tier);
   grp.err = err;
   grp.wait_ns = tc_wait_limit();
   if constexpr (!PAIR) {
@@ -944,7 +951,7 @@ void tune_save() {
 }
 
 Choice tune(const TcDesc &g, cudaStream_t st, int *err) {
-  const int dch = default_chunk(g.tier);
+  const int dch = default_chunk(g.tier, static_cast<int>(g.Kp / (tier_half(g.tier) ? 64 : 32)));
   const Choice cands[] = {{256, 0, dch}, {256, 1, dch}, {256, 16, dch},
                           {128, 0, dch}, {256, 0, 2 * dch}, {128, 1, dch}};
   void *scratch = nullptr;

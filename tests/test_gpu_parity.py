@@ -60,7 +60,9 @@ def test_gemm_accumulation_bias_flat_in_k(tier):
     """Same-sign products expose any systematic rounding of the tensor-core
     accumulation: without promotion from TMEM every few K blocks the
     relative bias grew linearly with K (about -2e-5 at K = 32768 in TF32x3).
-    With promotion it must stay at the per-chunk level for any K."""
+    With promotion it must stay at the per-chunk level for any K: 4 K blocks
+    in the split tiers (bias below 3e-6), 32 in the one-product tiers, whose
+    per-element rounding (~2^-11) is 50 times the 1e-5 allowed here."""
     P = _gpu()
     rng = np.random.default_rng(0)
     M, N, K = 192, 320, 32768
@@ -71,7 +73,7 @@ def test_gemm_accumulation_bias_flat_in_k(tier):
     P.zgemm_dev(_dev(A), _dev(B), C, tier)
     got = C.cpu().numpy().real
     bias = float(np.mean((got - ref) / ref))
-    assert abs(bias) < 3e-6, bias
+    assert abs(bias) < (1e-5 if tier in ("tf32", "fp16") else 3e-6), bias
     assert float(np.abs(got - ref).max() / ref.max()) < {"tf32": 5e-5, "fp16": 5e-5}.get(tier, 5e-6)
 
 
