@@ -131,6 +131,25 @@ int cc_get_sizes(const cc_ctx *ctx, int *n_occ, int *n_virt, int *n_aux);
 int fns_truncate(cc_ctx *ctx, double threshold, int *n_virt_kept);
 /* Same, keeping the n_keep natural spinors of largest occupation. */
 int fns_truncate_count(cc_ctx *ctx, int n_keep);
+/*
+ * Streamed natural spinors for systems whose virtual Cholesky block L_vv
+ * (X v^2 complex values) does not fit on the device. Call
+ * cc_begin_fns_stream right after cc_init_chunked; then
+ *   1. pass every P once with cc_add_cholesky: only the L_oo, L_ov and L_vo
+ *      blocks are kept (the input is still checked for NaN and Hermiticity);
+ *   2. fns_stream_truncate(threshold, n_keep): the Eq. 24 density from MP2
+ *      amplitudes formed for one occupied index at a time (the o^2 v^2
+ *      amplitudes and <ab||ij> are never held whole), then Eqs. 25-28 as in
+ *      fns_truncate; n_keep > 0 keeps that many natural spinors, else those
+ *      with occupation >= threshold; n_virt_kept (may be NULL) receives the
+ *      count;
+ *   3. pass every P once more with cc_add_cholesky: each chunk's L_vv^P is
+ *      rotated into the kept basis (U^H L^P U) as it arrives; after the last
+ *      one the context continues as after fns_truncate.
+ * Solver calls before the second pass ends fail with CC_ERR_STATE.
+ */
+int cc_begin_fns_stream(cc_ctx *ctx);
+int fns_stream_truncate(cc_ctx *ctx, double threshold, int n_keep, int *n_virt_kept);
 /* Host double[n_virt_before]: occupations of the last FNS step, descending. */
 int fns_get_occupations(const cc_ctx *ctx, double *occ_host, int n);
 

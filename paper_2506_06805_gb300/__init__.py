@@ -104,6 +104,8 @@ _SIGS = {
     "cc_set_wait_limit": (ctypes.c_int, [ctypes.c_ulonglong]),
     "cc_set_fault_injection": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "cc_set_davidson_guess": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "cc_begin_fns_stream": (ctypes.c_int, [_P]),
+    "fns_stream_truncate": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, _I]),
     "ipeom_guess_dev": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "cc_mlp_guess_features": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_long,
                                              ctypes.POINTER(ctypes.c_float)]),
@@ -355,6 +357,20 @@ class System:
         kept = ctypes.c_int()
         _check(lib().fns_truncate(self._ctx, float(threshold), ctypes.byref(kept)),
                self._ctx)
+        return kept.value
+
+    def fns_stream(self, chunks, threshold=None, n_keep=None):
+        """Streamed natural spinors (cc_begin_fns_stream) on a system made
+        with L=None: chunks() must return a fresh iterable of (p0, p1, L_chunk)
+        covering every P; it is consumed twice. Returns the kept count."""
+        _check(lib().cc_begin_fns_stream(self._ctx), self._ctx)
+        for p0, p1, Lc in chunks():
+            self.add_cholesky(p0, p1, Lc)
+        kept = ctypes.c_int()
+        _check(lib().fns_stream_truncate(self._ctx, float(threshold if threshold is not None else 0.0),
+                                         int(n_keep or 0), ctypes.byref(kept)), self._ctx)
+        for p0, p1, Lc in chunks():
+            self.add_cholesky(p0, p1, Lc)
         return kept.value
 
     def fns_occupations(self, n):

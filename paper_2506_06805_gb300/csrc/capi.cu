@@ -647,6 +647,23 @@ int cc_batch_solve(cc_ctx **systems, int n_sys, int n_roots, double ccsd_tol, do
   return CC_OK;
 }
 
+int cc_begin_fns_stream(cc_ctx *ctx) {
+  if (!ctx) return CC_ERR_ARG;
+  return guarded(ctx, [&] {
+    ctx->c.begin_fns_stream();
+    return CC_OK;
+  });
+}
+
+int fns_stream_truncate(cc_ctx *ctx, double threshold, int n_keep, int *n_virt_kept) {
+  if (!ctx || (n_keep <= 0 && !(threshold >= 0))) return CC_ERR_ARG;
+  return guarded(ctx, [&] {
+    const int nk = ctx->c.fns_stream_truncate(threshold, n_keep);
+    if (n_virt_kept) *n_virt_kept = nk;
+    return CC_OK;
+  });
+}
+
 int cc_set_wait_limit(unsigned long long ns) {
   cdfns::tc_set_wait_limit(ns);
   return CC_OK;

@@ -73,10 +73,16 @@ __global__ void split_kernel(const double2 *chunk, int np, int p0, int o, int v,
     mx = fmax(mx, fmax(fabs(x.x), fabs(x.y)));
     asym = fmax(asym, fmax(fabs(x.x - y.x), fabs(x.y + y.y)));
     const long PP = p0 + P;
-    if (p < o && q < o) Loo[(PP * o + p) * o + q] = x;
-    else if (p < o) Lov[(PP * o + p) * v + (q - o)] = x;
-    else if (q < o) Lvo[(PP * v + (p - o)) * o + q] = x;
-    else Lvv[(PP * v + (p - o)) * v + (q - o)] = x;
+    // a NULL destination block is skipped (streamed natural spinors)
+    if (p < o && q < o) {
+      if (Loo) Loo[(PP * o + p) * o + q] = x;
+    } else if (p < o) {
+      if (Lov) Lov[(PP * o + p) * v + (q - o)] = x;
+    } else if (q < o) {
+      if (Lvo) Lvo[(PP * v + (p - o)) * o + q] = x;
+    } else if (Lvv) {
+      Lvv[(PP * v + (p - o)) * v + (q - o)] = x;
+    }
   }
   for (int s = 16; s > 0; s >>= 1) {
     mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, s));
@@ -753,6 +759,28 @@ __global__ void dump_kernel(const double2 *Lpr, long aP, long ap, long ar, const
 }
 
 }  // namespace
+
+// t[j'][a][b] = (G[j'][a][b] - G[j'][b][a]) / (eps_i + eps_j - eps_a - eps_b)
+// for j = i + 1 + j' (MP2 amplitudes of the pairs (i, j > i), Eq. 24's t)
+__global__ void mp2_pair_kernel(const double2 *G, const double *eps, int o, int v, int i, int nj,
+                                double2 *t) {
+  const long vv = static_cast<long>(v) * v;
+  GRID_STRIDE(idx, static_cast<long>(nj) * vv) {
+    const long jp = idx / vv, r = idx - jp * vv;
+    const int a = static_cast<int>(r / v), b = static_cast<int>(r - (r / v) * v);
+    const double2 g1 = G[idx], g2 = G[jp * vv + static_cast<long>(b) * v + a];
+    const double D = eps[i] + eps[i + 1 + jp] - eps[o + a] - eps[o + b];
+    t[idx] = make_double2((g1.x - g2.x) / D, (g1.y - g2.y) / D);
+  }
+}
+
+void mp2_pair_amplitudes(const cplx *G, const double *eps, int o, int v, int i, int nj, cplx *t,
+                         cudaStream_t st) {
+  if (nj <= 0) return;
+  mp2_pair_kernel<<<grid_for(static_cast<long>(nj) * v * v), 256, 0, st>>>(G, eps, o, v, i, nj, t);
+  LAUNCH_CHECK();
+  count_launch();
+}
 
 void split_cholesky(const cplx *chunk, int np, int p0, int o, int v, cplx *Loo, cplx *Lov,
                     cplx *Lvo, cplx *Lvv, unsigned long long *stats, cudaStream_t st) {

@@ -71,6 +71,12 @@ void ladder_antisym(const void *V, bool f32, int v, int a0, int nA, long p0, lon
                     int tier, void *hi, void *lo, long kp, cplx *w64, cudaStream_t st,
                     const float *amax = nullptr);
 
+// MP2 amplitudes of the pairs (i, j) with j = i + 1 + j', j' < nj, from
+// G[j'][a][b] = sum_P L^P_ai L^P_bj: t[j'][a][b] = (G[j'][a][b] - G[j'][b][a])
+// / (eps_i + eps_j - eps_a - eps_b) (= <ab||ij> / D, Eqs. 23-24).
+void mp2_pair_amplitudes(const cplx *G, const double *eps, int o, int v, int i, int nj, cplx *t,
+                         cudaStream_t st);
+
 // R2[i][j][a][b] += R[(i<j)][(a<b)] with the four antisymmetric images.
 void unpack_pairs_add(const cplx *R, int o, int v, const int *ij_i, const int *ij_j,
                       const int *ab_a, const int *ab_b, cplx *R2, cudaStream_t st);

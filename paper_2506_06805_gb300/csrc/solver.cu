@@ -142,7 +142,11 @@ void Ctx::create(int n_occ, int n_virt, int n_aux, const double *eps_host) {
 void Ctx::add_chunk(int p0, int p1, const double *L_host) {
   if (p0 < 0 || p1 > X || p0 >= p1) fail(CC_ERR_ARG, "cholesky chunk range");
   if (!L_host) fail(CC_ERR_ARG, "L chunk is NULL");
-  if (ints) fail(CC_ERR_STATE, "Cholesky vectors already consumed");
+  if (fns_stream == 2) {
+    rotate_chunk(p0, p1, L_host);
+    return;
+  }
+  if (ints || fns_stream == 3) fail(CC_ERR_STATE, "Cholesky vectors already consumed");
   const int n = o + v;
   const size_t per = sizeof(cplx) * n * n;
   const int step = static_cast<int>(std::max<size_t>(1, (size_t(256) << 20) / per));
@@ -150,8 +154,8 @@ void Ctx::add_chunk(int p0, int p1, const double *L_host) {
   for (int q0 = p0; q0 < p1; q0 += step) {
     const int q1 = std::min(p1, q0 + step);
     h2d(stage.p, L_host + static_cast<size_t>(q0 - p0) * 2 * n * n, per * (q1 - q0), st);
-    split_cholesky(stage.c(), q1 - q0, q0, o, v, Loo.c(), Lov.c(), Lvo.c(), Lvv.c(),
-                   stats_d.as<unsigned long long>(), st);
+    split_cholesky(stage.c(), q1 - q0, q0, o, v, Loo.c(), Lov.c(), Lvo.c(),
+                   fns_stream == 1 ? nullptr : Lvv.c(), stats_d.as<unsigned long long>(), st);
   }
   CUDA_CHECK(cudaStreamSynchronize(st));
   for (int P = p0; P < p1; ++P)
@@ -177,6 +181,8 @@ void Ctx::validate_input() {
 
 // Integrals are built at the first solver call, in the tier current then.
 void Ctx::ensure_ready() {
+  if (fns_stream == 1 || fns_stream == 2)
+    fail(CC_ERR_STATE, "streamed natural spinors: both passes over the Cholesky vectors must end first");
   validate_input();
   if (!ints) build_integrals();
 }
@@ -274,6 +280,7 @@ cplx Ctx::energy(const cplx *t1p, const cplx *t2p) {
 // frozen natural spinors (Eqs. 24-28)
 // ===========================================================================
 int Ctx::fns(double threshold, int n_keep) {
+  if (fns_stream) fail(CC_ERR_STATE, "use fns_stream_truncate with cc_begin_fns_stream");
   ensure_ready();
   if (ccsd_done || amps_user) fail(CC_ERR_STATE, "fns_truncate must precede ccsd_solve");
   const double t0 = now_ms();
@@ -361,6 +368,152 @@ int Ctx::fns(double threshold, int n_keep) {
   fns_done = true;
   stat[3] += now_ms() - t0;
   return CC_OK;
+}
+
+// ===========================================================================
+// Streamed frozen natural spinors (Eqs. 24-28) for systems whose L_vv does
+// not fit on the device (X v^2 complex: 184 GB at v = 1698, X = 4000). The
+// first pass over the Cholesky chunks keeps only L_oo, L_ov and L_vo; the
+// density of Eq. 24 is then built from MP2 amplitudes of one occupied index
+// i at a time, D = sum_{i<j} T_ij T_ij^H with T_ij[a][c] = <ac||ij> / D_ij^ac
+// (the unrestricted sum of Eq. 24 counts each pair twice with its 1/2), so
+// the o^2 v^2 amplitudes are never held whole; U follows as in fns(). The
+// second pass rotates each chunk's L_vv^P into the kept basis (U^H L^P U) as
+// it arrives.
+// ===========================================================================
+void Ctx::begin_fns_stream() {
+  if (n_have > 0 || ints || fns_stream) fail(CC_ERR_STATE, "cc_begin_fns_stream must precede cc_add_cholesky");
+  if (ccsd_done || amps_user || fns_done) fail(CC_ERR_STATE, "natural spinors must precede CCSD");
+  Lvv.release();
+  fns_stream = 1;
+}
+
+int Ctx::fns_stream_truncate(double threshold, int n_keep) {
+  if (fns_stream != 1) fail(CC_ERR_STATE, "fns_stream_truncate follows the first pass over the chunks");
+  validate_input();
+  const double t0 = now_ms();
+  const int tr = int_tier();
+  const long vv = static_cast<long>(v) * v;
+  Buf Dm(&al, sizeof(cplx) * vv);
+  zero(Dm.p, sizeof(cplx) * vv, st);
+  {
+    const long nmax = std::max(o - 1, 1);
+    Buf G(&al, sizeof(cplx) * nmax * vv), tm(&al, sizeof(cplx) * nmax * vv);
+    for (int i = 0; i + 1 < o; ++i) {
+      const int nj = o - i - 1;
+      // G[j'][a][b] = sum_P L^P_ai L^P_bj, j = i + 1 + j'
+      eng.contract(C1(), Tv(Lvo.c() + i, "Pa", {X, v}, {static_cast<long>(v) * o, o}),
+                   Tv(Lvo.c() + i + 1, "Pbj", {X, v, nj}, {static_cast<long>(v) * o, o, 1}), C0(),
+                   T(G.c(), "jab", {nj, v, v}), tr);
+      mp2_pair_amplitudes(G.c(), eps_d.as<double>(), o, v, i, nj, tm.c(), st);
+      // D_ab += sum_{j,c} t_ij^ac conj(t_ij^bc), stored column-major
+      eng.contract(C1(), T(tm.c(), "jac", {nj, v, v}), conj(T(tm.c(), "jbc", {nj, v, v})), C1(),
+                   T(Dm.c(), "ba", {v, v}), tr);
+    }
+  }
+  // Eq. 25
+  Buf w(&al, sizeof(double) * v);
+  heevd(&al, st, Dm.c(), v, w.as<double>());
+  std::vector<double> occ(v);
+  d2h(occ.data(), w.p, sizeof(double) * v, st);
+  std::reverse(occ.begin(), occ.end());
+  fns_occ = occ;
+  int nk = n_keep;
+  if (nk <= 0) {
+    nk = 0;
+    for (double x : occ)
+      if (x >= threshold) ++nk;
+  }
+  if (nk < 1) fail(CC_ERR_STATE, "FNS threshold keeps no virtual spinor");
+  if (nk > v) fail(CC_ERR_ARG, "n_keep exceeds n_virt");
+  Buf Vt(&al, sizeof(cplx) * nk * v);
+  eng.permute_into(C1(), Tv(Dm.c() + static_cast<long>(v - 1) * v, "ka", {nk, v}, {-v, 1}), C0(),
+                   T(Vt.c(), "ka", {nk, v}));
+  // Eqs. 26-28 in FP64, as in fns()
+  std::vector<cplx> Ed(static_cast<size_t>(vv), mk(0, 0));
+  for (int a = 0; a < v; ++a) Ed[static_cast<size_t>(a) * v + a] = mk(eps[o + a], 0);
+  Buf Ev(&al, sizeof(cplx) * vv);
+  h2d(Ev.p, Ed.data(), sizeof(cplx) * vv, st);
+  Buf EVt(&al, sizeof(cplx) * nk * v), Fm(&al, sizeof(cplx) * nk * nk);
+  eng.contract(C1(), T(Vt.c(), "kb", {nk, v}), T(Ev.c(), "ab", {v, v}), C0(),
+               T(EVt.c(), "ka", {nk, v}), TIER_FP64);
+  eng.contract(C1(), conj(T(Vt.c(), "ka", {nk, v})), T(EVt.c(), "la", {nk, v}), C0(),
+               T(Fm.c(), "lk", {nk, nk}), TIER_FP64);
+  Buf w2(&al, sizeof(double) * nk);
+  heevd(&al, st, Fm.c(), nk, w2.as<double>());
+  eps_kept.resize(nk);
+  d2h(eps_kept.data(), w2.p, sizeof(double) * nk, st);
+  U_fns.reset(&al, sizeof(cplx) * v * nk);
+  eng.contract(C1(), T(Vt.c(), "ka", {nk, v}), T(Fm.c(), "lk", {nk, nk}), C0(),
+               T(U_fns.c(), "al", {v, nk}), TIER_FP64);
+  Lvv_kept.reset(&al, sizeof(cplx) * X * nk * nk);
+  have_P2.assign(X, 0);
+  n_have2 = 0;
+  fns_stream = 2;
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  check_err_flag();
+  fns_ms = now_ms() - t0;
+  return nk;
+}
+
+void Ctx::rotate_chunk(int p0, int p1, const double *L_host) {
+  const double t0 = now_ms();
+  const int n = o + v;
+  const int nk = static_cast<int>(eps_kept.size());
+  const int rt = int_tier();
+  const size_t per = sizeof(cplx) * n * n;
+  const int step = static_cast<int>(std::max<size_t>(1, (size_t(512) << 20) / per));
+  const int cap = std::min(step, p1 - p0);
+  Buf stage(&al, per * cap), lvv(&al, sizeof(cplx) * cap * v * v), tmp(&al, sizeof(cplx) * cap * v * nk);
+  Buf scratch_stats(&al, 64);
+  zero(scratch_stats.p, 64, st);
+  for (int q0 = p0; q0 < p1; q0 += step) {
+    const int q1 = std::min(p1, q0 + step), nq = q1 - q0;
+    h2d(stage.p, L_host + static_cast<size_t>(q0 - p0) * 2 * n * n, per * nq, st);
+    split_cholesky(stage.c(), nq, 0, o, v, nullptr, nullptr, nullptr, lvv.c(),
+                   scratch_stats.as<unsigned long long>(), st);
+    eng.contract(C1(), T(lvv.c(), "Pab", {nq, v, v}), T(U_fns.c(), "bl", {v, nk}), C0(),
+                 T(tmp.c(), "Pal", {nq, v, nk}), rt);
+    eng.contract(C1(), conj(T(U_fns.c(), "ak", {v, nk})), T(tmp.c(), "Pal", {nq, v, nk}), C0(),
+                 T(Lvv_kept.c() + static_cast<long>(q0) * nk * nk, "Pkl", {nq, nk, nk}), rt);
+  }
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  check_err_flag();
+  for (int P = p0; P < p1; ++P)
+    if (!have_P2[P]) {
+      have_P2[P] = 1;
+      ++n_have2;
+    }
+  fns_ms += now_ms() - t0;
+  if (n_have2 == X) finish_fns_stream();
+}
+
+void Ctx::finish_fns_stream() {
+  const int nk = static_cast<int>(eps_kept.size());
+  const int rt = int_tier();
+  Buf Lov2(&al, sizeof(cplx) * X * o * nk), Lvo2(&al, sizeof(cplx) * X * nk * o);
+  eng.contract(C1(), T(Lov.c(), "Pia", {X, o, v}), T(U_fns.c(), "al", {v, nk}), C0(),
+               T(Lov2.c(), "Pil", {X, o, nk}), rt);
+  eng.contract(C1(), conj(T(U_fns.c(), "al", {v, nk})), T(Lvo.c(), "Pai", {X, v, o}), C0(),
+               T(Lvo2.c(), "Pli", {X, nk, o}), rt);
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  check_err_flag();
+  Lov = std::move(Lov2);
+  Lvo = std::move(Lvo2);
+  Lvv = std::move(Lvv_kept);
+  U_fns.release();
+  v = nk;
+  eps.resize(o + v);
+  for (int a = 0; a < v; ++a) eps[o + a] = eps_kept[a];
+  eps_d.reset(&al, sizeof(double) * (o + v));
+  h2d(eps_d.p, eps.data(), sizeof(double) * (o + v), st);
+  ints = false;
+  hbar_done = false;
+  amps = false;
+  eng.clear_cache();
+  fns_done = true;
+  fns_stream = 3;
+  stat[3] += fns_ms;
 }
 
 // ===========================================================================

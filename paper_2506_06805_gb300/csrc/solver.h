@@ -61,6 +61,15 @@ struct Ctx {
   long sig_gen = 0;  // bumped whenever H-bar or the sigma workspace changes
 
   std::vector<double> fns_occ;
+  // streamed natural spinors (cc_begin_fns_stream): 0 off, 1 first pass
+  // over the Cholesky chunks (occupied blocks kept, L_vv dropped), 2 second
+  // pass (each chunk's L_vv rotated into the kept basis), 3 done
+  int fns_stream = 0;
+  Buf U_fns, Lvv_kept;        // rotation [v][nk] and the rotated L_vv [X][nk][nk]
+  std::vector<double> eps_kept;
+  std::vector<char> have_P2;
+  long n_have2 = 0;
+  double fns_ms = 0;
   double stat[24] = {0};
   // CUDA events around each batched sigma build this context took part in,
   // shared by the systems of that batch (destroyed with the last reference)
@@ -99,6 +108,10 @@ struct Ctx {
   void build_integrals();
   // --- solvers ---
   int fns(double threshold, int n_keep);
+  void begin_fns_stream();
+  int fns_stream_truncate(double threshold, int n_keep);
+  void rotate_chunk(int p0, int p1, const double *L_host);
+  void finish_fns_stream();
   int ccsd(double tol, int max_iter, double *e_out, int *n_iter);
   int ipeom(int n_roots, double tol, int max_iter, double *omega, double *r1w, int *n_iter);
   // right and left vectors (Eqs. 18-20), biorthonormal: L^T R = 1

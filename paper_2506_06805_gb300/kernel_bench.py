@@ -66,6 +66,8 @@ def main():
     p.add_argument("--warmup", type=int, default=1)
     p.add_argument("--left", action="store_true",
                    help="solve: left vectors too (ipeom_solve_lr)")
+    p.add_argument("--fns-keep", type=int, default=0,
+                   help="solve: streamed natural spinors keeping this many virtuals")
     a = p.parse_args()
     if a.what == "solve":
         return solve_run(a)
@@ -214,12 +216,26 @@ def solve_run(a):
     eps = synth.make_eps(rng, o, v, c.kramers)
     out = {"config": a.config, "o": o, "v": v, "X": X, "roots": nr, "tier": a.tier,
            "eom_tier": a.eom_tier}
+    def chunks():
+        # the same draws each time: eps first, then the vectors P in order
+        r = np.random.default_rng(c.seed)
+        synth.make_eps(r, o, v, c.kramers)
+        for p0 in range(0, X, 200):
+            p1 = min(X, p0 + 200)
+            yield p0, p1, synth.cholesky_chunks(r, o + v, X, p0, p1, c.kramers)
+
     t0 = time.perf_counter()
     with System(eps, None, n_occ=o, n_aux=X, tier=a.tier, eom_tier=a.eom_tier,
                 torch_memory=False) as s:
-        for p0 in range(0, X, 200):
-            p1 = min(X, p0 + 200)
-            s.add_cholesky(p0, p1, synth.cholesky_chunks(rng, o + v, X, p0, p1, c.kramers))
+        if a.fns_keep > 0:
+            out["fns_kept"] = s.fns_stream(chunks, n_keep=a.fns_keep)
+            out["fns_s"] = s.stats()["fns_ms"] / 1e3
+            occ = s.fns_occupations(v)
+            out["fns_occ_range"] = [float(occ[0]), float(occ[a.fns_keep - 1]), float(occ[-1])]
+            out["fns_kept_at_1e-5"] = int(np.count_nonzero(occ >= 1e-5))
+        else:
+            for p0, p1, Lc in chunks():
+                s.add_cholesky(p0, p1, Lc)
         t1 = time.perf_counter()
         e = s.ccsd(tol=c.ccsd_tol, max_iter=60)
         t2 = time.perf_counter()

@@ -320,6 +320,32 @@ def test_fns_fast_tier_matches_oracle(tier, eom_tier, tol_occ, tol_ip):
     assert np.abs(np.sort_complex(w) - w_ref).max() <= tol_ip
 
 
+def test_streamed_fns_matches_oracle():
+    """Streamed natural spinors (two passes over chunks of L, the density
+    from MP2 amplitudes one occupied index at a time) against the oracle's
+    FNS pipeline (Eqs. 24-28): occupations, kept count, E_corr and IPs after
+    truncation, FP64 tier."""
+    P = _gpu()
+    from oracle import fns
+    o, v, X = 8, 40, 120
+    eps, L = _system(o, v, X, seed=6, scale=4.0)
+    out = fns.frozen_natural_spinors(L, eps, o, n_keep=18)
+    e_ref, w_ref = _oracle_roots(out["eps"], out["L"], o, 4, tol=1e-11)
+
+    def chunks():
+        for p0 in range(0, X, 32):
+            yield p0, min(X, p0 + 32), L[p0:min(X, p0 + 32)]
+    with P.System(eps, None, n_occ=o, n_aux=X) as s:
+        kept = s.fns_stream(chunks, n_keep=18)
+        occ = s.fns_occupations(v)
+        e = s.ccsd(tol=1e-11)
+        w, _ = s.ipeom(4, tol=1e-9)
+    assert kept == 18
+    assert np.abs(occ - out["occupations"]).max() <= 1e-12 * out["occupations"][0]
+    assert abs(e - e_ref) <= 1e-10
+    assert np.abs(np.sort_complex(w) - w_ref).max() <= 1e-9
+
+
 # --- boundary behaviour on a live device --------------------------------------------
 
 def test_rejects_non_hermitian_and_nan():
