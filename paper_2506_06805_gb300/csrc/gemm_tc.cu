@@ -787,7 +787,8 @@ void check_desc(const TcDesc &g) {
 
 // CTA pairs (cta_group::2) for wide tiles: on unless CDFNS_PAIR is "0"
 // (read once), and used when the launch has enough 256-row units to give
-// every SM pair one.
+// every SM pair one and padding the rows to 256 instead of 128 adds less
+// than 3 % to the tensor work.
 bool pair_enabled() {
   static const bool on = [] {
     const char *e = std::getenv("CDFNS_PAIR");
@@ -796,15 +797,21 @@ bool pair_enabled() {
   return on;
 }
 
-long pair_units(const TcDesc *d, int n) {
-  long u = 0;
-  for (int q = 0; q < n; ++q)
-    if (d[q].M > 0 && d[q].N > 0) u += ((2 * d[q].M + 255) / 256) * ((d[q].N + 255) / 256);
-  return u;
+bool pair_pays(const TcDesc *d, int n) {
+  long units = 0;
+  double rows1 = 0, rows2 = 0;
+  for (int q = 0; q < n; ++q) {
+    if (d[q].M <= 0 || d[q].N <= 0) continue;
+    const long r = 2 * d[q].M, nt = (d[q].N + 255) / 256;
+    units += ((r + 255) / 256) * nt;
+    rows1 += static_cast<double>((r + 127) / 128 * 128) * nt;
+    rows2 += static_cast<double>((r + 255) / 256 * 256) * nt;
+  }
+  return units >= 76 && rows2 <= 1.03 * rows1;
 }
 
 void dispatch(const TcDesc *d, int n, bool wide, cudaStream_t st, int *err) {
-  const bool pair = wide && pair_enabled() && pair_units(d, n) >= 76;
+  const bool pair = wide && pair_enabled() && pair_pays(d, n);
   switch (d[0].tier) {
     case TIER_TF32:
       if (pair) launch<256, 6, false, 0, true>(d, n, st, err);
