@@ -101,6 +101,11 @@ int cc_init(int n_occ, int n_virt, int n_aux, const double *eps,
 int cc_init_chunked(int n_occ, int n_virt, int n_aux, const double *eps,
                     cc_ctx **out);
 int cc_add_cholesky(cc_ctx *ctx, int p0, int p1, const double *L_chunk);
+/* Same from device memory (L_chunk_dev: complex128 [p1-p0][n][n] on the
+ * context's device, complete in the order of the context's stream); the
+ * call returns once the chunk has been consumed, so the caller may reuse the
+ * buffer. For inputs generated or already resident on the GPU. */
+int cc_add_cholesky_dev(cc_ctx *ctx, int p0, int p1, const double *L_chunk_dev);
 
 /* Tier of the CCSD contractions and of the H-bar build (CC_TIER_*; default
  * FP64). Set after ccsd_solve, it also replaces the tier that ccsd_solve

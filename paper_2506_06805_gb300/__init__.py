@@ -46,6 +46,7 @@ _SIGS = {
     "cc_init_chunked": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        _D, ctypes.POINTER(_P)]),
     "cc_add_cholesky": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _D]),
+    "cc_add_cholesky_dev": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P]),
     "cc_set_precision": (ctypes.c_int, [_P, ctypes.c_int]),
     "cc_set_precision_eom": (ctypes.c_int, [_P, ctypes.c_int]),
     "cc_set_stream": (ctypes.c_int, [_P, _P]),
@@ -345,6 +346,11 @@ class System:
         return o.value, v.value, x.value
 
     def add_cholesky(self, p0, p1, Lc):
+        """Cholesky vectors P in [p0, p1): a numpy array (host) or a
+        contiguous torch complex128 CUDA tensor (device), [p1-p0][n][n]."""
+        if hasattr(Lc, "is_cuda") and Lc.is_cuda:
+            _check(lib().cc_add_cholesky_dev(self._ctx, p0, p1, _P(Lc.data_ptr())), self._ctx)
+            return
         Lc = np.ascontiguousarray(Lc, dtype=np.complex128)
         _check(lib().cc_add_cholesky(self._ctx, p0, p1,
                                      Lc.view(np.float64).ctypes.data_as(_D)), self._ctx)

@@ -180,6 +180,14 @@ int cc_add_cholesky(cc_ctx *ctx, int p0, int p1, const double *L_chunk) {
   });
 }
 
+int cc_add_cholesky_dev(cc_ctx *ctx, int p0, int p1, const double *L_chunk_dev) {
+  if (!ctx) return CC_ERR_ARG;
+  return guarded(ctx, [&] {
+    ctx->c.add_chunk(p0, p1, L_chunk_dev, true);
+    return CC_OK;
+  });
+}
+
 int cc_init(int n_occ, int n_virt, int n_aux, const double *eps, const double *L, cc_ctx **out) {
   if (!out) return CC_ERR_ARG;
   *out = nullptr;

@@ -139,23 +139,28 @@ void Ctx::create(int n_occ, int n_virt, int n_aux, const double *eps_host) {
   n_have = 0;
 }
 
-void Ctx::add_chunk(int p0, int p1, const double *L_host) {
+void Ctx::add_chunk(int p0, int p1, const double *L, bool on_device) {
   if (p0 < 0 || p1 > X || p0 >= p1) fail(CC_ERR_ARG, "cholesky chunk range");
-  if (!L_host) fail(CC_ERR_ARG, "L chunk is NULL");
+  if (!L) fail(CC_ERR_ARG, "L chunk is NULL");
   if (fns_stream == 2) {
-    rotate_chunk(p0, p1, L_host);
+    rotate_chunk(p0, p1, L, on_device);
     return;
   }
   if (ints || fns_stream == 3) fail(CC_ERR_STATE, "Cholesky vectors already consumed");
   const int n = o + v;
   const size_t per = sizeof(cplx) * n * n;
-  const int step = static_cast<int>(std::max<size_t>(1, (size_t(256) << 20) / per));
-  Buf stage(&al, per * std::min(step, p1 - p0));
-  for (int q0 = p0; q0 < p1; q0 += step) {
-    const int q1 = std::min(p1, q0 + step);
-    h2d(stage.p, L_host + static_cast<size_t>(q0 - p0) * 2 * n * n, per * (q1 - q0), st);
-    split_cholesky(stage.c(), q1 - q0, q0, o, v, Loo.c(), Lov.c(), Lvo.c(),
+  if (on_device) {
+    split_cholesky(reinterpret_cast<const cplx *>(L), p1 - p0, p0, o, v, Loo.c(), Lov.c(), Lvo.c(),
                    fns_stream == 1 ? nullptr : Lvv.c(), stats_d.as<unsigned long long>(), st);
+  } else {
+    const int step = static_cast<int>(std::max<size_t>(1, (size_t(256) << 20) / per));
+    Buf stage(&al, per * std::min(step, p1 - p0));
+    for (int q0 = p0; q0 < p1; q0 += step) {
+      const int q1 = std::min(p1, q0 + step);
+      h2d(stage.p, L + static_cast<size_t>(q0 - p0) * 2 * n * n, per * (q1 - q0), st);
+      split_cholesky(stage.c(), q1 - q0, q0, o, v, Loo.c(), Lov.c(), Lvo.c(),
+                     fns_stream == 1 ? nullptr : Lvv.c(), stats_d.as<unsigned long long>(), st);
+    }
   }
   CUDA_CHECK(cudaStreamSynchronize(st));
   for (int P = p0; P < p1; ++P)
@@ -456,7 +461,7 @@ int Ctx::fns_stream_truncate(double threshold, int n_keep) {
   return nk;
 }
 
-void Ctx::rotate_chunk(int p0, int p1, const double *L_host) {
+void Ctx::rotate_chunk(int p0, int p1, const double *L, bool on_device) {
   const double t0 = now_ms();
   const int n = o + v;
   const int nk = static_cast<int>(eps_kept.size());
@@ -464,13 +469,18 @@ void Ctx::rotate_chunk(int p0, int p1, const double *L_host) {
   const size_t per = sizeof(cplx) * n * n;
   const int step = static_cast<int>(std::max<size_t>(1, (size_t(512) << 20) / per));
   const int cap = std::min(step, p1 - p0);
-  Buf stage(&al, per * cap), lvv(&al, sizeof(cplx) * cap * v * v), tmp(&al, sizeof(cplx) * cap * v * nk);
+  Buf stage, lvv(&al, sizeof(cplx) * cap * v * v), tmp(&al, sizeof(cplx) * cap * v * nk);
+  if (!on_device) stage.reset(&al, per * cap);
   Buf scratch_stats(&al, 64);
   zero(scratch_stats.p, 64, st);
   for (int q0 = p0; q0 < p1; q0 += step) {
     const int q1 = std::min(p1, q0 + step), nq = q1 - q0;
-    h2d(stage.p, L_host + static_cast<size_t>(q0 - p0) * 2 * n * n, per * nq, st);
-    split_cholesky(stage.c(), nq, 0, o, v, nullptr, nullptr, nullptr, lvv.c(),
+    const cplx *src = reinterpret_cast<const cplx *>(L) + static_cast<size_t>(q0 - p0) * n * n;
+    if (!on_device) {
+      h2d(stage.p, src, per * nq, st);
+      src = stage.c();
+    }
+    split_cholesky(src, nq, 0, o, v, nullptr, nullptr, nullptr, lvv.c(),
                    scratch_stats.as<unsigned long long>(), st);
     eng.contract(C1(), T(lvv.c(), "Pab", {nq, v, v}), T(U_fns.c(), "bl", {v, nk}), C0(),
                  T(tmp.c(), "Pal", {nq, v, nk}), rt);

@@ -102,7 +102,8 @@ struct Ctx {
 
   // --- lifecycle ---
   void create(int n_occ, int n_virt, int n_aux, const double *eps_host);
-  void add_chunk(int p0, int p1, const double *L_host);
+  // L chunk [p1-p0][n][n] complex128 in host memory, or device memory (on_device)
+  void add_chunk(int p0, int p1, const double *L, bool on_device = false);
   void validate_input();
   void ensure_ready();
   void build_integrals();
@@ -110,7 +111,7 @@ struct Ctx {
   int fns(double threshold, int n_keep);
   void begin_fns_stream();
   int fns_stream_truncate(double threshold, int n_keep);
-  void rotate_chunk(int p0, int p1, const double *L_host);
+  void rotate_chunk(int p0, int p1, const double *L, bool on_device);
   void finish_fns_stream();
   int ccsd(double tol, int max_iter, double *e_out, int *n_iter);
   int ipeom(int n_roots, double tol, int max_iter, double *omega, double *r1w, int *n_iter);

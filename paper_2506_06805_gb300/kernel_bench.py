@@ -27,6 +27,8 @@ the ladder rate, the DIIS depth the device memory allowed and the high-water
 mark of the library's device memory; with --left it then solves for the
 right and left vectors together (ipeom_solve_lr) and reports their
 biorthonormality and 1h overlaps.
+``warmstart`` trains the amplitude and Davidson-start networks on generated
+smaller systems and solves a configured system with and without them.
 ``cholesky`` times the single-step pivoted Cholesky decomposition (Eq. 21)
 of M = B B^H for a seeded generator B [N][r] and reports the HBM rate on its
 algorithmic bytes.
@@ -45,7 +47,10 @@ def main():
 
     from . import System, synth, use_torch_memory, zgemm_dev
     p = argparse.ArgumentParser()
-    p.add_argument("what", choices=["ladder", "gemm", "fns", "batch", "solve", "cholesky"])
+    p.add_argument("what", choices=["ladder", "gemm", "fns", "batch", "solve", "cholesky",
+                                    "warmstart"])
+    p.add_argument("--train", default="12,96,384,3",
+                   help="warmstart: o,v,X,count of the generated training systems")
     p.add_argument("--pairs", type=int, default=435600, help="cholesky: N (orbital pairs)")
     p.add_argument("--rank", type=int, default=600, help="cholesky: columns of the generator")
     p.add_argument("--tau", type=float, default=0.0, help="cholesky: threshold")
@@ -68,9 +73,13 @@ def main():
                    help="solve: left vectors too (ipeom_solve_lr)")
     p.add_argument("--fns-keep", type=int, default=0,
                    help="solve: streamed natural spinors keeping this many virtuals")
+    p.add_argument("--device-inputs", action="store_true",
+                   help="solve: draw the Cholesky vectors on the GPU (synth.cholesky_chunks_device)")
     a = p.parse_args()
     if a.what == "solve":
         return solve_run(a)
+    if a.what == "warmstart":
+        return warmstart_run(a)
     use_torch_memory()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -216,12 +225,19 @@ def solve_run(a):
     eps = synth.make_eps(rng, o, v, c.kramers)
     out = {"config": a.config, "o": o, "v": v, "X": X, "roots": nr, "tier": a.tier,
            "eom_tier": a.eom_tier}
+    step = max(1, min(200, int(2e9 // (16 * (o + v) ** 2))))
+
     def chunks():
         # the same draws each time: eps first, then the vectors P in order
+        if a.device_inputs:
+            for p0 in range(0, X, step):
+                p1 = min(X, p0 + step)
+                yield p0, p1, synth.cholesky_chunks_device(c.seed, o + v, X, p0, p1)
+            return
         r = np.random.default_rng(c.seed)
         synth.make_eps(r, o, v, c.kramers)
-        for p0 in range(0, X, 200):
-            p1 = min(X, p0 + 200)
+        for p0 in range(0, X, step):
+            p1 = min(X, p0 + step)
             yield p0, p1, synth.cholesky_chunks(r, o + v, X, p0, p1, c.kramers)
 
     t0 = time.perf_counter()
@@ -263,6 +279,64 @@ def solve_run(a):
         "ladder_ms_per_call": st["ladder_ms"] / max(1.0, st["ladder_calls"]),
         "diis_depth": int(st["diis_depth"]), "device_peak_gb": st["device_peak_bytes"] / 1e9,
     })
+    print(json.dumps(out))
+
+
+def warmstart_run(a):
+    """Learned starts on a configured system: the amplitude network (t2 =
+    rho t_MP2) and the Davidson-start network (rho on first-order 2h1p
+    components), both trained on generated smaller systems of the same
+    recipe, against the MP2 / unit-vector start: CCSD and Davidson
+    iterations, their times, and the IP differences."""
+    import time
+
+    import torch
+
+    from . import Mlp, System, synth
+    o_t, v_t, x_t, n_t = (int(x) for x in a.train.split(","))
+    c = synth.CONFIGS[a.config]
+    nr = a.roots if a.roots > 0 else c.n_roots
+    t0 = time.perf_counter()
+    amp, guess = Mlp(seed=0), Mlp(seed=1)
+    for k in range(n_t):
+        rng = np.random.default_rng([c.seed, 100 + k])
+        eps = synth.make_eps(rng, o_t, v_t, c.kramers)
+        L = synth.make_cholesky(rng, o_t + v_t, x_t, c.kramers)
+        with System(eps, L, n_occ=o_t, tier=a.tier, eom_tier=a.eom_tier) as s:
+            s.ccsd(tol=c.ccsd_tol, max_iter=100)
+            s.ipeom(nr, tol=c.eom_tol, max_iter=200)
+            amp.add_samples(s, 200000)
+            guess.add_guess_samples(s, 200000)
+    for net in (amp, guess):
+        perm = np.random.default_rng(0).permutation(net.num_samples())
+        net.train(2000, batch=2048, lr=2e-3, perm=perm)
+    torch.cuda.synchronize()
+    out = {"config": a.config, "tier": a.tier, "eom_tier": a.eom_tier, "roots": nr,
+           "train_systems": [o_t, v_t, x_t, n_t], "train_s": time.perf_counter() - t0}
+    c2, eps, L = synth.make_config(a.config)
+    res = {}
+    with System(eps, L, n_occ=c.n_occ, tier=a.tier, eom_tier=a.eom_tier) as s:
+        for mode in ("plain", "learned", "plain", "learned"):  # second round timed
+            s.reset_amplitudes()
+            s.set_davidson_guess("unit" if mode == "plain" else "learned",
+                                 None if mode == "plain" else guess)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            if mode == "learned":
+                amp.warm_start(s)
+            e = s.ccsd(tol=c.ccsd_tol, max_iter=100)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            w, _ = s.ipeom(nr, tol=c.eom_tol, max_iter=200)
+            torch.cuda.synchronize()
+            t3 = time.perf_counter()
+            res[mode] = {"ccsd_iter": s.ccsd_iterations, "davidson_iter": s.davidson_iterations,
+                         "ccsd_s": t2 - t1, "ipeom_s": t3 - t2, "time_to_roots_s": t3 - t1,
+                         "e_corr": [e.real, e.imag], "ips": np.sort_complex(w)}
+    d = float(np.abs(res["plain"]["ips"] - res["learned"]["ips"]).max())
+    for m in res:
+        res[m]["ips"] = [float(x) for x in res[m]["ips"].real]
+    out.update({"plain": res["plain"], "learned": res["learned"], "max_dIP_learned_vs_plain": d})
     print(json.dumps(out))
 
 
