@@ -524,18 +524,31 @@ __global__ void __launch_bounds__(256) antisym_tile_kernel(
   const int C0 = ct * 32, D0 = dt * 32;
   const long ld = static_cast<long>(v - a0) * v;
   const float sc = (PT >= 2 && amax) ? fp16_scale(*amax) : 1.0f;
-  for (long r = blockIdx.y; r < np; r += gridDim.y) {
+  // Each block walks many pairs r; the tiles of the next pair are loaded into
+  // registers while the current one is antisymmetrised and stored, so every
+  // thread keeps eight loads in flight across the loop.
+  float2 n1[4], n2[4];
+  auto fetch = [&](long r) {
     const int a = pair_a[p0 + r], b = pair_b[p0 + r];
     const long ra = static_cast<long>(a - a0) * v, cb = static_cast<long>(b - a0) * v;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int row = ty + 8 * j;
       const int c = C0 + row, d = D0 + tx;
-      s1[row][tx] = (c < v && d < v) ? V[(ra + c) * ld + cb + d] : make_float2(0.f, 0.f);
+      n1[j] = (c < v && d < v) ? V[(ra + c) * ld + cb + d] : make_float2(0.f, 0.f);
       const int d2 = D0 + row, c2 = C0 + tx;
-      s2[row][tx] = (d2 < v && c2 < v) ? V[(ra + d2) * ld + cb + c2] : make_float2(0.f, 0.f);
+      n2[j] = (d2 < v && c2 < v) ? V[(ra + d2) * ld + cb + c2] : make_float2(0.f, 0.f);
+    }
+  };
+  if (blockIdx.y < np) fetch(blockIdx.y);
+  for (long r = blockIdx.y; r < np; r += gridDim.y) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      s1[ty + 8 * j][tx] = n1[j];
+      s2[ty + 8 * j][tx] = n2[j];
     }
     __syncthreads();
+    if (r + gridDim.y < np) fetch(r + gridDim.y);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int row = ty + 8 * j;
@@ -959,8 +972,11 @@ void ladder_antisym(const void *V, bool f32, int v, int a0, int nA, long p0, lon
   if (!f32) fail(CC_ERR_ARG, "ladder_antisym: tensor-core tiers take an FP32 slab");
   if (tier_scaled(tier) && !amax) fail(CC_ERR_ARG, "ladder_antisym: FP16 needs the W bound");
   const int nt = (v + 31) / 32;
-  dim3 grid(static_cast<unsigned>(nt * (nt + 1) / 2),
-            static_cast<unsigned>(std::min<long>(np, 65535)));
+  // one wave of resident blocks (8 of 256 threads per SM); each walks many
+  // (a, b) pairs
+  const long ntp = static_cast<long>(nt) * (nt + 1) / 2;
+  dim3 grid(static_cast<unsigned>(ntp),
+            static_cast<unsigned>(std::max<long>(1, std::min<long>(np, (152L * 8 + ntp - 1) / ntp))));
   const float2 *Vf = reinterpret_cast<const float2 *>(V);
   if (tier == TIER_BF16X3) {
     antisym_tile_kernel<1><<<grid, dim3(32, 8), 0, st>>>(Vf, v, a0, p0, np, pair_a, pair_b, hi, lo,

@@ -313,10 +313,28 @@ def warmstart_run(a):
     torch.cuda.synchronize()
     out = {"config": a.config, "tier": a.tier, "eom_tier": a.eom_tier, "roots": nr,
            "train_systems": [o_t, v_t, x_t, n_t], "train_s": time.perf_counter() - t0}
-    c2, eps, L = synth.make_config(a.config)
     res = {}
-    with System(eps, L, n_occ=c.n_occ, tier=a.tier, eom_tier=a.eom_tier) as s:
-        for mode in ("plain", "learned", "plain", "learned"):  # second round timed
+    o, v, X = c.n_occ, c.n_virt, c.n_aux
+    if a.fns_keep > 0:
+        # streamed natural spinors from GPU-drawn vectors (the large configuration)
+        rng = np.random.default_rng(c.seed)
+        eps = synth.make_eps(rng, o, v, c.kramers)
+        step = max(1, min(200, int(2e9 // (16 * (o + v) ** 2))))
+
+        def chunks():
+            for p0 in range(0, X, step):
+                yield p0, min(X, p0 + step), synth.cholesky_chunks_device(c.seed, o + v, X, p0,
+                                                                           min(X, p0 + step))
+        sys_ = System(eps, None, n_occ=o, n_aux=X, tier=a.tier, eom_tier=a.eom_tier)
+        out["fns_kept"] = sys_.fns_stream(chunks, n_keep=a.fns_keep)
+    else:
+        _, eps, L = synth.make_config(a.config)
+        sys_ = System(eps, L, n_occ=o, tier=a.tier, eom_tier=a.eom_tier)
+        del L
+    # with two rounds (small systems), the second is the one reported
+    rounds = ("plain", "learned") if a.fns_keep > 0 else ("plain", "learned", "plain", "learned")
+    with sys_ as s:
+        for mode in rounds:
             s.reset_amplitudes()
             s.set_davidson_guess("unit" if mode == "plain" else "learned",
                                  None if mode == "plain" else guess)
@@ -330,7 +348,9 @@ def warmstart_run(a):
             w, _ = s.ipeom(nr, tol=c.eom_tol, max_iter=200)
             torch.cuda.synchronize()
             t3 = time.perf_counter()
+            st = s.stats()
             res[mode] = {"ccsd_iter": s.ccsd_iterations, "davidson_iter": s.davidson_iterations,
+                         "diis_depth": int(st["diis_depth"]),
                          "ccsd_s": t2 - t1, "ipeom_s": t3 - t2, "time_to_roots_s": t3 - t1,
                          "e_corr": [e.real, e.imag], "ips": np.sort_complex(w)}
     d = float(np.abs(res["plain"]["ips"] - res["learned"]["ips"]).max())
