@@ -617,3 +617,22 @@ def test_mlp_features_are_gauge_invariant():
     f1 = mlp.features(L, eps, o, 20)
     f2 = mlp.features(synth.gauge_transform(L, theta), eps, o, 20)
     assert np.abs(f1 - f2).max() <= 1e-10
+
+
+def test_guess_features_are_gauge_invariant_and_first_order_consistent():
+    """The Davidson-start features do not change under spinor phase changes
+    (each is a magnitude, a diagonal element or an indicator), and the first
+    feature is log10 of the first-order component the start is built from."""
+    from oracle import mlp
+    o, v, X = 3, 5, 10
+    eps, L = _system(o, v, X, seed=3, scale=5.0)
+    theta = np.random.default_rng(2).uniform(0, 2 * np.pi, o + v)
+    out = []
+    for Lx in (L, synth.gauge_transform(L, theta)):
+        g = integrals.blocks_from_cholesky(Lx, o)
+        res = ccsd.solve(g, eps, tol=1e-12, max_iter=300)
+        H = ipeom.hbar(g, eps, res["t1"], res["t2"])
+        out.append((mlp.guess_features(H, g, eps, o, 1, 15), ipeom.first_order_guess(H, o, v, 1)))
+    assert np.abs(out[0][0] - out[1][0]).max() <= 1e-8
+    c = out[0][1][o:o + 15]
+    assert np.abs(out[0][0][:, 0] - np.log10(np.abs(c) + 1e-30)).max() <= 1e-12
