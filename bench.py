@@ -43,10 +43,11 @@ sys.path.insert(0, ROOT)
 METRIC = ("IP-EOM-CCSD time-to-roots & ladder TFLOP/s vs plain FP64, "
           "at |ΔIP|≤1e-5 Eh")
 
-# DRAM bytes per ladder call of the current kernels at the medium workload,
-# from the ncu capture summarised in profiles/ (None until it is taken for
-# the kernels as they stand)
-LADDER_TRAFFIC = None
+# DRAM bytes (read + write) per ladder call at the medium workload in the
+# FP16 tier, from the one-pass ncu capture summarised in
+# profiles/launches_medium_fp16.md; to be retaken whenever the ladder's
+# kernels change
+LADDER_TRAFFIC = 131.4e9
 WORKLOAD = "medium"
 
 
@@ -376,7 +377,8 @@ def run_ours(args):
         "bound": "tensor",
         "kernel": f"particle-particle ladder (tcgen05 kind::{kind} GEMMs + antisymmetrise)",
         "achieved": ladder_tf, "peak": peak, "unit": "TFLOP/s",
-        "frac": (ladder_tf / peak) if ladder_tf else None, "traffic": LADDER_TRAFFIC,
+        "frac": (ladder_tf / peak) if ladder_tf else None,
+        "traffic": LADDER_TRAFFIC if (args.config, args.tier) == (WORKLOAD, "fp16") else None,
         "peak_source": f"{src} bf16 sustained x {ratio} (of measured)",
         "algorithmic_flops_per_call": st1["ladder_flops"], "ms_per_call": ladder_ms,
     }
