@@ -139,11 +139,45 @@ __device__ __forceinline__ double scale_c(double x, int half) {
   return 0.5 * x;
 }
 
+// max(|Re|, |Im|) in FP32 of one complex value (the FP16 tiers' scale source)
+__device__ __forceinline__ float mag32(double2 x) {
+  return fmaxf(fabsf(f64_to_f32(x.x)), fabsf(f64_to_f32(x.y)));
+}
+
+// Block maxima of three values combined into mx[0..2] (device floats, zeroed
+// by the caller) with unsigned atomicMax on the float bits; a block skips the
+// atomic when the stored value is already as large (the maximum only grows,
+// so a stale read costs an extra atomic, never a wrong result).
+__device__ __forceinline__ void block_max3(float m0, float m1, float m2, float *mx) {
+  __shared__ float sh[3][8];
+  for (int s = 16; s > 0; s >>= 1) {
+    m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, s));
+    m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, s));
+    m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, s));
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][w] = m0;
+    sh[1][w] = m1;
+    sh[2][w] = m2;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    float x = 0.0f;
+    for (int i = 0; i < static_cast<int>(blockDim.x >> 5); ++i) x = fmaxf(x, sh[threadIdx.x][i]);
+    unsigned *dst = reinterpret_cast<unsigned *>(mx + threadIdx.x);
+    if (__float_as_uint(x) > *reinterpret_cast<volatile unsigned *>(dst))
+      atomicMax(dst, __float_as_uint(x));
+  }
+}
+
+// mx (optional, three zeroed device floats): the maxima of t2, out0 and out1
+// over the whole tensors, for the FP16 tiers' operand scales.
 template <typename T, bool ANTI>
 __global__ void __launch_bounds__(256) t1t1_kernel(const double2 *__restrict__ t1,
                                                    const double2 *__restrict__ t2, double2 *out0,
                                                    double2 *out1, int o, int v, int c0_half,
-                                                   double c0, float f0, float f1) {
+                                                   double c0, float f0, float f1, float *mx) {
   extern __shared__ __align__(16) unsigned char t1t1_sm[];
   T *ti = reinterpret_cast<T *>(t1t1_sm);
   T *tj = ti + v;
@@ -157,6 +191,7 @@ __global__ void __launch_bounds__(256) t1t1_kernel(const double2 *__restrict__ t
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long base = static_cast<long>(ij) * v * v;
   const int a_end = min(v, static_cast<int>(blockIdx.x) * 32 + 32);
+  float m_t = 0.0f, m_0 = 0.0f, m_1 = 0.0f;
   for (int a = blockIdx.x * 32 + warp; a < a_end; a += 8) {
     const T tia = ti[a], tja = tj[a];
     const long row = base + static_cast<long>(a) * v;
@@ -172,12 +207,19 @@ __global__ void __launch_bounds__(256) t1t1_kernel(const double2 *__restrict__ t
         r0 = make_double2(c0 * t.x + p0.x, c0 * t.y + p0.y);
       }
       out0[row + b] = r0;
+      if (mx) {
+        m_t = fmaxf(m_t, mag32(t));
+        m_0 = fmaxf(m_0, mag32(r0));
+      }
       if (out1) {
         const double2 p1 = widen_scaled(x, f1);
-        out1[row + b] = make_double2(t.x + p1.x, t.y + p1.y);
+        const double2 r1 = make_double2(t.x + p1.x, t.y + p1.y);
+        out1[row + b] = r1;
+        if (mx) m_1 = fmaxf(m_1, mag32(r1));
       }
     }
   }
+  if (mx) block_max3(m_t, m_0, m_1, mx);
 }
 
 
@@ -813,7 +855,7 @@ inline dim3 grid2d(int o, int v) {
 namespace {
 template <bool ANTI>
 void t1t1_launch(const cplx *t1, const cplx *t2, cplx *out0, cplx *out1, int o, int v, double c0,
-                 double f0, double f1, bool f32, cudaStream_t st) {
+                 double f0, double f1, bool f32, cudaStream_t st, float *mx) {
   if (o <= 0 || v <= 0) return;
   if (static_cast<long>(o) * o > 65535) fail(CC_ERR_ARG, "t1t1: n_occ too large");
   const int c0_half = c0 == 1.0 ? 0 : (c0 == 0.5 ? 1 : -1);
@@ -824,31 +866,34 @@ void t1t1_launch(const cplx *t1, const cplx *t2, cplx *out0, cplx *out1, int o, 
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(sm)));
   }
+  if (mx) CUDA_CHECK(cudaMemsetAsync(mx, 0, 3 * sizeof(float), st));
   if (f32)
     t1t1_kernel<float2, ANTI><<<grid, 256, sm, st>>>(t1, t2, out0, out1, o, v, c0_half, c0,
-                                                     static_cast<float>(f0), static_cast<float>(f1));
+                                                     static_cast<float>(f0), static_cast<float>(f1),
+                                                     mx);
   else
     t1t1_kernel<double2, ANTI><<<grid, 256, sm, st>>>(t1, t2, out0, out1, o, v, c0_half, c0,
-                                                      static_cast<float>(f0), static_cast<float>(f1));
+                                                      static_cast<float>(f0), static_cast<float>(f1),
+                                                      mx);
   LAUNCH_CHECK();
   count_launch();
 }
 }  // namespace
 
 void make_tau(const cplx *t1, const cplx *t2, cplx *out, int o, int v, double f, cudaStream_t st,
-              bool fp32_t1) {
+              bool fp32_t1, float *mx) {
   if (!fp32_t1 && f != 1.0 && f != 0.5) fail(CC_ERR_ARG, "make_tau: f must be 1 or 1/2");
-  t1t1_launch<true>(t1, t2, out, nullptr, o, v, 1.0, f, 0.0, fp32_t1, st);
+  t1t1_launch<true>(t1, t2, out, nullptr, o, v, 1.0, f, 0.0, fp32_t1, st, mx);
 }
 
 void make_tau_pair(const cplx *t1, const cplx *t2, cplx *tau, cplx *taut, int o, int v,
-                   cudaStream_t st, bool fp32_t1) {
-  t1t1_launch<true>(t1, t2, tau, taut, o, v, 1.0, 1.0, 0.5, fp32_t1, st);
+                   cudaStream_t st, bool fp32_t1, float *mx) {
+  t1t1_launch<true>(t1, t2, tau, taut, o, v, 1.0, 1.0, 0.5, fp32_t1, st, mx);
 }
 
 void make_z(const cplx *t1, const cplx *t2, cplx *out, int o, int v, double c2, cudaStream_t st,
-            bool fp32_t1) {
-  t1t1_launch<false>(t1, t2, out, nullptr, o, v, c2, 1.0, 0.0, fp32_t1, st);
+            bool fp32_t1, float *mx) {
+  t1t1_launch<false>(t1, t2, out, nullptr, o, v, c2, 1.0, 0.0, fp32_t1, st, mx);
 }
 
 void jacobi(const cplx *R1, const cplx *R2, const double *eps, int o, int v, cplx *t1, cplx *t2,

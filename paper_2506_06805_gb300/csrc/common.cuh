@@ -138,6 +138,11 @@ enum Tier {
   TIER_FP16X3 = 5
 };
 constexpr int TIER_LAST = TIER_FP16X3;
+// Engine-internal, not a CC_TIER_*: the CUDA-core path with FP32 products
+// (runs summed in FP64) in the kernels that have that form, FP64 elsewhere.
+// Memory-bound matrix-vector shapes of the tensor-core tiers take it: the
+// FP64 pipe of GB300 is far narrower than its memory.
+constexpr int TIER_SIMT32 = 16;
 // hi/lo operand planes, three products
 __host__ __device__ inline bool tier_split(int t) {
   return t == TIER_TF32X3 || t == TIER_BF16X3 || t == TIER_FP16X3;

@@ -37,6 +37,18 @@ TRef Tv(const cplx *p, const char *idx, std::initializer_list<long> dims,
   return t;
 }
 
+bool whole_view(const TRef &t) {
+  long s = 1;
+  for (int i = static_cast<int>(t.dims.size()) - 1; i >= 0; --i) {
+    if (t.dims[i] != 1 && t.str[i] != s) return false;
+    s *= t.dims[i];
+  }
+  for (size_t i = 0; i < t.idx.size(); ++i)
+    for (size_t j = i + 1; j < t.idx.size(); ++j)
+      if (t.idx[i] == t.idx[j]) return false;
+  return true;
+}
+
 const long *Engine::table(const std::vector<long> &dims, const std::vector<long> &strides) {
   std::ostringstream key;
   for (size_t i = 0; i < dims.size(); ++i) key << dims[i] << ':' << strides[i] << ',';
@@ -83,7 +95,12 @@ std::pair<void *, void *> Engine::packed(const std::string &key, bool a_side, co
   if (tier_split(tier)) pk.lo.reset(al, n);
   if (tier_scaled(tier)) {
     pk.amax.reset(al, sizeof(float));
-    tc_absmax(t.p, rt, kt, ld, rows, K, pk.amax.as<float>(), st);
+    if (t.amax)
+      CUDA_CHECK(cudaMemcpyAsync(pk.amax.p, t.amax, sizeof(float), cudaMemcpyDeviceToDevice, st));
+    else if (whole_view(t))
+      tc_absmax(t.p, nullptr, nullptr, 0, 1, t.size(), pk.amax.as<float>(), st);
+    else
+      tc_absmax(t.p, rt, kt, ld, rows, K, pk.amax.as<float>(), st);
   }
   if (a_side)
     tc_pack_A(t.p, rt, kt, ld, t.conj, rows, K, Kp, tier, pk.hi.p, pk.lo.p, st, pk.amax.as<float>());
@@ -143,12 +160,18 @@ bool linear(const std::vector<long> &dims, const std::vector<long> &str, long *s
 
 void Engine::contract(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef &C,
                       int tier) {
+  if (C.amax_out && !whole_view(C))
+    fail(CC_ERR_ARG, "contract: an output maximum needs the whole output tensor as the view");
+  amax_done_ = false;
   run(alpha, A, B, beta, C, tier, -1, nullptr);
+  // the tensor-core epilogue records it for plain stores; otherwise one pass
+  if (C.amax_out && !amax_done_) tc_absmax(C.p, nullptr, nullptr, 0, 1, C.size(), C.amax_out, st);
 }
 
 bool Engine::prepare(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef &C, int tier,
                      int slot, TcDesc *out) {
   if (slot < 0 || !out) fail(CC_ERR_ARG, "prepare: slot and descriptor required");
+  if (C.amax_out) fail(CC_ERR_ARG, "prepare: output maxima are not tracked in grouped launches");
   return run(alpha, A, B, beta, C, tier, slot, out);
 }
 
@@ -248,6 +271,26 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
   if (M == 0 || N == 0) return false;
   flops += 8.0 * M * N * K;
   const bool tiny = static_cast<double>(M) * N * K < 2.0e6 || K < 16 || M < 8 || N < 8;
+  const bool simt = tier == TIER_FP64 || tier == TIER_SIMT32 || tiny;
+  if (simt && (M == 1 || N == 1)) {
+    // matrix-vector shape: order the outputs by decreasing stride in the
+    // matrix operand, so that neighbouring threads read neighbouring elements
+    // (each output's own sum over k is unchanged)
+    std::vector<long> &d = N == 1 ? mdim : ndim, &s = N == 1 ? amstr : bnstr,
+                      &c = N == 1 ? cmstr : cnstr;
+    std::vector<size_t> ord(d.size());
+    for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return s[x] > s[y]; });
+    std::vector<long> d2, s2, c2;
+    for (size_t i : ord) {
+      d2.push_back(d[i]);
+      s2.push_back(s[i]);
+      c2.push_back(c[i]);
+    }
+    d.swap(d2);
+    s.swap(s2);
+    c.swap(c2);
+  }
   const int trec =
       trace_on_ ? trace_open((out ? "prep " : "") + A.idx + (A.conj ? "*" : "") + "," + B.idx +
                                  (B.conj ? "*" : "") + "->" + C.idx,
@@ -277,8 +320,8 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
   if (mdim.empty()) { lda = 0; ldc = 0; }
   if (ndim.empty()) ldb = 0;
 
-  // small or skinny products stay on the FP64 path (GEMV or a few tiles)
-  if (tier == TIER_FP64 || tiny) {
+  // small or skinny products stay on the CUDA-core path (GEMV or a few tiles)
+  if (simt) {
     GemmDesc g;
     g.M = M; g.N = N; g.K = K;
     g.A = A.p; g.am = am; g.ak = ak; g.lda = lda; g.conjA = A.conj;
@@ -335,7 +378,10 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
       xa = A.amax;
     } else if (f16) {
       float *x = plane_amax(pb + 0);
-      tc_absmax(A.p, am, ak, lda, M, K, x, st);
+      if (whole_view(A))
+        tc_absmax(A.p, nullptr, nullptr, 0, 1, A.size(), x, st);
+      else
+        tc_absmax(A.p, am, ak, lda, M, K, x, st);
       xa = x;
     }
     tc_pack_A(A.p, am, ak, lda, A.conj, M, K, Kp, tier, Ah, Al, st, xa);
@@ -350,7 +396,10 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
       xb = B.amax;
     } else if (f16) {
       float *x = plane_amax(pb + 2);
-      tc_absmax(B.p, bn, bk, ldb, N, K, x, st);
+      if (whole_view(B))
+        tc_absmax(B.p, nullptr, nullptr, 0, 1, B.size(), x, st);
+      else
+        tc_absmax(B.p, bn, bk, ldb, N, K, x, st);
       xb = x;
     }
     tc_pack_B(B.p, bn, bk, ldb, B.conj, N, K, Kp, tier, Bh, Bl, st, xb);
@@ -375,6 +424,12 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
   if (out) {
     *out = t;
     return true;
+  }
+  if (C.amax_out && t.out == TC_OUT_F64 && beta.x == 0.0 && beta.y == 0.0) {
+    CUDA_CHECK(cudaMemsetAsync(C.amax_out, 0, sizeof(float), st));
+    t.amax_out = C.amax_out;
+    t.amax_mul = 1.0f;
+    amax_done_ = true;
   }
   Region r = region("gemm " + A.idx + "," + B.idx + "->" + C.idx);
   gemm_tc(t, st, err_flag);

@@ -28,6 +28,10 @@ struct TRef {
   // FP16 tiers: device float >= max(|Re|, |Im|) over the whole tensor, when
   // the caller already has it (saves the operand's own maximum pass)
   const float *amax = nullptr;
+  // output only: a device float that receives max(|Re|, |Im|) in FP32 over
+  // the whole tensor once the contraction has written it (the view must be
+  // the whole tensor); read by the next contraction's FP16 scale
+  float *amax_out = nullptr;
   long size() const {
     long s = 1;
     for (long d : dims) s *= d;
@@ -49,6 +53,14 @@ inline TRef with_amax(TRef t, const float *m) {
   t.amax = m;
   return t;
 }
+inline TRef with_amax_out(TRef t, float *m) {
+  t.amax_out = m;
+  return t;
+}
+// Whether a view addresses every element of its tensor exactly once
+// (row-major strides of its dims and no repeated index letter): its
+// maximum is then the maximum of the contiguous block.
+bool whole_view(const TRef &t);
 // Mark an operand whose contents stay fixed across calls (integrals, H-bar):
 // its packed tensor-core planes are then built once and reused.
 inline TRef stable(TRef t) {
@@ -130,6 +142,7 @@ class Engine {
   // device float of plane slot `which` for the FP16 operand maximum
   float *plane_amax(int which);
   std::map<int, Buf> amax_planes_;
+  bool amax_done_ = false;  // the last contract() recorded C.amax_out in the GEMM epilogue
   std::map<std::string, Buf> cache_;
   std::map<std::string, Packed> packs_;
   std::set<std::string> uncached_;

@@ -262,9 +262,12 @@ __global__ void gemv_warp_kernel(long N, long K, const double2 *__restrict__ A,
   }
 }
 
-// Few outputs over a long K (Davidson subspace overlaps): one warp per
-// output element and a K range per blockIdx.y; partial sums are added
-// atomically when K is split (C scaled by beta beforehand).
+// Outputs too few to fill the GPU with 64 x 64 tiles (Davidson subspace
+// overlaps, the singles intermediates): one warp per output element and a K
+// range per blockIdx.y; partial sums are added atomically when K is split (C
+// scaled by beta beforehand). F32: runs of four products per lane in FP32,
+// each run added in FP64, as in gemv_warp_kernel.
+template <bool F32>
 __global__ void __launch_bounds__(256) dots_kernel(long M, long N, long K,
                                                    const double2 *__restrict__ A,
                                                    const long *__restrict__ am,
@@ -285,6 +288,18 @@ __global__ void __launch_bounds__(256) dots_kernel(long M, long N, long K,
   double2 ac[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
                    make_double2(0.0, 0.0)};
   long k = k0 + lane;
+  if (F32) {
+    for (; k + 96 < k1; k += 128) {
+      float xr = 0.f, xi = 0.f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long kk = k + 32 * u;
+        cfma32(A[ao + (ak ? ak[kk] : kk)], B[bo + (bk ? bk[kk] : kk)], conjA, conjB, xr, xi);
+      }
+      ac[0].x += f32_to_f64(xr);
+      ac[0].y += f32_to_f64(xi);
+    }
+  }
   for (; k + 96 < k1; k += 128) {
     double2 a[4], b[4];
 #pragma unroll
@@ -398,23 +413,27 @@ void gemm_f64(const GemmDesc &g, cudaStream_t st, int num_sms) {
     gemm_skinny(d, st);
     return;
   }
-  // few outputs over a long K
-  if (g.M * g.N <= 4096 && g.K >= 1024) {
+  // Outputs that would leave most SMs without a 64 x 64 tile: one warp per
+  // output, K split over blocks until about four blocks per SM. GB300's FP64
+  // pipe is narrow (a few FP64 FMAs per clock per SM), so a product on a
+  // handful of tiles would run on a handful of SMs.
+  const long tiles = ((g.M + TM - 1) / TM) * ((g.N + TN - 1) / TN);
+  if (tiles < num_sms && g.M * g.N <= 65535L * 8 && (g.K >= 32 || g.M * g.N <= 4096)) {
     const long gx = (g.M * g.N + 7) / 8;
-    long split = std::max<long>(1, std::min<long>(g.K / 1024, (4L * num_sms + gx - 1) / gx));
+    long split = std::max<long>(1, std::min<long>(g.K / 256, (4L * num_sms + gx - 1) / gx));
     const long kchunk = (g.K + split - 1) / split;
     split = (g.K + kchunk - 1) / kchunk;
     const bool atomic = split > 1;
     if (atomic) scale_2d(g.C, g.cm, g.cn, g.ldc, g.M, g.N, g.beta, st);
     dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(split));
-    dots_kernel<<<grid, 256, 0, st>>>(g.M, g.N, g.K, g.A, g.am, g.ak, g.lda, g.conjA, g.B, g.bn,
-                                      g.bk, g.ldb, g.conjB, g.C, g.cm, g.cn, g.ldc, g.alpha, g.beta,
-                                      kchunk, atomic);
+    auto kern = g.f32 ? dots_kernel<true> : dots_kernel<false>;
+    kern<<<grid, 256, 0, st>>>(g.M, g.N, g.K, g.A, g.am, g.ak, g.lda, g.conjA, g.B, g.bn, g.bk,
+                               g.ldb, g.conjB, g.C, g.cm, g.cn, g.ldc, g.alpha, g.beta, kchunk,
+                               atomic);
     LAUNCH_CHECK();
     count_launch();
     return;
   }
-  const long tiles = ((g.M + TM - 1) / TM) * ((g.N + TN - 1) / TN);
   long split = 1;
   const long target = 2L * num_sms;
   if (tiles < target && g.K >= 4 * TK * 16) {

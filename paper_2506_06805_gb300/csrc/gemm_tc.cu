@@ -569,13 +569,15 @@ __global__ void __launch_bounds__(320, 1)
             const long off = (args.cm ? args.cm[mc] : mc * args.ldc) + cno;
             // alpha in FP32 (the product carries FP32 rounding already),
             // widened on the integer pipes; FP64 arithmetic only for beta
-            const double xr = f32_to_f64(args.alpha_f.x * re - args.alpha_f.y * im);
-            const double xi = f32_to_f64(args.alpha_f.x * im + args.alpha_f.y * re);
+            const float fr = args.alpha_f.x * re - args.alpha_f.y * im;
+            const float fi = args.alpha_f.x * im + args.alpha_f.y * re;
+            const double xr = f32_to_f64(fr), xi = f32_to_f64(fi);
             if (args.out == TC_OUT_F64_ATOMIC) {
               atomicAdd(&C[off].x, xr);
               atomicAdd(&C[off].y, xi);
             } else if (args.beta.x == 0.0 && args.beta.y == 0.0) {
               C[off] = make_double2(xr, xi);
+              if (args.amax_out) omax = fmaxf(omax, fmaxf(fabsf(fr), fabsf(fi)));
             } else if (args.beta.x == 1.0 && args.beta.y == 0.0) {
               // one writer per element: the addition runs in L2 (no read
               // round trip, no FP64 work on the SM)
@@ -736,7 +738,10 @@ void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
     a.alpha_f = make_float2(static_cast<float>(g.alpha.x), static_cast<float>(g.alpha.y));
     a.amax_a = g.amax_a;
     a.amax_b = g.amax_b;
-    a.amax_out = g.out == TC_OUT_F32 ? g.amax_out : nullptr;
+    const bool plain = g.out == TC_OUT_F64 && g.beta.x == 0.0 && g.beta.y == 0.0;
+    if (g.amax_out && g.out != TC_OUT_F32 && !plain)
+      fail(CC_ERR_ARG, "gemm_tc: output maxima need plain stores (F32, or F64 with beta = 0)");
+    a.amax_out = g.amax_out;
     a.amax_mul = g.amax_mul;
     if ((g.amax_a == nullptr) != (g.amax_b == nullptr))
       fail(CC_ERR_ARG, "gemm_tc: FP16 operand scales come in pairs");
@@ -1108,10 +1113,20 @@ __global__ void __launch_bounds__(256) pack_kernel(const double2 *__restrict__ s
   const float sc = (PT >= 2 && amax) ? fp16_scale(*amax) : 1.0f;
   const long kof = kc < K ? (kt ? kt[kc] : kc) : 0;
   const long step = static_cast<long>(gridDim.y) * blockDim.y;
-  for (long r = blockIdx.y * static_cast<long>(blockDim.y) + threadIdx.y; r < rows; r += step) {
-    double2 a = make_double2(0.0, 0.0);
-    if (kc < K) a = src[(rt ? rt[r] : r * ld) + kof];
-    pack_store<PT, EXPAND>(hi, lo, r, kc, Kp, a, conj, sc);
+  // four rows per pass: their loads are all in flight before the stores
+  for (long r = blockIdx.y * static_cast<long>(blockDim.y) + threadIdx.y; r < rows; r += 4 * step) {
+    double2 a[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long ru = r + u * step;
+      a[u] = make_double2(0.0, 0.0);
+      if (kc < K && ru < rows) a[u] = src[(rt ? rt[ru] : ru * ld) + kof];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long ru = r + u * step;
+      if (ru < rows) pack_store<PT, EXPAND>(hi, lo, ru, kc, Kp, a[u], conj, sc);
+    }
   }
 }
 
@@ -1176,11 +1191,40 @@ __global__ void __launch_bounds__(256) absmax_kernel(const double2 *__restrict__
   const long xstep = static_cast<long>(gridDim.x) * blockDim.x;
   const long ystep = static_cast<long>(gridDim.y) * blockDim.y;
   for (long xi = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; xi < X; xi += xstep) {
-    for (long yi = blockIdx.y * static_cast<long>(blockDim.y) + threadIdx.y; yi < Y; yi += ystep) {
-      const long r = rows_inner ? xi : yi, k = rows_inner ? yi : xi;
-      const double2 a = src[(rt ? rt[r] : r * ld) + (kt ? kt[k] : k)];
-      m = fmaxf(m, fmaxf(fabsf(f64_to_f32(a.x)), fabsf(f64_to_f32(a.y))));
+    // four elements per pass, loads in flight together
+    for (long yi = blockIdx.y * static_cast<long>(blockDim.y) + threadIdx.y; yi < Y; yi += 4 * ystep) {
+      double2 a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long yu = yi + u * ystep;
+        const long r = rows_inner ? xi : yu, k = rows_inner ? yu : xi;
+        a[u] = yu < Y ? src[(rt ? rt[r] : r * ld) + (kt ? kt[k] : k)] : make_double2(0.0, 0.0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        m = fmaxf(m, fmaxf(fabsf(f64_to_f32(a[u].x)), fabsf(f64_to_f32(a[u].y))));
     }
+  }
+  block_max_store(m, amax);
+}
+
+// Contiguous operand: four independent 16-byte loads per thread in flight.
+__global__ void __launch_bounds__(256) absmax_flat_kernel(const double2 *__restrict__ src, long n,
+                                                          float *amax) {
+  float m = 0.0f;
+  const long step = static_cast<long>(gridDim.x) * blockDim.x;
+  long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x;
+  for (; i + 3 * step < n; i += 4 * step) {
+    double2 a[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) a[u] = src[i + u * step];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      m = fmaxf(m, fmaxf(fabsf(f64_to_f32(a[u].x)), fabsf(f64_to_f32(a[u].y))));
+  }
+  for (; i < n; i += step) {
+    const double2 a = src[i];
+    m = fmaxf(m, fmaxf(fabsf(f64_to_f32(a.x)), fabsf(f64_to_f32(a.y))));
   }
   block_max_store(m, amax);
 }
@@ -1207,8 +1251,11 @@ void pack_launch(const cplx *src, const long *rt, const long *kt, long ld, bool 
     const int bx = static_cast<int>(std::min<long>(256, std::max<long>(32, (kh + 31) / 32 * 32)));
     const int by = 256 / bx;
     dim3 block(bx, by);
-    dim3 grid(static_cast<unsigned>((kh + bx - 1) / bx),
-              static_cast<unsigned>(std::min<long>((rows + by - 1) / by, 65535)));
+    // four rows per thread when there are blocks enough to fill the GPU
+    const long gx = (kh + bx - 1) / bx;
+    const long rpt = gx * ((rows + 4L * by - 1) / (4L * by)) >= 8L * 152 ? 4 : 1;
+    dim3 grid(static_cast<unsigned>(gx),
+              static_cast<unsigned>(std::min<long>((rows + rpt * by - 1) / (rpt * by), 65535)));
     switch (pt) {
       case 1: pack_kernel<1, EXPAND><<<grid, block, 0, st>>>(src, rt, kt, ld, conj, rows, K, Kp, hi, l, amax); break;
       case 2: pack_kernel<2, EXPAND><<<grid, block, 0, st>>>(src, rt, kt, ld, conj, rows, K, Kp, hi, l, amax); break;
@@ -1237,6 +1284,15 @@ void tc_absmax(const cplx *src, const long *rt, const long *kt, long ld, long ro
                float *amax, cudaStream_t st) {
   CUDA_CHECK(cudaMemsetAsync(amax, 0, sizeof(float), st));
   if (rows <= 0 || K <= 0) return;
+  if (!rt && !kt && (rows == 1 || ld == K)) {
+    // one contiguous block of rows * K elements
+    const long n = rows * K;
+    const long blocks = std::max<long>(1, std::min<long>((n + 1023) / 1024, 152L * 8));
+    absmax_flat_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(src, n, amax);
+    LAUNCH_CHECK();
+    count_launch();
+    return;
+  }
   const bool rows_inner = !rt && ld == 1;  // unit row stride: sweep rows fastest
   const long X = rows_inner ? rows : K, Y = rows_inner ? K : rows;
   const int bx = static_cast<int>(std::min<long>(256, std::max<long>(32, (X + 31) / 32 * 32)));

@@ -79,8 +79,9 @@ struct TcDesc {
   // were packed with fp16_scale() of these and the product is unscaled in
   // the epilogue (nullptr: unscaled)
   const float *amax_a = nullptr, *amax_b = nullptr;
-  // TC_OUT_F32 only: atomically raised to amax_mul x max |Re|, |Im| over
-  // the values written (the caller zeroes it); nullptr: not tracked
+  // TC_OUT_F32, or TC_OUT_F64 with beta = 0: atomically raised to amax_mul
+  // x max |Re|, |Im| (in FP32) over the values written (the caller zeroes
+  // it); nullptr: not tracked
   float *amax_out = nullptr;
   float amax_mul = 1.0f;
   // never time tile candidates for this call (the autotuner allocates a

@@ -529,7 +529,7 @@ void Ctx::finish_fns_stream() {
 // ===========================================================================
 // ladder: R2 += 1/2 sum_cd <ab||cd> tau_ij^cd with <ab||cd> from Lv (Eq. 23)
 // ===========================================================================
-void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr) {
+void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr, const float *tau_amax) {
   ensure_pairs();
   const long vv = static_cast<long>(v) * v;
   const long n_ij = nij(), n_cd = nab(), n_ab = nab();
@@ -608,13 +608,17 @@ void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr) {
     // FP16: operand maxima of L~ and tau, and a bound on |W|
     Buf amx(&al, 4 * sizeof(float));
     float *amx_L = f16 ? amx.as<float>() : nullptr;
-    float *amx_t = f16 ? amx.as<float>() + 1 : nullptr;
+    // tau's maximum over i<j, c<d is its maximum over all elements (the
+    // others are zero or equal in magnitude by antisymmetry), so a caller's
+    // whole-tensor maximum serves
+    const float *amx_t = f16 ? (tau_amax ? tau_amax : amx.as<float>() + 1) : nullptr;
     float *amx_W = f16 ? amx.as<float>() + 2 : nullptr;
     {
       Engine::Region r = eng.region("ladder pack");
       if (f16) {
         tc_absmax(Lv, nullptr, ptab, 1, vv, X, amx_L, st);
-        tc_absmax(tau, rt.as<long>(), kt.as<long>(), 0, n_ij, n_cd, amx_t, st);
+        if (!tau_amax)
+          tc_absmax(tau, rt.as<long>(), kt.as<long>(), 0, n_ij, n_cd, amx.as<float>() + 1, st);
         // |W| <= 2 max |V|: each GEMM1 raises amx_W to twice the largest
         // slab value it writes, before the antisymmetriser of its block
         zero(amx_W, sizeof(float), st);
@@ -701,26 +705,26 @@ void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr) {
 // ===========================================================================
 void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
   const int tr = res_tier();
+  // the singles intermediates (matrix-vector shapes, memory bound): FP64 in
+  // the FP64 tier, FP32 products summed in FP64 on the CUDA cores otherwise
+  const int sx = tr == TIER_FP64 ? TIER_FP64 : TIER_SIMT32;
   const long oo = static_cast<long>(o) * o, vv = static_cast<long>(v) * v, n2 = oo * vv;
   Buf tau(&al, sizeof(cplx) * n2), taut(&al, sizeof(cplx) * n2);
-  {
-    Engine::Region r = eng.region("make_tau x2");
-    make_tau_pair(t1p, t2p, tau.c(), taut.c(), o, v, st, tr != TIER_FP64);
-  }
-  // FP16 tiers: one maximum pass per doubles-sized operand, shared by all
-  // of its uses ([0] t2, [1] tau, [2] tau~, [3] Z)
+  // FP16 tiers: the maximum of each doubles-sized operand, shared by all of
+  // its uses ([0] t2, [1] tau, [2] tau~; [3..5] t2 again, Z and unused from
+  // make_z), found by the kernels that read or write them
   const bool scaled = tier_scaled(tr);
-  Buf amx(&al, 4 * sizeof(float));
+  Buf amx(&al, 6 * sizeof(float));
   float *amx_t2 = nullptr, *amx_tau = nullptr, *amx_taut = nullptr, *amx_z = nullptr;
   if (scaled) {
     amx_t2 = amx.as<float>();
     amx_tau = amx_t2 + 1;
     amx_taut = amx_t2 + 2;
-    amx_z = amx_t2 + 3;
-    Engine::Region r = eng.region("absmax t2 tau tau~");
-    tc_absmax(t2p, nullptr, nullptr, 0, 1, n2, amx_t2, st);
-    tc_absmax(tau.c(), nullptr, nullptr, 0, 1, n2, amx_tau, st);
-    tc_absmax(taut.c(), nullptr, nullptr, 0, 1, n2, amx_taut, st);
+    amx_z = amx_t2 + 4;
+  }
+  {
+    Engine::Region r = eng.region("make_tau x2");
+    make_tau_pair(t1p, t2p, tau.c(), taut.c(), o, v, st, tr != TIER_FP64, amx_t2);
   }
   auto t2 = [&](const char *ix) { return with_amax(T(t2p, ix, {o, o, v, v}), amx_t2); };
   auto tauT = [&](const char *ix) { return with_amax(T(tau.c(), ix, {o, o, v, v}), amx_tau); };
@@ -738,26 +742,26 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
   auto Lvv_ = [&](const char *ix) { return stable(T(Lvv.c(), ix, {X, v, v})); };
 
   // F_me = sum_nf t_n^f <mn||ef>
-  eng.contract(C1(), t1("nf"), g_oovv("mnef"), C0(), T(Fme.c(), "me", {o, v}), TIER_FP64);
+  eng.contract(C1(), t1("nf"), g_oovv("mnef"), C0(), T(Fme.c(), "me", {o, v}), sx);
   // F_ae = sum_mf t_m^f <ma||fe> - 1/2 tau~_mn^af <mn||ef>; the first term
   // through L: sum_P c_P L^P_ae - sum_Pm L^P_me Y^P_am, Y^P_am = sum_f L^P_af t_m^f
-  eng.contract(C1(), t1("mf"), Lov_("Pmf"), C0(), T(cP.c(), "P", {X}), TIER_FP64);
+  eng.contract(C1(), t1("mf"), Lov_("Pmf"), C0(), T(cP.c(), "P", {X}), sx);
   eng.contract(C1(), Lvv_("Paf"), t1("mf"), C0(), T(Y.c(), "Pam", {X, v, o}), tr);
-  eng.contract(C1(), T(cP.c(), "P", {X}), Lvv_("Pae"), C0(), T(Fae.c(), "ae", {v, v}), TIER_FP64);
+  eng.contract(C1(), T(cP.c(), "P", {X}), Lvv_("Pae"), C0(), T(Fae.c(), "ae", {v, v}), sx);
   eng.contract(Cr(-1), Lov_("Pme"), T(Y.c(), "Pam", {X, v, o}), C1(), T(Fae.c(), "ae", {v, v}), tr);
   eng.contract(Cr(-0.5), tautT("mnaf"), g_oovv("mnef"), C1(),
                T(Fae.c(), "ae", {v, v}), tr);
   // F_mi = sum_ne t_n^e <mn||ie> + 1/2 tau~_in^ef <mn||ef>
-  eng.contract(C1(), g_ooov("mnie"), t1("ne"), C0(), T(Fmi.c(), "mi", {o, o}), TIER_FP64);
+  eng.contract(C1(), g_ooov("mnie"), t1("ne"), C0(), T(Fmi.c(), "mi", {o, o}), sx);
   eng.contract(Cr(0.5), g_oovv("mnef"), tautT("inef"), C1(),
                T(Fmi.c(), "mi", {o, o}), tr);
   taut.release();
 
   // ---------------- singles (Eq. 13) ----------------
-  eng.contract(C1(), t1("ie"), T(Fae.c(), "ae", {v, v}), C0(), T(R1, "ia", {o, v}), TIER_FP64);
-  eng.contract(Cr(-1), t1("ma"), T(Fmi.c(), "mi", {o, o}), C1(), T(R1, "ia", {o, v}), TIER_FP64);
-  eng.contract(C1(), t2("imae"), T(Fme.c(), "me", {o, v}), C1(), T(R1, "ia", {o, v}), TIER_FP64);
-  eng.contract(C1(), t1("nf"), g_ovvo("nafi"), C1(), T(R1, "ia", {o, v}), TIER_FP64);
+  eng.contract(C1(), t1("ie"), T(Fae.c(), "ae", {v, v}), C0(), T(R1, "ia", {o, v}), sx);
+  eng.contract(Cr(-1), t1("ma"), T(Fmi.c(), "mi", {o, o}), C1(), T(R1, "ia", {o, v}), sx);
+  eng.contract(C1(), t2("imae"), T(Fme.c(), "me", {o, v}), C1(), T(R1, "ia", {o, v}), sx);
+  eng.contract(C1(), t1("nf"), g_ovvo("nafi"), C1(), T(R1, "ia", {o, v}), sx);
   // -1/2 t_im^ef <ma||ef> = -sum_Pf L^P_af Q^P_if, Q^P_if = sum_me t_im^ef L^P_me
   eng.contract(C1(), t2("imef"), Lov_("Pme"), C0(), T(Q.c(), "Pif", {X, o, v}), tr);
   eng.contract(Cr(-1), Lvv_("Paf"), T(Q.c(), "Pif", {X, o, v}), C1(), T(R1, "ia", {o, v}), tr);
@@ -778,7 +782,7 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
     Buf Fbe(&al, sizeof(cplx) * vv);
     d2d(Fbe.p, Fae.p, sizeof(cplx) * vv, st);
     eng.contract(Cr(-0.5), t1("mb"), T(Fme.c(), "me", {o, v}), C1(), T(Fbe.c(), "be", {v, v}),
-                 TIER_FP64);
+                 sx);
     eng.contract(C1(), t2("ijae"), T(Fbe.c(), "be", {v, v}), C0(), Xt("ijab"), tr);
     eng.contract(Cr(-1), t1("ma"), conj(g_ooov("ijmb")), C1(), Xt("ijab"), tr);
     { Engine::Region r_ = eng.region("antisym_add"); antisym_add(R2, Xb.c(), o, v, 1.0, 2, st); }
@@ -789,7 +793,7 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
     Buf Fmj(&al, sizeof(cplx) * oo);
     d2d(Fmj.p, Fmi.p, sizeof(cplx) * oo, st);
     eng.contract(Cr(0.5), t1("je"), T(Fme.c(), "me", {o, v}), C1(), T(Fmj.c(), "mj", {o, o}),
-                 TIER_FP64);
+                 sx);
     // the tensor-core product first, with beta = 0: plain stores rather
     // than atomic additions for the first writer of X
     eng.contract(C1(), T(Y.c(), "Pai", {X, v, o}), Lvo_("Pbj"), C0(), Xt("ijab"), tr);
@@ -819,7 +823,7 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
     d2d(Lt.p, Lvv.p, sizeof(cplx) * X * vv, st);
     eng.contract(Cr(-1), t1("ma"), Lov_("Pmc"), C1(), T(Lt.c(), "Pac", {X, v, v}), tr);
     Engine::Region r = eng.region("ladder total");
-    ladder(Lt.c(), tau.c(), R2, tr);
+    ladder(Lt.c(), tau.c(), R2, tr, amx_tau);
   }
   // W_mbej, stored as W[j][b][m][e]: its producers then write rows of
   // contiguous (m, e) and the ring contraction below reads contiguous K
@@ -840,8 +844,7 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
     Buf z(&al, sizeof(cplx) * n2);
     {
       Engine::Region r = eng.region("make_z");
-      make_z(t1p, t2p, z.c(), o, v, 0.5, st, tr != TIER_FP64);
-      if (scaled) tc_absmax(z.c(), nullptr, nullptr, 0, 1, n2, amx_z, st);
+      make_z(t1p, t2p, z.c(), o, v, 0.5, st, tr != TIER_FP64, scaled ? amx_t2 + 3 : nullptr);
     }
     eng.contract(Cr(-1), with_amax(T(z.c(), "jnfb", {o, o, v, v}), amx_z), g_oovv("mnef"), C1(),
                  Wt("jbme"), tr);
@@ -1085,17 +1088,26 @@ void Ctx::build_hbar() {
   } reset_reserve{eng};
   ++sig_gen;
   const int tr = hbar_tier();
+  const int sx = tr == TIER_FP64 ? TIER_FP64 : TIER_SIMT32;
   const long oo = static_cast<long>(o) * o, vv = static_cast<long>(v) * v, ov = static_cast<long>(o) * v;
   const long n2 = oo * vv;
+  // the amplitudes, tau and the integrals stay fixed during the build: their
+  // packed tensor-core planes are made once (the pack cache is cleared on
+  // entry and on exit); t2 and tau carry the maxima found while forming tau
+  const bool scaled = tier_scaled(tr);
+  Buf hmx(&al, 3 * sizeof(float)), gmx(&al, sizeof(float));
+  const float *amx_t2 = scaled ? hmx.as<float>() : nullptr;
+  const float *amx_tau = scaled ? hmx.as<float>() + 1 : nullptr;
   auto a1 = [&](const char *ix) { return T(t1.c(), ix, {o, v}); };
-  auto t2t = [&](const char *ix) { return T(t2.c(), ix, {o, o, v, v}); };
-  auto g_oovv = [&](const char *ix) { return T(oovv.c(), ix, {o, o, v, v}); };
-  auto g_ooov = [&](const char *ix) { return T(ooov.c(), ix, {o, o, o, v}); };
-  auto Lov_ = [&](const char *ix) { return T(Lov.c(), ix, {X, o, v}); };
-  auto Lvv_ = [&](const char *ix) { return T(Lvv.c(), ix, {X, v, v}); };
+  auto t2t = [&](const char *ix) { return stable(with_amax(T(t2.c(), ix, {o, o, v, v}), amx_t2)); };
+  auto g_oovv = [&](const char *ix) { return stable(T(oovv.c(), ix, {o, o, v, v})); };
+  auto g_ooov = [&](const char *ix) { return stable(T(ooov.c(), ix, {o, o, o, v})); };
+  auto Lov_ = [&](const char *ix) { return stable(T(Lov.c(), ix, {X, o, v})); };
+  auto Lvv_ = [&](const char *ix) { return stable(T(Lvv.c(), ix, {X, v, v})); };
   const std::initializer_list<long> d4 = {o, o, o, o};
   Buf tau(&al, sizeof(cplx) * n2), Qh;
-  make_tau(t1.c(), t2.c(), tau.c(), o, v, 1.0, st);
+  make_tau(t1.c(), t2.c(), tau.c(), o, v, 1.0, st, false, scaled ? hmx.as<float>() : nullptr);
+  auto tauH = [&](const char *ix) { return stable(with_amax(T(tau.c(), ix, {o, o, v, v}), amx_tau)); };
   B(Hov, ov);
   B(Hoo, oo);
   B(Hvv, vv);
@@ -1104,20 +1116,20 @@ void Ctx::build_hbar() {
   B(Hovvo, n2);
   B(Hovoo, oo * ov);
   // H_me
-  eng.contract(C1(), a1("nf"), g_oovv("mnef"), C0(), T(Hov.c(), "me", {o, v}), TIER_FP64);
+  eng.contract(C1(), a1("nf"), g_oovv("mnef"), C0(), T(Hov.c(), "me", {o, v}), sx);
   // H_mi = f_mi + t_n^e <mn||ie> + 1/2 tau_in^ef <mn||ef>
-  eng.contract(C1(), g_ooov("mnie"), a1("ne"), C0(), T(Hoo.c(), "mi", {o, o}), TIER_FP64);
-  eng.contract(Cr(0.5), g_oovv("mnef"), T(tau.c(), "inef", {o, o, v, v}), C1(),
+  eng.contract(C1(), g_ooov("mnie"), a1("ne"), C0(), T(Hoo.c(), "mi", {o, o}), sx);
+  eng.contract(Cr(0.5), g_oovv("mnef"), tauH("inef"), C1(),
                T(Hoo.c(), "mi", {o, o}), tr);
   add_diag(Hoo.c(), eps_d.as<double>(), o, st);
   // H_ae = f_ae + t_m^f <am||ef> - 1/2 tau_mn^af <mn||ef>
   {
     Buf cP(&al, sizeof(cplx) * X), Y(&al, sizeof(cplx) * X * v * o);
-    eng.contract(C1(), a1("mf"), Lov_("Pmf"), C0(), T(cP.c(), "P", {X}), TIER_FP64);
+    eng.contract(C1(), a1("mf"), Lov_("Pmf"), C0(), T(cP.c(), "P", {X}), sx);
     eng.contract(C1(), Lvv_("Paf"), a1("mf"), C0(), T(Y.c(), "Pam", {X, v, o}), tr);
-    eng.contract(C1(), T(cP.c(), "P", {X}), Lvv_("Pae"), C0(), T(Hvv.c(), "ae", {v, v}), TIER_FP64);
+    eng.contract(C1(), T(cP.c(), "P", {X}), Lvv_("Pae"), C0(), T(Hvv.c(), "ae", {v, v}), sx);
     eng.contract(Cr(-1), Lov_("Pme"), T(Y.c(), "Pam", {X, v, o}), C1(), T(Hvv.c(), "ae", {v, v}), tr);
-    eng.contract(Cr(-0.5), T(tau.c(), "mnaf", {o, o, v, v}), g_oovv("mnef"), C1(),
+    eng.contract(Cr(-0.5), tauH("mnaf"), g_oovv("mnef"), C1(),
                  T(Hvv.c(), "ae", {v, v}), tr);
     add_diag(Hvv.c(), eps_d.as<double>() + o, v, st);
     // H_mbej = <mb||ej> + t_j^f <mb||ef> - t_n^b <mn||ej> - (t_jn^fb + t_j^f t_n^b) <mn||ef>
@@ -1145,7 +1157,7 @@ void Ctx::build_hbar() {
     eng.contract(C1(), g_ooov("mnie"), a1("je"), C0(), T(tmp.c(), "mnij", d4), tr);
     eng.permute_into(C1(), T(tmp.c(), "mnij", d4), C1(), T(Hoooo.c(), "mnij", d4));
     eng.permute_into(Cr(-1), T(tmp.c(), "mnji", d4), C1(), T(Hoooo.c(), "mnij", d4));
-    eng.contract(Cr(0.5), g_oovv("mnef"), T(tau.c(), "ijef", {o, o, v, v}), C1(),
+    eng.contract(Cr(0.5), g_oovv("mnef"), tauH("ijef"), C1(),
                  T(Hoooo.c(), "mnij", d4), tr);
   }
   // H_mnie = <mn||ie> + t_i^f <mn||fe>
@@ -1165,9 +1177,13 @@ void Ctx::build_hbar() {
     Buf G(&al, per_m * mb);
     for (int m0 = 0; m0 < o; m0 += mb) {
       const int mc = std::min(mb, o - m0);
+      // the GEMM writing the block records its maximum for the next one's scale
       eng.contract(C1(), Tv(Lov.c() + static_cast<long>(m0) * v, "Pme", {X, mc, v}, {ov, v, 1}),
-                   Lvv_("Pbf"), C0(), T(G.c(), "mebf", {mc, v, v, v}), tr);
-      eng.contract(C1(), T(G.c(), "mebf", {mc, v, v, v}), T(tau.c(), "ijef", {o, o, v, v}), C1(),
+                   Lvv_("Pbf"), C0(),
+                   with_amax_out(T(G.c(), "mebf", {mc, v, v, v}), scaled ? gmx.as<float>() : nullptr),
+                   tr);
+      eng.contract(C1(), with_amax(T(G.c(), "mebf", {mc, v, v, v}), scaled ? gmx.as<float>() : nullptr),
+                   tauH("ijef"), C1(),
                    T(Hovoo.c() + static_cast<long>(m0) * v * oo, "mbij", {mc, v, o, o}), tr);
     }
     G.release();

@@ -120,7 +120,9 @@ struct Ctx {
                int *n_iter);
   // --- components ---
   void residual(const cplx *t1, const cplx *t2, cplx *R1, cplx *R2);
-  void ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tier);
+  // tau_amax (FP16 tiers, optional): a device float >= max |tau| (FP32 of
+  // |Re|, |Im|) over the whole tensor
+  void ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tier, const float *tau_amax = nullptr);
   void build_hbar();
   void sigma(int k, const cplx *r, cplx *s);
   void left_sigma(int k, const cplx *l, cplx *s);
