@@ -660,6 +660,58 @@ __global__ void unpack_pairs_kernel(const double2 *R, int o, int v, const int *i
   }
 }
 
+// Same update, one block (32, 8) per (i<j) pair and (A <= B) pair of 32-wide
+// tiles of a and b: the packed values of the tile are read along b into
+// shared memory, then R2[ij] and R2[ji] are updated along b at [a][b] and,
+// through the transposed tile, along a at [b][a]. Every element of R2 has
+// one writer (no atomics) and every access runs along a contiguous index.
+__global__ void __launch_bounds__(256) unpack_pairs_tile_kernel(const double2 *__restrict__ R,
+                                                                int o, int v,
+                                                                const int *__restrict__ ij_i,
+                                                                const int *__restrict__ ij_j,
+                                                                double2 *R2, int nt) {
+  __shared__ double2 s[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  int at = 0, t = blockIdx.x;
+  while (t >= nt - at) {
+    t -= nt - at;
+    ++at;
+  }
+  const int A0 = at * 32, B0 = (at + t) * 32;
+  const long pr = blockIdx.y;
+  const long nab = static_cast<long>(v) * (v - 1) / 2;
+  const double2 *Rp = R + pr * nab;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int a = A0 + ty + 8 * j, b = B0 + tx;
+    double2 x = make_double2(0.0, 0.0);
+    if (a < b && b < v) x = Rp[static_cast<long>(a) * (2L * v - a - 1) / 2 + (b - a - 1)];
+    s[ty + 8 * j][tx] = x;
+  }
+  __syncthreads();
+  const int i = ij_i[pr], jj = ij_j[pr];
+  const long vv = static_cast<long>(v) * v;
+  double2 *Rij = R2 + (static_cast<long>(i) * o + jj) * vv;
+  double2 *Rji = R2 + (static_cast<long>(jj) * o + i) * vv;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int a = A0 + ty + 8 * j, b = B0 + tx;  // [a][b], a < b: + R(a, b)
+    if (a < b && b < v) {
+      const double2 x = s[ty + 8 * j][tx];
+      const long e = static_cast<long>(a) * v + b;
+      Rij[e] = cadd(Rij[e], x);
+      Rji[e] = csub(Rji[e], x);
+    }
+    const int b2 = B0 + ty + 8 * j, a2 = A0 + tx;  // [b2][a2], a2 < b2: - R(a2, b2)
+    if (a2 < b2 && b2 < v) {
+      const double2 x = s[tx][ty + 8 * j];
+      const long e = static_cast<long>(b2) * v + a2;
+      Rij[e] = csub(Rij[e], x);
+      Rji[e] = cadd(Rji[e], x);
+    }
+  }
+}
+
 __global__ void pairs_kernel(int n, int *pi, int *pj) {
   const long np = static_cast<long>(n) * (n - 1) / 2;
   GRID_STRIDE(p, np) {
@@ -1017,11 +1069,24 @@ void ladder_antisym(const void *V, bool f32, int v, int a0, int nA, long p0, lon
   if (!f32) fail(CC_ERR_ARG, "ladder_antisym: tensor-core tiers take an FP32 slab");
   if (tier_scaled(tier) && !amax) fail(CC_ERR_ARG, "ladder_antisym: FP16 needs the W bound");
   const int nt = (v + 31) / 32;
-  // one wave of resident blocks (8 of 256 threads per SM); each walks many
-  // (a, b) pairs
+  // one wave of resident blocks, each walking many (a, b) pairs: a grid
+  // beyond what the SMs hold at once would leave a last, mostly empty wave
   const long ntp = static_cast<long>(nt) * (nt + 1) / 2;
+  const int pt = tier == TIER_BF16X3 ? 1 : tier == TIER_FP16 ? 2 : tier == TIER_FP16X3 ? 3 : 0;
+  static int resident[4] = {0, 0, 0, 0};
+  if (!resident[pt]) {
+    int dev = 0, sms = 0, per_sm = 0;
+    CUDA_CHECK(cudaGetDevice(&dev));
+    CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const void *k = pt == 1 ? reinterpret_cast<const void *>(antisym_tile_kernel<1>)
+                    : pt == 2 ? reinterpret_cast<const void *>(antisym_tile_kernel<2>)
+                    : pt == 3 ? reinterpret_cast<const void *>(antisym_tile_kernel<3>)
+                              : reinterpret_cast<const void *>(antisym_tile_kernel<0>);
+    CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, 0));
+    resident[pt] = std::max(1, sms * per_sm);
+  }
   dim3 grid(static_cast<unsigned>(ntp),
-            static_cast<unsigned>(std::max<long>(1, std::min<long>(np, (152L * 8 + ntp - 1) / ntp))));
+            static_cast<unsigned>(std::max<long>(1, std::min<long>(np, resident[pt] / ntp))));
   const float2 *Vf = reinterpret_cast<const float2 *>(V);
   if (tier == TIER_BF16X3) {
     antisym_tile_kernel<1><<<grid, dim3(32, 8), 0, st>>>(Vf, v, a0, p0, np, pair_a, pair_b, hi, lo,
@@ -1065,7 +1130,14 @@ void unpack_pairs_add(const cplx *R, int o, int v, const int *ij_i, const int *i
                       const int *ab_a, const int *ab_b, cplx *R2, cudaStream_t st) {
   const long n = static_cast<long>(o) * (o - 1) / 2 * (static_cast<long>(v) * (v - 1) / 2);
   if (n <= 0) return;
-  unpack_pairs_kernel<<<grid_for(n), 256, 0, st>>>(R, o, v, ij_i, ij_j, ab_a, ab_b, R2);
+  const long nij = static_cast<long>(o) * (o - 1) / 2;
+  const int nt = (v + 31) / 32;
+  if (nij <= 65535) {
+    dim3 grid(static_cast<unsigned>(static_cast<long>(nt) * (nt + 1) / 2), static_cast<unsigned>(nij));
+    unpack_pairs_tile_kernel<<<grid, dim3(32, 8), 0, st>>>(R, o, v, ij_i, ij_j, R2, nt);
+  } else {
+    unpack_pairs_kernel<<<grid_for(n), 256, 0, st>>>(R, o, v, ij_i, ij_j, ab_a, ab_b, R2);
+  }
   LAUNCH_CHECK();
   count_launch();
 }

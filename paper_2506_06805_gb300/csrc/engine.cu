@@ -81,7 +81,7 @@ bool Engine::may_cache(const std::string &key, size_t n) {
 
 std::pair<void *, void *> Engine::packed(const std::string &key, bool a_side, const TRef &t,
                                          const long *rt, const long *kt, long ld, long rows, long K,
-                                         long Kp, int tier, const float **amax) {
+                                         long Kp, int tier, const float **amax, bool rows_unit) {
   auto it = packs_.find(key);
   if (it != packs_.end()) {
     *amax = it->second.amax.as<float>();
@@ -91,6 +91,7 @@ std::pair<void *, void *> Engine::packed(const std::string &key, bool a_side, co
   const size_t n = eb * (a_side ? 2 : 1) * rows * Kp;
   Packed pk;
   ++gen;
+  pk.src = t.p;
   pk.hi.reset(al, n);
   if (tier_split(tier)) pk.lo.reset(al, n);
   if (tier_scaled(tier)) {
@@ -103,13 +104,37 @@ std::pair<void *, void *> Engine::packed(const std::string &key, bool a_side, co
       tc_absmax(t.p, rt, kt, ld, rows, K, pk.amax.as<float>(), st);
   }
   if (a_side)
-    tc_pack_A(t.p, rt, kt, ld, t.conj, rows, K, Kp, tier, pk.hi.p, pk.lo.p, st, pk.amax.as<float>());
+    tc_pack_A(t.p, rt, kt, ld, t.conj, rows, K, Kp, tier, pk.hi.p, pk.lo.p, st, pk.amax.as<float>(),
+              rows_unit);
   else
-    tc_pack_B(t.p, rt, kt, ld, t.conj, rows, K, Kp, tier, pk.hi.p, pk.lo.p, st, pk.amax.as<float>());
+    tc_pack_B(t.p, rt, kt, ld, t.conj, rows, K, Kp, tier, pk.hi.p, pk.lo.p, st, pk.amax.as<float>(),
+              rows_unit);
   std::pair<void *, void *> r{pk.hi.p, pk.lo.p};
   *amax = pk.amax.as<float>();
   packs_[key] = std::move(pk);
   return r;
+}
+
+void Engine::forget_packs(const void *p) {
+  bool any = false;
+  for (auto it = packs_.begin(); it != packs_.end();) {
+    if (it->second.src == p) {
+      it = packs_.erase(it);
+      any = true;
+    } else {
+      ++it;
+    }
+  }
+  std::ostringstream a, b;
+  a << 'A' << p << ':';
+  b << 'B' << p << ':';
+  for (auto it = uncached_.begin(); it != uncached_.end();) {
+    if (it->compare(0, a.str().size(), a.str()) == 0 || it->compare(0, b.str().size(), b.str()) == 0)
+      it = uncached_.erase(it);
+    else
+      ++it;
+  }
+  if (any) ++gen;
 }
 
 float *Engine::plane_amax(int which) {
@@ -365,11 +390,15 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
   const bool f16 = tier_scaled(tier);
   const float *xa = nullptr, *xb = nullptr;  // FP16 operand maxima
   const size_t nA_bytes = eb * 2 * M * Kp * (split ? 2 : 1), nB_bytes = eb * N * Kp * (split ? 2 : 1);
+  // read along rows (transposing through shared memory) when k is strided
+  // but neighbouring rows are neighbouring elements
+  const bool a_rows = !mdim.empty() && amstr.back() == 1 && !kdim.empty() && akstr.back() != 1;
+  const bool b_rows = !ndim.empty() && bnstr.back() == 1 && !kdim.empty() && bkstr.back() != 1;
   std::string keyA, keyB;
   if (A.stable) keyA = pack_key(true, A, am, ak, lda, M, K, Kp, tier);
   if (B.stable) keyB = pack_key(false, B, bn, bk, ldb, N, K, Kp, tier);
   if (A.stable && may_cache(keyA, nA_bytes)) {
-    std::tie(Ah, Al) = packed(keyA, true, A, am, ak, lda, M, K, Kp, tier, &xa);
+    std::tie(Ah, Al) = packed(keyA, true, A, am, ak, lda, M, K, Kp, tier, &xa, a_rows);
   } else {
     Ah = plane(pb + 0, eb * 2 * M * Kp);
     Al = split ? plane(pb + 1, eb * 2 * M * Kp) : nullptr;
@@ -384,10 +413,10 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
         tc_absmax(A.p, am, ak, lda, M, K, x, st);
       xa = x;
     }
-    tc_pack_A(A.p, am, ak, lda, A.conj, M, K, Kp, tier, Ah, Al, st, xa);
+    tc_pack_A(A.p, am, ak, lda, A.conj, M, K, Kp, tier, Ah, Al, st, xa, a_rows);
   }
   if (B.stable && may_cache(keyB, nB_bytes)) {
-    std::tie(Bh, Bl) = packed(keyB, false, B, bn, bk, ldb, N, K, Kp, tier, &xb);
+    std::tie(Bh, Bl) = packed(keyB, false, B, bn, bk, ldb, N, K, Kp, tier, &xb, b_rows);
   } else {
     Bh = plane(pb + 2, eb * N * Kp);
     Bl = split ? plane(pb + 3, eb * N * Kp) : nullptr;
@@ -402,7 +431,7 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
         tc_absmax(B.p, bn, bk, ldb, N, K, x, st);
       xb = x;
     }
-    tc_pack_B(B.p, bn, bk, ldb, B.conj, N, K, Kp, tier, Bh, Bl, st, xb);
+    tc_pack_B(B.p, bn, bk, ldb, B.conj, N, K, Kp, tier, Bh, Bl, st, xb, b_rows);
   }
   TcDesc t;
   t.M = M; t.N = N; t.Kp = Kp;

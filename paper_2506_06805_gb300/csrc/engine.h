@@ -108,6 +108,10 @@ class Engine {
     uncached_.clear();
     ++gen;
   }
+  // Drop the cached packed planes of the tensor at p: a tensor marked stable
+  // for a stretch of work (the amplitudes within one residual) whose contents
+  // change or whose memory is freed afterwards.
+  void forget_packs(const void *p);
 
   // Optional device-time trace, on when the environment variable
   // CDFNS_TRACE names a file: every contraction (operand packing and GEMM)
@@ -129,6 +133,7 @@ class Engine {
  private:
   struct Packed {
     Buf hi, lo, amax;
+    const void *src = nullptr;
   };
   static std::string pack_key(bool a_side, const TRef &t, const long *rt, const long *kt, long ld,
                               long rows, long K, long Kp, int tier);
@@ -138,7 +143,7 @@ class Engine {
   // *amax receives its FP16 scale source (TIER_FP16) or nullptr
   std::pair<void *, void *> packed(const std::string &key, bool a_side, const TRef &t,
                                    const long *rt, const long *kt, long ld, long rows, long K,
-                                   long Kp, int tier, const float **amax);
+                                   long Kp, int tier, const float **amax, bool rows_unit);
   // device float of plane slot `which` for the FP16 operand maximum
   float *plane_amax(int which);
   std::map<int, Buf> amax_planes_;

@@ -161,17 +161,46 @@ __global__ void gemv_kt_kernel(long N, long K, const double2 *__restrict__ A,
   double2 acc = make_double2(0.0, 0.0);
   if (n < N) {
     const long bo = bn ? bn[n] : n * ldb;
+    // four loads per thread in flight; the sums keep their sequential order
     if (F32) {
       for (long k0 = ty; k0 < K; k0 += 8 * 16) {
         float xr = 0.f, xi = 0.f;
         const long k1 = min(K, k0 + 8 * 16);
-        for (long k = k0; k < k1; k += 8)
+        long k = k0;
+        for (; k + 24 < k1; k += 32) {
+          double2 a[4], b[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const long kk = k + 8 * u;
+            a[u] = A[ak ? ak[kk] : kk];
+            b[u] = B[bo + (bk ? bk[kk] : kk)];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) cfma32(a[u], b[u], conjA, conjB, xr, xi);
+        }
+        for (; k < k1; k += 8)
           cfma32(A[ak ? ak[k] : k], B[bo + (bk ? bk[k] : k)], conjA, conjB, xr, xi);
         acc.x += f32_to_f64(xr);
         acc.y += f32_to_f64(xi);
       }
     } else {
-      for (long k = ty; k < K; k += 8) {
+      long k = ty;
+      for (; k + 24 < K; k += 32) {
+        double2 a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const long kk = k + 8 * u;
+          a[u] = A[ak ? ak[kk] : kk];
+          b[u] = B[bo + (bk ? bk[kk] : kk)];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (conjA) a[u].y = -a[u].y;
+          if (conjB) b[u].y = -b[u].y;
+          acc = cfma(a[u], b[u], acc);
+        }
+      }
+      for (; k < K; k += 8) {
         double2 a = A[ak ? ak[k] : k];
         double2 b = B[bo + (bk ? bk[k] : k)];
         if (conjA) a.y = -a.y;

@@ -1130,11 +1130,13 @@ __global__ void __launch_bounds__(256) pack_kernel(const double2 *__restrict__ s
   }
 }
 
-// Rows contiguous in the source (unit row stride, k through a table or a
-// large stride): 32 x 32 tiles transposed through shared memory so that the
-// loads run along rows and the stores along k. Block (32, 8).
+// Rows (mostly) contiguous in the source (unit stride or a table whose
+// neighbouring entries are neighbours; k through a table or a large
+// stride): 32 x 32 tiles transposed through shared memory so that the loads
+// run along rows and the stores along k. Block (32, 8).
 template <int PT, bool EXPAND>
 __global__ void __launch_bounds__(256) pack_t_kernel(const double2 *__restrict__ src,
+                                                     const long *__restrict__ rt, long ld,
                                                      const long *__restrict__ kt, bool conj,
                                                      long rows, long K, long Kp, void *hi,
                                                      void *lo, const float *amax) {
@@ -1147,7 +1149,7 @@ __global__ void __launch_bounds__(256) pack_t_kernel(const double2 *__restrict__
     for (int j = 0; j < 4; ++j) {
       const long k = k0 + ty + 8 * j, r = r0 + tx;
       double2 a = make_double2(0.0, 0.0);
-      if (k < K && r < rows) a = src[r + kt[k]];
+      if (k < K && r < rows) a = src[(rt ? rt[r] : r * ld) + (kt ? kt[k] : k)];
       tile[ty + 8 * j][tx] = a;
     }
     __syncthreads();
@@ -1232,24 +1234,27 @@ __global__ void __launch_bounds__(256) absmax_flat_kernel(const double2 *__restr
 template <bool EXPAND>
 void pack_launch(const cplx *src, const long *rt, const long *kt, long ld, bool conj, long rows,
                  long K, long Kp, int tier, void *hi, void *lo, cudaStream_t st,
-                 const float *amax) {
+                 const float *amax, bool rows_unit) {
   if (rows <= 0) return;
   void *l = tier_split(tier) ? lo : nullptr;
   const int pt = tier == TIER_BF16X3 ? 1 : (tier == TIER_FP16 ? 2 : (tier == TIER_FP16X3 ? 3 : 0));
   const long kh = Kp / 2;
-  if (!rt && ld == 1 && kt && rows > 1 && K > 1) {
+  if (kt && rows > 1 && K > 1 && ((!rt && ld == 1) || rows_unit)) {
     dim3 block(32, 8);
     dim3 grid(static_cast<unsigned>((kh + 31) / 32),
               static_cast<unsigned>(std::min<long>((rows + 31) / 32, 65535)));
     switch (pt) {
-      case 1: pack_t_kernel<1, EXPAND><<<grid, block, 0, st>>>(src, kt, conj, rows, K, Kp, hi, l, amax); break;
-      case 2: pack_t_kernel<2, EXPAND><<<grid, block, 0, st>>>(src, kt, conj, rows, K, Kp, hi, l, amax); break;
-      case 3: pack_t_kernel<3, EXPAND><<<grid, block, 0, st>>>(src, kt, conj, rows, K, Kp, hi, l, amax); break;
-      default: pack_t_kernel<0, EXPAND><<<grid, block, 0, st>>>(src, kt, conj, rows, K, Kp, hi, l, amax);
+      case 1: pack_t_kernel<1, EXPAND><<<grid, block, 0, st>>>(src, rt, ld, kt, conj, rows, K, Kp, hi, l, amax); break;
+      case 2: pack_t_kernel<2, EXPAND><<<grid, block, 0, st>>>(src, rt, ld, kt, conj, rows, K, Kp, hi, l, amax); break;
+      case 3: pack_t_kernel<3, EXPAND><<<grid, block, 0, st>>>(src, rt, ld, kt, conj, rows, K, Kp, hi, l, amax); break;
+      default: pack_t_kernel<0, EXPAND><<<grid, block, 0, st>>>(src, rt, ld, kt, conj, rows, K, Kp, hi, l, amax);
     }
   } else {
-    const int bx = static_cast<int>(std::min<long>(256, std::max<long>(32, (kh + 31) / 32 * 32)));
-    const int by = 256 / bx;
+    // x over complex k: as few 32-wide groups per block row as cover it in
+    // ceil(kh / 256) blocks, so a short K leaves few threads idle
+    const long nbx = (kh + 255) / 256;
+    const int bx = static_cast<int>(32 * (((kh + 31) / 32 + nbx - 1) / nbx));
+    const int by = std::max(1, 256 / bx);
     dim3 block(bx, by);
     // four rows per thread when there are blocks enough to fill the GPU
     const long gx = (kh + bx - 1) / bx;
@@ -1270,14 +1275,16 @@ void pack_launch(const cplx *src, const long *rt, const long *kt, long ld, bool 
 }  // namespace
 
 void tc_pack_A(const cplx *src, const long *am, const long *ak, long lda, bool conj, long M,
-               long K, long Kp, int tier, void *hi, void *lo, cudaStream_t st, const float *amax) {
+               long K, long Kp, int tier, void *hi, void *lo, cudaStream_t st, const float *amax,
+               bool rows_unit) {
   if (tier_scaled(tier) && !amax) fail(CC_ERR_ARG, "tc_pack_A: FP16 planes need amax");
-  pack_launch<true>(src, am, ak, lda, conj, M, K, Kp, tier, hi, lo, st, amax);
+  pack_launch<true>(src, am, ak, lda, conj, M, K, Kp, tier, hi, lo, st, amax, rows_unit);
 }
 void tc_pack_B(const cplx *src, const long *bn, const long *bk, long ldb, bool conj, long N,
-               long K, long Kp, int tier, void *hi, void *lo, cudaStream_t st, const float *amax) {
+               long K, long Kp, int tier, void *hi, void *lo, cudaStream_t st, const float *amax,
+               bool rows_unit) {
   if (tier_scaled(tier) && !amax) fail(CC_ERR_ARG, "tc_pack_B: FP16 planes need amax");
-  pack_launch<false>(src, bn, bk, ldb, conj, N, K, Kp, tier, hi, lo, st, amax);
+  pack_launch<false>(src, bn, bk, ldb, conj, N, K, Kp, tier, hi, lo, st, amax, rows_unit);
 }
 
 void tc_absmax(const cplx *src, const long *rt, const long *kt, long ld, long rows, long K,

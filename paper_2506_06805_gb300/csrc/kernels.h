@@ -113,12 +113,15 @@ size_t tc_elem_bytes(int tier);
 // Expand/convert operands for gemm_tc from FP64 tensors addressed by tables.
 // A side: rows 2m, 2m+1 (M complex rows) x Kp real columns (2 per complex k).
 // TIER_FP16: amax (device float, from tc_absmax) sets the operand's scale.
+// rows_unit: neighbouring rows are (mostly) neighbouring elements while k
+// is strided; the operand is then read along rows and transposed through
+// shared memory.
 void tc_pack_A(const cplx *src, const long *am, const long *ak, long lda,
                bool conj, long M, long K, long Kp, int tier, void *hi,
-               void *lo, cudaStream_t st, const float *amax = nullptr);
+               void *lo, cudaStream_t st, const float *amax = nullptr, bool rows_unit = false);
 void tc_pack_B(const cplx *src, const long *bn, const long *bk, long ldb,
                bool conj, long N, long K, long Kp, int tier, void *hi,
-               void *lo, cudaStream_t st, const float *amax = nullptr);
+               void *lo, cudaStream_t st, const float *amax = nullptr, bool rows_unit = false);
 // *amax = max over the operand's elements of max(|Re|, |Im|), addressed like
 // tc_pack_A / tc_pack_B (rows x K through tables or strides).
 void tc_absmax(const cplx *src, const long *rt, const long *kt, long ld, long rows, long K,

@@ -727,6 +727,12 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
     make_tau_pair(t1p, t2p, tau.c(), taut.c(), o, v, st, tr != TIER_FP64, amx_t2);
   }
   auto t2 = [&](const char *ix) { return with_amax(T(t2p, ix, {o, o, v, v}), amx_t2); };
+  // packed planes of t2 kept within this call are dropped on every way out
+  struct ForgetPacks {
+    Engine &e;
+    const void *p;
+    ~ForgetPacks() { e.forget_packs(p); }
+  } forget_t2{eng, t2p};
   auto tauT = [&](const char *ix) { return with_amax(T(tau.c(), ix, {o, o, v, v}), amx_tau); };
   auto tautT = [&](const char *ix) { return with_amax(T(taut.c(), ix, {o, o, v, v}), amx_taut); };
   Buf Fae(&al, sizeof(cplx) * vv), Fmi(&al, sizeof(cplx) * oo), Fme(&al, sizeof(cplx) * o * v);
@@ -763,7 +769,9 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
   eng.contract(C1(), t2("imae"), T(Fme.c(), "me", {o, v}), C1(), T(R1, "ia", {o, v}), sx);
   eng.contract(C1(), t1("nf"), g_ovvo("nafi"), C1(), T(R1, "ia", {o, v}), sx);
   // -1/2 t_im^ef <ma||ef> = -sum_Pf L^P_af Q^P_if, Q^P_if = sum_me t_im^ef L^P_me
-  eng.contract(C1(), t2("imef"), Lov_("Pme"), C0(), T(Q.c(), "Pif", {X, o, v}), tr);
+  // t2 with rows (i, f) and K (m, e): the same packed planes serve the ring
+  // product below (rows (i, a), K (m, e)), so they are kept until then
+  eng.contract(C1(), stable(t2("imef")), Lov_("Pme"), C0(), T(Q.c(), "Pif", {X, o, v}), tr);
   eng.contract(Cr(-1), Lvv_("Paf"), T(Q.c(), "Pif", {X, o, v}), C1(), T(R1, "ia", {o, v}), tr);
   // -1/2 t_mn^ae <nm||ei> = +1/2 t_mn^ae <nm||ie>
   eng.contract(Cr(0.5), t2("mnae"), g_ooov("nmie"), C1(), T(R1, "ia", {o, v}), tr);
@@ -777,14 +785,33 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
   eng.permute_into(C1(), conj(g_oovv("ijab")), C0(), R2t("ijab"));
   // Terms sharing one antisymmetriser are summed into X first, so each
   // symmetry class costs one pass over R2.
-  // P(ab) [t_ij^ae (F_be - 1/2 t_m^b F_me) - t_m^a <mb||ij>], <mb||ij> = conj(<ij||mb>)
+  // Hole-ladder intermediate W'_mnij = <mn||ij> + P(ij) t_j^e <mn||ie>,
+  // antisymmetric in (m, n). The hole ladder 1/2 tau_mn^ab W'_mnij splits
+  // into its t2 part (taken below with the Z term) and its t1 t1 part,
+  // sum_mn t_m^a t_n^b W'_mnij, which is antisymmetric in (a, b): it joins
+  // the P(ab) class as 1/2 sum_mn t_m^a t_n^b W'_mnij.
+  const std::initializer_list<long> d4 = {o, o, o, o};
+  Buf Wp(&al, sizeof(cplx) * oo * oo);
+  {
+    Buf tmp(&al, sizeof(cplx) * oo * oo);
+    d2d(Wp.p, oooo.p, sizeof(cplx) * oo * oo, st);
+    eng.contract(C1(), g_ooov("mnie"), t1("je"), C0(), T(tmp.c(), "mnij", d4), tr);
+    eng.permute_into(C1(), T(tmp.c(), "mnij", d4), C1(), T(Wp.c(), "mnij", d4));
+    eng.permute_into(Cr(-1), T(tmp.c(), "mnji", d4), C1(), T(Wp.c(), "mnij", d4));
+  }
+  // P(ab) [t_ij^ae (F_be - 1/2 t_m^b F_me) + sum_m t_m^a Q_ijmb] with
+  // Q_ijmb = -<mb||ij> + 1/2 sum_n W'_mnij t_n^b, <mb||ij> = conj(<ij||mb>)
   {
     Buf Fbe(&al, sizeof(cplx) * vv);
     d2d(Fbe.p, Fae.p, sizeof(cplx) * vv, st);
     eng.contract(Cr(-0.5), t1("mb"), T(Fme.c(), "me", {o, v}), C1(), T(Fbe.c(), "be", {v, v}),
                  sx);
     eng.contract(C1(), t2("ijae"), T(Fbe.c(), "be", {v, v}), C0(), Xt("ijab"), tr);
-    eng.contract(Cr(-1), t1("ma"), conj(g_ooov("ijmb")), C1(), Xt("ijab"), tr);
+    Buf Qm(&al, sizeof(cplx) * oo * o * v);
+    auto Qt = [&](const char *ix) { return T(Qm.c(), ix, {o, o, o, v}); };
+    eng.permute_into(Cr(-1), conj(g_ooov("ijmb")), C0(), Qt("ijmb"));
+    eng.contract(Cr(0.5), T(Wp.c(), "mnij", d4), t1("nb"), C1(), Qt("ijmb"), tr);
+    eng.contract(C1(), t1("ma"), Qt("ijmb"), C1(), Xt("ijab"), tr);
     { Engine::Region r_ = eng.region("antisym_add"); antisym_add(R2, Xb.c(), o, v, 1.0, 2, st); }
   }
   // P(ij) [-t_im^ab (F_mj + 1/2 t_j^e F_me) + t_i^e <ab||ej>], the second as
@@ -801,22 +828,16 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
     eng.contract(Cr(-1), t2("imab"), T(Fmj.c(), "mj", {o, o}), C1(), Xt("ijab"), tr);
     { Engine::Region r_ = eng.region("antisym_add"); antisym_add(R2, Xb.c(), o, v, 1.0, 1, st); }
   }
-  // hole ladder: 1/2 tau_mn^ab W'_mnij + 1/4 t_mn^ab Z_mnij, with
-  // W' = <mn||ij> + P(ij) t_j^e <mn||ie>, Z = sum_ef <mn||ef> tau_ij^ef
+  // hole ladder, t2 part: sum_mn t_mn^ab (1/2 W'_mnij + 1/4 Z_mnij), with
+  // Z_mnij = sum_ef <mn||ef> tau_ij^ef
   {
-    Buf Wp(&al, sizeof(cplx) * oo * oo), Zb(&al, sizeof(cplx) * oo * oo), tmp(&al, sizeof(cplx) * oo * oo);
-    const std::initializer_list<long> d4 = {o, o, o, o};
-    d2d(Wp.p, oooo.p, sizeof(cplx) * oo * oo, st);
-    eng.contract(C1(), g_ooov("mnie"), t1("je"), C0(), T(tmp.c(), "mnij", d4), tr);
-    eng.permute_into(C1(), T(tmp.c(), "mnij", d4), C1(), T(Wp.c(), "mnij", d4));
-    eng.permute_into(Cr(-1), T(tmp.c(), "mnji", d4), C1(), T(Wp.c(), "mnij", d4));
-    eng.contract(C1(), g_oovv("mnef"), tauT("ijef"), C0(), T(Zb.c(), "mnij", d4),
-                 tr);
+    Buf Zb(&al, sizeof(cplx) * oo * oo);
+    eng.contract(C1(), g_oovv("mnef"), tauT("ijef"), C0(), T(Zb.c(), "mnij", d4), tr);
+    axpby(oo * oo, Cr(0.5), Wp.c(), Cr(0.25), Zb.c(), st);
     // (i,j) as the GEMM rows so the output rows (a,b) are contiguous
-    eng.contract(Cr(0.5), T(Wp.c(), "mnij", d4), tauT("mnab"), C1(), R2t("ijab"),
-                 tr);
-    eng.contract(Cr(0.25), T(Zb.c(), "mnij", d4), t2("mnab"), C1(), R2t("ijab"), tr);
+    eng.contract(C1(), T(Zb.c(), "mnij", d4), t2("mnab"), C1(), R2t("ijab"), tr);
   }
+  Wp.release();
   // particle ladder with T1-dressed vectors: L~^P_ac = L^P_ac - sum_m t_m^a L^P_mc
   {
     Buf Lt(&al, sizeof(cplx) * X * vv);
@@ -850,7 +871,8 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
                  Wt("jbme"), tr);
   }
   // P(ij)P(ab) [t_im^ae W_mbej - t_i^e t_m^a <mb||ej>]
-  eng.contract(C1(), t2("imae"), Wt("jbme"), C0(), Xt("ijab"), tr);
+  eng.contract(C1(), stable(t2("imae")), Wt("jbme"), C0(), Xt("ijab"), tr);
+  eng.forget_packs(t2p);
   {
     Buf y2(&al, sizeof(cplx) * oo * o * v);
     eng.contract(C1(), t1("ie"), g_ovvo("mbej"), C0(), T(y2.c(), "mbij", {o, v, o, o}), tr);
@@ -1106,7 +1128,7 @@ void Ctx::build_hbar() {
   auto Lvv_ = [&](const char *ix) { return stable(T(Lvv.c(), ix, {X, v, v})); };
   const std::initializer_list<long> d4 = {o, o, o, o};
   Buf tau(&al, sizeof(cplx) * n2), Qh;
-  make_tau(t1.c(), t2.c(), tau.c(), o, v, 1.0, st, false, scaled ? hmx.as<float>() : nullptr);
+  make_tau(t1.c(), t2.c(), tau.c(), o, v, 1.0, st, tr != TIER_FP64, scaled ? hmx.as<float>() : nullptr);
   auto tauH = [&](const char *ix) { return stable(with_amax(T(tau.c(), ix, {o, o, v, v}), amx_tau)); };
   B(Hov, ov);
   B(Hoo, oo);

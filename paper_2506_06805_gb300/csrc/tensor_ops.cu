@@ -43,36 +43,78 @@ __global__ void scale2d_kernel(double2 *C, const long *cm, const long *cn, long 
   }
 }
 
+// y = a x + b y. Real coefficients take two FP64 operations per component
+// instead of a complex multiply (GB300's FP64 pipe, not memory, otherwise
+// bounds this kernel); a = +-1 with b = 1 only adds.
+template <int MODE>  // 0 complex a, b; 1 real a, b; 2 y +- x (sign in a.x)
 __global__ void axpby_kernel(long n, double2 a, const double2 *x, double2 b, double2 *y) {
   for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<long>(gridDim.x) * blockDim.x) {
-    const double2 yy = (b.x == 0.0 && b.y == 0.0) ? make_double2(0.0, 0.0) : cmul(b, y[i]);
-    y[i] = cadd(cmul(a, x[i]), yy);
+    const double2 xv = x[i];
+    if (MODE == 2) {
+      const double2 yv = y[i];
+      y[i] = a.x > 0 ? make_double2(yv.x + xv.x, yv.y + xv.y) : make_double2(yv.x - xv.x, yv.y - xv.y);
+    } else if (MODE == 1) {
+      if (b.x == 0.0) {
+        y[i] = make_double2(a.x * xv.x, a.x * xv.y);
+      } else {
+        const double2 yv = y[i];
+        y[i] = make_double2(fma(a.x, xv.x, b.x * yv.x), fma(a.x, xv.y, b.x * yv.y));
+      }
+    } else {
+      const double2 yy = (b.x == 0.0 && b.y == 0.0) ? make_double2(0.0, 0.0) : cmul(b, y[i]);
+      y[i] = cadd(cmul(a, xv), yy);
+    }
   }
 }
 
-__global__ void permute_kernel(double2 *out, const double2 *in, long total, Dims D, double2 alpha,
-                               double2 beta, bool conj) {
-  for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < total;
-       i += static_cast<long>(gridDim.x) * blockDim.x) {
-    long rem = i, off = 0;
-    for (int k = D.nd - 1; k >= 0; --k) {
-      const long digit = rem % D.d[k];
-      rem /= D.d[k];
-      off += digit * D.s[k];
+// I: the index type of the digit arithmetic (32-bit when every index fits:
+// 64-bit division is a long instruction sequence). Four elements per thread
+// and pass, their loads issued before the stores (in and out never overlap).
+template <typename I>
+__global__ void permute_kernel(double2 *__restrict__ out, const double2 *__restrict__ in,
+                               long total, Dims D, double2 alpha, double2 beta, bool conj) {
+  const long stride = static_cast<long>(gridDim.x) * blockDim.x;
+  const bool pm1 = alpha.y == 0.0 && (alpha.x == 1.0 || alpha.x == -1.0);
+  const bool b1 = beta.x == 1.0 && beta.y == 0.0, b0 = beta.x == 0.0 && beta.y == 0.0;
+  for (long i0 = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i0 < total;
+       i0 += 4 * stride) {
+    double2 x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long i = i0 + u * stride;
+      if (i >= total) break;
+      long off = 0;
+      if (D.nd == 1) {
+        off = i * D.s[0];
+      } else {
+        I rem = static_cast<I>(i);
+        for (int k = D.nd - 1; k >= 0; --k) {
+          const I dk = static_cast<I>(D.d[k]);
+          const I q = rem / dk;
+          off += static_cast<long>(rem - q * dk) * D.s[k];
+          rem = q;
+        }
+      }
+      x[u] = in[off];
     }
-    double2 x = in[off];
-    if (conj) x.y = -x.y;
-    // +-1 scalings and beta in {0, 1} without FP64 multiplies (GB300's FP64
-    // rate makes them the cost of this memory-bound kernel)
-    if (alpha.y == 0.0 && (alpha.x == 1.0 || alpha.x == -1.0)) {
-      if (alpha.x < 0) x = make_double2(-x.x, -x.y);
-    } else {
-      x = cmul(alpha, x);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long i = i0 + u * stride;
+      if (i >= total) break;
+      double2 v = x[u];
+      if (conj) v.y = -v.y;
+      // +-1 scalings and beta in {0, 1} without FP64 multiplies (GB300's
+      // FP64 rate makes them the cost of this memory-bound kernel)
+      if (pm1) {
+        if (alpha.x < 0) v = make_double2(-v.x, -v.y);
+      } else {
+        v = cmul(alpha, v);
+      }
+      if (b1) v = cadd(v, out[i]);
+      else if (!b0) v = cadd(v, cmul(beta, out[i]));
+      out[i] = v;
     }
-    if (beta.x == 1.0 && beta.y == 0.0) x = cadd(x, out[i]);
-    else if (!(beta.x == 0.0 && beta.y == 0.0)) x = cadd(x, cmul(beta, out[i]));
-    out[i] = x;
   }
 }
 
@@ -298,7 +340,13 @@ void scale_2d(cplx *C, const long *cm, const long *cn, long ldc, long M, long N,
 
 void axpby(long n, cplx alpha, const cplx *x, cplx beta, cplx *y, cudaStream_t st) {
   if (n <= 0) return;
-  axpby_kernel<<<grid_for(n), 256, 0, st>>>(n, alpha, x, beta, y);
+  const bool real = alpha.y == 0.0 && beta.y == 0.0;
+  if (real && (alpha.x == 1.0 || alpha.x == -1.0) && beta.x == 1.0)
+    axpby_kernel<2><<<grid_for(n), 256, 0, st>>>(n, alpha, x, beta, y);
+  else if (real)
+    axpby_kernel<1><<<grid_for(n), 256, 0, st>>>(n, alpha, x, beta, y);
+  else
+    axpby_kernel<0><<<grid_for(n), 256, 0, st>>>(n, alpha, x, beta, y);
   LAUNCH_CHECK();
   count_launch();
 }
@@ -307,15 +355,33 @@ void permute(cplx *out, const cplx *in, int nd, const long *odims, const long *i
              cplx beta, bool conj, cudaStream_t st) {
   if (nd > MAXD) fail(CC_ERR_ARG, "permute: rank too large");
   Dims D;
-  D.nd = nd;
+  D.nd = 0;
   long total = 1;
+  // drop unit dims and merge neighbours that are contiguous in the input too
+  // (out is row-major): an identity layout becomes one dimension
   for (int i = 0; i < nd; ++i) {
-    D.d[i] = odims[i];
-    D.s[i] = istr[i];
     total *= odims[i];
+    if (odims[i] == 1) continue;
+    if (D.nd > 0 && D.s[D.nd - 1] == istr[i] * odims[i]) {
+      D.d[D.nd - 1] *= odims[i];
+      D.s[D.nd - 1] = istr[i];
+    } else {
+      D.d[D.nd] = odims[i];
+      D.s[D.nd] = istr[i];
+      ++D.nd;
+    }
   }
   if (total <= 0) return;
-  permute_kernel<<<grid_for(total), 256, 0, st>>>(out, in, total, D, alpha, beta, conj);
+  if (D.nd == 0) {
+    D.nd = 1;
+    D.d[0] = 1;
+    D.s[0] = 0;
+  }
+  if (total <= 0xffffffffL)
+    permute_kernel<unsigned><<<grid_for(total), 256, 0, st>>>(out, in, total, D, alpha, beta, conj);
+  else
+    permute_kernel<unsigned long long><<<grid_for(total), 256, 0, st>>>(out, in, total, D, alpha,
+                                                                        beta, conj);
   LAUNCH_CHECK();
   count_launch();
 }
