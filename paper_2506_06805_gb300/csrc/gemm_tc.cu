@@ -272,8 +272,12 @@ struct alignas(64) TcProblem {
   int group_m;      // m tiles per raster group (A panels kept in L2)
   int chunk;        // K blocks accumulated in TMEM before promotion
   int out;
+  int wmode;        // epilogue write, decided on the host (WM_*): no FP64 tests per element
   int tile_start;   // first index of this problem in the launch's tile space
 };
+// Epilogue write modes. The FP64 pipe of this GPU retires about two
+// operations per SM clock, so the per-element path tests integers only.
+enum { WM_F32 = 0, WM_F64_ADD = 1, WM_F64_STORE = 2, WM_F64_BETA = 3 };
 constexpr int MAX_PROBLEMS = 16;
 struct TcGroup {
   TcProblem p[MAX_PROBLEMS];
@@ -560,7 +564,8 @@ __global__ void __launch_bounds__(320, 1)
           const float im = usc * stg[(2 * rr + 1) * 32 + (lane ^ (2 * rr + 1))];
           const long mc = mbase + rr;
           if (!col_ok || mc >= args.M) continue;
-          if (args.out == TC_OUT_F32) {
+          const int wm = args.wmode;
+          if (wm == WM_F32) {
             float2 *Cf = reinterpret_cast<float2 *>(args.C);
             Cf[mc * args.ldc + n] = make_float2(re, im);
             omax = fmaxf(omax, fmaxf(fabsf(re), fabsf(im)));
@@ -568,21 +573,20 @@ __global__ void __launch_bounds__(320, 1)
             double2 *C = reinterpret_cast<double2 *>(args.C);
             const long off = (args.cm ? args.cm[mc] : mc * args.ldc) + cno;
             // alpha in FP32 (the product carries FP32 rounding already),
-            // widened on the integer pipes; FP64 arithmetic only for beta
+            // widened on the integer pipes; FP64 arithmetic only for a
+            // general beta
             const float fr = args.alpha_f.x * re - args.alpha_f.y * im;
             const float fi = args.alpha_f.x * im + args.alpha_f.y * re;
             const double xr = f32_to_f64(fr), xi = f32_to_f64(fi);
-            if (args.out == TC_OUT_F64_ATOMIC) {
+            if (wm == WM_F64_ADD) {
+              // split-K partials, or beta = 1 with one writer per element:
+              // the addition runs in L2 (no read round trip, no FP64 work
+              // on the SM)
               atomicAdd(&C[off].x, xr);
               atomicAdd(&C[off].y, xi);
-            } else if (args.beta.x == 0.0 && args.beta.y == 0.0) {
+            } else if (wm == WM_F64_STORE) {
               C[off] = make_double2(xr, xi);
-              if (args.amax_out) omax = fmaxf(omax, fmaxf(fabsf(fr), fabsf(fi)));
-            } else if (args.beta.x == 1.0 && args.beta.y == 0.0) {
-              // one writer per element: the addition runs in L2 (no read
-              // round trip, no FP64 work on the SM)
-              atomicAdd(&C[off].x, xr);
-              atomicAdd(&C[off].y, xi);
+              omax = fmaxf(omax, fmaxf(fabsf(fr), fabsf(fi)));
             } else {
               const double2 cv = C[off];
               C[off] = make_double2(xr + args.beta.x * cv.x - args.beta.y * cv.y,
@@ -729,6 +733,11 @@ void launch(const TcDesc *descs, int n, cudaStream_t st, int *err) {
                               : static_cast<int>(std::max(1.0, std::min<double>(a.m_tiles, 24.0e6 / panel)));
     a.chunk = g.chunk > 0 ? g.chunk : default_chunk(g.tier, a.kb_per_split);
     a.out = g.out;
+    a.wmode = g.out == TC_OUT_F32 ? WM_F32
+              : g.out == TC_OUT_F64_ATOMIC ? WM_F64_ADD
+              : (g.beta.x == 0.0 && g.beta.y == 0.0) ? WM_F64_STORE
+              : (g.beta.x == 1.0 && g.beta.y == 0.0) ? WM_F64_ADD
+                                                     : WM_F64_BETA;
     a.C = g.C;
     a.cm = g.cm;
     a.cn = g.cn;

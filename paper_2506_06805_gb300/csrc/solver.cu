@@ -783,13 +783,16 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
   auto R2t = [&](const char *ix) { return T(R2, ix, {o, o, v, v}); };
   // driver <ab||ij> = conj(<ij||ab>)
   eng.permute_into(C1(), conj(g_oovv("ijab")), C0(), R2t("ijab"));
-  // Terms sharing one antisymmetriser are summed into X first, so each
-  // symmetry class costs one pass over R2.
+  // Terms that need an antisymmetriser are summed into one scratch X, and a
+  // single P(ij)P(ab) pass adds X to R2 at the end. A P(ab) term f that is
+  // itself antisymmetric in (i, j) equals 1/2 P(ij)P(ab) f, and a P(ij) term
+  // antisymmetric in (a, b) equals 1/2 P(ij)P(ab) of itself, so every
+  // one-pair term enters X with a factor 1/2.
   // Hole-ladder intermediate W'_mnij = <mn||ij> + P(ij) t_j^e <mn||ie>,
   // antisymmetric in (m, n). The hole ladder 1/2 tau_mn^ab W'_mnij splits
   // into its t2 part (taken below with the Z term) and its t1 t1 part,
   // sum_mn t_m^a t_n^b W'_mnij, which is antisymmetric in (a, b): it joins
-  // the P(ab) class as 1/2 sum_mn t_m^a t_n^b W'_mnij.
+  // the P(ab) terms as 1/2 sum_mn t_m^a t_n^b W'_mnij.
   const std::initializer_list<long> d4 = {o, o, o, o};
   Buf Wp(&al, sizeof(cplx) * oo * oo);
   {
@@ -800,33 +803,31 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
     eng.permute_into(Cr(-1), T(tmp.c(), "mnji", d4), C1(), T(Wp.c(), "mnij", d4));
   }
   // P(ab) [t_ij^ae (F_be - 1/2 t_m^b F_me) + sum_m t_m^a Q_ijmb] with
-  // Q_ijmb = -<mb||ij> + 1/2 sum_n W'_mnij t_n^b, <mb||ij> = conj(<ij||mb>)
+  // Q_ijmb = -<mb||ij> + 1/2 sum_n W'_mnij t_n^b, <mb||ij> = conj(<ij||mb>);
+  // both parts are antisymmetric in (i, j). The tensor-core product is the
+  // first writer of X (plain stores rather than atomic additions).
   {
     Buf Fbe(&al, sizeof(cplx) * vv);
     d2d(Fbe.p, Fae.p, sizeof(cplx) * vv, st);
     eng.contract(Cr(-0.5), t1("mb"), T(Fme.c(), "me", {o, v}), C1(), T(Fbe.c(), "be", {v, v}),
                  sx);
-    eng.contract(C1(), t2("ijae"), T(Fbe.c(), "be", {v, v}), C0(), Xt("ijab"), tr);
+    eng.contract(Cr(0.5), t2("ijae"), T(Fbe.c(), "be", {v, v}), C0(), Xt("ijab"), tr);
     Buf Qm(&al, sizeof(cplx) * oo * o * v);
     auto Qt = [&](const char *ix) { return T(Qm.c(), ix, {o, o, o, v}); };
     eng.permute_into(Cr(-1), conj(g_ooov("ijmb")), C0(), Qt("ijmb"));
     eng.contract(Cr(0.5), T(Wp.c(), "mnij", d4), t1("nb"), C1(), Qt("ijmb"), tr);
-    eng.contract(C1(), t1("ma"), Qt("ijmb"), C1(), Xt("ijab"), tr);
-    { Engine::Region r_ = eng.region("antisym_add"); antisym_add(R2, Xb.c(), o, v, 1.0, 2, st); }
+    eng.contract(Cr(0.5), t1("ma"), Qt("ijmb"), C1(), Xt("ijab"), tr);
   }
-  // P(ij) [-t_im^ab (F_mj + 1/2 t_j^e F_me) + t_i^e <ab||ej>], the second as
-  // sum_P (Y^P_ai L^P_bj - L^P_aj Y^P_bi)
+  // P(ij) t_i^e <ab||ej> = P(ij)P(ab) T_ijab with T_ijab = sum_P Y^P_ai L^P_bj,
+  // since t_i^e <ab||ej> = sum_P (Y^P_ai L^P_bj - L^P_aj Y^P_bi) = T_ijab - T_ijba
+  eng.contract(C1(), T(Y.c(), "Pai", {X, v, o}), Lvo_("Pbj"), C1(), Xt("ijab"), tr);
+  // P(ij) [-t_im^ab (F_mj + 1/2 t_j^e F_me)], antisymmetric in (a, b)
   {
     Buf Fmj(&al, sizeof(cplx) * oo);
     d2d(Fmj.p, Fmi.p, sizeof(cplx) * oo, st);
     eng.contract(Cr(0.5), t1("je"), T(Fme.c(), "me", {o, v}), C1(), T(Fmj.c(), "mj", {o, o}),
                  sx);
-    // the tensor-core product first, with beta = 0: plain stores rather
-    // than atomic additions for the first writer of X
-    eng.contract(C1(), T(Y.c(), "Pai", {X, v, o}), Lvo_("Pbj"), C0(), Xt("ijab"), tr);
-    eng.contract(Cr(-1), Lvo_("Paj"), T(Y.c(), "Pbi", {X, v, o}), C1(), Xt("ijab"), tr);
-    eng.contract(Cr(-1), t2("imab"), T(Fmj.c(), "mj", {o, o}), C1(), Xt("ijab"), tr);
-    { Engine::Region r_ = eng.region("antisym_add"); antisym_add(R2, Xb.c(), o, v, 1.0, 1, st); }
+    eng.contract(Cr(-0.5), t2("imab"), T(Fmj.c(), "mj", {o, o}), C1(), Xt("ijab"), tr);
   }
   // hole ladder, t2 part: sum_mn t_mn^ab (1/2 W'_mnij + 1/4 Z_mnij), with
   // Z_mnij = sum_ef <mn||ef> tau_ij^ef
@@ -871,7 +872,7 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
                  Wt("jbme"), tr);
   }
   // P(ij)P(ab) [t_im^ae W_mbej - t_i^e t_m^a <mb||ej>]
-  eng.contract(C1(), stable(t2("imae")), Wt("jbme"), C0(), Xt("ijab"), tr);
+  eng.contract(C1(), stable(t2("imae")), Wt("jbme"), C1(), Xt("ijab"), tr);
   eng.forget_packs(t2p);
   {
     Buf y2(&al, sizeof(cplx) * oo * o * v);
