@@ -175,11 +175,9 @@ __device__ __forceinline__ void block_max3(float m0, float m1, float m2, float *
 // over the whole tensors, for the FP16 tiers' operand scales.
 template <typename T, bool ANTI>
 __global__ void __launch_bounds__(256) t1t1_kernel(const double2 *__restrict__ t1,
-                                                   const double2 *__restrict__ t2,
-                                                   double2 *__restrict__ out0,
-                                                   double2 *__restrict__ out1, int o, int v,
-                                                   int c0_half, double c0, float f0, float f1,
-                                                   float *mx) {
+                                                   const double2 *__restrict__ t2, double2 *out0,
+                                                   double2 *out1, int o, int v, int c0_half,
+                                                   double c0, float f0, float f1, float *mx) {
   extern __shared__ __align__(16) unsigned char t1t1_sm[];
   T *ti = reinterpret_cast<T *>(t1t1_sm);
   T *tj = ti + v;
@@ -194,42 +192,30 @@ __global__ void __launch_bounds__(256) t1t1_kernel(const double2 *__restrict__ t
   const long base = static_cast<long>(ij) * v * v;
   const int a_end = min(v, static_cast<int>(blockIdx.x) * 32 + 32);
   float m_t = 0.0f, m_0 = 0.0f, m_1 = 0.0f;
-  constexpr int U = 4;  // t2 loads per lane in flight
   for (int a = blockIdx.x * 32 + warp; a < a_end; a += 8) {
     const T tia = ti[a], tja = tj[a];
     const long row = base + static_cast<long>(a) * v;
-    for (int b0 = lane; b0 < v; b0 += 32 * U) {
-      double2 tv[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int b = b0 + 32 * u;
-        tv[u] = b < v ? t2[row + b] : make_double2(0.0, 0.0);
+    for (int b = lane; b < v; b += 32) {
+      T x = tmul(tia, tj[b]);
+      if (ANTI) x = tsub(x, tmul(ti[b], tja));
+      const double2 t = t2[row + b];
+      const double2 p0 = widen_scaled(x, f0);
+      double2 r0;
+      if (c0_half >= 0) {
+        r0 = make_double2(scale_c(t.x, c0_half) + p0.x, scale_c(t.y, c0_half) + p0.y);
+      } else {
+        r0 = make_double2(c0 * t.x + p0.x, c0 * t.y + p0.y);
       }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int b = b0 + 32 * u;
-        if (b >= v) break;
-        T x = tmul(tia, tj[b]);
-        if (ANTI) x = tsub(x, tmul(ti[b], tja));
-        const double2 t = tv[u];
-        const double2 p0 = widen_scaled(x, f0);
-        double2 r0;
-        if (c0_half >= 0) {
-          r0 = make_double2(scale_c(t.x, c0_half) + p0.x, scale_c(t.y, c0_half) + p0.y);
-        } else {
-          r0 = make_double2(c0 * t.x + p0.x, c0 * t.y + p0.y);
-        }
-        out0[row + b] = r0;
-        if (mx) {
-          m_t = fmaxf(m_t, mag32(t));
-          m_0 = fmaxf(m_0, mag32(r0));
-        }
-        if (out1) {
-          const double2 p1 = widen_scaled(x, f1);
-          const double2 r1 = make_double2(t.x + p1.x, t.y + p1.y);
-          out1[row + b] = r1;
-          if (mx) m_1 = fmaxf(m_1, mag32(r1));
-        }
+      out0[row + b] = r0;
+      if (mx) {
+        m_t = fmaxf(m_t, mag32(t));
+        m_0 = fmaxf(m_0, mag32(r0));
+      }
+      if (out1) {
+        const double2 p1 = widen_scaled(x, f1);
+        const double2 r1 = make_double2(t.x + p1.x, t.y + p1.y);
+        out1[row + b] = r1;
+        if (mx) m_1 = fmaxf(m_1, mag32(r1));
       }
     }
   }

@@ -71,9 +71,10 @@ __global__ void __launch_bounds__(SK_THREADS) skinny_kernel(const SkinnyDesc d, 
       const long co0 = cb + (d.cs ? d.cs[s0 + s] : static_cast<long>(s0 + s) * d.ldcs);
       const long co1 = two ? cb + (d.cs ? d.cs[s0 + s + 1] : static_cast<long>(s0 + s + 1) * d.ldcs)
                            : co0;
-      // beta != 0: the old values (each output has one writer: this thread)
+      // beta = 1 (one writer per element): the additions run in L2 as
+      // atomics, with no read round trip; general beta reads the old values
       double2 old0 = make_double2(0.0, 0.0), old1 = make_double2(0.0, 0.0);
-      if (beta_mode != 0) {
+      if (beta_mode == 2) {
         old0 = d.C[co0];
         if (two) old1 = d.C[co1];
       }
@@ -102,8 +103,19 @@ __global__ void __launch_bounds__(SK_THREADS) skinny_kernel(const SkinnyDesc d, 
         bi1 = fmaf(b.x, u.w, bi1);
         bi1 = fmaf(b.y, u.z, bi1);
       }
-      d.C[co0] = epilogue(ar0 + ar1, ai0 + ai1, old0, alpha_f, beta_mode, d.beta);
-      if (two) d.C[co1] = epilogue(br0 + br1, bi0 + bi1, old1, alpha_f, beta_mode, d.beta);
+      if (beta_mode == 1) {
+        const double2 x0 = epilogue(ar0 + ar1, ai0 + ai1, old0, alpha_f, 0, d.beta);
+        atomicAdd(&d.C[co0].x, x0.x);
+        atomicAdd(&d.C[co0].y, x0.y);
+        if (two) {
+          const double2 x1 = epilogue(br0 + br1, bi0 + bi1, old1, alpha_f, 0, d.beta);
+          atomicAdd(&d.C[co1].x, x1.x);
+          atomicAdd(&d.C[co1].y, x1.y);
+        }
+      } else {
+        d.C[co0] = epilogue(ar0 + ar1, ai0 + ai1, old0, alpha_f, beta_mode, d.beta);
+        if (two) d.C[co1] = epilogue(br0 + br1, bi0 + bi1, old1, alpha_f, beta_mode, d.beta);
+      }
     }
   }
 }

@@ -550,6 +550,11 @@ __global__ void __launch_bounds__(320, 1)
       if (args.amax_a) usc = 1.0f / (fp16_scale(*args.amax_a) * fp16_scale(*args.amax_b));
       const long nbase = static_cast<long>(n_tile) * BN + h * HALF;
       const long mbase = (static_cast<long>(m_tile) * UNIT_ROWS + TC_RANK * BM) / 2 + q * 16;
+      // output row offsets of this warp's 16 complex rows, one per lane,
+      // fetched once per tile (the row loop takes them by shuffle)
+      long roff = 0;
+      if (lane < 16 && mbase + lane < args.M)
+        roff = args.cm ? args.cm[mbase + lane] : (mbase + lane) * args.ldc;
 #pragma unroll
       for (int j = 0; j < HALF; j += 32) {
 #pragma unroll
@@ -563,6 +568,7 @@ __global__ void __launch_bounds__(320, 1)
           const float re = usc * stg[(2 * rr) * 32 + (lane ^ (2 * rr))];
           const float im = usc * stg[(2 * rr + 1) * 32 + (lane ^ (2 * rr + 1))];
           const long mc = mbase + rr;
+          const long ro = __shfl_sync(0xffffffffu, roff, rr);
           if (!col_ok || mc >= args.M) continue;
           const int wm = args.wmode;
           if (wm == WM_F32) {
@@ -571,7 +577,7 @@ __global__ void __launch_bounds__(320, 1)
             omax = fmaxf(omax, fmaxf(fabsf(re), fabsf(im)));
           } else {
             double2 *C = reinterpret_cast<double2 *>(args.C);
-            const long off = (args.cm ? args.cm[mc] : mc * args.ldc) + cno;
+            const long off = ro + cno;
             // alpha in FP32 (the product carries FP32 rounding already),
             // widened on the integer pipes; FP64 arithmetic only for a
             // general beta
