@@ -316,6 +316,34 @@ bool Engine::run(cplx alpha, const TRef &A, const TRef &B, cplx beta, const TRef
     s.swap(s2);
     c.swap(c2);
   }
+  // Tensor-core products with a long K: when an operand's K is strided but
+  // one of its free indices has unit stride, that index becomes the fastest
+  // of the GEMM rows, so the operand is packed by the transposing kernel
+  // (reads along its rows) instead of by strided gathers. The output is then
+  // written in a less regular order, which costs little against the long
+  // accumulation of each tile.
+  const bool skinny_shape = K <= SKINNY_MAX_K && std::min(M, N) <= 1024 && std::max(M, N) >= 2048;
+  static const long rows_min_k = [] {
+    // smallest K for the reordering; CDFNS_ROWS_MIN_K (read once) replaces
+    // it, for tuning and for checking this path at small sizes
+    const char *e = std::getenv("CDFNS_ROWS_MIN_K");
+    return e ? std::atol(e) : 4096L;
+  }();
+  if (!simt && !skinny_shape && K >= rows_min_k) {
+    auto unit_last = [](std::vector<long> &d, std::vector<long> &s, std::vector<long> &c,
+                        const std::vector<long> &ks) {
+      if (d.size() < 2 || s.back() == 1 || ks.empty() || ks.back() == 1) return;
+      for (size_t u = 0; u + 1 < d.size(); ++u) {
+        if (s[u] != 1) continue;
+        std::rotate(d.begin() + u, d.begin() + u + 1, d.end());
+        std::rotate(s.begin() + u, s.begin() + u + 1, s.end());
+        std::rotate(c.begin() + u, c.begin() + u + 1, c.end());
+        return;
+      }
+    };
+    unit_last(mdim, amstr, cmstr, akstr);
+    unit_last(ndim, bnstr, cnstr, bkstr);
+  }
   const int trec =
       trace_on_ ? trace_open((out ? "prep " : "") + A.idx + (A.conj ? "*" : "") + "," + B.idx +
                                  (B.conj ? "*" : "") + "->" + C.idx,

@@ -548,6 +548,8 @@ __global__ void __launch_bounds__(320, 1)
       // undo the FP16 operand scales (an exact power of two)
       float usc = 1.0f;
       if (args.amax_a) usc = 1.0f / (fp16_scale(*args.amax_a) * fp16_scale(*args.amax_b));
+      // alpha with the scales folded in (exact: usc is a power of two)
+      const float2 al = make_float2(usc * args.alpha_f.x, usc * args.alpha_f.y);
       const long nbase = static_cast<long>(n_tile) * BN + h * HALF;
       const long mbase = (static_cast<long>(m_tile) * UNIT_ROWS + TC_RANK * BM) / 2 + q * 16;
       // output row offsets of this warp's 16 complex rows, one per lane,
@@ -565,14 +567,15 @@ __global__ void __launch_bounds__(320, 1)
         const long cno = col_ok ? (args.cn ? args.cn[n] : n) : 0;
 #pragma unroll 4
         for (int rr = 0; rr < 16; ++rr) {
-          const float re = usc * stg[(2 * rr) * 32 + (lane ^ (2 * rr))];
-          const float im = usc * stg[(2 * rr + 1) * 32 + (lane ^ (2 * rr + 1))];
+          const float sr = stg[(2 * rr) * 32 + (lane ^ (2 * rr))];
+          const float si = stg[(2 * rr + 1) * 32 + (lane ^ (2 * rr + 1))];
           const long mc = mbase + rr;
           const long ro = __shfl_sync(0xffffffffu, roff, rr);
           if (!col_ok || mc >= args.M) continue;
           const int wm = args.wmode;
           if (wm == WM_F32) {
             float2 *Cf = reinterpret_cast<float2 *>(args.C);
+            const float re = usc * sr, im = usc * si;
             Cf[mc * args.ldc + n] = make_float2(re, im);
             omax = fmaxf(omax, fmaxf(fabsf(re), fabsf(im)));
           } else {
@@ -581,8 +584,8 @@ __global__ void __launch_bounds__(320, 1)
             // alpha in FP32 (the product carries FP32 rounding already),
             // widened on the integer pipes; FP64 arithmetic only for a
             // general beta
-            const float fr = args.alpha_f.x * re - args.alpha_f.y * im;
-            const float fi = args.alpha_f.x * im + args.alpha_f.y * re;
+            const float fr = al.x * sr - al.y * si;
+            const float fi = al.x * si + al.y * sr;
             const double xr = f32_to_f64(fr), xi = f32_to_f64(fi);
             if (wm == WM_F64_ADD) {
               // split-K partials, or beta = 1 with one writer per element:
