@@ -802,16 +802,25 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
     eng.permute_into(C1(), T(tmp.c(), "mnij", d4), C1(), T(Wp.c(), "mnij", d4));
     eng.permute_into(Cr(-1), T(tmp.c(), "mnji", d4), C1(), T(Wp.c(), "mnij", d4));
   }
+  // P(ij) [-t_im^ab (F_mj + 1/2 t_j^e F_me)], antisymmetric in (a, b): the
+  // first writer of X (plain stores; measured a little faster than taking
+  // the tensor-core product below first)
+  {
+    Buf Fmj(&al, sizeof(cplx) * oo);
+    d2d(Fmj.p, Fmi.p, sizeof(cplx) * oo, st);
+    eng.contract(Cr(0.5), t1("je"), T(Fme.c(), "me", {o, v}), C1(), T(Fmj.c(), "mj", {o, o}),
+                 sx);
+    eng.contract(Cr(-0.5), t2("imab"), T(Fmj.c(), "mj", {o, o}), C0(), Xt("ijab"), tr);
+  }
   // P(ab) [t_ij^ae (F_be - 1/2 t_m^b F_me) + sum_m t_m^a Q_ijmb] with
   // Q_ijmb = -<mb||ij> + 1/2 sum_n W'_mnij t_n^b, <mb||ij> = conj(<ij||mb>);
-  // both parts are antisymmetric in (i, j). The tensor-core product is the
-  // first writer of X (plain stores rather than atomic additions).
+  // both parts are antisymmetric in (i, j)
   {
     Buf Fbe(&al, sizeof(cplx) * vv);
     d2d(Fbe.p, Fae.p, sizeof(cplx) * vv, st);
     eng.contract(Cr(-0.5), t1("mb"), T(Fme.c(), "me", {o, v}), C1(), T(Fbe.c(), "be", {v, v}),
                  sx);
-    eng.contract(Cr(0.5), t2("ijae"), T(Fbe.c(), "be", {v, v}), C0(), Xt("ijab"), tr);
+    eng.contract(Cr(0.5), t2("ijae"), T(Fbe.c(), "be", {v, v}), C1(), Xt("ijab"), tr);
     Buf Qm(&al, sizeof(cplx) * oo * o * v);
     auto Qt = [&](const char *ix) { return T(Qm.c(), ix, {o, o, o, v}); };
     eng.permute_into(Cr(-1), conj(g_ooov("ijmb")), C0(), Qt("ijmb"));
@@ -821,14 +830,6 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
   // P(ij) t_i^e <ab||ej> = P(ij)P(ab) T_ijab with T_ijab = sum_P Y^P_ai L^P_bj,
   // since t_i^e <ab||ej> = sum_P (Y^P_ai L^P_bj - L^P_aj Y^P_bi) = T_ijab - T_ijba
   eng.contract(C1(), T(Y.c(), "Pai", {X, v, o}), Lvo_("Pbj"), C1(), Xt("ijab"), tr);
-  // P(ij) [-t_im^ab (F_mj + 1/2 t_j^e F_me)], antisymmetric in (a, b)
-  {
-    Buf Fmj(&al, sizeof(cplx) * oo);
-    d2d(Fmj.p, Fmi.p, sizeof(cplx) * oo, st);
-    eng.contract(Cr(0.5), t1("je"), T(Fme.c(), "me", {o, v}), C1(), T(Fmj.c(), "mj", {o, o}),
-                 sx);
-    eng.contract(Cr(-0.5), t2("imab"), T(Fmj.c(), "mj", {o, o}), C1(), Xt("ijab"), tr);
-  }
   // hole ladder, t2 part: sum_mn t_mn^ab (1/2 W'_mnij + 1/4 Z_mnij), with
   // Z_mnij = sum_ef <mn||ef> tau_ij^ef
   {
