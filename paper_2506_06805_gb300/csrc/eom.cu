@@ -56,6 +56,29 @@ cudaStream_t capture_stream() {
   return g_cap_stream;
 }
 
+// dst = src / |src| from the squared norm n2 (a device value, its real
+// part), or zero when |src| < thr: the Davidson's normalisation decided on
+// the device, so a block of new vectors needs no host round trip per vector.
+__global__ void normalize_or_zero_kernel(double2 *__restrict__ dst, const double2 *__restrict__ src,
+                                         long n, const double2 *__restrict__ n2, double thr) {
+  const double nn = sqrt(fmax(n2->x, 0.0));
+  const bool keep = !(nn < thr);
+  const double s = keep ? 1.0 / nn : 0.0;
+  for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long>(gridDim.x) * blockDim.x) {
+    const double2 x = src[i];
+    dst[i] = keep ? make_double2(x.x * s, x.y * s) : make_double2(0.0, 0.0);
+  }
+}
+
+void normalize_or_zero(cplx *dst, const cplx *src, long n, const cplx *n2, double thr,
+                       cudaStream_t st) {
+  const unsigned blocks = static_cast<unsigned>(std::min<long>((n + 255) / 256, 4096));
+  normalize_or_zero_kernel<<<blocks, 256, 0, st>>>(dst, src, n, n2, thr);
+  LAUNCH_CHECK();
+  count_launch();
+}
+
 }  // namespace
 
 // Drop every graph that refers to ctx (called when a context goes away).
@@ -327,6 +350,7 @@ struct Dav {
   long dim = 0;
   int max_sp = 0;
   Buf V, S, d, Xr, SX, R, G, Gm, wv, VR, Ysel, wsel, cproj, corr;
+  Buf nrm;  // squared norms of new vectors / residuals, on the device
   int m = 0, it = 0, added = 0;
   enum { FULL, ADDED } pending = FULL;
   bool done = false, converged = false;
@@ -346,7 +370,12 @@ struct Dav {
                     TIER_FP64);
   }
   // orthogonalise rows vecs[0..nnew) against V[0..mbase) (two passes) and
-  // among themselves; accepted rows are appended to V at mbase
+  // among themselves; accepted rows are appended to V at mbase. Row j is
+  // projected (two passes) against the rows of the block before it, which
+  // already sit normalised in V, and normalised on the device; a row whose
+  // norm falls below 1e-10 is zeroed in place (later projections then skip
+  // it) and dropped when the block is compacted after the one read of the
+  // norms at the end.
   int orth_new(cplx *vecs, int nnew, int mbase) {
     if (mbase > 0) {
       for (int pass = 0; pass < 2; ++pass) {
@@ -356,21 +385,33 @@ struct Dav {
                         C1(), T(vecs, "rd", {nnew, dim}), TIER_FP64);
       }
     }
-    int acc = 0;
+    const size_t z = sizeof(cplx);
+    cplx *Vb = V.c() + static_cast<long>(mbase) * dim;
     for (int j = 0; j < nnew; ++j) {
       cplx *x = vecs + static_cast<long>(j) * dim;
-      for (int pass = 0; pass < 2; ++pass)
-        for (int i = 0; i < acc; ++i) {
-          cplx *y = V.c() + static_cast<long>(mbase + i) * dim;
-          const cplx cc = dot(y, x, dim, true, st(), c->red.c());
-          axpby(dim, mk(-cc.x, -cc.y), y, C1(), x, st());
+      if (j > 0)
+        for (int pass = 0; pass < 2; ++pass) {
+          // <V_a|x> for the block's rows a < j, up to 16 per pass over x
+          // (each sum split over many blocks)
+          for (int a0 = 0; a0 < j; a0 += 16) {
+            const int na = std::min(16, j - a0);
+            const cplx *ys[16];
+            for (int a = 0; a < na; ++a) ys[a] = Vb + static_cast<long>(a0 + a) * dim;
+            dot_multi(ys, na, x, dim, false, cproj.c() + a0, 1, c->red.c(), 4096, st());
+          }
+          c->eng.contract(Cr(-1), T(cproj.c(), "ra", {1, j}), T(Vb, "ad", {j, dim}), C1(),
+                          T(x, "rd", {1, dim}), TIER_FP64);
         }
-      const cplx n2 = dot(x, x, dim, true, st(), c->red.c());
-      const double nrm = std::sqrt(std::max(n2.x, 0.0));
-      if (nrm < 1e-10) continue;
-      cplx *dst = V.c() + static_cast<long>(mbase + acc) * dim;
-      d2d(dst, x, sizeof(cplx) * dim, st());
-      axpby(dim, mk(1.0 / nrm, 0.0), dst, C0(), dst, st());
+      dot_dev(x, x, dim, true, nrm.c() + j, st(), c->red.c());
+      normalize_or_zero(Vb + static_cast<long>(j) * dim, x, dim, nrm.c() + j, 1e-10, st());
+    }
+    std::vector<cplx> nh(nnew);
+    d2h(nh.data(), nrm.p, z * nnew, st());
+    int acc = 0;
+    for (int j = 0; j < nnew; ++j) {
+      if (std::sqrt(std::max(nh[j].x, 0.0)) < 1e-10) continue;
+      if (acc != j)
+        d2d(Vb + static_cast<long>(acc) * dim, Vb + static_cast<long>(j) * dim, z * dim, st());
       ++acc;
     }
     return acc;
@@ -399,6 +440,7 @@ struct Dav {
     Ysel.reset(al, z * nr * max_sp);
     wsel.reset(al, z * nr);
     cproj.reset(al, z * nr * max_sp);
+    nrm.reset(al, z * nr);
     w_out.assign(nr, mk(0, 0));
     rn.assign(nr, 0.0);
     ip_diag(c->Hoo.c(), c->Hvv.c(), c->o, c->v, d.c(), st());
@@ -454,8 +496,8 @@ struct Dav {
     }
     geev_dev(&c->al, st(), G.c(), m, wv.c(), VR.c());
     std::vector<cplx> wh(m), vh(static_cast<size_t>(m) * m);
-    d2h(wh.data(), wv.p, z * m, st());
-    d2h(vh.data(), VR.p, z * m * m, st());
+    CUDA_CHECK(cudaMemcpyAsync(wh.data(), wv.p, z * m, cudaMemcpyDeviceToHost, st()));
+    d2h(vh.data(), VR.p, z * m * m, st());  // one synchronisation for both
     std::vector<int> ord(m);
     std::iota(ord.begin(), ord.end(), 0);
     std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return wh[a].x < wh[b].x; });
@@ -476,11 +518,15 @@ struct Dav {
     c->eng.contract(C1(), T(Ysel.c(), "ra", {nr, m}), T(S.c(), "ad", {m, dim}), C0(),
                     T(SX.c(), "rd", {nr, dim}), TIER_FP64);
     d2d(R.p, SX.p, z * nr * dim, st());
-    bool all = true;
     for (int r = 0; r < nr; ++r) {
       axpby(dim, mk(-w_out[r].x, -w_out[r].y), Xr.c() + r * dim, C1(), R.c() + r * dim, st());
-      const cplx n2 = dot(R.c() + r * dim, R.c() + r * dim, dim, true, st(), c->red.c());
-      rn[r] = std::sqrt(std::max(n2.x, 0.0));
+      dot_dev(R.c() + r * dim, R.c() + r * dim, dim, true, nrm.c() + r, st(), c->red.c());
+    }
+    std::vector<cplx> n2h(nr);
+    d2h(n2h.data(), nrm.p, z * nr, st());
+    bool all = true;
+    for (int r = 0; r < nr; ++r) {
+      rn[r] = std::sqrt(std::max(n2h[r].x, 0.0));
       if (!std::isfinite(rn[r])) {
         if (!isolate) fail(CC_ERR_NUMERIC, "Davidson residual NaN");
         failed = CC_ERR_NUMERIC;

@@ -565,21 +565,27 @@ __global__ void __launch_bounds__(320, 1)
         const long n = nbase + j + lane;
         const bool col_ok = n < args.N;
         const long cno = col_ok ? (args.cn ? args.cn[n] : n) : 0;
+        const int wm = args.wmode;  // the same for the whole tile
+        if (wm == WM_F32) {
+          float2 *Cf = reinterpret_cast<float2 *>(args.C);
 #pragma unroll 4
-        for (int rr = 0; rr < 16; ++rr) {
-          const float sr = stg[(2 * rr) * 32 + (lane ^ (2 * rr))];
-          const float si = stg[(2 * rr + 1) * 32 + (lane ^ (2 * rr + 1))];
-          const long mc = mbase + rr;
-          const long ro = __shfl_sync(0xffffffffu, roff, rr);
-          if (!col_ok || mc >= args.M) continue;
-          const int wm = args.wmode;
-          if (wm == WM_F32) {
-            float2 *Cf = reinterpret_cast<float2 *>(args.C);
-            const float re = usc * sr, im = usc * si;
+          for (int rr = 0; rr < 16; ++rr) {
+            const long mc = mbase + rr;
+            if (!col_ok || mc >= args.M) continue;
+            const float re = usc * stg[(2 * rr) * 32 + (lane ^ (2 * rr))];
+            const float im = usc * stg[(2 * rr + 1) * 32 + (lane ^ (2 * rr + 1))];
             Cf[mc * args.ldc + n] = make_float2(re, im);
             omax = fmaxf(omax, fmaxf(fabsf(re), fabsf(im)));
-          } else {
-            double2 *C = reinterpret_cast<double2 *>(args.C);
+          }
+        } else {
+          double2 *C = reinterpret_cast<double2 *>(args.C);
+#pragma unroll 4
+          for (int rr = 0; rr < 16; ++rr) {
+            const float sr = stg[(2 * rr) * 32 + (lane ^ (2 * rr))];
+            const float si = stg[(2 * rr + 1) * 32 + (lane ^ (2 * rr + 1))];
+            const long mc = mbase + rr;
+            const long ro = __shfl_sync(0xffffffffu, roff, rr);
+            if (!col_ok || mc >= args.M) continue;
             const long off = ro + cno;
             // alpha in FP32 (the product carries FP32 rounding already),
             // widened on the integer pipes; FP64 arithmetic only for a
