@@ -19,7 +19,8 @@ CCSD and IP-EOM with CCSD in --tier and in --eom-tier (the EOM sigma in
 n_aux = 4 n_virt, shapes and inputs from ``synth.batch_specs``), solves
 CCSD for each, then times IP-EOM for all of them one after another and as
 one batch (batched sigma in grouped launches, with and without CUDA graphs)
-and compares the roots.
+and compares the roots; ``--small`` draws systems with n_occ 6-12 and
+n_virt 30-80 instead, none of which fills the GPU alone.
 ``solve`` runs one configured system end to end (Cholesky vectors fed in
 chunks of 200, CCSD, IP-EOM with all roots in one block) on the library's
 own cudaMalloc allocations, and reports the phase times, iteration counts,
@@ -56,6 +57,8 @@ def main():
     p.add_argument("--tau", type=float, default=0.0, help="cholesky: threshold")
     p.add_argument("--max-vec", type=int, default=600, help="cholesky: vector limit")
     p.add_argument("--n-sys", type=int, default=8)
+    p.add_argument("--small", action="store_true",
+                   help="batch: systems with n_occ 6-12 and n_virt 30-80 instead of 20-50 / 150-400")
     p.add_argument("--roots", type=int, default=8)
     p.add_argument("--config", default="fns")
     p.add_argument("--keep-frac", type=float, default=0.4)
@@ -366,7 +369,8 @@ def batch_run(a):
     import torch
 
     from . import System, batch_ipeom, synth
-    specs = synth.batch_specs(a.n_sys)
+    specs = (synth.batch_specs(a.n_sys, occ_range=(6, 12), virt_range=(30, 80)) if a.small
+             else synth.batch_specs(a.n_sys))
     systems = []
     t0 = time.perf_counter()
     for sp in specs:

@@ -176,15 +176,16 @@ def make_config(name):
     return c, eps, L
 
 
-def batch_specs(n_sys=8, seed=0):
-    """Shapes of the uneven batch: n_occ in [20, 50], n_virt in [150, 400].
+def batch_specs(n_sys=8, seed=0, occ_range=(20, 50), virt_range=(150, 400)):
+    """Shapes of the uneven batch: n_occ in [20, 50], n_virt in [150, 400]
+    (inclusive ranges, replaceable for batches of smaller systems).
 
     Shapes come from ``default_rng(seed)``; system s draws its own inputs from
     ``default_rng([seed, s + 1])`` with n_aux = 4 n_virt.
     """
     rng = np.random.default_rng(seed)
-    occ = rng.integers(20, 51, size=n_sys)
-    virt = rng.integers(150, 401, size=n_sys)
+    occ = rng.integers(occ_range[0], occ_range[1] + 1, size=n_sys)
+    virt = rng.integers(virt_range[0], virt_range[1] + 1, size=n_sys)
     return [
         _spec(int(o), int(v), int(4 * v), seed=[seed, s + 1])
         for s, (o, v) in enumerate(zip(occ, virt))
