@@ -39,15 +39,29 @@ void *Allocator::get(size_t bytes) {
     fail(CC_ERR_OOM, "device allocation of " + std::to_string(bytes) +
                          " bytes exceeds the context's memory limit");
   void *p = nullptr;
-  if (alloc) {
-    p = alloc(bytes, user);
-    if (!p) fail(CC_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
-  } else {
-    const cudaError_t e = cudaMalloc(&p, bytes);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      fail(CC_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  for (size_t i = held.size(); i-- > 0;) {
+    const Held &h = held[i];
+    if (h.bytes == bytes && h.fr == free && h.fr_user == user) {
+      p = h.p;
+      held_bytes -= bytes;
+      held.erase(held.begin() + static_cast<long>(i));
+      break;
     }
+  }
+  for (int attempt = 0; !p; ++attempt) {
+    if (alloc) {
+      p = alloc(bytes, user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    if (p) break;
+    if (attempt == 0 && !held.empty()) {
+      flush_held();  // the kept blocks back to their allocator, then once more
+      continue;
+    }
+    fail(CC_ERR_OOM, (alloc ? "device allocation of " : "cudaMalloc of ") +
+                         std::to_string(bytes) + " bytes failed");
   }
   in_use += bytes;
   peak = std::max(peak, in_use);
@@ -57,9 +71,24 @@ void *Allocator::get(size_t bytes) {
 
 void Allocator::put(void *p, size_t bytes, void (*fr)(void *, void *), void *fr_user) {
   if (!p) return;
-  in_use -= std::min(in_use, bytes ? bytes : size_t(16));
+  const size_t n = bytes ? bytes : size_t(16);
+  in_use -= std::min(in_use, n);
+  if (recycle && limit == 0) {
+    held.push_back(Held{p, n, fr, fr_user});
+    held_bytes += n;
+    return;
+  }
   if (fr) fr(p, fr_user);
   else cudaFree(p);
+}
+
+void Allocator::flush_held() {
+  for (const Held &h : held) {
+    if (h.fr) h.fr(h.p, h.fr_user);
+    else cudaFree(h.p);
+  }
+  held.clear();
+  held_bytes = 0;
 }
 
 size_t device_avail(const Allocator *al) {
@@ -70,7 +99,10 @@ size_t device_avail(const Allocator *al) {
   }
   const size_t reserve = size_t(2) << 30;
   fr = fr > reserve ? fr - reserve : 0;
+  // (blocks kept for reuse are part of that difference; with cudaMalloc
+  // they are added here, as a failed allocation returns them first)
   if (al && al->alloc) fr += al->peak - std::min(al->peak, al->in_use);
+  else if (al) fr += al->held_bytes;
   if (al && al->limit) fr = std::min(fr, al->limit - std::min(al->limit, al->in_use));
   return fr;
 }
@@ -97,8 +129,27 @@ using cdfns::Error;
 
 namespace {
 
+// For the length of one call, blocks the context releases are kept for
+// reuse by its next requests of the same size; all are returned at the end.
+struct RecycleScope {
+  cdfns::Allocator *al;
+  bool was;
+  explicit RecycleScope(cc_ctx *ctx) : al(ctx ? &ctx->c.al : nullptr), was(al && al->recycle) {
+    if (al) al->recycle = true;
+  }
+  ~RecycleScope() {
+    if (!al || was) return;
+    al->recycle = false;
+    try {
+      al->flush_held();
+    } catch (...) {
+    }
+  }
+};
+
 template <class F>
 int guarded(cc_ctx *ctx, F &&f) {
+  RecycleScope recycle(ctx);
   try {
     return f();
   } catch (const Error &e) {
@@ -384,7 +435,9 @@ int cc_ladder_dev(cc_ctx *ctx, const double *tau_dev, double *out_dev) {
     c.ladder(c.Lvv.c(), reinterpret_cast<const cdfns::cplx *>(tau_dev),
              reinterpret_cast<cdfns::cplx *>(out_dev), c.tier);
     CUDA_CHECK(cudaStreamSynchronize(c.st));
+    c.settle_ladder_timing();
     c.eng.trace_flush();
+    c.check_err_flag();
     return CC_OK;
   });
 }
@@ -398,6 +451,7 @@ int cc_residual_dev(cc_ctx *ctx, const double *t1_dev, const double *t2_dev, dou
     c.residual(reinterpret_cast<const cdfns::cplx *>(t1_dev), reinterpret_cast<const cdfns::cplx *>(t2_dev),
                reinterpret_cast<cdfns::cplx *>(r1_dev), reinterpret_cast<cdfns::cplx *>(r2_dev));
     CUDA_CHECK(cudaStreamSynchronize(c.st));
+    c.settle_ladder_timing();
     c.check_err_flag();
     return CC_OK;
   });

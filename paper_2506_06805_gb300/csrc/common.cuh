@@ -92,10 +92,27 @@ struct Allocator {
   size_t peak = 0;    // high-water mark of in_use
   size_t window = 0;  // high-water mark of in_use since the caller last set it
   size_t limit = 0;   // cap on in_use (0: none); a get() beyond it fails
+  // While `recycle` is set (for the length of one library call, and only
+  // without a limit), released blocks are kept here and handed to the next
+  // request of the same size: the solvers allocate the same buffers in
+  // every iteration, and each round trip through a caller's allocator
+  // callback or cudaMalloc/cudaFree costs host time, cudaFree a device
+  // synchronisation. Kept blocks do not count in in_use; a failed
+  // allocation returns them all and tries once more.
+  struct Held {
+    void *p;
+    size_t bytes;
+    void (*fr)(void *, void *);
+    void *fr_user;
+  };
+  std::vector<Held> held;
+  size_t held_bytes = 0;
+  bool recycle = false;
   void *get(size_t bytes);
   // release p (bytes long) through the functions that allocated it (the
   // allocator may have been replaced since)
   void put(void *p, size_t bytes, void (*fr)(void *, void *), void *fr_user);
+  void flush_held();  // return every kept block
 };
 // Device bytes an allocation through `al` can still obtain: the driver's free
 // memory less 2 GiB for work outside the allocator (library workspaces,

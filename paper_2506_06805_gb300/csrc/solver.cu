@@ -534,10 +534,10 @@ void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr, const float 
   const long vv = static_cast<long>(v) * v;
   const long n_ij = nij(), n_cd = nab(), n_ab = nab();
   if (n_ij == 0 || n_ab == 0) return;
-  cudaEvent_t e0, e1;
-  CUDA_CHECK(cudaEventCreate(&e0));
-  CUDA_CHECK(cudaEventCreate(&e1));
-  CUDA_CHECK(cudaEventRecord(e0, st));
+  auto tm = std::make_shared<EventPair>();
+  CUDA_CHECK(cudaEventCreate(&tm->e0));
+  CUDA_CHECK(cudaEventCreate(&tm->e1));
+  CUDA_CHECK(cudaEventRecord(tm->e0, st));
   Buf Rp(&al, sizeof(cplx) * n_ij * n_ab);
   // tau gather tables: row (i<j) -> (i*o + j)*vv, col (c<d) -> c*v + d
   std::vector<long> rows(n_ij), cols(n_cd);
@@ -687,17 +687,21 @@ void Ctx::ladder(const cplx *Lv, const cplx *tau, cplx *R2, int tr, const float 
   }
   unpack_pairs_add(Rp.c(), o, v, ij_i.as<int>(), ij_j.as<int>(), ab_a.as<int>(), ab_b.as<int>(), R2,
                    st);
-  CUDA_CHECK(cudaEventRecord(e1, st));
-  CUDA_CHECK(cudaEventSynchronize(e1));
-  float ms = 0;
-  CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  stat[0] += ms;
-  stat[1] += 1;
+  CUDA_CHECK(cudaEventRecord(tm->e1, st));
+  ladder_timing.push_back(tm);
   stat[2] = 8.0 * (static_cast<double>(X) * v * v * v * (v - 1) / 2.0 +
                    static_cast<double>(n_cd) * n_cd * n_ij);
-  check_err_flag();
+}
+
+void Ctx::settle_ladder_timing() {
+  for (const auto &t : ladder_timing) {
+    CUDA_CHECK(cudaEventSynchronize(t->e1));
+    float ms = 0;
+    CUDA_CHECK(cudaEventElapsedTime(&ms, t->e0, t->e1));
+    stat[0] += ms;
+    stat[1] += 1;
+  }
+  ladder_timing.clear();
 }
 
 // ===========================================================================
@@ -1085,6 +1089,7 @@ int Ctx::ccsd(double tol, int max_iter, double *e_out, int *n_iter) {
   }
   if (n_iter) *n_iter = it;
   eng.trace_flush();
+  settle_ladder_timing();
   stat[4] += now_ms() - t0;
   stat[7] = it;
   stat[13] = static_cast<double>(loop_peak);

@@ -81,6 +81,12 @@ struct Ctx {
     }
   };
   std::vector<std::shared_ptr<EventPair>> sig_timing;
+  // CUDA events around each ladder call, read when the calling solve ends
+  // (no synchronisation in the middle of a residual)
+  std::vector<std::shared_ptr<EventPair>> ladder_timing;
+  // adds the device time of the recorded ladder calls to stat[0] and their
+  // count to stat[1], and releases the events
+  void settle_ladder_timing();
   // adds the device time of the recorded sigma builds to stat[16], their
   // count to stat[17], and releases the events
   void settle_sigma_timing();
