@@ -273,6 +273,28 @@ def test_kramers_pairs_on_gpu():
     assert np.abs(w[0::2] - w[1::2]).max() < 1e-7
 
 
+@pytest.mark.parametrize("tier,eom_tier,tol", [("fp16", "fp16x3", 1e-5), ("fp16x3", "fp16x3", 1e-7)])
+def test_kramers_fast_tiers_match_oracle(tier, eom_tier, tol):
+    """A Kramers-paired system in the tiers the benchmark runs (FP16 CCSD and
+    H-bar with an FP16x3 sigma) and in FP16x3 throughout: correlation energy
+    and IPs against the oracle, and the pairs still degenerate."""
+    P = _gpu()
+    o, v, X = 8, 40, 120
+    eps, L = _system(o, v, X, seed=2, scale=4.0, kramers=True)
+    e_ref, w_ref = _oracle_roots(eps, L, o, 6)
+    with P.System(eps, L, n_occ=o, tier=tier, eom_tier=eom_tier) as s:
+        e = s.ccsd(tol=1e-7 if tier == "fp16" else 1e-9, max_iter=100)
+        w, _ = s.ipeom(6, tol=1e-8, max_iter=200)
+    assert abs(e - e_ref) <= tol
+    # a degenerate pair of the non-Hermitian H-bar converges as w and conj(w)
+    # with imaginary parts at the square root of the solver tolerance
+    # (~3e-6 here, in the oracle too): compare the real parts
+    wr, wr_ref = np.sort(w.real), np.sort(w_ref.real)
+    assert np.abs(wr - wr_ref).max() <= tol
+    assert np.abs(w.imag).max() <= 1e-4
+    assert np.abs(wr[0::2] - wr[1::2]).max() <= 1e-7
+
+
 def test_fns_matches_oracle():
     P = _gpu()
     from oracle import ccsd, fns, integrals
