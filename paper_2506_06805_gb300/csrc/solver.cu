@@ -818,7 +818,9 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
   }
   // P(ab) [t_ij^ae (F_be - 1/2 t_m^b F_me) + sum_m t_m^a Q_ijmb] with
   // Q_ijmb = -<mb||ij> + 1/2 sum_n W'_mnij t_n^b, <mb||ij> = conj(<ij||mb>);
-  // both parts are antisymmetric in (i, j)
+  // both parts are antisymmetric in (i, j). The P(ij)P(ab) term
+  // -t_m^a y_mbij with y_mbij = sum_e t_i^e <mb||ej> has the same form, so
+  // one product over m takes both: X += sum_m t_m^a (1/2 Q_ijmb - y_mbij).
   {
     Buf Fbe(&al, sizeof(cplx) * vv);
     d2d(Fbe.p, Fae.p, sizeof(cplx) * vv, st);
@@ -827,9 +829,14 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
     eng.contract(Cr(0.5), t2("ijae"), T(Fbe.c(), "be", {v, v}), C1(), Xt("ijab"), tr);
     Buf Qm(&al, sizeof(cplx) * oo * o * v);
     auto Qt = [&](const char *ix) { return T(Qm.c(), ix, {o, o, o, v}); };
-    eng.permute_into(Cr(-1), conj(g_ooov("ijmb")), C0(), Qt("ijmb"));
-    eng.contract(Cr(0.5), T(Wp.c(), "mnij", d4), t1("nb"), C1(), Qt("ijmb"), tr);
-    eng.contract(Cr(0.5), t1("ma"), Qt("ijmb"), C1(), Xt("ijab"), tr);
+    eng.permute_into(Cr(-0.5), conj(g_ooov("ijmb")), C0(), Qt("ijmb"));
+    eng.contract(Cr(0.25), T(Wp.c(), "mnij", d4), t1("nb"), C1(), Qt("ijmb"), tr);
+    {
+      Buf y2(&al, sizeof(cplx) * oo * o * v);
+      eng.contract(C1(), t1("ie"), g_ovvo("mbej"), C0(), T(y2.c(), "mbij", {o, v, o, o}), tr);
+      eng.permute_into(Cr(-1), T(y2.c(), "mbij", {o, v, o, o}), C1(), Qt("ijmb"));
+    }
+    eng.contract(C1(), t1("ma"), Qt("ijmb"), C1(), Xt("ijab"), tr);
   }
   // P(ij) t_i^e <ab||ej> = P(ij)P(ab) T_ijab with T_ijab = sum_P Y^P_ai L^P_bj,
   // since t_i^e <ab||ej> = sum_P (Y^P_ai L^P_bj - L^P_aj Y^P_bi) = T_ijab - T_ijba
@@ -876,14 +883,10 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
     eng.contract(Cr(-1), with_amax(T(z.c(), "jnfb", {o, o, v, v}), amx_z), g_oovv("mnef"), C1(),
                  Wt("jbme"), tr);
   }
-  // P(ij)P(ab) [t_im^ae W_mbej - t_i^e t_m^a <mb||ej>]
+  // P(ij)P(ab) [t_im^ae W_mbej - t_i^e t_m^a <mb||ej>], the second part
+  // taken with the Q product above
   eng.contract(C1(), stable(t2("imae")), Wt("jbme"), C1(), Xt("ijab"), tr);
   eng.forget_packs(t2p);
-  {
-    Buf y2(&al, sizeof(cplx) * oo * o * v);
-    eng.contract(C1(), t1("ie"), g_ovvo("mbej"), C0(), T(y2.c(), "mbij", {o, v, o, o}), tr);
-    eng.contract(Cr(-1), t1("ma"), T(y2.c(), "mbij", {o, v, o, o}), C1(), Xt("ijab"), tr);
-  }
   { Engine::Region r_ = eng.region("antisym_add"); antisym_add(R2, Xb.c(), o, v, 1.0, 3, st); }
 }
 
