@@ -943,11 +943,6 @@ void make_tau_pair(const cplx *t1, const cplx *t2, cplx *tau, cplx *taut, int o,
   t1t1_launch<true>(t1, t2, tau, taut, o, v, 1.0, 1.0, 0.5, fp32_t1, st, mx);
 }
 
-void make_z(const cplx *t1, const cplx *t2, cplx *out, int o, int v, double c2, cudaStream_t st,
-            bool fp32_t1, float *mx) {
-  t1t1_launch<false>(t1, t2, out, nullptr, o, v, c2, 1.0, 0.0, fp32_t1, st, mx);
-}
-
 void jacobi(const cplx *R1, const cplx *R2, const double *eps, int o, int v, cplx *t1, cplx *t2,
             cudaStream_t st) {
   if (static_cast<long>(o) * v > static_cast<long>(v) * v)

@@ -24,9 +24,6 @@ void make_tau(const cplx *t1, const cplx *t2, cplx *out, int o, int v, double f,
 // tau (f = 1) and tau~ (f = 1/2) in one pass over t2
 void make_tau_pair(const cplx *t1, const cplx *t2, cplx *tau, cplx *taut, int o, int v,
                    cudaStream_t st, bool fp32_t1 = false, float *mx = nullptr);
-// out[jnfb] = c2 * t2[jnfb] + t1[jf] t1[nb]
-void make_z(const cplx *t1, const cplx *t2, cplx *out, int o, int v, double c2,
-            cudaStream_t st, bool fp32_t1 = false, float *mx = nullptr);
 // t_new = R / D with D from eps (FP64); exact zeros on i=j or a=b.
 void jacobi(const cplx *R1, const cplx *R2, const double *eps, int o, int v, cplx *t1,
             cplx *t2, cudaStream_t st);

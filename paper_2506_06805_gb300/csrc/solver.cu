@@ -715,16 +715,14 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
   const long oo = static_cast<long>(o) * o, vv = static_cast<long>(v) * v, n2 = oo * vv;
   Buf tau(&al, sizeof(cplx) * n2), taut(&al, sizeof(cplx) * n2);
   // FP16 tiers: the maximum of each doubles-sized operand, shared by all of
-  // its uses ([0] t2, [1] tau, [2] tau~; [3..5] t2 again, Z and unused from
-  // make_z), found by the kernels that read or write them
+  // its uses ([0] t2, [1] tau, [2] tau~), found by the kernel that forms tau
   const bool scaled = tier_scaled(tr);
-  Buf amx(&al, 6 * sizeof(float));
-  float *amx_t2 = nullptr, *amx_tau = nullptr, *amx_taut = nullptr, *amx_z = nullptr;
+  Buf amx(&al, 3 * sizeof(float));
+  float *amx_t2 = nullptr, *amx_tau = nullptr, *amx_taut = nullptr;
   if (scaled) {
     amx_t2 = amx.as<float>();
     amx_tau = amx_t2 + 1;
     amx_taut = amx_t2 + 2;
-    amx_z = amx_t2 + 4;
   }
   {
     Engine::Region r = eng.region("make_tau x2");
@@ -871,18 +869,17 @@ void Ctx::residual(const cplx *t1p, const cplx *t2p, cplx *R1, cplx *R2) {
   eng.contract(C1(), T(Y.c(), "Pbj", {X, v, o}), Lov_("Pme"), C1(), Wt("jbme"), tr);
   eng.contract(C1(), Lov_("Pmf"), t1("jf"), C0(), T(Zm.c(), "Pmj", {X, o, o}), tr);
   eng.contract(Cr(-1), T(Zm.c(), "Pmj", {X, o, o}), Lvv_("Pbe"), C1(), Wt("jbme"), tr);
-  //   - t_n^b <mn||ej> = + t_n^b <mn||je>
-  eng.contract(C1(), g_ooov("mnje"), t1("nb"), C1(), Wt("jbme"), tr);
-  //   - (1/2 t_jn^fb + t_j^f t_n^b) <mn||ef>
+  //   - t_n^b <mn||ej> - t_j^f t_n^b <mn||ef> = t_n^b (<mn||je> - u_mnje)
+  //   with u_mnje = sum_f <mn||ef> t_j^f: one product over n for both
   {
-    Buf z(&al, sizeof(cplx) * n2);
-    {
-      Engine::Region r = eng.region("make_z");
-      make_z(t1p, t2p, z.c(), o, v, 0.5, st, tr != TIER_FP64, scaled ? amx_t2 + 3 : nullptr);
-    }
-    eng.contract(Cr(-1), with_amax(T(z.c(), "jnfb", {o, o, v, v}), amx_z), g_oovv("mnef"), C1(),
-                 Wt("jbme"), tr);
+    const std::initializer_list<long> d3v = {o, o, o, v};
+    Buf u(&al, sizeof(cplx) * oo * o * v);
+    eng.contract(C1(), g_oovv("mnef"), t1("jf"), C0(), T(u.c(), "mnje", d3v), tr);
+    axpby(oo * o * v, C1(), ooov.c(), Cr(-1), u.c(), st);
+    eng.contract(C1(), T(u.c(), "mnje", d3v), t1("nb"), C1(), Wt("jbme"), tr);
   }
+  //   - 1/2 t_jn^fb <mn||ef>
+  eng.contract(Cr(-0.5), t2("jnfb"), g_oovv("mnef"), C1(), Wt("jbme"), tr);
   // P(ij)P(ab) [t_im^ae W_mbej - t_i^e t_m^a <mb||ej>], the second part
   // taken with the Q product above
   eng.contract(C1(), stable(t2("imae")), Wt("jbme"), C1(), Xt("ijab"), tr);
