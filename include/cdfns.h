@@ -65,6 +65,10 @@ typedef struct cc_ctx cc_ctx; /* one molecular (synthetic) system */
 /* Process-wide defaults picked up by contexts created afterwards.
  * alloc(bytes, user) must return device memory aligned to 256 bytes or NULL;
  * free(ptr, user) releases it. Pass NULLs to restore cudaMalloc/cudaFree.
+ * During one library call, a context without a memory limit keeps the
+ * blocks it releases and hands them to its next requests of the same size;
+ * it frees whatever it still keeps before the call returns (and at once,
+ * then retries, when an allocation fails).
  * stream is a cudaStream_t (NULL = legacy default stream). */
 int cc_set_default_allocator(void *(*alloc)(size_t, void *),
                              void (*free_fn)(void *, void *), void *user);
